@@ -1,0 +1,35 @@
+"""FP64 CPU oracle for the block omega-circulant preconditioned all-at-once solver
+(Fung & Hon, "Block omega-circulant preconditioners for parabolic optimal control problems").
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
+(and --impl reference) leg may import this package.  It shares no code with the CUDA path and
+imports nothing from it; both sides draw their inputs from the separate `synth` module.
+
+Everything here is plain NumPy/SciPy in float64, written to be checked against the paper by eye:
+library primitives (FFT, DST, sparse/dense solves, eigendecompositions) serve as single steps,
+with no blocking, fusion or reordering beyond what the paper's definitions state.
+
+Parity status per function (what pins it, see tests/test_oracle_pins.py):
+  discretisation.*      pinned: sparse direct solve of the paper's block system (Sec. 1) and the
+                        Example-1 errors e_h and iteration counts of Table 1 (Crank-Nicolson).
+                        For theta != 1/2 the time level paired with each g and f sample in the
+                        right-hand side follows the printed g~, f~ formulas and is pinned only by
+                        consistency (first-order convergence): partially pinned.
+  operators.matvec_*    pinned: dense A built from Eq. (matrix_A) / (matrix_A_hat), |A|^{-1}A = +-1
+                        (Prop. 3.2), sparse direct solve round trip.
+  spectra.*             pinned: dense omega-circulant eigendecomposition (Eq. decompositiob_S12),
+                        Lemma 3.4 closed form, DST orthogonality and K S = S diag(kappa).
+  precond.apply_abs_ps_inv, apply_ps_inv, apply_pms_inv
+                        pinned: dense constructions of |P_S|, P_S, P_MS (Eqs. matrix_P,
+                        matrix_P_GMRES, matrix_P_MS); Prop. 3.1 rank bound; Thm 3.3 clustering;
+                        Thm 3.11 / Remark 4 spectral bounds.
+  precond.apply_mg_ps_inv
+                        pinned: Lemma 3.14 decomposition (scalar 2x2 check); with many V-cycles it
+                        converges to apply_ps_inv on a = 1 (the paper's exact route).
+  multigrid.vcycle      partly pinned: converges to the exact shifted solve with a grid-independent
+                        contraction factor; the fixed-count V-cycle itself (smoother, transfer
+                        operators, coarse coefficients) is a reading of a method the paper does not
+                        specify -- parity unpinned beyond that.
+  krylov.*              pinned: sparse direct solve; Table 1 iteration counts.
+"""
+from . import discretisation, operators, spectra, precond, multigrid, krylov  # noqa: F401

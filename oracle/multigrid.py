@@ -1,0 +1,103 @@
+"""Geometric multigrid V-cycle for the per-frequency shifted spatial systems (mu I + tau K) z = r
+named in Sec. 3.5 (Step 2 of the P_S^{-1} and P_MS^{-1} applications) and Sec. 4.
+
+The paper does not specify its multigrid.  Reading used here (parity against the paper unpinned;
+pinned only by convergence to the exact shifted solve):
+  * vertex-centred coarsening N -> (N-1)/2 (N = 2^k - 1 down to N = 1), spacing doubles;
+  * coarse edge coefficient = mean of the two collinear fine edge coefficients it spans;
+  * full-weighting restriction ([1 2 1; 2 4 2; 1 2 1]/16), bilinear prolongation;
+  * damped Jacobi smoother, weight 4/5, nu1 pre- and nu2 post-sweeps;
+  * exact solve on the single-unknown coarsest grid;
+  * zero initial guess, a fixed number of cycles, so the solver is a fixed linear operator.
+The shift mu is complex in general; K is real.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+JACOBI_WEIGHT = 0.8
+
+
+class Level:
+    def __init__(self, N, ax, ay, tau):
+        self.N, self.ax, self.ay, self.tau = N, ax, ay, tau
+        self.h = 1.0 / (N + 1)
+        self.diagK = (ax[:, :-1] + ax[:, 1:] + ay[:-1, :] + ay[1:, :]) / self.h ** 2
+
+    def K(self, U):
+        """K applied to U[..., j, i] with zero Dirichlet boundary."""
+        N = self.N
+        P = np.zeros(U.shape[:-2] + (N + 2, N + 2), dtype=U.dtype)
+        P[..., 1:-1, 1:-1] = U
+        c = P[..., 1:-1, 1:-1]
+        return (self.ax[:, :-1] * (c - P[..., 1:-1, :-2]) + self.ax[:, 1:] * (c - P[..., 1:-1, 2:])
+                + self.ay[:-1, :] * (c - P[..., :-2, 1:-1]) + self.ay[1:, :] * (c - P[..., 2:, 1:-1])) / self.h ** 2
+
+
+def hierarchy(N, ax, ay, tau):
+    """Levels from fine (N) to the 1 x 1 grid; requires N = 2^k - 1."""
+    if N < 1 or (N + 1) & N:
+        raise ValueError("multigrid needs N = 2^k - 1")
+    levels = [Level(N, ax, ay, tau)]
+    while levels[-1].N > 1:
+        f = levels[-1]
+        Nc = (f.N - 1) // 2
+        # coarse x1-edge e (between coarse nodes e, e+1) on coarse row J spans fine edges 2e, 2e+1 on fine row 2J+1
+        axc = 0.5 * (f.ax[1::2, 0::2] + f.ax[1::2, 1::2])
+        ayc = 0.5 * (f.ay[0::2, 1::2] + f.ay[1::2, 1::2])
+        levels.append(Level(Nc, axc, ayc, tau))
+    return levels
+
+
+def restrict(R):
+    """Full weighting from a fine (Nf x Nf) grid to the coarse ((Nf-1)/2)^2 grid."""
+    Nf = R.shape[-1]
+    P = np.zeros(R.shape[:-2] + (Nf + 2, Nf + 2), dtype=R.dtype)
+    P[..., 1:-1, 1:-1] = R
+    c = slice(2, Nf, 2)          # padded index of fine node 2J (1-based), J = 1..Nc
+    cm = slice(1, Nf - 1, 2)
+    cp = slice(3, Nf + 1, 2)
+    return (4 * P[..., c, c] + 2 * (P[..., c, cm] + P[..., c, cp] + P[..., cm, c] + P[..., cp, c])
+            + P[..., cm, cm] + P[..., cm, cp] + P[..., cp, cm] + P[..., cp, cp]) / 16.0
+
+
+def prolong(E, Nf):
+    """Bilinear interpolation from the coarse grid to the fine (Nf x Nf) grid."""
+    Nc = E.shape[-1]
+    P = np.zeros(E.shape[:-2] + (Nc + 2, Nc + 2), dtype=E.dtype)
+    P[..., 1:-1, 1:-1] = E
+    out = np.zeros(E.shape[:-2] + (Nf, Nf), dtype=E.dtype)
+    # fine 1-based index 2J sits on coarse node J; odd fine indices lie between coarse nodes
+    out[..., 1::2, 1::2] = E
+    out[..., 1::2, 0::2] = 0.5 * (P[..., 1:-1, :-1] + P[..., 1:-1, 1:])
+    out[..., 0::2, 1::2] = 0.5 * (P[..., :-1, 1:-1] + P[..., 1:, 1:-1])
+    out[..., 0::2, 0::2] = 0.25 * (P[..., :-1, :-1] + P[..., :-1, 1:] + P[..., 1:, :-1] + P[..., 1:, 1:])
+    return out
+
+
+def vcycle(levels, mu, R, nu1=2, nu2=2, lev=0):
+    """One V-cycle with zero initial guess for (mu I + tau K) Z = R; mu broadcasts against
+    R[..., j, i] (shape (...,) -> use mu[..., None, None])."""
+    L = levels[lev]
+    diag = mu + L.tau * L.diagK
+    if L.N == 1:
+        return R / diag
+    Z = np.zeros_like(R)
+    for _ in range(nu1):
+        Z = Z + JACOBI_WEIGHT * (R - (mu * Z + L.tau * L.K(Z))) / diag
+    res = R - (mu * Z + L.tau * L.K(Z))
+    Ec = vcycle(levels, mu, restrict(res), nu1, nu2, lev + 1)
+    Z = Z + prolong(Ec, L.N)
+    for _ in range(nu2):
+        Z = Z + JACOBI_WEIGHT * (R - (mu * Z + L.tau * L.K(Z))) / diag
+    return Z
+
+
+def solve(levels, mu, R, cycles=2, nu1=2, nu2=2):
+    """`cycles` V-cycles from a zero initial guess (each further cycle corrects the residual)."""
+    L = levels[0]
+    Z = np.zeros_like(R)
+    for _ in range(cycles):
+        res = R - (mu * Z + L.tau * L.K(Z))
+        Z = Z + vcycle(levels, mu, res, nu1, nu2)
+    return Z
