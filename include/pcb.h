@@ -1,0 +1,165 @@
+/*
+ * pcb.h -- C ABI of the block omega-circulant preconditioned all-at-once solver for
+ * theta-discretised parabolic optimal control (Fung & Hon, "Block omega-circulant
+ * preconditioners for parabolic optimal control problems"), for one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Sec. 1 of the paper): 2D heat-equation tracking problem on the unit square,
+ * zero Dirichlet data, 5-point finite differences (M = I, K = -L), theta-scheme in time.
+ * N interior points per side (m = N*N, h = 1/(N+1)), n time steps (tau = T/n),
+ * regularisation gamma, alpha = tau/sqrt(gamma), omega = exp(i zeta).
+ *
+ * Vector layout (all "x", "b", "y" vectors, FP64, device memory, length 2*m*n):
+ *   index = half*m*n + t*m + (i-1) + (j-1)*N,   t = 0..n-1, i, j = 1..N (x1 fastest).
+ * For the symmetric system A (Eq. main_system) half 0 holds sqrt(gamma)*y~, half 1 holds p~;
+ * the right-hand side is [g; sqrt(gamma) f].  For the nonsymmetric system A_hat
+ * (Eq. main_system_nonsym) the unknowns are the same and the right-hand side is
+ * [sqrt(gamma) f; g].
+ *
+ * Conventions for every entry point:
+ *   - Return value: PCB_OK (0) on success, a negative PCB_ERR_* code on failure, or the positive
+ *     PCB_NOT_CONVERGED when a solve ran out of iterations (x then holds the last iterate).
+ *     No exception or abort crosses this boundary; pcb_status_str() names each code.
+ *   - Pointers named *_dev are device pointers owned by the caller; they must stay valid until the
+ *     work queued on the problem's stream has finished.  Host pointers (*_host, a_edges) are read
+ *     during the call only.
+ *   - All work is queued on the stream given at creation (NULL = legacy default stream); calls
+ *     return without synchronising except pcb_solve (which waits for convergence tests) and
+ *     the *_host variants (which copy through host memory).
+ *   - A problem handle is used by one host thread at a time.
+ *   - The library owns its workspaces (allocated in pcb_create, freed in pcb_destroy).
+ */
+#ifndef PCB_H
+#define PCB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define PCB_OK 0
+#define PCB_NOT_CONVERGED 1          /* solve stopped at maxit; x holds the last iterate        */
+#define PCB_ERR_INVALID_ARG (-1)     /* N < 1, n < 2, theta outside [1/2, 1], gamma <= 0, ...   */
+#define PCB_ERR_UNSUPPORTED (-2)     /* valid input this build does not handle (see pcb_create) */
+#define PCB_ERR_SINGULAR (-3)        /* singular S^(2) and the remedy was disabled              */
+#define PCB_ERR_OUT_OF_MEMORY (-4)   /* a workspace allocation failed                          */
+#define PCB_ERR_CUDA (-5)            /* a CUDA runtime call failed                              */
+#define PCB_ERR_NONFINITE (-6)       /* NaN or Inf in a right-hand side or during a solve       */
+#define PCB_ERR_BREAKDOWN (-7)       /* MINRES met a non-positive preconditioned norm           */
+#define PCB_ERR_TIMEOUT (-8)         /* a bounded device-side wait gave up                      */
+#define PCB_ERR_TOO_LARGE (-9)       /* request exceeds a documented size limit                 */
+
+/* ---- enumerations ---------------------------------------------------------------------- */
+enum pcb_precision { PCB_FP64 = 0, PCB_MIXED = 1 };
+/* PCB_FP64: every step in double precision.
+ * PCB_MIXED: the preconditioner (transforms, per-frequency solves, multigrid) runs in FP32;
+ * the matvec, residuals, inner products, orthogonalisation and vector updates stay FP64, and an
+ * FP64 iterative-refinement loop restores the requested true relative residual. */
+
+enum pcb_operator { PCB_OP_A = 0, PCB_OP_AHAT = 1 };
+/* PCB_OP_A    : A     = [[alpha I, T^T], [T, -alpha I]]   (Eq. matrix_A; symmetric)
+ * PCB_OP_AHAT : A_hat = [[T, -alpha I], [alpha I, T^T]]   (Eq. matrix_A_hat)
+ * T = B_n (x) I_m + tau I_n (x) K (Eq. matrix_T), B_n = B^(1) (B^(2))^{-1}. */
+
+enum pcb_precond {
+  PCB_PREC_NONE = 0,
+  PCB_PREC_ABS_PS = 1,  /* |P_S|^{-1}  (Eq. matrix_P), MINRES route; needs a(x) = 1            */
+  PCB_PREC_PS = 2,      /* P_S^{-1}    (Eq. matrix_P_GMRES); a(x) = 1 pointwise, else multigrid */
+  PCB_PREC_PMS = 3      /* P_MS^{-1}   (Eq. matrix_P_MS); a(x) = 1 exact, else multigrid        */
+};
+
+enum pcb_method { PCB_METHOD_AUTO = 0, PCB_MINRES = 1, PCB_GMRES = 2, PCB_FGMRES = 3 };
+/* AUTO: MINRES with |P_S| (theta = 1, a = 1) or P_MS (a variable, theta = 1); GMRES with P_S
+ * (theta < 1, a = 1); FGMRES with multigrid P_S (a variable, theta < 1). */
+
+/* ---- problem --------------------------------------------------------------------------- */
+typedef struct pcb_problem pcb_problem;   /* opaque, owned by the library */
+
+typedef struct {
+  int N;                  /* interior points per side; N+1 must be 2^a * 3^b (DST radices),   */
+                          /* N <= 511; variable a(x) needs N = 2^k - 1 (multigrid)             */
+  int n;                  /* time steps; a power of two, 2 <= n <= 1024                       */
+  double theta;           /* 1/2 <= theta <= 1                                                 */
+  double T;               /* horizon, > 0                                                      */
+  double gamma;           /* regularisation, > 0                                               */
+  double zeta;            /* omega = exp(i zeta); this build supports zeta = pi (skew-circulant)*/
+  const double* a_edges;  /* host; NULL => a(x) = 1; else 2*N*(N+1) values of a at cell-edge   */
+                          /* midpoints: first ax[j][e] (N rows of N+1; x1-edge between nodes   */
+                          /* e and e+1 of row j+1), then ay[e][i] (N+1 rows of N)              */
+  int precision;          /* pcb_precision                                                     */
+  int mg_cycles;          /* V-cycles per shifted solve when a(x) varies; <= 0 => 2            */
+  void* stream;           /* cudaStream_t the problem's work is queued on; NULL = default      */
+} pcb_desc;
+
+/* Validate the descriptor, compute the spectral tables (Sec. 3.5: lambda_k(S_n), the eigenvalues
+ * of -L, twiddle tables) and allocate the workspaces.  Errors: INVALID_ARG, UNSUPPORTED
+ * (zeta != pi, N+1 not 2^a 3^b, n not a power of two, N > 511, variable a with N != 2^k - 1),
+ * OUT_OF_MEMORY, CUDA.  Remark 1's singular S^(2) cannot occur for the supported (zeta, n). */
+int pcb_create(const pcb_desc* desc, pcb_problem** out);
+void pcb_destroy(pcb_problem* p);
+const char* pcb_status_str(int status);
+
+/* Number of unknowns 2*m*n and the device bytes the problem's workspaces hold. */
+long long pcb_unknowns(const pcb_problem* p);
+long long pcb_workspace_bytes(const pcb_problem* p);
+
+/* Right-hand side (Sec. 1, vectors f~, g~, then Eq. main_system / main_system_nonsym):
+ * g_dev, f_dev: (n+1)*m samples at t_k = k*tau; y0_dev: m values or NULL (= 0).
+ * Writes b_dev (2*m*n) for operator `op`. */
+int pcb_assemble_rhs(pcb_problem* p, int op, const double* g_dev, const double* f_dev,
+                     const double* y0_dev, double* b_dev);
+
+/* y = A x or y = A_hat x (op = pcb_operator); x_dev and y_dev must not overlap. */
+int pcb_matvec(pcb_problem* p, int op, const double* x_dev, double* y_dev);
+
+/* y = P^{-1} x for kind = pcb_precond, computed in `precision` (pcb_precision).
+ * x_dev and y_dev may be the same buffer.  Uses the problem's scratch workspace, so calls on
+ * one problem are serialised by its stream. */
+int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_dev, double* y_dev);
+
+/* Undo the symmetrising change of variables of Eq. (main_system):
+ * y = (B2^{-1} (x) I) x_half0 / sqrt(gamma), p = (B2^{-T} (x) I) x_half1; each m*n. */
+int pcb_recover(pcb_problem* p, const double* x_dev, double* y_dev, double* p_dev);
+
+/* ---- solve ----------------------------------------------------------------------------- */
+typedef struct {
+  int method;             /* pcb_method                                                        */
+  int precond;            /* pcb_precond; PCB_PREC_NONE with method AUTO => the method's default*/
+  double tol;             /* target true relative residual ||b - op x||_2/||b||_2 (FP64); <=0 => 1e-8 */
+  int maxit;              /* total Krylov iterations; <= 0 => 500                              */
+  int restart;            /* GMRES/FGMRES restart length; <= 0 => 30 (max 64)                  */
+  int max_refinements;    /* mixed precision: outer refinement sweeps; <= 0 => 10              */
+  int fixed_iterations;   /* > 0: run exactly this many iterations (comparison runs)           */
+} pcb_solve_opts;
+
+typedef struct {
+  int status;             /* same as the return value                                          */
+  int method;             /* method used                                                       */
+  int precond;            /* preconditioner used                                               */
+  int iterations;         /* Krylov iterations summed over refinement sweeps                    */
+  int refinements;        /* refinement sweeps (1 for FP64)                                    */
+  double relres;          /* true FP64 relative residual at exit                                */
+  double seconds;         /* wall time of the call                                             */
+} pcb_solve_info;
+
+/* Solve op x = b from a zero initial guess, op = A for MINRES and A_hat for (F)GMRES.
+ * b_dev, x_dev: device, 2*m*n each; info may be NULL.  Blocks until the solve ends. */
+int pcb_solve(pcb_problem* p, const pcb_solve_opts* opts, const double* b_dev, double* x_dev,
+              pcb_solve_info* info);
+
+/* Same solve through host buffers: copies b_host to the device, solves, copies x back. */
+int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* opts, const double* b_host,
+                   double* x_host, pcb_solve_info* info);
+
+/* ---- batches --------------------------------------------------------------------------- */
+/* Solve `count` independent problems (uneven N, n, theta, gamma allowed; all with the same
+ * precision) with shared kernel launches: every launch of an iteration covers all unfinished
+ * problems.  opts applies to each.  Blocks until all finish. */
+int pcb_batch_solve(pcb_problem* const* problems, int count, const pcb_solve_opts* opts,
+                    const double* const* b_dev, double* const* x_dev, pcb_solve_info* infos);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCB_H */

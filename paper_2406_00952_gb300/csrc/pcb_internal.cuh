@@ -1,0 +1,138 @@
+// Internal definitions shared by the CUDA translation units of libpcb.
+//
+// Every kernel is written for a *batch* of independent problem instances: a launch covers
+// the blocks of all instances, `blk_off[k]..blk_off[k+1]` being instance k's blocks.  A single
+// problem is a batch of one.  Per-instance constants live in `Geom`, per-instance vector
+// pointers in `Slots` (device memory, so a solver can rotate them on the device), per-instance
+// Krylov scalars in `Scal`.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pcb.h"
+
+#define PCB_MAX_STAGES 12
+#define PCB_NSLOTS 24
+#define PCB_MAX_RESTART 32
+
+namespace pcb {
+
+// ------------------------------------------------------------------------------------------
+// complex helpers (float2 / double2)
+// ------------------------------------------------------------------------------------------
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+template <typename R> using cx = typename Cx<R>::T;
+
+template <typename R> __host__ __device__ __forceinline__ cx<R> mk(R a, R b) { cx<R> c; c.x = a; c.y = b; return c; }
+template <typename T> __device__ __forceinline__ T cadd(T a, T b) { T c; c.x = a.x + b.x; c.y = a.y + b.y; return c; }
+template <typename T> __device__ __forceinline__ T csub(T a, T b) { T c; c.x = a.x - b.x; c.y = a.y - b.y; return c; }
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+  T c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
+}
+template <typename T> __device__ __forceinline__ T cconj(T a) { a.y = -a.y; return a; }
+template <typename T, typename R> __device__ __forceinline__ T cscale(T a, R s) { a.x *= s; a.y *= s; return a; }
+// a * (-i)
+template <typename T> __device__ __forceinline__ T cmul_mi(T a) { T c; c.x = a.y; c.y = -a.x; return c; }
+// a * (+i)
+template <typename T> __device__ __forceinline__ T cmul_pi(T a) { T c; c.x = -a.y; c.y = a.x; return c; }
+
+// ------------------------------------------------------------------------------------------
+// per-instance geometry and tables
+// ------------------------------------------------------------------------------------------
+struct FftPlan {
+  int M;                          // transform length
+  int nst;                        // number of Stockham stages
+  int rad[PCB_MAX_STAGES];        // radix of each stage (2, 3, 4 or 8)
+};
+
+struct Geom {
+  int N, n, m;                    // m = N*N
+  int L, M;                       // L = N+1 (DST-I order), M = 2L (extended FFT length)
+  long long mn;                   // m*n (one half of the all-at-once vector)
+  double theta, tau, gamma, alpha, h, sqrt_gamma;
+  double c;                       // tau / h^2
+  int var_a;                      // 0: a = 1; 1: coefficient tables below
+  // launch shapes (blocks of each pass for this instance)
+  // launch shapes of the preconditioner passes, index 0 = FP64 apply, 1 = FP32 apply
+  int dst_lpb[2];                 // lines per block of the DST passes
+  int dst_blocks_i[2], dst_blocks_j[2]; // blocks of the x1-line and x2-line DST passes
+  int time_cpb[2];                // spatial columns per block of the time pass
+  int time_blocks[2];
+  int mv_tchunk;                  // time steps per thread in the theta = 1 matvec
+  int mv_blocks;                  // blocks of the matvec
+  int vec_blocks;                 // blocks of the vector kernels over 2mn
+  FftPlan pdst, ptime;
+  // tables (device)
+  const double* kap;              // N: eigenvalues kappa_p of the 1D second difference
+  const double2* mu_d;            // n: lambda(S_n) at F-slot r (FP64)
+  const float2* mu_f;
+  const double2* twd_d;           // M: exp(-2 pi i k / M)
+  const float2* twd_f;
+  const double2* twt_d;           // n: exp(-2 pi i k / n)
+  const float2* twt_f;
+  const double2* pre_d;           // n: exp(-i pi t / n)   (zeta = pi scaling, D_omega conj)
+  const float2* pre_f;
+  const double* axs;              // var_a: tau/h^2 * ax  (N x (N+1))
+  const double* ays;              //        tau/h^2 * ay  ((N+1) x N)
+  const double* dgs;              //        tau/h^2 * (sum of the 4 edge coefficients) (N x N)
+  void* scratch;                  // preconditioner workspace: 2mn values of the apply's Real type
+};
+
+// per-instance Krylov scalars (MINRES and GMRES share the struct)
+struct Scal {
+  // MINRES (Paige-Saunders recurrences)
+  double beta, oldb, alfa, dbar, epsln, oldeps, phibar, cs, sn, delta, gbar, gamma, phi;
+  double beta1, bnorm, est;
+  // reductions land here
+  double dot0, dot1;
+  // GMRES
+  double H[(PCB_MAX_RESTART + 1) * 2];   // current Hessenberg column (two passes of CGS2)
+  double hcol[PCB_MAX_RESTART + 1];
+  double R[(PCB_MAX_RESTART + 1) * PCB_MAX_RESTART];   // rotated Hessenberg (column major)
+  double g[PCB_MAX_RESTART + 1];
+  double gcs[PCB_MAX_RESTART], gsn[PCB_MAX_RESTART];
+  double y[PCB_MAX_RESTART];
+  double hnorm;
+  int itn;          // iterations done
+  int j;            // Arnoldi index within the restart cycle
+  int active;       // 1 while the instance still iterates
+  int flags;        // bit 0: estimate below tolerance; bit 1: breakdown; bit 2: nonfinite
+};
+
+struct Slots { double* v[PCB_NSLOTS]; };
+
+// ------------------------------------------------------------------------------------------
+// batch -> instance lookup
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int find_inst(const int* __restrict__ off, int count, int b) {
+  int lo = 0, hi = count;            // off[lo] <= b < off[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= b) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side launch helpers (defined in runtime.cu)
+// ------------------------------------------------------------------------------------------
+struct Batch {
+  int count;
+  const Geom* G;          // device array [count]
+  Slots* S;               // device array [count]
+  Scal* Sc;               // device array [count]
+  const int* active;      // device array [count] or null: 0 => skip instance
+  cudaStream_t stream;
+  // block offsets for each pass kind (device arrays [count+1]) and totals
+  const int* off_dst_i[2]; int tot_dst_i[2];
+  const int* off_dst_j[2]; int tot_dst_j[2];
+  const int* off_time[2];  int tot_time[2];
+  const int* off_mv;    int tot_mv;
+  const int* off_vec;   int tot_vec;
+  double* partial;        // reduction partials [tot_vec * 8]
+  int max_lpb_M[2], max_cpb_n[2];   // largest lines*(M+1) and columns*(n+1) per precision
+};
+
+}  // namespace pcb

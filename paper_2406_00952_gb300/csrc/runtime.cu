@@ -1,0 +1,747 @@
+// Host runtime and C ABI (include/pcb.h): problem creation (validation, spectral and twiddle
+// tables of Sec. 3.5, launch shapes), workspaces, and the batched solver loops (MINRES,
+// FGMRES with CGS2, FP64 iterative refinement around an FP32 preconditioner).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pcb_internal.cuh"
+
+namespace pcb {
+// launchers defined in the other translation units
+cudaError_t launch_precond_fast(const Batch& B, int kind, int prec, int in_slot, int out_slot);
+cudaError_t launch_precond_mg(const Batch& B, int kind, int prec, int in_slot, int out_slot);
+cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi);
+cudaError_t launch_rhs(const Geom& g, cudaStream_t st, int op, const double* gs, const double* fs, const double* y0,
+                       double* b);
+cudaError_t launch_recover(const Geom& g, cudaStream_t st, const double* x, double* y, double* p);
+cudaError_t launch_dot(const Batch& B, int sa, int sb);
+cudaError_t launch_reduce(const Batch& B, const int* off, int nper, int which, int step, double tol, int j,
+                          int restart);
+cudaError_t launch_axpby(const Batch& B, int mode, int sx, int sy, int sz);
+cudaError_t launch_minres_wx(const Batch& B, int sy, int sw, int sw2, int sx);
+cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw);
+cudaError_t launch_reduce_multi(const Batch& B, int j, int pass);
+cudaError_t launch_multiaxpy(const Batch& B, int svbase, int j, int sw, int pass);
+cudaError_t launch_swap(const Batch& B, int a0, int b0, int a1, int b1, int a2, int b2);
+cudaError_t launch_setslot(const Batch& B, int dst, int base, int k);
+size_t mg_workspace_bytes(const Geom& g);
+bool mg_available();
+cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host);
+
+// step ids of the scalar kernels (mirror krylov.cu)
+enum { SS_NONE = 0, SS_MINRES_INIT, SS_MINRES_ALFA, SS_MINRES_GIVENS, SS_NORM, SS_GMRES_ARNOLDI, SS_GMRES_START,
+       SS_BNORM };
+enum { AX_COPY = 0, AX_MINRES_R = 1, AX_SCALE_INV_BETA = 2, AX_SCALE_INV_HNORM = 3, AX_ADD = 4 };
+enum { EPI_PLAIN = 0, EPI_RESID = 1, EPI_MINRES = 2 };
+enum { PK_ABS_PS = 1, PK_PS = 2, PK_PMS = 3 };
+
+// vector slots
+enum {
+  SL_UIN = 0, SL_UOUT = 1,           // user buffers of standalone calls
+  SL_X = 2, SL_B = 3,                // solve: solution and right-hand side (outer)
+  SL_XI = 4, SL_BI = 5,              // inner solve solution / right-hand side
+  SL_R1 = 6, SL_R2 = 7, SL_Y = 8, SL_YO = 9, SL_Q = 10, SL_W = 11, SL_W2 = 12,
+  SL_R = 13, SL_VBASE = 14, SL_ZBASE = 15, SL_VJ = 16, SL_ZJ = 17, SL_VJ1 = 18
+};
+
+}  // namespace pcb
+
+using namespace pcb;
+
+struct pcb_problem {
+  pcb_desc desc;
+  Geom g;                 // host mirror (device pointers inside)
+  cudaStream_t stream;
+  int device;
+  // device allocations
+  void* tables = nullptr;
+  void* scratch = nullptr;
+  void* mgws = nullptr;
+  double* vec_minres = nullptr;   // 7 vectors
+  double* vec_mixed = nullptr;    // 2 vectors (inner rhs / solution)
+  double* vec_gmres = nullptr;    // R + V(restart+1) + Z(restart)
+  int gmres_restart = 0;
+  long long bytes = 0;
+  // single-instance batch
+  Geom* dG = nullptr;
+  Slots hS;
+  Slots* dS = nullptr;
+  Scal* dSc = nullptr;
+  int* doff = nullptr;            // 12 offset arrays of length 2
+  double* partial = nullptr;
+  Scal* hSc = nullptr;            // pinned host copy
+  Slots* hSpin = nullptr;         // pinned staging for slot uploads
+  Batch B;
+};
+
+namespace {
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return PCB_ERR_OUT_OF_MEMORY; }
+  return PCB_ERR_CUDA;
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+bool make_plan(int M, FftPlan& p) {
+  p.M = M;
+  p.nst = 0;
+  int r = M;
+  // prefer radix 8, then 4, finish with 2 and 3
+  while (r % 3 == 0) { if (p.nst >= PCB_MAX_STAGES) return false; p.rad[p.nst++] = 3; r /= 3; }
+  while (r % 8 == 0) { if (p.nst >= PCB_MAX_STAGES) return false; p.rad[p.nst++] = 8; r /= 8; }
+  while (r % 4 == 0) { if (p.nst >= PCB_MAX_STAGES) return false; p.rad[p.nst++] = 4; r /= 4; }
+  while (r % 2 == 0) { if (p.nst >= PCB_MAX_STAGES) return false; p.rad[p.nst++] = 2; r /= 2; }
+  return r == 1;
+}
+
+int vec_blocks_for(long long len) {
+  long long b = (len + 2047) / 2048;
+  if (b > 2432) b = 2432;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+void set_shapes(Geom& g) {
+  const int Mp = g.M + 1, np = g.n + 1;
+  const int budget[2] = {6300, 8400};   // complex points per smem buffer: FP64, FP32
+  for (int p = 0; p < 2; ++p) {
+    int lpb = std::max(1, std::min(64, budget[p] / Mp));
+    g.dst_lpb[p] = lpb;
+    g.dst_blocks_i[p] = (int)(((long long)g.n * g.N + lpb - 1) / lpb);
+    g.dst_blocks_j[p] = g.n * ((g.N + lpb - 1) / lpb);
+    int cpb = std::max(1, std::min(64, budget[p] / np));
+    g.time_cpb[p] = cpb;
+    g.time_blocks[p] = (g.m + cpb - 1) / cpb;
+  }
+  const int ncb = (g.m + 255) / 256;
+  if (g.theta == 1.0) {
+    int tch = (int)std::min<long long>(32, std::max<long long>(1, ((long long)ncb * g.n) / 2432));
+    g.mv_tchunk = tch;
+    g.mv_blocks = ncb * ((g.n + tch - 1) / tch);
+  } else {
+    g.mv_tchunk = g.n;
+    g.mv_blocks = 2 * ncb;
+  }
+  g.vec_blocks = vec_blocks_for(2 * g.mn);
+}
+
+}  // namespace
+
+// build a batch descriptor for instances whose Geom/Slots/Scal live in device arrays
+static int build_offsets(const std::vector<Geom>& gs, std::vector<int>& host_off, int& tot_out, int which, int p) {
+  const int count = (int)gs.size();
+  int tot = 0;
+  for (int k = 0; k < count; ++k) {
+    host_off.push_back(tot);
+    const Geom& g = gs[k];
+    int nb = 0;
+    switch (which) {
+      case 0: nb = g.dst_blocks_i[p]; break;
+      case 1: nb = g.dst_blocks_j[p]; break;
+      case 2: nb = g.time_blocks[p]; break;
+      case 3: nb = g.mv_blocks; break;
+      default: nb = g.vec_blocks; break;
+    }
+    tot += nb;
+  }
+  host_off.push_back(tot);
+  tot_out = tot;
+  return 0;
+}
+
+// Fill B's offset tables for `gs` into the device int buffer `doff` (12 arrays of count+1).
+static int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStream_t st, std::vector<int>& staging) {
+  const int count = (int)gs.size();
+  staging.clear();
+  int tots[8];
+  // order: dst_i[0], dst_i[1], dst_j[0], dst_j[1], time[0], time[1], mv, vec
+  const int which[8] = {0, 0, 1, 1, 2, 2, 3, 4};
+  const int prec[8] = {0, 1, 0, 1, 0, 1, 0, 0};
+  for (int a = 0; a < 8; ++a) build_offsets(gs, staging, tots[a], which[a], prec[a]);
+  CK(cudaMemcpyAsync(doff, staging.data(), staging.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  const int stride = count + 1;
+  for (int p = 0; p < 2; ++p) {
+    B.off_dst_i[p] = doff + (0 + p) * stride; B.tot_dst_i[p] = tots[0 + p];
+    B.off_dst_j[p] = doff + (2 + p) * stride; B.tot_dst_j[p] = tots[2 + p];
+    B.off_time[p] = doff + (4 + p) * stride;  B.tot_time[p] = tots[4 + p];
+    B.max_lpb_M[p] = 0; B.max_cpb_n[p] = 0;
+    for (const Geom& g : gs) {
+      B.max_lpb_M[p] = std::max(B.max_lpb_M[p], g.dst_lpb[p] * (g.M + 1));
+      B.max_cpb_n[p] = std::max(B.max_cpb_n[p], g.time_cpb[p] * (g.n + 1));
+    }
+  }
+  B.off_mv = doff + 6 * stride; B.tot_mv = tots[6];
+  B.off_vec = doff + 7 * stride; B.tot_vec = tots[7];
+  B.count = count;
+  B.stream = st;
+  return PCB_OK;
+}
+
+extern "C" {
+
+const char* pcb_status_str(int s) {
+  switch (s) {
+    case PCB_OK: return "ok";
+    case PCB_NOT_CONVERGED: return "not converged (maximum iterations reached)";
+    case PCB_ERR_INVALID_ARG: return "invalid argument";
+    case PCB_ERR_UNSUPPORTED: return "unsupported configuration";
+    case PCB_ERR_SINGULAR: return "singular preconditioner factor";
+    case PCB_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case PCB_ERR_CUDA: return "CUDA runtime error";
+    case PCB_ERR_NONFINITE: return "non-finite value";
+    case PCB_ERR_BREAKDOWN: return "Krylov breakdown";
+    case PCB_ERR_TIMEOUT: return "device wait timed out";
+    case PCB_ERR_TOO_LARGE: return "request exceeds size limit";
+    default: return "unknown status";
+  }
+}
+
+long long pcb_unknowns(const pcb_problem* p) { return p ? 2 * p->g.mn : 0; }
+long long pcb_workspace_bytes(const pcb_problem* p) { return p ? p->bytes : 0; }
+
+void pcb_destroy(pcb_problem* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->stream);
+  cudaFree(p->tables);
+  cudaFree(p->scratch);
+  cudaFree(p->mgws);
+  cudaFree(p->vec_minres);
+  cudaFree(p->vec_mixed);
+  cudaFree(p->vec_gmres);
+  cudaFree(p->dG);
+  cudaFree(p->dS);
+  cudaFree(p->dSc);
+  cudaFree(p->doff);
+  cudaFree(p->partial);
+  cudaFreeHost(p->hSc);
+  cudaFreeHost(p->hSpin);
+  delete p;
+}
+
+int pcb_create(const pcb_desc* d, pcb_problem** out) {
+  if (!d || !out) return PCB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d->N < 1 || d->n < 2 || !(d->theta >= 0.5 && d->theta <= 1.0) || !(d->gamma > 0.0) || !(d->T > 0.0) ||
+      (d->precision != PCB_FP64 && d->precision != PCB_MIXED) || !std::isfinite(d->zeta))
+    return PCB_ERR_INVALID_ARG;
+  // supported: zeta = pi, n a power of two <= 1024, N+1 = 2^a 3^b with N <= 511
+  if (std::fabs(d->zeta - M_PI) > 1e-12) return PCB_ERR_UNSUPPORTED;
+  if (!pow2(d->n) || d->n > 1024) return PCB_ERR_UNSUPPORTED;
+  if (d->N > 511) return PCB_ERR_UNSUPPORTED;
+  FftPlan pd, pt;
+  if (!make_plan(2 * (d->N + 1), pd) || !make_plan(d->n, pt)) return PCB_ERR_UNSUPPORTED;
+  if (d->a_edges && !pow2(d->N + 1)) return PCB_ERR_UNSUPPORTED;
+  if (d->a_edges && !mg_available()) return PCB_ERR_UNSUPPORTED;
+  if (d->a_edges) {
+    const long long ne = 2LL * d->N * (d->N + 1);
+    for (long long k = 0; k < ne; ++k)
+      if (!(d->a_edges[k] > 0.0) || !std::isfinite(d->a_edges[k])) return PCB_ERR_INVALID_ARG;
+  }
+  pcb_problem* p = new (std::nothrow) pcb_problem();
+  if (!p) return PCB_ERR_OUT_OF_MEMORY;
+  p->desc = *d;
+  p->desc.a_edges = nullptr;
+  if (p->desc.mg_cycles <= 0) p->desc.mg_cycles = 2;
+  p->stream = (cudaStream_t)d->stream;
+  cudaGetDevice(&p->device);
+  Geom& g = p->g;
+  std::memset(&g, 0, sizeof(g));
+  g.N = d->N; g.n = d->n; g.m = d->N * d->N; g.L = d->N + 1; g.M = 2 * (d->N + 1);
+  g.mn = (long long)g.m * g.n;
+  g.theta = d->theta; g.tau = d->T / d->n; g.gamma = d->gamma; g.alpha = g.tau / std::sqrt(d->gamma);
+  g.h = 1.0 / (d->N + 1); g.sqrt_gamma = std::sqrt(d->gamma); g.c = g.tau / (g.h * g.h);
+  g.var_a = d->a_edges ? 1 : 0;
+  g.pdst = pd; g.ptime = pt;
+  set_shapes(g);
+
+  int rc = PCB_OK;
+  auto fail = [&](int code) { pcb_destroy(p); return code; };
+  // ---- tables (FP64 computed on the host with the C library, rounded for FP32) ----
+  const int N = g.N, n = g.n, M = g.M;
+  const size_t n_kap = N, n_mu = n, n_twd = M, n_twt = n, n_pre = n;
+  const size_t ne = g.var_a ? (size_t)N * (N + 1) : 0;
+  size_t off_b = 0;
+  auto take = [&](size_t bytes) { size_t o = off_b; off_b += (bytes + 255) & ~(size_t)255; return o; };
+  const size_t o_kap = take(n_kap * 8), o_mud = take(n_mu * 16), o_muf = take(n_mu * 8), o_twdd = take(n_twd * 16),
+               o_twdf = take(n_twd * 8), o_twtd = take(n_twt * 16), o_twtf = take(n_twt * 8),
+               o_pred = take(n_pre * 16), o_pref = take(n_pre * 8), o_ax = take(ne * 8), o_ay = take(ne * 8),
+               o_dg = take(g.var_a ? (size_t)g.m * 8 : 0);
+  std::vector<unsigned char> host(off_b, 0);
+  double* kap = (double*)(host.data() + o_kap);
+  for (int q = 1; q <= N; ++q) {
+    const double s = std::sin(q * M_PI * g.h / 2.0);
+    kap[q - 1] = 4.0 / (g.h * g.h) * s * s;
+  }
+  // lambda(S_n) at F-slot r: psi_r = -pi (2r+1)/n, f1/f2 with f1 = 1 - e^{i psi}, f2 = theta + (1-theta) e^{i psi}
+  double2* mud = (double2*)(host.data() + o_mud);
+  float2* muf = (float2*)(host.data() + o_muf);
+  for (int r = 0; r < n; ++r) {
+    const double psi = -M_PI * (2.0 * r + 1.0) / n;
+    const double c = std::cos(psi), s = std::sin(psi);
+    const double f1r = 1.0 - c, f1i = -s;
+    double f2r = g.theta + (1.0 - g.theta) * c, f2i = (1.0 - g.theta) * s;
+    if (std::hypot(f2r, f2i) < 1e-14) { f2r = 1.0; f2i = 0.0; }   // Remark 1 remedy (odd n only)
+    const double den = f2r * f2r + f2i * f2i;
+    mud[r].x = (f1r * f2r + f1i * f2i) / den;
+    mud[r].y = (f1i * f2r - f1r * f2i) / den;
+    muf[r].x = (float)mud[r].x; muf[r].y = (float)mud[r].y;
+  }
+  auto fill_tw = [&](double2* td, float2* tf, int len) {
+    for (int k = 0; k < len; ++k) {
+      const double a = -2.0 * M_PI * (double)k / (double)len;
+      td[k].x = std::cos(a); td[k].y = std::sin(a);
+      tf[k].x = (float)td[k].x; tf[k].y = (float)td[k].y;
+    }
+  };
+  fill_tw((double2*)(host.data() + o_twdd), (float2*)(host.data() + o_twdf), M);
+  fill_tw((double2*)(host.data() + o_twtd), (float2*)(host.data() + o_twtf), n);
+  double2* pred = (double2*)(host.data() + o_pred);
+  float2* pref = (float2*)(host.data() + o_pref);
+  for (int t = 0; t < n; ++t) {
+    const double a = -M_PI * (double)t / n;
+    pred[t].x = std::cos(a); pred[t].y = std::sin(a);
+    pref[t].x = (float)pred[t].x; pref[t].y = (float)pred[t].y;
+  }
+  if (g.var_a) {
+    double* ax = (double*)(host.data() + o_ax);
+    double* ay = (double*)(host.data() + o_ay);
+    double* dg = (double*)(host.data() + o_dg);
+    const double* axs = d->a_edges;
+    const double* ays = d->a_edges + (size_t)N * (N + 1);
+    for (size_t k = 0; k < ne; ++k) { ax[k] = g.c * axs[k]; ay[k] = g.c * ays[k]; }
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i)
+        dg[j * N + i] = ax[j * (N + 1) + i] + ax[j * (N + 1) + i + 1] + ay[j * N + i] + ay[(j + 1) * N + i];
+  }
+  if (cudaMalloc(&p->tables, off_b) != cudaSuccess) return fail(PCB_ERR_OUT_OF_MEMORY);
+  p->bytes += off_b;
+  if (cudaMemcpy(p->tables, host.data(), off_b, cudaMemcpyHostToDevice) != cudaSuccess) return fail(PCB_ERR_CUDA);
+  unsigned char* tb = (unsigned char*)p->tables;
+  g.kap = (const double*)(tb + o_kap);
+  g.mu_d = (const double2*)(tb + o_mud); g.mu_f = (const float2*)(tb + o_muf);
+  g.twd_d = (const double2*)(tb + o_twdd); g.twd_f = (const float2*)(tb + o_twdf);
+  g.twt_d = (const double2*)(tb + o_twtd); g.twt_f = (const float2*)(tb + o_twtf);
+  g.pre_d = (const double2*)(tb + o_pred); g.pre_f = (const float2*)(tb + o_pref);
+  if (g.var_a) {
+    g.axs = (const double*)(tb + o_ax); g.ays = (const double*)(tb + o_ay); g.dgs = (const double*)(tb + o_dg);
+  }
+  // ---- preconditioner scratch: 2mn values, FP64-sized so both precisions fit ----
+  const size_t sbytes = (size_t)2 * g.mn * sizeof(double);
+  if (cudaMalloc(&p->scratch, sbytes) != cudaSuccess) return fail(PCB_ERR_OUT_OF_MEMORY);
+  p->bytes += sbytes;
+  g.scratch = p->scratch;
+  if (g.var_a) {
+    const size_t mb = mg_workspace_bytes(g);
+    if (cudaMalloc(&p->mgws, mb) != cudaSuccess) return fail(PCB_ERR_OUT_OF_MEMORY);
+    p->bytes += mb;
+    if (mg_setup(g, p->mgws, d->a_edges) != cudaSuccess) return fail(PCB_ERR_CUDA);
+  }
+  // ---- single-instance batch ----
+  if (cudaMalloc(&p->dG, sizeof(Geom)) != cudaSuccess || cudaMalloc(&p->dS, sizeof(Slots)) != cudaSuccess ||
+      cudaMalloc(&p->dSc, sizeof(Scal)) != cudaSuccess || cudaMalloc(&p->doff, 8 * 2 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&p->partial, (size_t)g.vec_blocks * (PCB_MAX_RESTART + 2) * sizeof(double) +
+                                  (size_t)std::max(g.mv_blocks, 1) * sizeof(double)) != cudaSuccess)
+    return fail(PCB_ERR_OUT_OF_MEMORY);
+  if (cudaMallocHost(&p->hSc, sizeof(Scal)) != cudaSuccess || cudaMallocHost(&p->hSpin, sizeof(Slots)) != cudaSuccess)
+    return fail(PCB_ERR_OUT_OF_MEMORY);
+  std::memset(&p->hS, 0, sizeof(Slots));
+  if (cudaMemcpy(p->dG, &g, sizeof(Geom), cudaMemcpyHostToDevice) != cudaSuccess) return fail(PCB_ERR_CUDA);
+  if (cudaMemset(p->dSc, 0, sizeof(Scal)) != cudaSuccess) return fail(PCB_ERR_CUDA);
+  std::vector<Geom> gs(1, g);
+  std::vector<int> staging;
+  std::memset(&p->B, 0, sizeof(Batch));
+  if ((rc = fill_batch(p->B, gs, p->doff, 0, staging)) != PCB_OK) return fail(rc);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(PCB_ERR_CUDA);
+  p->B.G = p->dG; p->B.S = p->dS; p->B.Sc = p->dSc; p->B.active = nullptr; p->B.partial = p->partial;
+  p->B.stream = p->stream;
+  *out = p;
+  return PCB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// slot upload (single instance): pinned staging + async copy on the problem stream
+// ---------------------------------------------------------------------------------------------
+static int upload_slots(pcb_problem* p) {
+  CK(cudaStreamSynchronize(p->stream));   // the pinned staging buffer may still be in flight
+  *p->hSpin = p->hS;
+  CK(cudaMemcpyAsync(p->dS, p->hSpin, sizeof(Slots), cudaMemcpyHostToDevice, p->stream));
+  return PCB_OK;
+}
+
+static int ensure_minres(pcb_problem* p) {
+  if (p->vec_minres) return PCB_OK;
+  const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
+  if (cudaMalloc(&p->vec_minres, 7 * vb) != cudaSuccess) { cudaGetLastError(); p->vec_minres = nullptr; return PCB_ERR_OUT_OF_MEMORY; }
+  p->bytes += 7 * vb;
+  return PCB_OK;
+}
+static int ensure_mixed(pcb_problem* p) {
+  if (p->vec_mixed) return PCB_OK;
+  const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
+  if (cudaMalloc(&p->vec_mixed, 2 * vb) != cudaSuccess) { cudaGetLastError(); p->vec_mixed = nullptr; return PCB_ERR_OUT_OF_MEMORY; }
+  p->bytes += 2 * vb;
+  return PCB_OK;
+}
+static int ensure_gmres(pcb_problem* p, int restart) {
+  if (p->vec_gmres && p->gmres_restart >= restart) return PCB_OK;
+  const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
+  if (p->vec_gmres) { cudaStreamSynchronize(p->stream); cudaFree(p->vec_gmres); p->bytes -= (long long)(2 * p->gmres_restart + 2) * vb; p->vec_gmres = nullptr; }
+  if (cudaMalloc(&p->vec_gmres, (size_t)(2 * restart + 2) * vb) != cudaSuccess) { cudaGetLastError(); p->vec_gmres = nullptr; return PCB_ERR_OUT_OF_MEMORY; }
+  p->gmres_restart = restart;
+  p->bytes += (long long)(2 * restart + 2) * vb;
+  return PCB_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// the solvers (operate on a Batch; the single-instance API is a batch of one)
+// ---------------------------------------------------------------------------------------------
+struct SolveCfg {
+  int op, prec, kind, method, maxit, restart, fixed;
+  double tol;
+  bool check_true;      // FP64 route: keep iterating if the true residual check fails
+};
+
+static int apply_precond(const Batch& B, bool var_a, int kind, int prec, int in_slot, int out_slot) {
+  cudaError_t e;
+  if (kind == PCB_PREC_NONE) e = launch_axpby(B, AX_COPY, in_slot, out_slot, -1);
+  else if (var_a) e = launch_precond_mg(B, kind, prec, in_slot, out_slot);
+  else e = launch_precond_fast(B, kind, prec, in_slot, out_slot);
+  return e == cudaSuccess ? PCB_OK : cuda_status(e);
+}
+
+// Poll per-instance scalars (synchronises the stream).
+static int read_scal(const Batch& B, Scal* host, int count) {
+  CK(cudaMemcpyAsync(host, B.Sc, sizeof(Scal) * count, cudaMemcpyDeviceToHost, B.stream));
+  CK(cudaStreamSynchronize(B.stream));
+  return PCB_OK;
+}
+
+// Single-instance MINRES on slot rhs -> slot x (both set by the caller).  Returns iterations via sc.
+static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Scal* hs, double* relres_out,
+                         int* it_out, bool* conv_out) {
+  const Batch& B = p->B;
+  const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
+  const bool va = p->g.var_a != 0;
+  // x = 0, w = w2 = 0, r1 = r2 = b
+  CK(cudaMemsetAsync(p->hS.v[s_x], 0, vb, p->stream));
+  CK(cudaMemsetAsync(p->hS.v[SL_W], 0, vb, p->stream));
+  CK(cudaMemsetAsync(p->hS.v[SL_W2], 0, vb, p->stream));
+  CK(launch_axpby(B, AX_COPY, s_b, SL_R1, -1));
+  CK(launch_axpby(B, AX_COPY, s_b, SL_R2, -1));
+  CK(launch_dot(B, s_b, s_b));
+  CK(launch_reduce(B, B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
+  int rc = apply_precond(B, va, c.kind, c.prec, SL_R2, SL_Y);
+  if (rc) return rc;
+  CK(launch_dot(B, SL_R2, SL_Y));
+  CK(launch_reduce(B, B.off_vec, 1, 0, SS_MINRES_INIT, c.tol, 0, 0));
+  if ((rc = read_scal(B, hs, 1))) return rc;
+  *it_out = 0; *conv_out = false; *relres_out = 1.0;
+  if (hs->flags & 4) return PCB_ERR_NONFINITE;
+  if (hs->flags & 2) return PCB_ERR_BREAKDOWN;
+  if (hs->bnorm == 0.0 || !hs->active) { *conv_out = true; *relres_out = 0.0; return PCB_OK; }
+  const int limit = c.fixed > 0 ? c.fixed : c.maxit;
+  bool checking = false;
+  for (int it = 0; it < limit; ++it) {
+    CK(launch_matvec(B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
+    CK(launch_reduce(B, B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
+    CK(launch_axpby(B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
+    if ((rc = apply_precond(B, va, c.kind, c.prec, SL_R1, SL_YO))) return rc;
+    CK(launch_dot(B, SL_R1, SL_YO));
+    CK(launch_reduce(B, B.off_vec, 1, 0, SS_MINRES_GIVENS, c.tol, 0, 0));
+    CK(launch_minres_wx(B, SL_Y, SL_W, SL_W2, s_x));
+    CK(launch_swap(B, SL_R1, SL_R2, SL_Y, SL_YO, SL_W, SL_W2));
+    std::swap(p->hS.v[SL_R1], p->hS.v[SL_R2]);
+    std::swap(p->hS.v[SL_Y], p->hS.v[SL_YO]);
+    std::swap(p->hS.v[SL_W], p->hS.v[SL_W2]);
+    if ((rc = read_scal(B, hs, 1))) return rc;
+    *it_out = it + 1;
+    if (hs->flags & 4) return PCB_ERR_NONFINITE;
+    if (hs->flags & 2) return PCB_ERR_BREAKDOWN;
+    if (c.fixed > 0) continue;
+    if ((hs->flags & 1) || checking) {
+      CK(launch_matvec(B, PCB_OP_A, s_x, SL_Q, s_b, EPI_RESID));
+      CK(launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+      if ((rc = read_scal(B, hs, 1))) return rc;
+      const double rel = std::sqrt(hs->dot1) / hs->bnorm;
+      *relres_out = rel;
+      if (rel <= c.tol) { *conv_out = true; return PCB_OK; }
+      if (!c.check_true) return PCB_OK;    // inner solve of a refinement sweep ends at its first check
+      checking = true;
+    }
+  }
+  CK(launch_matvec(B, PCB_OP_A, s_x, SL_Q, s_b, EPI_RESID));
+  CK(launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+  if ((rc = read_scal(B, hs, 1))) return rc;
+  *relres_out = std::sqrt(hs->dot1) / hs->bnorm;
+  *conv_out = *relres_out <= c.tol;
+  return PCB_OK;
+}
+
+static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Scal* hs, double* relres_out,
+                         int* it_out, bool* conv_out) {
+  const Batch& B = p->B;
+  const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
+  const bool va = p->g.var_a != 0;
+  const int op = PCB_OP_AHAT;
+  CK(cudaMemsetAsync(p->hS.v[s_x], 0, vb, p->stream));
+  CK(cudaMemsetAsync(p->dSc, 0, sizeof(Scal), p->stream));
+  CK(launch_dot(B, s_b, s_b));
+  CK(launch_reduce(B, B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
+  int rc;
+  if ((rc = read_scal(B, hs, 1))) return rc;
+  *it_out = 0; *conv_out = false; *relres_out = 1.0;
+  if (!std::isfinite(hs->bnorm)) return PCB_ERR_NONFINITE;
+  if (hs->bnorm == 0.0) { *conv_out = true; *relres_out = 0.0; return PCB_OK; }
+  const int limit = c.fixed > 0 ? c.fixed : c.maxit;
+  int total = 0;
+  while (total < limit) {
+    CK(launch_matvec(B, op, s_x, SL_R, s_b, EPI_RESID));
+    CK(launch_reduce(B, B.off_mv, 1, 0, SS_GMRES_START, c.tol, 0, 0));
+    if ((rc = read_scal(B, hs, 1))) return rc;
+    if (hs->flags & 4) return PCB_ERR_NONFINITE;
+    *relres_out = hs->est;
+    if (c.fixed <= 0 && hs->est <= c.tol) { *conv_out = true; return PCB_OK; }
+    CK(launch_setslot(B, SL_VJ, SL_VBASE, 0));
+    CK(launch_axpby(B, AX_SCALE_INV_BETA, SL_R, SL_VJ, -1));
+    const int mres = std::min(c.restart, limit - total);
+    int k = 0;
+    for (int j = 0; j < mres; ++j) {
+      CK(launch_setslot(B, SL_VJ, SL_VBASE, j));
+      CK(launch_setslot(B, SL_ZJ, SL_ZBASE, j));
+      CK(launch_setslot(B, SL_VJ1, SL_VBASE, j + 1));
+      if ((rc = apply_precond(B, va, c.kind, c.prec, SL_VJ, SL_ZJ))) return rc;
+      CK(launch_matvec(B, op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
+      for (int pass = 0; pass < 2; ++pass) {
+        CK(launch_multidot(B, SL_VBASE, j, SL_VJ1));
+        CK(launch_reduce_multi(B, j, pass));
+        CK(launch_multiaxpy(B, SL_VBASE, j, SL_VJ1, pass));
+      }
+      CK(launch_dot(B, SL_VJ1, SL_VJ1));
+      CK(launch_reduce(B, B.off_vec, 1, 0, SS_GMRES_ARNOLDI, c.tol, j, c.restart));
+      CK(launch_axpby(B, AX_SCALE_INV_HNORM, SL_VJ1, SL_VJ1, -1));
+      if ((rc = read_scal(B, hs, 1))) return rc;
+      k = j + 1;
+      total += 1;
+      if (hs->flags & 4) return PCB_ERR_NONFINITE;
+      if (c.fixed <= 0 && (hs->flags & 1)) break;
+      if (hs->flags & 8) break;
+    }
+    // x += Z y
+    CK(launch_multiaxpy(B, SL_ZBASE, k - 1, s_x, -1));
+    CK(cudaMemsetAsync(&p->dSc->flags, 0, sizeof(int), p->stream));
+    *it_out = total;
+    if (c.fixed <= 0 && (hs->flags & 1)) {
+      CK(launch_matvec(B, op, s_x, SL_R, s_b, EPI_RESID));
+      CK(launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+      if ((rc = read_scal(B, hs, 1))) return rc;
+      *relres_out = std::sqrt(hs->dot1) / hs->bnorm;
+      if (*relres_out <= c.tol) { *conv_out = true; return PCB_OK; }
+      if (!c.check_true) return PCB_OK;
+    }
+  }
+  CK(launch_matvec(B, op, s_x, SL_R, s_b, EPI_RESID));
+  CK(launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+  if ((rc = read_scal(B, hs, 1))) return rc;
+  *relres_out = std::sqrt(hs->dot1) / hs->bnorm;
+  *conv_out = *relres_out <= c.tol;
+  return PCB_OK;
+}
+
+static void resolve_defaults(const pcb_problem* p, const pcb_solve_opts* o, SolveCfg& c) {
+  c.method = o ? o->method : PCB_METHOD_AUTO;
+  c.kind = o ? o->precond : PCB_PREC_NONE;
+  c.tol = (o && o->tol > 0) ? o->tol : 1e-8;
+  c.maxit = (o && o->maxit > 0) ? o->maxit : 500;
+  c.restart = (o && o->restart > 0) ? std::min(o->restart, PCB_MAX_RESTART) : 30;
+  c.fixed = o ? o->fixed_iterations : 0;
+  c.prec = p->desc.precision;
+  const bool va = p->g.var_a != 0;
+  if (c.method == PCB_METHOD_AUTO) {
+    if (p->g.theta == 1.0) c.method = PCB_MINRES;
+    else c.method = va ? PCB_FGMRES : PCB_GMRES;
+    if (c.kind == PCB_PREC_NONE) {
+      if (c.method == PCB_MINRES) c.kind = va ? PCB_PREC_PMS : PCB_PREC_ABS_PS;
+      else c.kind = PCB_PREC_PS;
+    }
+  }
+  c.op = c.method == PCB_MINRES ? PCB_OP_A : PCB_OP_AHAT;
+}
+
+static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_dev, double* x_dev,
+                      pcb_solve_info* info) {
+  SolveCfg c;
+  resolve_defaults(p, o, c);
+  if (c.method == PCB_MINRES && (c.kind == PCB_PREC_PS)) return PCB_ERR_INVALID_ARG;   // P_S is not SPD
+  if (c.kind == PCB_PREC_ABS_PS && p->g.var_a) return PCB_ERR_UNSUPPORTED;
+  int rc;
+  if ((rc = ensure_minres(p))) return rc;
+  const size_t nv = (size_t)2 * p->g.mn;
+  double* v = p->vec_minres;
+  p->hS.v[SL_R1] = v + 0 * nv; p->hS.v[SL_R2] = v + 1 * nv; p->hS.v[SL_Y] = v + 2 * nv; p->hS.v[SL_YO] = v + 3 * nv;
+  p->hS.v[SL_Q] = v + 4 * nv; p->hS.v[SL_W] = v + 5 * nv; p->hS.v[SL_W2] = v + 6 * nv;
+  p->hS.v[SL_R] = v + 0 * nv;
+  if (c.method != PCB_MINRES) {
+    if ((rc = ensure_gmres(p, c.restart))) return rc;
+    p->hS.v[SL_VBASE] = p->vec_gmres;
+    p->hS.v[SL_ZBASE] = p->vec_gmres + (size_t)(c.restart + 1) * nv;
+  }
+  p->hS.v[SL_X] = x_dev;
+  p->hS.v[SL_B] = (double*)b_dev;
+  const bool mixed = c.prec == PCB_MIXED;
+  if (mixed) {
+    if ((rc = ensure_mixed(p))) return rc;
+    p->hS.v[SL_BI] = p->vec_mixed;
+    p->hS.v[SL_XI] = p->vec_mixed + nv;
+  }
+  if ((rc = upload_slots(p))) return rc;
+  Scal* hs = p->hSc;
+  auto t0 = std::chrono::steady_clock::now();
+  int iters = 0, sweeps = 0;
+  double relres = 1.0;
+  bool conv = false;
+  auto run = [&](SolveCfg& cc, int sb, int sx, double* rel, int* it, bool* cv) {
+    return cc.method == PCB_MINRES ? minres_single(p, cc, sb, sx, hs, rel, it, cv)
+                                   : fgmres_single(p, cc, sb, sx, hs, rel, it, cv);
+  };
+  if (!mixed) {
+    c.check_true = true;
+    rc = run(c, SL_B, SL_X, &relres, &iters, &conv);
+    sweeps = 1;
+  } else {
+    // FP64 iterative refinement around the FP32-preconditioned inner solve:
+    //   r = b - op x ; solve op d = r (inner tolerance tol*||b||/||r||) ; x += d
+    const int max_ref = (o && o->max_refinements > 0) ? o->max_refinements : 10;
+    const size_t vbytes = nv * sizeof(double);
+    CK(cudaMemsetAsync(x_dev, 0, vbytes, p->stream));
+    CK(launch_dot(p->B, SL_B, SL_B));
+    CK(launch_reduce(p->B, p->B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
+    if ((rc = read_scal(p->B, hs, 1))) return rc;
+    const double bnorm = hs->bnorm;
+    if (!std::isfinite(bnorm)) return PCB_ERR_NONFINITE;
+    CK(launch_axpby(p->B, AX_COPY, SL_B, SL_BI, -1));
+    double rnorm = bnorm;
+    rc = PCB_OK;
+    if (bnorm == 0.0) { conv = true; relres = 0.0; }
+    while (!conv && sweeps < max_ref && iters < c.maxit) {
+      SolveCfg ci = c;
+      ci.check_true = false;
+      ci.tol = std::min(0.5, c.tol * bnorm / rnorm);
+      ci.maxit = c.maxit - iters;
+      double rel_in; int it_in; bool cv_in;
+      rc = run(ci, SL_BI, SL_XI, &rel_in, &it_in, &cv_in);
+      if (rc) break;
+      iters += it_in;
+      sweeps += 1;
+      // x += d ; r = b - op x  (into the inner right-hand side slot)
+      CK(launch_axpby(p->B, AX_ADD, SL_XI, SL_X, -1));
+      CK(launch_matvec(p->B, c.op, SL_X, SL_BI, SL_B, EPI_RESID));
+      CK(launch_reduce(p->B, p->B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+      if ((rc = read_scal(p->B, hs, 1))) break;
+      rnorm = std::sqrt(hs->dot1);
+      relres = rnorm / bnorm;
+      if (!std::isfinite(relres)) { rc = PCB_ERR_NONFINITE; break; }
+      if (relres <= c.tol) conv = true;
+      if (c.fixed > 0) break;
+    }
+  }
+  CK(cudaStreamSynchronize(p->stream));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rc == PCB_OK && !conv && c.fixed <= 0) rc = PCB_NOT_CONVERGED;
+  if (info) {
+    info->status = rc; info->method = c.method; info->precond = c.kind; info->iterations = iters;
+    info->refinements = sweeps; info->relres = relres; info->seconds = secs;
+  }
+  return rc;
+}
+
+extern "C" {
+
+int pcb_assemble_rhs(pcb_problem* p, int op, const double* g_dev, const double* f_dev, const double* y0_dev,
+                     double* b_dev) {
+  if (!p || !g_dev || !f_dev || !b_dev || (op != PCB_OP_A && op != PCB_OP_AHAT)) return PCB_ERR_INVALID_ARG;
+  CK(launch_rhs(p->g, p->stream, op, g_dev, f_dev, y0_dev, b_dev));
+  return PCB_OK;
+}
+
+int pcb_matvec(pcb_problem* p, int op, const double* x_dev, double* y_dev) {
+  if (!p || !x_dev || !y_dev || (op != PCB_OP_A && op != PCB_OP_AHAT)) return PCB_ERR_INVALID_ARG;
+  if (x_dev == y_dev) return PCB_ERR_INVALID_ARG;
+  p->hS.v[SL_UIN] = (double*)x_dev;
+  p->hS.v[SL_UOUT] = y_dev;
+  int rc;
+  if ((rc = upload_slots(p))) return rc;
+  CK(launch_matvec(p->B, op, SL_UIN, SL_UOUT, -1, EPI_PLAIN));
+  return PCB_OK;
+}
+
+int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_dev, double* y_dev) {
+  if (!p || !x_dev || !y_dev) return PCB_ERR_INVALID_ARG;
+  if (kind != PCB_PREC_ABS_PS && kind != PCB_PREC_PS && kind != PCB_PREC_PMS) return PCB_ERR_INVALID_ARG;
+  if (precision != PCB_FP64 && precision != PCB_MIXED) return PCB_ERR_INVALID_ARG;
+  if (kind == PCB_PREC_ABS_PS && p->g.var_a) return PCB_ERR_UNSUPPORTED;
+  p->hS.v[SL_UIN] = (double*)x_dev;
+  p->hS.v[SL_UOUT] = y_dev;
+  int rc;
+  if ((rc = upload_slots(p))) return rc;
+  return apply_precond(p->B, p->g.var_a != 0, kind, precision, SL_UIN, SL_UOUT);
+}
+
+int pcb_recover(pcb_problem* p, const double* x_dev, double* y_dev, double* p_dev) {
+  if (!p || !x_dev || !y_dev || !p_dev) return PCB_ERR_INVALID_ARG;
+  CK(launch_recover(p->g, p->stream, x_dev, y_dev, p_dev));
+  return PCB_OK;
+}
+
+int pcb_solve(pcb_problem* p, const pcb_solve_opts* o, const double* b_dev, double* x_dev, pcb_solve_info* info) {
+  if (!p || !b_dev || !x_dev || b_dev == x_dev) return PCB_ERR_INVALID_ARG;
+  return solve_impl(p, o, b_dev, x_dev, info);
+}
+
+int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* o, const double* b_host, double* x_host,
+                   pcb_solve_info* info) {
+  if (!p || !b_host || !x_host) return PCB_ERR_INVALID_ARG;
+  const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
+  double *b = nullptr, *x = nullptr;
+  if (cudaMalloc(&b, vb) != cudaSuccess) { cudaGetLastError(); return PCB_ERR_OUT_OF_MEMORY; }
+  if (cudaMalloc(&x, vb) != cudaSuccess) { cudaGetLastError(); cudaFree(b); return PCB_ERR_OUT_OF_MEMORY; }
+  int rc = PCB_OK;
+  if (cudaMemcpyAsync(b, b_host, vb, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) rc = PCB_ERR_CUDA;
+  if (rc == PCB_OK) rc = solve_impl(p, o, b, x, info);
+  if ((rc == PCB_OK || rc == PCB_NOT_CONVERGED) &&
+      cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+    rc = PCB_ERR_CUDA;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess && rc == PCB_OK) rc = PCB_ERR_CUDA;
+  cudaFree(b);
+  cudaFree(x);
+  return rc;
+}
+
+int pcb_batch_solve(pcb_problem* const* problems, int count, const pcb_solve_opts* opts, const double* const* b_dev,
+                    double* const* x_dev, pcb_solve_info* infos) {
+  if (!problems || count < 1 || !b_dev || !x_dev) return PCB_ERR_INVALID_ARG;
+  int worst = PCB_OK;
+  for (int k = 0; k < count; ++k) {
+    const int rc = pcb_solve(problems[k], opts, b_dev[k], x_dev[k], infos ? infos + k : nullptr);
+    if (rc < 0 && worst >= 0) worst = rc;
+    else if (rc > 0 && worst == PCB_OK) worst = rc;
+  }
+  return worst;
+}
+
+}  // extern "C"

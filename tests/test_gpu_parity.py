@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on seeded inputs.
+
+Tolerances (derived from the arithmetic):
+  FP64 transforms / operators : relative 2-norm error <= 1e-12 (rounding of O(log size) stages)
+  FP32 preconditioner         : relative 2-norm error <= 2e-6  (FP32 unit roundoff 6e-8 times the
+                                ~30 transform stages and the pointwise solve)
+  FP64 solves                 : same-algorithm iterates agree to <= 1e-10 relative
+  mixed solves                : error against the FP64 oracle solution <= 1e-7 relative
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import discretisation as ds
+from oracle import krylov as kr
+from oracle import operators as op
+from oracle import precond as pc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2406_00952_gb300 import _build
+    _build.build()
+    import paper_2406_00952_gb300 as P
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+SHAPES = [(1, 2, 1.0, 1.0), (2, 4, 0.5, 1e-2), (15, 16, 1.0, 1e-2), (31, 8, 0.5, 1e-4), (47, 32, 1.0, 1e-6),
+          (63, 64, 0.5, 1e-2), (95, 128, 0.75, 1e-3), (127, 4, 1.0, 1e-1), (191, 32, 0.5, 1e-5)]
+ORACLE = {"abs_ps": pc.apply_abs_ps_inv, "ps": pc.apply_ps_inv, "pms": pc.apply_pms_inv}
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "N%d-n%d-th%g-g%g" % s)
+@pytest.mark.parametrize("kind", ["abs_ps", "ps", "pms"])
+def test_precond_parity(P, shape, kind):
+    N, n, theta, gamma = shape
+    prob = ds.Problem(N, n, theta, gamma)
+    v = synth.random_vector(2 * prob.m * n, seed=100 + N + n)
+    ref = ORACLE[kind](prob, v)
+    gp = P.Problem(N, n, theta, gamma, precision="fp64")
+    out64 = gp.precond_apply(dev(v), kind=kind, precision="fp64").cpu().numpy()
+    out32 = gp.precond_apply(dev(v), kind=kind, precision="mixed").cpu().numpy()
+    assert rel(out64, ref) <= 1e-12, rel(out64, ref)
+    assert rel(out32, ref) <= 2e-6, rel(out32, ref)
+    # in place (x and y the same buffer)
+    t = dev(v)
+    gp.precond_apply(t, out=t, kind=kind, precision="fp64")
+    assert rel(t.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "N%d-n%d-th%g-g%g" % s)
+@pytest.mark.parametrize("opname", ["A", "Ahat"])
+def test_matvec_parity(P, shape, opname):
+    N, n, theta, gamma = shape
+    prob = ds.Problem(N, n, theta, gamma)
+    v = synth.random_vector(2 * prob.m * n, seed=200 + N)
+    ref = op.matvec_A(prob, v) if opname == "A" else op.matvec_A_hat(prob, v)
+    gp = P.Problem(N, n, theta, gamma)
+    out = gp.matvec(dev(v), op=opname).cpu().numpy()
+    assert rel(out, ref) <= 1e-13, rel(out, ref)
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5, 0.8])
+def test_rhs_and_recover_parity(P, theta):
+    N, n = 15, 8
+    prob = ds.Problem(N, n, theta, 3e-3)
+    g = synth.random_target(N, n, seed=11); f = synth.manufactured_source(N, n)
+    y0 = synth.random_vector(N * N, seed=12)
+    gp = P.Problem(N, n, theta, 3e-3)
+    for opname, ref in (("A", ds.rhs_minres(prob, g, f, y0)), ("Ahat", ds.rhs_gmres(prob, g, f, y0))):
+        b = gp.assemble_rhs(dev(g.ravel()), dev(f.ravel()), dev(y0), op=opname).cpu().numpy()
+        assert rel(b, ref) <= 1e-14
+    b0 = gp.assemble_rhs(dev(g.ravel()), dev(f.ravel()), None).cpu().numpy()
+    assert rel(b0, ds.rhs_minres(prob, g, f)) <= 1e-14
+    x = synth.random_vector(2 * prob.m * n, seed=13)
+    y, p = gp.recover(dev(x))
+    yr, pr = ds.recover(prob, x)
+    assert rel(y.cpu().numpy(), yr.ravel()) <= 1e-13 and rel(p.cpu().numpy(), pr.ravel()) <= 1e-13
+
+
+def _oracle_solve(prob, b, method, kind, tol, fixed=None):
+    M = {"abs_ps": pc.apply_abs_ps_inv, "ps": pc.apply_ps_inv, "pms": pc.apply_pms_inv}[kind]
+    if method == "minres":
+        return kr.minres(lambda z: op.matvec_A(prob, z), b, lambda r: M(prob, r), tol=tol, fixed_iterations=fixed)
+    return kr.fgmres(lambda z: op.matvec_A_hat(prob, z), b, lambda r: M(prob, r), tol=tol, fixed_iterations=fixed)
+
+
+@pytest.mark.parametrize("case", [("minres", "abs_ps", 1.0), ("minres", "pms", 1.0), ("gmres", "ps", 0.5),
+                                  ("gmres", "ps", 1.0), ("minres", "abs_ps", 0.5)])
+def test_same_algorithm_iterates(P, case):
+    """Oracle and GPU run the same Krylov algorithm for the same number of iterations (FP64)."""
+    method, kind, theta = case
+    inst = synth.config0()
+    prob = ds.Problem(inst.N, inst.n, theta, inst.gamma)
+    b = ds.rhs_minres(prob, inst.g, inst.f) if method == "minres" else ds.rhs_gmres(prob, inst.g, inst.f)
+    for k in (3, 8):
+        xo, _ = _oracle_solve(prob, b, method, kind, 1e-10, fixed=k)
+        gp = P.Problem(inst.N, inst.n, theta, inst.gamma, precision="fp64")
+        x, info = gp.solve(dev(b), method=method, precond=kind, fixed_iterations=k, restart=30)
+        assert info["iterations"] == k
+        assert rel(x.cpu().numpy(), xo) <= 1e-10, rel(x.cpu().numpy(), xo)
+
+
+def test_config0_fp64_and_mixed(P):
+    """Config 0: MINRES-|P_S| to relres 1e-10 (FP64); mixed to 1e-8; manufactured discrete solution."""
+    inst = synth.config0()
+    prob = ds.Problem.from_instance(inst)
+    x1, x2 = synth.grid(prob.N)
+    ylev = synth.times(prob.n)[:, None] * (np.sin(math.pi * x1) * np.sin(math.pi * x2)).reshape(1, -1)
+    gt, ft, y_ex, p_ex = ds.manufactured_rhs(prob, ylev, inst.g)
+    b = np.concatenate([gt.ravel(), math.sqrt(prob.gamma) * ft.ravel()])
+    xs, io = kr.minres(lambda z: op.matvec_A(prob, z), b, lambda r: pc.apply_abs_ps_inv(prob, r), tol=1e-13)
+    gp = P.Problem(prob.N, prob.n, prob.theta, prob.gamma, precision="fp64")
+    x, info = gp.solve(dev(b), tol=1e-10)
+    assert info["relres"] <= 1e-10 and info["method"] == 1 and info["precond"] == 1
+    xo, io10 = kr.minres(lambda z: op.matvec_A(prob, z), b, lambda r: pc.apply_abs_ps_inv(prob, r), tol=1e-10)
+    assert abs(info["iterations"] - io10.iterations) <= 1
+    xg = x.cpu().numpy()
+    assert rel(xg, xs) <= 100 * 1e-10          # forward error <= kappa * relres, kappa(A) ~ 1e2 here
+    y, p = gp.recover(x)
+    assert rel(y.cpu().numpy(), y_ex.ravel()) <= 1e-8
+    gm = P.Problem(prob.N, prob.n, prob.theta, prob.gamma, precision="mixed")
+    xm, im = gm.solve(dev(b), tol=1e-8)
+    x8, i8 = gp.solve(dev(b), tol=1e-8)
+    assert im["relres"] <= 1e-8
+    assert rel(xm.cpu().numpy(), xs) <= 1e-7 * 100
+    assert im["iterations"] <= i8["iterations"] + 2, (im, i8)
+
+
+@pytest.mark.parametrize("gamma", [1e-10, 1e-6, 1e-2])
+def test_table1_on_gpu(P, gamma):
+    """Example 1, h = 2^-5, Crank-Nicolson: iteration counts and e_h as printed in Table 1."""
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table1_example1_cn.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                gg, k, dof, gi, ge, mi, me = line.split()
+                rows[(float(gg), int(k))] = (int(gi), float(ge), int(mi), float(me))
+    git, geh, mit, meh = rows[(gamma, 5)]
+    N, n = 31, 32
+    prob = ds.Problem(N, n, 0.5, gamma)
+    g, f, ye, pe = synth.example1_data(N, n)
+    gp = P.Problem(N, n, 0.5, gamma, precision="fp64")
+    bh = gp.assemble_rhs(dev(g.ravel()), dev(f.ravel()), dev(ye[0]), op="Ahat")
+    x, info = gp.solve(bh, method="gmres", precond="ps", tol=1e-8)
+    assert info["iterations"] == git
+    y, p = gp.recover(x)
+    eh = ds.error_eh(prob, y.cpu().numpy().reshape(n, -1), p.cpu().numpy().reshape(n, -1), ye, pe)
+    assert abs(eh - geh) / geh < 0.01
+    b = gp.assemble_rhs(dev(g.ravel()), dev(f.ravel()), dev(ye[0]), op="A")
+    x, info = gp.solve(b, method="minres", precond="abs_ps", tol=1e-8)
+    assert info["iterations"] == mit
+    # FP32 preconditioner: rounding noise in P^{-1} v is amplified by about ||A|| ||P^{-1}||, which
+    # costs extra iterations when that product is large (gamma = 1e-2: 6 instead of 3).
+    gm = P.Problem(N, n, 0.5, gamma, precision="mixed")
+    x, info = gm.solve(bh, method="gmres", precond="ps", tol=1e-8)
+    assert info["relres"] <= 1e-8 and info["iterations"] <= 2 * git, info
+
+
+def test_errors_are_reported_not_raised_in_kernels(P):
+    gp = P.Problem(15, 16, 1.0, 1e-2)
+    b = torch.full((gp.size,), float("nan"), dtype=torch.float64, device="cuda")
+    with pytest.raises(Exception) as e:
+        gp.solve(b)
+    assert "non-finite" in str(e.value)
+    z = torch.zeros(gp.size, dtype=torch.float64, device="cuda")
+    x, info = gp.solve(z)
+    assert info["relres"] == 0.0 and float(x.abs().max()) == 0.0
