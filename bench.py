@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the block omega-circulant preconditioned all-at-once solver on one GB300.
+
+Workload (the paper's problem family at the large single-instance size): 2D heat tracking control
+on the unit square, N = 511 (m = 261,121), n = 512 backward-Euler steps, T = 1, a(x) = 1,
+gamma in {1e-2, 1e-6}, random smooth target g (seed 1) and analytic source f; 267,387,904 unknowns.
+One step = one mixed-precision MINRES-|P_S| solve to true relative residual 1e-8 for each gamma
+(two solves), inputs resident in HBM.  Metric: solves/s (higher is better).
+
+Also reported: the same solves in plain FP64 on the GPU, an end-to-end figure through the host-buffer
+C-ABI call (host->device copy of b and device->host copy of x inside the timed region), the
+roofline of the preconditioner apply (the dominant kernel sequence) from CUDA events recorded on the
+library's stream during the timed region, and the FP64 CPU oracle timed on the host cores.
+
+Multi-GPU: every rank solves its own copy of the workload (independent problems, no data-path
+collective: weak scaling); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="heat-control N=511 n=512 backward-Euler a=1 (2.67e8 unknowns), gamma {1e-2,1e-6}",
+                N=511, n=512, theta=1.0, T=1.0, gammas=(1e-2, 1e-6))
+METRIC = "solves/s to relres 1e-8 (mixed-precision MINRES-|P_S|)"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "precond_apply_N511_n512.md")
+
+
+def args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--small", action="store_true", help="N=255, n=256 instead (quick checks only)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush(); self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def profile_traffic():
+    """DRAM bytes per preconditioner apply from the committed ncu summary, if it still matches the
+    kernel source (its source hash); else None."""
+    try:
+        import hashlib
+        txt = open(PROFILE_TRAFFIC).read()
+        want = None; traffic = None
+        for line in txt.splitlines():
+            if line.startswith("source_sha256:"):
+                want = line.split(":", 1)[1].strip()
+            if line.startswith("traffic_bytes_per_apply:"):
+                traffic = float(line.split(":", 1)[1].strip())
+        h = hashlib.sha256()
+        for f in ("fft.cuh", "precond.cu", "pcb_internal.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_2406_00952_gb300", "csrc", f), "rb").read())
+        return traffic if (want == h.hexdigest() and traffic) else None
+    except Exception:
+        return None
+
+
+SAMPLE = dict(N=255, n=256)
+
+
+def cpu_baseline(W):
+    """The FP64 oracle as it stands, timed on the host cores on a bounded sample: the oracle's own
+    MINRES-|P_S| run for one iteration on the same problem family at N=255, n=256 (gamma = 1e-2),
+    divided by its number of preconditioner applies (one iteration = one apply and one product),
+    then scaled to the full workload by the ratio of unknowns (the oracle's cost is O(mn log mn),
+    so the linear scaling slightly favours the CPU)."""
+    import synth
+    from oracle import discretisation as ds
+    from oracle import krylov as kr
+    from oracle import operators as op
+    from oracle import precond as pc
+    N, n = SAMPLE["N"], SAMPLE["n"]
+    prob = ds.Problem(N, n, W["theta"], W["gammas"][0], W["T"])
+    b = ds.rhs_minres(prob, synth.random_target(N, n, seed=1), synth.manufactured_source(N, n))
+    cnt = {"M": 0}
+
+    def M(r):
+        cnt["M"] += 1
+        return pc.apply_abs_ps_inv(prob, r)
+
+    t0 = time.perf_counter()
+    kr.minres(lambda z: op.matvec_A(prob, z), b, M, fixed_iterations=1)
+    dt = time.perf_counter() - t0
+    scale = (W["N"] ** 2 * W["n"]) / (N * N * n)
+    return dt / cnt["M"] * scale, oracle_iterations(W)
+
+
+def oracle_iterations(W):
+    """Iteration count of the oracle's MINRES-|P_S| on this workload (gamma = 1e-2), written by
+    oracle/count_iterations.py; None if that file is absent."""
+    p = os.path.join(ROOT, "tests", "golden", f"oracle_iterations_N{W['N']}_n{W['n']}.txt")
+    try:
+        for line in open(p):
+            if line.strip() and not line.startswith("#"):
+                return int(line.split()[-1])
+    except Exception:
+        return None
+    return None
+
+
+def reference_arm(a, W, rank, world):
+    """--impl reference: the FP64 oracle (CPU) timed on the host cores on the same workload; each
+    step is one bounded sample (one MINRES iteration's operator work at full size)."""
+    if rank != 0:
+        return
+    times = []
+    iters = oracle_iterations(W) or 0
+    for s in range(a.warmup + a.steps):
+        dt, _ = cpu_baseline(W)
+        if s >= a.warmup:
+            times.append(dt)
+    t_iter = statistics.median(times)
+    val = 1.0 / (t_iter * iters) if iters else None
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["name"], "sample": "one oracle MINRES iteration per step"},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle MINRES-|P_S| one-iteration run at N=255, n=256 per step, scaled by "
+                                       f"unknowns to {t_iter:.1f} s per full-size iteration, x {iters} "
+                                       f"oracle iterations"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    a = args()
+    rank = int(os.environ.get("RANK", 0)); world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    W = dict(WORKLOAD)
+    if a.small:
+        W.update(N=255, n=256, name="heat-control N=255 n=256 backward-Euler a=1, gamma {1e-2,1e-6}")
+    if a.impl == "reference":
+        return reference_arm(a, W, rank, world)
+
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2406_00952_gb300 as P
+    from paper_2406_00952_gb300 import _build
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    N, n = W["N"], W["n"]
+    stream = torch.cuda.current_stream()
+    probs, bs = [], []
+    g = torch.from_numpy(synth.random_target(N, n, seed=1).ravel()).cuda()
+    f = torch.from_numpy(synth.manufactured_source(N, n).ravel()).cuda()
+    for gam in W["gammas"]:
+        pr = P.Problem(N, n, W["theta"], gam, W["T"], precision="mixed", stream=stream)
+        probs.append(pr)
+        bs.append(pr.assemble_rhs(g, f))
+    del g, f
+    xs = [pr._empty() for pr in probs]
+    unknowns = probs[0].size
+    opts = dict(tol=1e-8, maxit=400)
+
+    def step(profile=False):
+        infos = []
+        for pr, b, x in zip(probs, bs, xs):
+            _, info = pr.solve(b, x, profile=profile, **opts)
+            infos.append(info)
+        return infos
+
+    for _ in range(a.warmup):
+        step()
+    barrier()
+    clk = Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(a.steps):
+        infos += step(profile=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    barrier()
+    solves = len(W["gammas"]) * a.steps * world
+    value = solves / (ms / 1e3)
+    hbm, peak_kind = peaks()
+    applies = sum(i["precond_applies"] for i in infos)
+    pms = sum(i["precond_ms"] for i in infos)
+    mvs = sum(i["matvecs"] for i in infos)
+    mvms = sum(i["matvec_ms"] for i in infos)
+    alg_bytes = 16.0 * unknowns            # precond apply: read 2mn + write 2mn FP64 values
+    achieved = alg_bytes / (pms / applies / 1e3) / 1e9
+    mv_ach = 16.0 * unknowns / (mvms / mvs / 1e3) / 1e9
+    iters = [i["iterations"] for i in infos]
+
+    # plain FP64 GPU solver on the same inputs (one solve per gamma)
+    fp64 = None
+    if not a.no_fp64:
+        t_fp = 0.0; it_fp = []
+        for gam, b in zip(W["gammas"], bs):
+            pr = P.Problem(N, n, W["theta"], gam, W["T"], precision="fp64", stream=stream)
+            x = pr._empty()
+            pr.solve(b, x, **opts)            # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, inf = pr.solve(b, x, **opts)
+            torch.cuda.synchronize()
+            t_fp += time.perf_counter() - t0
+            it_fp.append(inf["iterations"])
+            pr.close(); del x
+        fp64 = {"value": len(W["gammas"]) / t_fp, "unit": "solves/s", "iterations": it_fp}
+
+    # end to end through the host-buffer C-ABI call: b from pinned host memory, x back to host
+    e2e = None
+    if a.e2e_steps > 0:
+        bh = [b.cpu().pin_memory() for b in bs]
+        xh = [torch.empty_like(h).pin_memory() for h in bh]
+        for pr, b_, x_ in zip(probs, bh, xh):
+            pr.solve_host(b_, x_, **opts)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            for pr, b_, x_ in zip(probs, bh, xh):
+                pr.solve_host(b_, x_, **opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        nb = 8 * unknowns
+        e2e = {"value": len(W["gammas"]) * a.e2e_steps * world / dt, "unit": "solves/s",
+               "h2d_bytes_per_step": nb * len(W["gammas"]), "d2h_bytes_per_step": nb * len(W["gammas"])}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline and world == 1:
+        dt, it_o = cpu_baseline(W)
+        it_use = it_o if it_o else (fp64["iterations"][0] if fp64 else statistics.median(iters))
+        cpu = {"value": 1.0 / (dt * it_use), "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle MINRES-|P_S| one-iteration run at N=255, n=256 (gamma=1e-2), scaled by "
+                         f"unknowns to {dt:.1f} s per full-size iteration, x {it_use} iterations"
+                         + ("" if it_o else " (FP64 GPU iteration count; oracle count file absent)")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": W["name"], "unknowns": unknowns, "solver": "MINRES-|P_S| mixed",
+                       "tol": 1e-8, "l2": "inputs larger than L2 (2.1 GB vectors)", "parallelism": f"replicas x{world}",
+                       "iterations": iters},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": profile_traffic(), "kernel": "precond apply |P_S|^-1 (FP32)",
+                         "alg_bytes_per_launch": alg_bytes, "avg_ms": pms / applies, "peak_kind": peak_kind},
+            "kernels": {"precond_ms_share": pms / ms, "matvec_ms_share": mvms / ms, "matvec_avg_ms": mvms / mvs,
+                        "matvec_alg_gbs": mv_ach},
+            "fp64_gpu": fp64,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": sum(i["launches"] for i in infos),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -131,6 +131,8 @@ typedef struct {
   int restart;            /* GMRES/FGMRES restart length; <= 0 => 30 (max 64)                  */
   int max_refinements;    /* mixed precision: outer refinement sweeps; <= 0 => 10              */
   int fixed_iterations;   /* > 0: run exactly this many iterations (comparison runs)           */
+  int profile;            /* != 0: time every preconditioner apply and matvec with CUDA events  */
+                          /* recorded on the problem's stream (fills the *_ms fields of info)   */
 } pcb_solve_opts;
 
 typedef struct {
@@ -141,6 +143,11 @@ typedef struct {
   int refinements;        /* refinement sweeps (1 for FP64)                                    */
   double relres;          /* true FP64 relative residual at exit                                */
   double seconds;         /* wall time of the call                                             */
+  long long launches;     /* CUDA kernel launches the call issued                              */
+  int precond_applies;    /* preconditioner applications                                       */
+  double precond_ms;      /* profile != 0: summed device time of the applications              */
+  int matvecs;            /* operator products (Krylov and true-residual)                      */
+  double matvec_ms;       /* profile != 0: summed device time of the products                  */
 } pcb_solve_info;
 
 /* Solve op x = b from a zero initial guess, op = A for MINRES and A_hat for (F)GMRES.
@@ -148,7 +155,9 @@ typedef struct {
 int pcb_solve(pcb_problem* p, const pcb_solve_opts* opts, const double* b_dev, double* x_dev,
               pcb_solve_info* info);
 
-/* Same solve through host buffers: copies b_host to the device, solves, copies x back. */
+/* Same solve through host buffers: copies b_host to the device, solves, copies x back
+ * (device staging buffers are allocated on the first call and kept until pcb_destroy;
+ * page-locked host buffers give the fastest copies). */
 int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* opts, const double* b_host,
                    double* x_host, pcb_solve_info* info);
 

@@ -32,9 +32,10 @@ def _ptr(t: torch.Tensor | None, numel: int | None = None) -> int | None:
     return t.data_ptr()
 
 
-def _opts(method="auto", precond=None, tol=1e-8, maxit=500, restart=30, max_refinements=10, fixed_iterations=0):
+def _opts(method="auto", precond=None, tol=1e-8, maxit=500, restart=30, max_refinements=10, fixed_iterations=0,
+          profile=False):
     return PcbSolveOpts(METHODS[method], PRECONDS[precond], float(tol), int(maxit), int(restart),
-                        int(max_refinements), int(fixed_iterations))
+                        int(max_refinements), int(fixed_iterations), int(bool(profile)))
 
 
 class Problem:

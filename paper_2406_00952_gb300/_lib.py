@@ -27,12 +27,15 @@ class PcbDesc(ctypes.Structure):
 
 class PcbSolveOpts(ctypes.Structure):
     _fields_ = [("method", c_int), ("precond", c_int), ("tol", c_double), ("maxit", c_int),
-                ("restart", c_int), ("max_refinements", c_int), ("fixed_iterations", c_int)]
+                ("restart", c_int), ("max_refinements", c_int), ("fixed_iterations", c_int),
+                ("profile", c_int)]
 
 
 class PcbSolveInfo(ctypes.Structure):
     _fields_ = [("status", c_int), ("method", c_int), ("precond", c_int), ("iterations", c_int),
-                ("refinements", c_int), ("relres", c_double), ("seconds", c_double)]
+                ("refinements", c_int), ("relres", c_double), ("seconds", c_double),
+                ("launches", c_longlong), ("precond_applies", c_int), ("precond_ms", c_double),
+                ("matvecs", c_int), ("matvec_ms", c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -4,6 +4,7 @@
 namespace pcb {
 
 bool mg_available() { return false; }
+int mg_launch_count(int kind) { (void)kind; return 0; }
 size_t mg_workspace_bytes(const Geom& g) { (void)g; return 256; }
 cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host) {
   (void)g; (void)ws; (void)a_edges_host;

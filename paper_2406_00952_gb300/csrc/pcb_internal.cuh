@@ -56,7 +56,9 @@ struct Geom {
   int var_a;                      // 0: a = 1; 1: coefficient tables below
   // launch shapes (blocks of each pass for this instance)
   // launch shapes of the preconditioner passes, index 0 = FP64 apply, 1 = FP32 apply
-  int dst_lpb[2];                 // lines per block of the DST passes
+  int dst_lpb[2];                 // lines per block of the x1-line DST pass
+  int dst_lpb_j[2];               // lines per block of the x2-line DST pass
+  int dst_q, time_q;              // values per lane of the register FFTs (line length / lanes)
   int dst_blocks_i[2], dst_blocks_j[2]; // blocks of the x1-line and x2-line DST passes
   int time_cpb[2];                // spatial columns per block of the time pass
   int time_blocks[2];
@@ -132,7 +134,8 @@ struct Batch {
   const int* off_mv;    int tot_mv;
   const int* off_vec;   int tot_vec;
   double* partial;        // reduction partials [tot_vec * 8]
-  int max_lpb_M[2], max_cpb_n[2];   // largest lines*(M+1) and columns*(n+1) per precision
+  int dst_q, time_q;      // register-FFT variant shared by every instance of the batch
+  size_t dst_smem[2], time_smem[2];   // dynamic shared memory per block, per precision
 };
 
 }  // namespace pcb

@@ -4,7 +4,7 @@
 // |P_S|, P_S and P_MS are block diagonal in Q's basis (Sec. 3.5, three-step applications), so
 //     P^{-1} v = Q^{-1} (pointwise solve) Q v.
 // The transforms along the three axes commute, so the apply runs as five batched passes, each
-// along one full axis inside shared memory:
+// along one full axis:
 //     DST along x1  ->  DST along x2  ->  [time DFT, pointwise solve, inverse time DFT]
 //     ->  DST along x2  ->  DST along x1.
 // The spatial passes keep the data real: the two halves (y~ and p~ blocks) of the all-at-once
@@ -12,11 +12,18 @@
 // comes from the length-2L FFT of the odd extension (Y_p = -2i * DST(x)_p).
 // The time pass packs the two halves the same way; for zeta = pi the F-slot r of a real series
 // and slot n-1-r are complex conjugates, which separates the halves per frequency pair.
-#include "fft.cuh"
+//
+// Each pass stages a tile of lines through padded shared memory (coalesced global access in both
+// directions); each line is transformed by a group of P <= 32 lanes holding Q values each
+// (register DFT + warp-shuffle stages, fft_reg.cuh).
+#include <algorithm>
+
+#include "fft_reg.cuh"
 
 namespace pcb {
 
 enum { PK_ABS_PS = 1, PK_PS = 2, PK_PMS = 3 };
+int mg_launch_count(int kind);
 
 template <typename R> __device__ __forceinline__ const cx<R>* twd(const Geom& g);
 template <> __device__ __forceinline__ const float2* twd<float>(const Geom& g) { return g.twd_f; }
@@ -35,12 +42,66 @@ template <typename R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
 
+// padded line length (in complex elements) able to hold indices 0..len-1 under pidx(), odd so
+// that consecutive lines start in different banks
+__host__ __device__ __forceinline__ int padded_len(int len) { return (len + (len >> 5) + 1) | 1; }
+
+// ------------------------------------------------------------------------------------------
+// Line transform shared by the passes.  On entry lane t of a P-lane group has x[q] = element
+// t + P q of its line.  Afterwards the lane owns Q transform values; owned(j) gives the output
+// index of the j-th one and value(j) its register.
+//   Q < 32 : register DFT, twiddle, cross-lane DIF; owned(j) = j + Q bitrev_P(t).
+//   Q = 32 (P = 32): register DFT, twiddle, transpose through the warp's 32 x 33 scratch,
+//            second 32-point register DFT; owned(j) = t + 32 j (natural, lane-strided order).
+// ------------------------------------------------------------------------------------------
+template <typename T, typename R, int Q>
+struct LineFFT {
+  T x[Q];
+  __device__ __forceinline__ void run(int t, int P, const LaneStages<T, R>& st, const T* __restrict__ tw,
+                                      const T* twq, T* scratch, bool inv) {
+    reg_dft<T, R, Q>(x, inv);
+    if constexpr (Q == 32) {
+      // twiddle and transpose-store in groups of eight; the empty asm with a memory clobber keeps
+      // the compiler from hoisting all 31 twiddle loads (register pressure)
+#pragma unroll
+      for (int g8 = 0; g8 < 4; ++g8) {
+        T w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) w[u] = __ldg(&tw[t * (g8 * 8 + u)]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k1 = g8 * 8 + u;
+          T v = x[pos<32>(k1)];
+          if (k1) { T ww = w[u]; if (inv) ww.y = -ww.y; v = cmul(v, ww); }
+          scratch[k1 * 33 + t] = v;
+        }
+        asm volatile("" ::: "memory");
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < 32; ++u) x[u] = scratch[t * 33 + u];
+      __syncwarp();
+      reg_dft<T, R, 32>(x, inv);
+    } else {
+#pragma unroll
+      for (int k1 = 1; k1 < Q; ++k1) {
+        T w = twq[k1];
+        if (inv) w.y = -w.y;
+        x[pos<Q>(k1)] = cmul(x[pos<Q>(k1)], w);
+      }
+      lane_dif<T, R, Q>(x, P, st);
+    }
+  }
+  __device__ __forceinline__ static int owned(int j, int t, int k2) { return Q == 32 ? t + 32 * j : j + Q * k2; }
+  __device__ __forceinline__ T value(int j) const { return x[pos<Q>(j)]; }
+};
+
 // ------------------------------------------------------------------------------------------
 // DST-I pass along x1 (axis 0) or x2 (axis 1), both halves at once.
 // in_slot / out_slot >= 0 select a vector slot (FP64), -1 selects the instance scratch (R).
 // ------------------------------------------------------------------------------------------
-template <typename TIn, typename TOut, typename R>
-__global__ void __launch_bounds__(256) k_dst(const Geom* __restrict__ G, const Slots* __restrict__ S,
+template <typename TIn, typename TOut, typename R, int Q>
+__global__ void __launch_bounds__(256, 2) k_dst(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                              const int* __restrict__ off, int count,
                                              const int* __restrict__ active, int axis, int in_slot,
                                              int out_slot) {
@@ -51,69 +112,146 @@ __global__ void __launch_bounds__(256) k_dst(const Geom* __restrict__ G, const S
   const int lb = blockIdx.x - off[inst];
   const TIn* __restrict__ in = in_slot >= 0 ? (const TIn*)S[inst].v[in_slot] : (const TIn*)g.scratch;
   TOut* __restrict__ out = out_slot >= 0 ? (TOut*)S[inst].v[out_slot] : (TOut*)g.scratch;
-  const int N = g.N, M = g.M, L = g.L, lpb = g.dst_lpb[sizeof(R) == 4], ls = M + 1;
+  const int N = g.N, L = N + 1, M = 2 * L;
+  const int lpb = axis == 0 ? g.dst_lpb[sizeof(R) == 4] : g.dst_lpb_j[sizeof(R) == 4];   // power of two
+  const int ls = padded_len(L);
   const long long mn = g.mn;
+  const int m = g.m;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* b0 = (T*)smem_raw;
-  T* b1 = b0 + lpb * ls;
+  T* tile = (T*)smem_raw;
+  const int nthr = blockDim.x, tid = threadIdx.x;
 
   long long line0 = 0;
-  int t = 0, i0 = 0;
+  int t0 = 0, i0 = 0;
   if (axis == 0) {
     line0 = (long long)lb * lpb;
   } else {
     const int nbt = (N + lpb - 1) / lpb;
-    t = lb / nbt;
-    i0 = (lb - t * nbt) * lpb;
+    t0 = lb / nbt;
+    i0 = (lb - t0 * nbt) * lpb;
   }
   const long long nlines0 = (long long)g.n * N;
-  const int tot = lpb * N;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    int l, q;
-    long long addr;
-    bool valid;
-    if (axis == 0) {
-      l = e / N; q = e - l * N;
-      const long long line = line0 + l;
-      valid = line < nlines0;
-      addr = line * N + q;
-    } else {
-      q = e / lpb; l = e - q * lpb;
-      const int i = i0 + l;
-      valid = i < N;
-      addr = (long long)t * g.m + (long long)q * N + i;
+  const int lsh = __ffs(lpb) - 1;
+  // ---- load tile: line l, element q (0-based) at padded index q+1.  Each thread walks the
+  // flattened tile with incremental indices and issues eight independent loads per step.
+  if (axis == 0) {
+    const long long nval = (nlines0 - line0) * N;        // valid elements from line0 on
+    const int tot = lpb * N;
+    const TIn* src = in + line0 * N;
+    int e = tid;
+    int l = e / N, q = e - l * N;                          // one division per thread
+    const int dl = nthr / N, dq = nthr - dl * N;
+    for (; e < tot; ) {
+      R v0[8], v1[8];
+      int ls_[8], qs_[8];
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (e < tot) {
+          const bool ok = e < nval;
+          v0[u] = ok ? (R)src[e] : (R)0;
+          v1[u] = ok ? (R)src[mn + e] : (R)0;
+          ls_[u] = l; qs_[u] = q;
+          ++cnt;
+          e += nthr; l += dl; q += dq;
+          if (q >= N) { q -= N; ++l; }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (u < cnt) tile[ls_[u] * ls + pidx(qs_[u] + 1)] = mk<R>(v0[u], v1[u]);
     }
-    R v0 = 0, v1 = 0;
-    if (valid) { v0 = (R)in[addr]; v1 = (R)in[mn + addr]; }
-    b0[l * ls + q + 1] = mk<R>(v0, v1);
-    b0[l * ls + M - q - 1] = mk<R>(-v0, -v1);
-  }
-  for (int l = threadIdx.x; l < lpb; l += blockDim.x) {
-    b0[l * ls] = mk<R>(0, 0);
-    b0[l * ls + L] = mk<R>(0, 0);
+  } else {
+    const int l = tid & (lpb - 1), qs = nthr >> lsh;
+    const int i = i0 + l;
+    const TIn* src = in + (long long)t0 * m + i;
+    T* dst = tile + l * ls;
+    const bool iv = i < N;
+    for (int q = tid >> lsh; q < N; q += 8 * qs) {
+      R v0[8], v1[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int qq = q + u * qs;
+        const bool ok = iv && qq < N;
+        v0[u] = ok ? (R)src[(long long)qq * N] : (R)0;
+        v1[u] = ok ? (R)src[mn + (long long)qq * N] : (R)0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int qq = q + u * qs;
+        if (qq < N) dst[pidx(qq + 1)] = mk<R>(v0[u], v1[u]);
+      }
+    }
   }
   __syncthreads();
-  const T* res = fft_lines<R>(b0, b1, g.pdst, lpb, ls, twd<R>(g), false);
-  const R s = (R)(0.5 * sqrt(2.0 / (double)L));
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    int l, q;
-    long long addr;
-    bool valid;
-    if (axis == 0) {
-      l = e / N; q = e - l * N;
-      const long long line = line0 + l;
-      valid = line < nlines0;
-      addr = line * N + q;
-    } else {
-      q = e / lpb; l = e - q * lpb;
-      const int i = i0 + l;
-      valid = i < N;
-      addr = (long long)t * g.m + (long long)q * N + i;
+  // ---- transform: groups of P lanes, one line each
+  const int P = M / Q;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  const int lpw = 32 / P;
+  const int t = lane % P;
+  LaneStages<T, R> st;
+  lane_stages<T, R>(st, t, P, false);
+  const T* __restrict__ tw = twd<R>(g);
+  T twq[Q < 32 ? Q : 1];
+  if constexpr (Q < 32) {
+#pragma unroll
+    for (int k1 = 0; k1 < Q; ++k1) twq[k1] = __ldg(&tw[t * k1]);
+  }
+  T* wscr = tile + lpb * ls + warp * (32 * 33);
+  const R sc = (R)(0.5 * sqrt(2.0 / (double)L));
+  const int k2 = bitrev(t, P);
+  for (int lbase = warp * lpw; lbase < lpb; lbase += nw * lpw) {
+    const int l = lbase + lane / P;
+    const bool lv = l < lpb;
+    T* line = tile + (lv ? l : 0) * ls;
+    LineFFT<T, R, Q> f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int s = t + P * q;
+      T v = mk<R>(0, 0);
+      if (lv) {
+        if (s > 0 && s < L) v = line[pidx(s)];
+        else if (s > L) { v = line[pidx(M - s)]; v.x = -v.x; v.y = -v.y; }
+      }
+      f.x[q] = v;
     }
-    if (valid) {
-      const T Y = res[l * ls + q + 1];
-      out[addr] = (TOut)(-Y.y * s);
-      out[mn + addr] = (TOut)(Y.x * s);
+    f.run(t, P, st, tw, twq, wscr, false);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const int p = LineFFT<T, R, Q>::owned(j, t, k2);
+      if (lv && p >= 1 && p <= N) {
+        const T Y = f.value(j);
+        line[pidx(p)] = mk<R>(-Y.y * sc, Y.x * sc);
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // ---- store tile
+  if (axis == 0) {
+    for (int l = 0; l < lpb; ++l) {
+      const long long line = line0 + l;
+      if (line >= nlines0) break;
+      const T* srcs = tile + l * ls;
+      TOut* d = out + line * N;
+      for (int q = tid; q < N; q += nthr) {
+        const T Y = srcs[pidx(q + 1)];
+        d[q] = (TOut)Y.x;
+        d[mn + q] = (TOut)Y.y;
+      }
+    }
+  } else {
+    const int l = tid & (lpb - 1), qs = nthr >> lsh;
+    const int i = i0 + l;
+    if (i < N) {
+      TOut* d = out + (long long)t0 * m + i;
+      const T* srcs = tile + l * ls;
+      for (int q = tid >> lsh; q < N; q += qs) {
+        const T Y = srcs[pidx(q + 1)];
+        d[(long long)q * N] = (TOut)Y.x;
+        d[mn + (long long)q * N] = (TOut)Y.y;
+      }
     }
   }
 }
@@ -122,8 +260,8 @@ __global__ void __launch_bounds__(256) k_dst(const Geom* __restrict__ G, const S
 // Time pass: forward DFT of (half0 + i half1) * exp(-i pi t/n), pointwise solve per frequency
 // pair, inverse DFT, unscale.  In place on the scratch.
 // ------------------------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(256) k_time(const Geom* __restrict__ G, const int* __restrict__ off, int count,
+template <typename R, int Q>
+__global__ void __launch_bounds__(256, 2) k_time(const Geom* __restrict__ G, const int* __restrict__ off, int count,
                                               const int* __restrict__ active, int kind) {
   using T = cx<R>;
   const int inst = find_inst(off, count, blockIdx.x);
@@ -131,108 +269,241 @@ __global__ void __launch_bounds__(256) k_time(const Geom* __restrict__ G, const 
   const Geom& g = G[inst];
   const int lb = blockIdx.x - off[inst];
   R* __restrict__ y = (R*)g.scratch;
-  const int n = g.n, m = g.m, N = g.N, cpb = g.time_cpb[sizeof(R) == 4], ls = n + 1;
+  const int n = g.n, m = g.m, N = g.N, cpb = g.time_cpb[sizeof(R) == 4];   // cpb: power of two
+  const int ls = padded_len(n);
   const long long mn = g.mn;
   const int c0 = lb * cpb;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* b0 = (T*)smem_raw;
-  T* b1 = b0 + cpb * ls;
+  T* tile = (T*)smem_raw;
   const T* __restrict__ pr = pre<R>(g);
-
-  const int tot = cpb * n;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int tt = e / cpb, l = e - tt * cpb;
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  const int csh = __ffs(cpb) - 1;
+  {
+    const int l = tid & (cpb - 1), ts = nthr >> csh;
     const int col = c0 + l;
-    T v = mk<R>(0, 0);
-    if (col < m) {
-      const long long a = (long long)tt * m + col;
-      v = cmul(mk<R>(y[a], y[mn + a]), pr[tt]);
+    T* dst = tile + l * ls;
+    const bool cv = col < m;
+    for (int tt = tid >> csh; tt < n; tt += 8 * ts) {
+      R a0[8], a1[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t2 = tt + u * ts;
+        const bool ok = cv && t2 < n;
+        const long long a = (long long)t2 * m + col;
+        a0[u] = ok ? y[a] : (R)0;
+        a1[u] = ok ? y[mn + a] : (R)0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t2 = tt + u * ts;
+        if (t2 < n) dst[pidx(t2)] = cmul(mk<R>(a0[u], a1[u]), __ldg(&pr[t2]));
+      }
     }
-    b0[l * ls + tt] = v;
   }
   __syncthreads();
-  T* f = fft_lines<R>(b0, b1, g.ptime, cpb, ls, twt<R>(g), false);
-  T* other = (f == b0) ? b1 : b0;
 
+  const int P = n / Q;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  const int lpw = 32 / P;
+  const int t = lane % P;
+  LaneStages<T, R> stf, sti;
+  lane_stages<T, R>(stf, t, P, false);
+  lane_stages<T, R>(sti, t, P, true);
+  const T* __restrict__ tw = twt<R>(g);
+  T twq[Q < 32 ? Q : 1];
+  if constexpr (Q < 32) {
+#pragma unroll
+    for (int k1 = 0; k1 < Q; ++k1) twq[k1] = __ldg(&tw[t * k1]);
+  }
   const T* __restrict__ mu = mutab<R>(g);
   const R alpha = (R)g.alpha, a2 = (R)(g.alpha * g.alpha);
   const int half = n / 2;
-  const int totp = cpb * half;
-  for (int e = threadIdx.x; e < totp; e += blockDim.x) {
-    const int l = e / half, r = e - l * half;
-    const int col = c0 + l;
-    if (col >= m) continue;
-    const int j = col / N, i = col - j * N;
-    const R c = (R)(g.tau * (g.kap[i] + g.kap[j]));
-    const int rp = n - 1 - r;
-    T* line = f + l * ls;
-    const T mr = mu[r];
-    const T lam = mk<R>(mr.x + c, mr.y);
-    const R mod2 = lam.x * lam.x + lam.y * lam.y;
-    if (kind == PK_ABS_PS) {
-      const R w = rsqrt_<R>(mod2 + a2);
-      line[r] = cscale(line[r], w);
-      line[rp] = cscale(line[rp], w);
-    } else if (kind == PK_PMS) {
-      const R sig = sqrt(mr.x * mr.x + mr.y * mr.y + a2);
-      const R w = (R)1 / (sig + c);
-      line[r] = cscale(line[r], w);
-      line[rp] = cscale(line[rp], w);
-    } else {
-      const T Cr = line[r], Cq = cconj(line[rp]);
-      const T F1 = cscale(cadd(Cr, Cq), (R)0.5);
-      const T F2 = cmul_mi(cscale(csub(Cr, Cq), (R)0.5));
-      const R inv = (R)1 / (mod2 + a2);
-      // U1 = (conj(lam) F1 + alpha F2)/det, U2 = (lam F2 - alpha F1)/det
-      const T U1 = cscale(cadd(cmul(cconj(lam), F1), cscale(F2, alpha)), inv);
-      const T U2 = cscale(csub(cmul(lam, F2), cscale(F1, alpha)), inv);
-      line[r] = cadd(U1, cmul_pi(U2));
-      line[rp] = cadd(cconj(U1), cmul_pi(cconj(U2)));
+  const int k2 = bitrev(t, P);
+  for (int lbase = warp * lpw; lbase < cpb; lbase += nw * lpw) {
+    const int l = lbase + lane / P;
+    const bool lv = l < cpb;
+    T* line = tile + (lv ? l : 0) * ls;
+    const int col = c0 + (lv ? l : 0);
+    LineFFT<T, R, Q> f;
+    // forward
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f.x[q] = lv ? line[pidx(t + P * q)] : mk<R>(0, 0);
+    __syncwarp();
+    f.run(t, P, stf, tw, twq, line, false);
+    __syncwarp();
+    if (lv) {
+#pragma unroll
+      for (int j = 0; j < Q; ++j) line[pidx(LineFFT<T, R, Q>::owned(j, t, k2))] = f.value(j);
     }
+    __syncwarp();
+    // pointwise solve on frequency pairs (r, n-1-r)
+    if (lv && col < m) {
+      const int j = col / N, i = col - j * N;
+      const R c = (R)(g.tau * (__ldg(&g.kap[i]) + __ldg(&g.kap[j])));
+      for (int r = t; r < half; r += P) {
+        const int rp = n - 1 - r;
+        const T mr = __ldg(&mu[r]);
+        const T lam = mk<R>(mr.x + c, mr.y);
+        const R mod2 = lam.x * lam.x + lam.y * lam.y;
+        T* pa = line + pidx(r);
+        T* pb = line + pidx(rp);
+        if (kind == PK_ABS_PS) {
+          const R w = rsqrt_<R>(mod2 + a2);
+          *pa = cscale(*pa, w);
+          *pb = cscale(*pb, w);
+        } else if (kind == PK_PMS) {
+          const R sig = sqrt(mr.x * mr.x + mr.y * mr.y + a2);
+          const R w = (R)1 / (sig + c);
+          *pa = cscale(*pa, w);
+          *pb = cscale(*pb, w);
+        } else {
+          const T Cr = *pa, Cq = cconj(*pb);
+          const T F1 = cscale(cadd(Cr, Cq), (R)0.5);
+          const T F2 = cmul_mi(cscale(csub(Cr, Cq), (R)0.5));
+          const R inv = (R)1 / (mod2 + a2);
+          const T U1 = cscale(cadd(cmul(cconj(lam), F1), cscale(F2, alpha)), inv);
+          const T U2 = cscale(csub(cmul(lam, F2), cscale(F1, alpha)), inv);
+          *pa = cadd(U1, cmul_pi(U2));
+          *pb = cadd(cconj(U1), cmul_pi(cconj(U2)));
+        }
+      }
+    }
+    __syncwarp();
+    // inverse
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f.x[q] = lv ? line[pidx(t + P * q)] : mk<R>(0, 0);
+    __syncwarp();
+    f.run(t, P, sti, tw, twq, line, true);
+    __syncwarp();
+    if (lv) {
+#pragma unroll
+      for (int j = 0; j < Q; ++j) line[pidx(LineFFT<T, R, Q>::owned(j, t, k2))] = f.value(j);
+    }
+    __syncwarp();
   }
   __syncthreads();
-  T* res = fft_lines<R>(f, other, g.ptime, cpb, ls, twt<R>(g), true);
   const R sc = (R)1 / (R)n;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int tt = e / cpb, l = e - tt * cpb;
+  {
+    const int l = tid & (cpb - 1), ts = nthr >> csh;
     const int col = c0 + l;
     if (col < m) {
-      const T v = cscale(cmul(res[l * ls + tt], cconj(pr[tt])), sc);
-      const long long a = (long long)tt * m + col;
-      y[a] = v.x;
-      y[mn + a] = v.y;
+      const T* srcs = tile + l * ls;
+      for (int tt = tid >> csh; tt < n; tt += ts) {
+        const T v = cscale(cmul(srcs[pidx(tt)], cconj(__ldg(&pr[tt]))), sc);
+        const long long a = (long long)tt * m + col;
+        y[a] = v.x;
+        y[mn + a] = v.y;
+      }
     }
   }
 }
 
 // ------------------------------------------------------------------------------------------
-// host launchers
+// host side: shapes, constant tables, launchers
 // ------------------------------------------------------------------------------------------
-template <typename R>
-static size_t dst_smem(const Batch& B) { return (size_t)2 * B.max_lpb_M[sizeof(R) == 4] * sizeof(cx<R>); }
-template <typename R>
-static size_t time_smem(const Batch& B) { return (size_t)2 * B.max_cpb_n[sizeof(R) == 4] * sizeof(cx<R>); }
+static int largest_pow2_divisor(int v) { return v & (-v); }
+
+int dst_Q(int N) {
+  const int M = 2 * (N + 1);
+  const int P = std::min(32, largest_pow2_divisor(M));
+  return M / P;
+}
+int time_Q(int n) { return n / std::min(32, n); }
+bool q_supported(int Q) {
+  return Q == 1 || Q == 2 || Q == 3 || Q == 4 || Q == 6 || Q == 8 || Q == 12 || Q == 16 || Q == 24 || Q == 32;
+}
+size_t dst_smem_bytes(const Geom& g, int p) {
+  const size_t elems = (size_t)std::max(g.dst_lpb[p], g.dst_lpb_j[p]) * padded_len(g.N + 1) +
+                       (g.dst_q == 32 ? (size_t)8 * 32 * 33 : 0);   // per-warp transpose scratch
+  return elems * (p ? sizeof(float2) : sizeof(double2));
+}
+int padded_len_host(int len) { return padded_len(len); }
+size_t time_smem_bytes(const Geom& g, int p) {
+  return (size_t)g.time_cpb[p] * padded_len(g.n) * (p ? sizeof(float2) : sizeof(double2));
+}
+
+cudaError_t upload_constants() { return upload_w96(); }
+
+template <typename R, int Q>
+static void launch_dst_q(const Batch& B, int axis, int in_slot, int out_slot, size_t smem) {
+  const int p = sizeof(R) == 4;
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_dst<double, R, R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_dst<R, R, R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_dst<R, double, R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    done = true;
+  }
+  const int* off = axis == 0 ? B.off_dst_i[p] : B.off_dst_j[p];
+  const int tot = axis == 0 ? B.tot_dst_i[p] : B.tot_dst_j[p];
+  if (in_slot >= 0)
+    k_dst<double, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, in_slot, -1);
+  else if (out_slot >= 0)
+    k_dst<R, double, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, -1, out_slot);
+  else
+    k_dst<R, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, -1, -1);
+}
+
+template <typename R, int Q>
+static void launch_time_q(const Batch& B, int kind, size_t smem) {
+  const int p = sizeof(R) == 4;
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_time<R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    done = true;
+  }
+  k_time<R, Q><<<B.tot_time[p], 256, smem, B.stream>>>(B.G, B.off_time[p], B.count, B.active, kind);
+}
 
 template <typename R>
-static cudaError_t precond_passes(const Batch& B, int kind, int in_slot, int out_slot) {
-  const size_t sd = dst_smem<R>(B), st = time_smem<R>(B);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_dst<double, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_dst<R, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_dst<R, double, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_time<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr_done = true;
-  }
+static cudaError_t dispatch_dst(const Batch& B, int axis, int in_slot, int out_slot) {
   const int p = sizeof(R) == 4;
-  k_dst<double, R, R><<<B.tot_dst_i[p], 256, sd, B.stream>>>(B.G, B.S, B.off_dst_i[p], B.count, B.active, 0, in_slot, -1);
-  k_dst<R, R, R><<<B.tot_dst_j[p], 256, sd, B.stream>>>(B.G, B.S, B.off_dst_j[p], B.count, B.active, 1, -1, -1);
-  k_time<R><<<B.tot_time[p], 256, st, B.stream>>>(B.G, B.off_time[p], B.count, B.active, kind);
-  k_dst<R, R, R><<<B.tot_dst_j[p], 256, sd, B.stream>>>(B.G, B.S, B.off_dst_j[p], B.count, B.active, 1, -1, -1);
-  k_dst<R, double, R><<<B.tot_dst_i[p], 256, sd, B.stream>>>(B.G, B.S, B.off_dst_i[p], B.count, B.active, 0, -1, out_slot);
+  const size_t smem = B.dst_smem[p];
+  switch (B.dst_q) {
+    case 1: launch_dst_q<R, 1>(B, axis, in_slot, out_slot, smem); break;
+    case 2: launch_dst_q<R, 2>(B, axis, in_slot, out_slot, smem); break;
+    case 3: launch_dst_q<R, 3>(B, axis, in_slot, out_slot, smem); break;
+    case 4: launch_dst_q<R, 4>(B, axis, in_slot, out_slot, smem); break;
+    case 6: launch_dst_q<R, 6>(B, axis, in_slot, out_slot, smem); break;
+    case 8: launch_dst_q<R, 8>(B, axis, in_slot, out_slot, smem); break;
+    case 12: launch_dst_q<R, 12>(B, axis, in_slot, out_slot, smem); break;
+    case 16: launch_dst_q<R, 16>(B, axis, in_slot, out_slot, smem); break;
+    case 24: launch_dst_q<R, 24>(B, axis, in_slot, out_slot, smem); break;
+    case 32: launch_dst_q<R, 32>(B, axis, in_slot, out_slot, smem); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
+template <typename R>
+static cudaError_t dispatch_time(const Batch& B, int kind) {
+  const int p = sizeof(R) == 4;
+  const size_t smem = B.time_smem[p];
+  switch (B.time_q) {
+    case 1: launch_time_q<R, 1>(B, kind, smem); break;
+    case 2: launch_time_q<R, 2>(B, kind, smem); break;
+    case 4: launch_time_q<R, 4>(B, kind, smem); break;
+    case 8: launch_time_q<R, 8>(B, kind, smem); break;
+    case 16: launch_time_q<R, 16>(B, kind, smem); break;
+    case 32: launch_time_q<R, 32>(B, kind, smem); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t precond_passes(const Batch& B, int kind, int in_slot, int out_slot) {
+  cudaError_t e;
+  if ((e = dispatch_dst<R>(B, 0, in_slot, -1)) != cudaSuccess) return e;
+  if ((e = dispatch_dst<R>(B, 1, -1, -1)) != cudaSuccess) return e;
+  if ((e = dispatch_time<R>(B, kind)) != cudaSuccess) return e;
+  if ((e = dispatch_dst<R>(B, 1, -1, -1)) != cudaSuccess) return e;
+  return dispatch_dst<R>(B, 0, -1, out_slot);
+}
+
+int precond_launch_count(bool var_a, int kind) { return var_a ? mg_launch_count(kind) : 5; }
+
+// All instances of B must share dst_q and time_q (the batch engine groups them that way).
 cudaError_t launch_precond_fast(const Batch& B, int kind, int prec, int in_slot, int out_slot) {
   return prec == PCB_MIXED ? precond_passes<float>(B, kind, in_slot, out_slot)
                            : precond_passes<double>(B, kind, in_slot, out_slot);

@@ -33,6 +33,13 @@ cudaError_t launch_swap(const Batch& B, int a0, int b0, int a1, int b1, int a2, 
 cudaError_t launch_setslot(const Batch& B, int dst, int base, int k);
 size_t mg_workspace_bytes(const Geom& g);
 bool mg_available();
+int dst_Q(int N);
+int time_Q(int n);
+bool q_supported(int Q);
+size_t dst_smem_bytes(const Geom& g, int p);
+size_t time_smem_bytes(const Geom& g, int p);
+int padded_len_host(int len);
+cudaError_t upload_constants();
 cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host);
 
 // step ids of the scalar kernels (mirror krylov.cu)
@@ -79,6 +86,13 @@ struct pcb_problem {
   Scal* hSc = nullptr;            // pinned host copy
   Slots* hSpin = nullptr;         // pinned staging for slot uploads
   Batch B;
+  double* host_io = nullptr;      // device staging for pcb_solve_host (b, x)
+  // per-solve counters and optional event profiling
+  long long launches = 0;
+  int prec_applies = 0, matvecs = 0;
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_prec, ev_mv;   // pairs (start, stop)
+  int ev_prec_used = 0, ev_mv_used = 0;
 };
 
 namespace {
@@ -115,15 +129,25 @@ int vec_blocks_for(long long len) {
   return (int)b;
 }
 
+int round_down(int v, int q) { return std::max(q, (v / q) * q); }
+int pow2_floor(int v) { int p = 1; while (p * 2 <= v) p *= 2; return p; }
+
 void set_shapes(Geom& g) {
-  const int Mp = g.M + 1, np = g.n + 1;
-  const int budget[2] = {6300, 8400};   // complex points per smem buffer: FP64, FP32
+  const int lsd = padded_len_host(g.L), lst = padded_len_host(g.n);
+  const int Pd = 2 * g.L / g.dst_q, Pt = g.n / g.time_q;
+  const int lpwd = 32 / Pd, lpwt = 32 / Pt;
+  const int budget[2] = {4300, 8600};   // complex elements per tile: FP64, FP32 (~68 KB)
   for (int p = 0; p < 2; ++p) {
-    int lpb = std::max(1, std::min(64, budget[p] / Mp));
+    // powers of two (the kernels split thread indices with shifts) that are multiples of lpw
+    // Q = 32 lines use one warp each plus a per-warp transpose scratch: 8 lines per block
+    int lpb = g.dst_q == 32 ? 8 : std::max(lpwd, pow2_floor(std::min(256, std::max(1, budget[p] / lsd))));
     g.dst_lpb[p] = lpb;
+    int lpbj = std::max(lpwd, std::min(lpb, pow2_floor(std::max(1, g.N))));
+    g.dst_lpb_j[p] = lpbj;
     g.dst_blocks_i[p] = (int)(((long long)g.n * g.N + lpb - 1) / lpb);
-    g.dst_blocks_j[p] = g.n * ((g.N + lpb - 1) / lpb);
-    int cpb = std::max(1, std::min(64, budget[p] / np));
+    g.dst_blocks_j[p] = g.n * ((g.N + lpbj - 1) / lpbj);
+    int cpb = pow2_floor(std::min(256, std::max(1, budget[p] / lst)));
+    cpb = std::max(lpwt, std::min(cpb, pow2_floor(std::max(1, g.m))));
     g.time_cpb[p] = cpb;
     g.time_blocks[p] = (g.m + cpb - 1) / cpb;
   }
@@ -178,16 +202,18 @@ static int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStre
     B.off_dst_i[p] = doff + (0 + p) * stride; B.tot_dst_i[p] = tots[0 + p];
     B.off_dst_j[p] = doff + (2 + p) * stride; B.tot_dst_j[p] = tots[2 + p];
     B.off_time[p] = doff + (4 + p) * stride;  B.tot_time[p] = tots[4 + p];
-    B.max_lpb_M[p] = 0; B.max_cpb_n[p] = 0;
+    B.dst_smem[p] = 0; B.time_smem[p] = 0;
     for (const Geom& g : gs) {
-      B.max_lpb_M[p] = std::max(B.max_lpb_M[p], g.dst_lpb[p] * (g.M + 1));
-      B.max_cpb_n[p] = std::max(B.max_cpb_n[p], g.time_cpb[p] * (g.n + 1));
+      B.dst_smem[p] = std::max(B.dst_smem[p], dst_smem_bytes(g, p));
+      B.time_smem[p] = std::max(B.time_smem[p], time_smem_bytes(g, p));
     }
   }
   B.off_mv = doff + 6 * stride; B.tot_mv = tots[6];
   B.off_vec = doff + 7 * stride; B.tot_vec = tots[7];
   B.count = count;
   B.stream = st;
+  B.dst_q = gs[0].dst_q;
+  B.time_q = gs[0].time_q;
   return PCB_OK;
 }
 
@@ -229,6 +255,9 @@ void pcb_destroy(pcb_problem* p) {
   cudaFree(p->partial);
   cudaFreeHost(p->hSc);
   cudaFreeHost(p->hSpin);
+  cudaFree(p->host_io);
+  for (cudaEvent_t e : p->ev_prec) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_mv) cudaEventDestroy(e);
   delete p;
 }
 
@@ -266,6 +295,10 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
   g.h = 1.0 / (d->N + 1); g.sqrt_gamma = std::sqrt(d->gamma); g.c = g.tau / (g.h * g.h);
   g.var_a = d->a_edges ? 1 : 0;
   g.pdst = pd; g.ptime = pt;
+  g.dst_q = dst_Q(g.N);
+  g.time_q = time_Q(g.n);
+  if (!q_supported(g.dst_q) || !q_supported(g.time_q)) { delete p; return PCB_ERR_UNSUPPORTED; }
+  if (upload_constants() != cudaSuccess) { delete p; return PCB_ERR_CUDA; }
   set_shapes(g);
 
   int rc = PCB_OK;
@@ -425,6 +458,54 @@ static int apply_precond(const Batch& B, bool var_a, int kind, int prec, int in_
   return e == cudaSuccess ? PCB_OK : cuda_status(e);
 }
 
+namespace pcb { int precond_launch_count(bool var_a, int kind); }
+
+// event pair from a pool (grown on demand); returns false when profiling is off
+static bool ev_pair(std::vector<cudaEvent_t>& pool, int& used, cudaEvent_t& a, cudaEvent_t& b) {
+  if ((int)pool.size() < 2 * (used + 1)) {
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return false;
+      pool.push_back(e);
+    }
+  }
+  a = pool[2 * used]; b = pool[2 * used + 1];
+  ++used;
+  return true;
+}
+
+static int P_precond(pcb_problem* p, const Batch& B, int kind, int prec, int in_slot, int out_slot) {
+  const bool va = p->g.var_a != 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  const bool ev = p->prof && ev_pair(p->ev_prec, p->ev_prec_used, a, b);
+  if (ev) cudaEventRecord(a, B.stream);
+  const int rc = apply_precond(B, va, kind, prec, in_slot, out_slot);
+  if (ev) cudaEventRecord(b, B.stream);
+  p->launches += precond_launch_count(va, kind);
+  p->prec_applies += 1;
+  return rc;
+}
+
+static cudaError_t P_matvec(pcb_problem* p, const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  const bool ev = p->prof && ev_pair(p->ev_mv, p->ev_mv_used, a, b);
+  if (ev) cudaEventRecord(a, B.stream);
+  const cudaError_t e = launch_matvec(B, op, x_slot, out_slot, aux_slot, epi);
+  if (ev) cudaEventRecord(b, B.stream);
+  p->launches += 1;
+  p->matvecs += 1;
+  return e;
+}
+
+static double ev_sum(const std::vector<cudaEvent_t>& pool, int used) {
+  double s = 0.0;
+  for (int k = 0; k < used; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pool[2 * k], pool[2 * k + 1]) == cudaSuccess) s += ms;
+  }
+  return s;
+}
+
 // Poll per-instance scalars (synchronises the stream).
 static int read_scal(const Batch& B, Scal* host, int count) {
   CK(cudaMemcpyAsync(host, B.Sc, sizeof(Scal) * count, cudaMemcpyDeviceToHost, B.stream));
@@ -433,6 +514,7 @@ static int read_scal(const Batch& B, Scal* host, int count) {
 }
 
 // Single-instance MINRES on slot rhs -> slot x (both set by the caller).  Returns iterations via sc.
+#define LC(p) (++(p)->launches, 0) ? cudaSuccess :
 static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Scal* hs, double* relres_out,
                          int* it_out, bool* conv_out) {
   const Batch& B = p->B;
@@ -442,14 +524,14 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   CK(cudaMemsetAsync(p->hS.v[s_x], 0, vb, p->stream));
   CK(cudaMemsetAsync(p->hS.v[SL_W], 0, vb, p->stream));
   CK(cudaMemsetAsync(p->hS.v[SL_W2], 0, vb, p->stream));
-  CK(launch_axpby(B, AX_COPY, s_b, SL_R1, -1));
-  CK(launch_axpby(B, AX_COPY, s_b, SL_R2, -1));
-  CK(launch_dot(B, s_b, s_b));
-  CK(launch_reduce(B, B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
-  int rc = apply_precond(B, va, c.kind, c.prec, SL_R2, SL_Y);
+  CK(LC(p) launch_axpby(B, AX_COPY, s_b, SL_R1, -1));
+  CK(LC(p) launch_axpby(B, AX_COPY, s_b, SL_R2, -1));
+  CK(LC(p) launch_dot(B, s_b, s_b));
+  CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
+  int rc = P_precond(p, B, c.kind, c.prec, SL_R2, SL_Y);
   if (rc) return rc;
-  CK(launch_dot(B, SL_R2, SL_Y));
-  CK(launch_reduce(B, B.off_vec, 1, 0, SS_MINRES_INIT, c.tol, 0, 0));
+  CK(LC(p) launch_dot(B, SL_R2, SL_Y));
+  CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_MINRES_INIT, c.tol, 0, 0));
   if ((rc = read_scal(B, hs, 1))) return rc;
   *it_out = 0; *conv_out = false; *relres_out = 1.0;
   if (hs->flags & 4) return PCB_ERR_NONFINITE;
@@ -458,14 +540,14 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   const int limit = c.fixed > 0 ? c.fixed : c.maxit;
   bool checking = false;
   for (int it = 0; it < limit; ++it) {
-    CK(launch_matvec(B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
-    CK(launch_reduce(B, B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
-    CK(launch_axpby(B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
-    if ((rc = apply_precond(B, va, c.kind, c.prec, SL_R1, SL_YO))) return rc;
-    CK(launch_dot(B, SL_R1, SL_YO));
-    CK(launch_reduce(B, B.off_vec, 1, 0, SS_MINRES_GIVENS, c.tol, 0, 0));
-    CK(launch_minres_wx(B, SL_Y, SL_W, SL_W2, s_x));
-    CK(launch_swap(B, SL_R1, SL_R2, SL_Y, SL_YO, SL_W, SL_W2));
+    CK(P_matvec(p, B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
+    CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
+    CK(LC(p) launch_axpby(B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
+    if ((rc = P_precond(p, B, c.kind, c.prec, SL_R1, SL_YO))) return rc;
+    CK(LC(p) launch_dot(B, SL_R1, SL_YO));
+    CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_MINRES_GIVENS, c.tol, 0, 0));
+    CK(LC(p) launch_minres_wx(B, SL_Y, SL_W, SL_W2, s_x));
+    CK(LC(p) launch_swap(B, SL_R1, SL_R2, SL_Y, SL_YO, SL_W, SL_W2));
     std::swap(p->hS.v[SL_R1], p->hS.v[SL_R2]);
     std::swap(p->hS.v[SL_Y], p->hS.v[SL_YO]);
     std::swap(p->hS.v[SL_W], p->hS.v[SL_W2]);
@@ -475,8 +557,8 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
     if (hs->flags & 2) return PCB_ERR_BREAKDOWN;
     if (c.fixed > 0) continue;
     if ((hs->flags & 1) || checking) {
-      CK(launch_matvec(B, PCB_OP_A, s_x, SL_Q, s_b, EPI_RESID));
-      CK(launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+      CK(P_matvec(p, B, PCB_OP_A, s_x, SL_Q, s_b, EPI_RESID));
+      CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
       if ((rc = read_scal(B, hs, 1))) return rc;
       const double rel = std::sqrt(hs->dot1) / hs->bnorm;
       *relres_out = rel;
@@ -485,8 +567,8 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
       checking = true;
     }
   }
-  CK(launch_matvec(B, PCB_OP_A, s_x, SL_Q, s_b, EPI_RESID));
-  CK(launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+  CK(P_matvec(p, B, PCB_OP_A, s_x, SL_Q, s_b, EPI_RESID));
+  CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
   if ((rc = read_scal(B, hs, 1))) return rc;
   *relres_out = std::sqrt(hs->dot1) / hs->bnorm;
   *conv_out = *relres_out <= c.tol;
@@ -501,8 +583,8 @@ static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   const int op = PCB_OP_AHAT;
   CK(cudaMemsetAsync(p->hS.v[s_x], 0, vb, p->stream));
   CK(cudaMemsetAsync(p->dSc, 0, sizeof(Scal), p->stream));
-  CK(launch_dot(B, s_b, s_b));
-  CK(launch_reduce(B, B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
+  CK(LC(p) launch_dot(B, s_b, s_b));
+  CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
   int rc;
   if ((rc = read_scal(B, hs, 1))) return rc;
   *it_out = 0; *conv_out = false; *relres_out = 1.0;
@@ -511,30 +593,30 @@ static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   const int limit = c.fixed > 0 ? c.fixed : c.maxit;
   int total = 0;
   while (total < limit) {
-    CK(launch_matvec(B, op, s_x, SL_R, s_b, EPI_RESID));
-    CK(launch_reduce(B, B.off_mv, 1, 0, SS_GMRES_START, c.tol, 0, 0));
+    CK(P_matvec(p, B, op, s_x, SL_R, s_b, EPI_RESID));
+    CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_GMRES_START, c.tol, 0, 0));
     if ((rc = read_scal(B, hs, 1))) return rc;
     if (hs->flags & 4) return PCB_ERR_NONFINITE;
     *relres_out = hs->est;
     if (c.fixed <= 0 && hs->est <= c.tol) { *conv_out = true; return PCB_OK; }
-    CK(launch_setslot(B, SL_VJ, SL_VBASE, 0));
-    CK(launch_axpby(B, AX_SCALE_INV_BETA, SL_R, SL_VJ, -1));
+    CK(LC(p) launch_setslot(B, SL_VJ, SL_VBASE, 0));
+    CK(LC(p) launch_axpby(B, AX_SCALE_INV_BETA, SL_R, SL_VJ, -1));
     const int mres = std::min(c.restart, limit - total);
     int k = 0;
     for (int j = 0; j < mres; ++j) {
-      CK(launch_setslot(B, SL_VJ, SL_VBASE, j));
-      CK(launch_setslot(B, SL_ZJ, SL_ZBASE, j));
-      CK(launch_setslot(B, SL_VJ1, SL_VBASE, j + 1));
-      if ((rc = apply_precond(B, va, c.kind, c.prec, SL_VJ, SL_ZJ))) return rc;
-      CK(launch_matvec(B, op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
+      CK(LC(p) launch_setslot(B, SL_VJ, SL_VBASE, j));
+      CK(LC(p) launch_setslot(B, SL_ZJ, SL_ZBASE, j));
+      CK(LC(p) launch_setslot(B, SL_VJ1, SL_VBASE, j + 1));
+      if ((rc = P_precond(p, B, c.kind, c.prec, SL_VJ, SL_ZJ))) return rc;
+      CK(P_matvec(p, B, op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
       for (int pass = 0; pass < 2; ++pass) {
-        CK(launch_multidot(B, SL_VBASE, j, SL_VJ1));
-        CK(launch_reduce_multi(B, j, pass));
-        CK(launch_multiaxpy(B, SL_VBASE, j, SL_VJ1, pass));
+        CK(LC(p) launch_multidot(B, SL_VBASE, j, SL_VJ1));
+        CK(LC(p) launch_reduce_multi(B, j, pass));
+        CK(LC(p) launch_multiaxpy(B, SL_VBASE, j, SL_VJ1, pass));
       }
-      CK(launch_dot(B, SL_VJ1, SL_VJ1));
-      CK(launch_reduce(B, B.off_vec, 1, 0, SS_GMRES_ARNOLDI, c.tol, j, c.restart));
-      CK(launch_axpby(B, AX_SCALE_INV_HNORM, SL_VJ1, SL_VJ1, -1));
+      CK(LC(p) launch_dot(B, SL_VJ1, SL_VJ1));
+      CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_GMRES_ARNOLDI, c.tol, j, c.restart));
+      CK(LC(p) launch_axpby(B, AX_SCALE_INV_HNORM, SL_VJ1, SL_VJ1, -1));
       if ((rc = read_scal(B, hs, 1))) return rc;
       k = j + 1;
       total += 1;
@@ -543,20 +625,20 @@ static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
       if (hs->flags & 8) break;
     }
     // x += Z y
-    CK(launch_multiaxpy(B, SL_ZBASE, k - 1, s_x, -1));
+    CK(LC(p) launch_multiaxpy(B, SL_ZBASE, k - 1, s_x, -1));
     CK(cudaMemsetAsync(&p->dSc->flags, 0, sizeof(int), p->stream));
     *it_out = total;
     if (c.fixed <= 0 && (hs->flags & 1)) {
-      CK(launch_matvec(B, op, s_x, SL_R, s_b, EPI_RESID));
-      CK(launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+      CK(P_matvec(p, B, op, s_x, SL_R, s_b, EPI_RESID));
+      CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
       if ((rc = read_scal(B, hs, 1))) return rc;
       *relres_out = std::sqrt(hs->dot1) / hs->bnorm;
       if (*relres_out <= c.tol) { *conv_out = true; return PCB_OK; }
       if (!c.check_true) return PCB_OK;
     }
   }
-  CK(launch_matvec(B, op, s_x, SL_R, s_b, EPI_RESID));
-  CK(launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+  CK(P_matvec(p, B, op, s_x, SL_R, s_b, EPI_RESID));
+  CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
   if ((rc = read_scal(B, hs, 1))) return rc;
   *relres_out = std::sqrt(hs->dot1) / hs->bnorm;
   *conv_out = *relres_out <= c.tol;
@@ -611,6 +693,9 @@ static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_d
   }
   if ((rc = upload_slots(p))) return rc;
   Scal* hs = p->hSc;
+  p->launches = 0; p->prec_applies = 0; p->matvecs = 0;
+  p->prof = o && o->profile;
+  p->ev_prec_used = 0; p->ev_mv_used = 0;
   auto t0 = std::chrono::steady_clock::now();
   int iters = 0, sweeps = 0;
   double relres = 1.0;
@@ -629,12 +714,12 @@ static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_d
     const int max_ref = (o && o->max_refinements > 0) ? o->max_refinements : 10;
     const size_t vbytes = nv * sizeof(double);
     CK(cudaMemsetAsync(x_dev, 0, vbytes, p->stream));
-    CK(launch_dot(p->B, SL_B, SL_B));
-    CK(launch_reduce(p->B, p->B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
+    CK(LC(p) launch_dot(p->B, SL_B, SL_B));
+    CK(LC(p) launch_reduce(p->B, p->B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
     if ((rc = read_scal(p->B, hs, 1))) return rc;
     const double bnorm = hs->bnorm;
     if (!std::isfinite(bnorm)) return PCB_ERR_NONFINITE;
-    CK(launch_axpby(p->B, AX_COPY, SL_B, SL_BI, -1));
+    CK(LC(p) launch_axpby(p->B, AX_COPY, SL_B, SL_BI, -1));
     double rnorm = bnorm;
     rc = PCB_OK;
     if (bnorm == 0.0) { conv = true; relres = 0.0; }
@@ -649,9 +734,9 @@ static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_d
       iters += it_in;
       sweeps += 1;
       // x += d ; r = b - op x  (into the inner right-hand side slot)
-      CK(launch_axpby(p->B, AX_ADD, SL_XI, SL_X, -1));
-      CK(launch_matvec(p->B, c.op, SL_X, SL_BI, SL_B, EPI_RESID));
-      CK(launch_reduce(p->B, p->B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+      CK(LC(p) launch_axpby(p->B, AX_ADD, SL_XI, SL_X, -1));
+      CK(P_matvec(p, p->B, c.op, SL_X, SL_BI, SL_B, EPI_RESID));
+      CK(LC(p) launch_reduce(p->B, p->B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
       if ((rc = read_scal(p->B, hs, 1))) break;
       rnorm = std::sqrt(hs->dot1);
       relres = rnorm / bnorm;
@@ -666,6 +751,9 @@ static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_d
   if (info) {
     info->status = rc; info->method = c.method; info->precond = c.kind; info->iterations = iters;
     info->refinements = sweeps; info->relres = relres; info->seconds = secs;
+    info->launches = p->launches; info->precond_applies = p->prec_applies; info->matvecs = p->matvecs;
+    info->precond_ms = p->prof ? ev_sum(p->ev_prec, p->ev_prec_used) : 0.0;
+    info->matvec_ms = p->prof ? ev_sum(p->ev_mv, p->ev_mv_used) : 0.0;
   }
   return rc;
 }
@@ -717,9 +805,12 @@ int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* o, const double* b_host
                    pcb_solve_info* info) {
   if (!p || !b_host || !x_host) return PCB_ERR_INVALID_ARG;
   const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
-  double *b = nullptr, *x = nullptr;
-  if (cudaMalloc(&b, vb) != cudaSuccess) { cudaGetLastError(); return PCB_ERR_OUT_OF_MEMORY; }
-  if (cudaMalloc(&x, vb) != cudaSuccess) { cudaGetLastError(); cudaFree(b); return PCB_ERR_OUT_OF_MEMORY; }
+  if (!p->host_io) {
+    if (cudaMalloc(&p->host_io, 2 * vb) != cudaSuccess) { cudaGetLastError(); p->host_io = nullptr; return PCB_ERR_OUT_OF_MEMORY; }
+    p->bytes += 2 * vb;
+  }
+  double* b = p->host_io;
+  double* x = p->host_io + 2 * p->g.mn;
   int rc = PCB_OK;
   if (cudaMemcpyAsync(b, b_host, vb, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) rc = PCB_ERR_CUDA;
   if (rc == PCB_OK) rc = solve_impl(p, o, b, x, info);
@@ -727,8 +818,6 @@ int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* o, const double* b_host
       cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
     rc = PCB_ERR_CUDA;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess && rc == PCB_OK) rc = PCB_ERR_CUDA;
-  cudaFree(b);
-  cudaFree(x);
   return rc;
 }
 
