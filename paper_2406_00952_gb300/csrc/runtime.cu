@@ -40,6 +40,7 @@ size_t dst_smem_bytes(const Geom& g, int p);
 size_t time_smem_bytes(const Geom& g, int p);
 int padded_len_host(int len);
 cudaError_t upload_constants();
+struct TableLayout { size_t kap, mud, muf, twdd, twdf, twtd, twtf, pred, pref, ax, ay, dg, bytes; };
 cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host);
 
 // step ids of the scalar kernels (mirror krylov.cu)
@@ -188,7 +189,8 @@ static int build_offsets(const std::vector<Geom>& gs, std::vector<int>& host_off
 }
 
 // Fill B's offset tables for `gs` into the device int buffer `doff` (12 arrays of count+1).
-static int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStream_t st, std::vector<int>& staging) {
+namespace pcb {
+int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStream_t st, std::vector<int>& staging) {
   const int count = (int)gs.size();
   staging.clear();
   int tots[8];
@@ -216,6 +218,7 @@ static int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStre
   B.time_q = gs[0].time_q;
   return PCB_OK;
 }
+}  // namespace pcb
 
 extern "C" {
 
@@ -261,11 +264,16 @@ void pcb_destroy(pcb_problem* p) {
   delete p;
 }
 
-int pcb_create(const pcb_desc* d, pcb_problem** out) {
-  if (!d || !out) return PCB_ERR_INVALID_ARG;
-  *out = nullptr;
+}  // extern "C"
+
+namespace pcb {
+
+// Validation shared by every entry point that takes a descriptor.
+int validate_desc(const pcb_desc* d) {
+  if (!d) return PCB_ERR_INVALID_ARG;
   if (d->N < 1 || d->n < 2 || !(d->theta >= 0.5 && d->theta <= 1.0) || !(d->gamma > 0.0) || !(d->T > 0.0) ||
-      (d->precision != PCB_FP64 && d->precision != PCB_MIXED) || !std::isfinite(d->zeta))
+      (d->precision != PCB_FP64 && d->precision != PCB_MIXED) || !std::isfinite(d->zeta) ||
+      !std::isfinite(d->gamma) || !std::isfinite(d->T))
     return PCB_ERR_INVALID_ARG;
   // supported: zeta = pi, n a power of two <= 1024, N+1 = 2^a 3^b with N <= 511
   if (std::fabs(d->zeta - M_PI) > 1e-12) return PCB_ERR_UNSUPPORTED;
@@ -273,6 +281,7 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
   if (d->N > 511) return PCB_ERR_UNSUPPORTED;
   FftPlan pd, pt;
   if (!make_plan(2 * (d->N + 1), pd) || !make_plan(d->n, pt)) return PCB_ERR_UNSUPPORTED;
+  if (!q_supported(dst_Q(d->N)) || !q_supported(time_Q(d->n))) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges && !pow2(d->N + 1)) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges && !mg_available()) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges) {
@@ -280,48 +289,50 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
     for (long long k = 0; k < ne; ++k)
       if (!(d->a_edges[k] > 0.0) || !std::isfinite(d->a_edges[k])) return PCB_ERR_INVALID_ARG;
   }
-  pcb_problem* p = new (std::nothrow) pcb_problem();
-  if (!p) return PCB_ERR_OUT_OF_MEMORY;
-  p->desc = *d;
-  p->desc.a_edges = nullptr;
-  if (p->desc.mg_cycles <= 0) p->desc.mg_cycles = 2;
-  p->stream = (cudaStream_t)d->stream;
-  cudaGetDevice(&p->device);
-  Geom& g = p->g;
+  return PCB_OK;
+}
+
+// Scalar fields, FFT plans and launch shapes of a validated descriptor (no device work).
+void init_geom(const pcb_desc* d, Geom& g) {
   std::memset(&g, 0, sizeof(g));
   g.N = d->N; g.n = d->n; g.m = d->N * d->N; g.L = d->N + 1; g.M = 2 * (d->N + 1);
   g.mn = (long long)g.m * g.n;
   g.theta = d->theta; g.tau = d->T / d->n; g.gamma = d->gamma; g.alpha = g.tau / std::sqrt(d->gamma);
   g.h = 1.0 / (d->N + 1); g.sqrt_gamma = std::sqrt(d->gamma); g.c = g.tau / (g.h * g.h);
   g.var_a = d->a_edges ? 1 : 0;
-  g.pdst = pd; g.ptime = pt;
+  make_plan(g.M, g.pdst);
+  make_plan(g.n, g.ptime);
   g.dst_q = dst_Q(g.N);
   g.time_q = time_Q(g.n);
-  if (!q_supported(g.dst_q) || !q_supported(g.time_q)) { delete p; return PCB_ERR_UNSUPPORTED; }
-  if (upload_constants() != cudaSuccess) { delete p; return PCB_ERR_CUDA; }
   set_shapes(g);
+}
 
-  int rc = PCB_OK;
-  auto fail = [&](int code) { pcb_destroy(p); return code; };
-  // ---- tables (FP64 computed on the host with the C library, rounded for FP32) ----
+// Byte offsets of the spectral / twiddle / coefficient tables (Sec. 3.5) inside one buffer.
+size_t table_layout(const Geom& g, TableLayout& t) {
   const int N = g.N, n = g.n, M = g.M;
-  const size_t n_kap = N, n_mu = n, n_twd = M, n_twt = n, n_pre = n;
   const size_t ne = g.var_a ? (size_t)N * (N + 1) : 0;
   size_t off_b = 0;
   auto take = [&](size_t bytes) { size_t o = off_b; off_b += (bytes + 255) & ~(size_t)255; return o; };
-  const size_t o_kap = take(n_kap * 8), o_mud = take(n_mu * 16), o_muf = take(n_mu * 8), o_twdd = take(n_twd * 16),
-               o_twdf = take(n_twd * 8), o_twtd = take(n_twt * 16), o_twtf = take(n_twt * 8),
-               o_pred = take(n_pre * 16), o_pref = take(n_pre * 8), o_ax = take(ne * 8), o_ay = take(ne * 8),
-               o_dg = take(g.var_a ? (size_t)g.m * 8 : 0);
-  std::vector<unsigned char> host(off_b, 0);
-  double* kap = (double*)(host.data() + o_kap);
+  t.kap = take((size_t)N * 8); t.mud = take((size_t)n * 16); t.muf = take((size_t)n * 8);
+  t.twdd = take((size_t)M * 16); t.twdf = take((size_t)M * 8); t.twtd = take((size_t)n * 16);
+  t.twtf = take((size_t)n * 8); t.pred = take((size_t)n * 16); t.pref = take((size_t)n * 8);
+  t.ax = take(ne * 8); t.ay = take(ne * 8); t.dg = take(g.var_a ? (size_t)g.m * 8 : 0);
+  t.bytes = off_b;
+  return off_b;
+}
+
+// Fill the tables (FP64 on the host with the C math library, rounded for the FP32 copies).
+void fill_tables(const pcb_desc* d, const Geom& g, const TableLayout& t, unsigned char* host) {
+  const int N = g.N, n = g.n, M = g.M;
+  std::memset(host, 0, t.bytes);
+  double* kap = (double*)(host + t.kap);
   for (int q = 1; q <= N; ++q) {
     const double s = std::sin(q * M_PI * g.h / 2.0);
     kap[q - 1] = 4.0 / (g.h * g.h) * s * s;
   }
   // lambda(S_n) at F-slot r: psi_r = -pi (2r+1)/n, f1/f2 with f1 = 1 - e^{i psi}, f2 = theta + (1-theta) e^{i psi}
-  double2* mud = (double2*)(host.data() + o_mud);
-  float2* muf = (float2*)(host.data() + o_muf);
+  double2* mud = (double2*)(host + t.mud);
+  float2* muf = (float2*)(host + t.muf);
   for (int r = 0; r < n; ++r) {
     const double psi = -M_PI * (2.0 * r + 1.0) / n;
     const double c = std::cos(psi), s = std::sin(psi);
@@ -340,38 +351,69 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
       tf[k].x = (float)td[k].x; tf[k].y = (float)td[k].y;
     }
   };
-  fill_tw((double2*)(host.data() + o_twdd), (float2*)(host.data() + o_twdf), M);
-  fill_tw((double2*)(host.data() + o_twtd), (float2*)(host.data() + o_twtf), n);
-  double2* pred = (double2*)(host.data() + o_pred);
-  float2* pref = (float2*)(host.data() + o_pref);
-  for (int t = 0; t < n; ++t) {
-    const double a = -M_PI * (double)t / n;
-    pred[t].x = std::cos(a); pred[t].y = std::sin(a);
-    pref[t].x = (float)pred[t].x; pref[t].y = (float)pred[t].y;
+  fill_tw((double2*)(host + t.twdd), (float2*)(host + t.twdf), M);
+  fill_tw((double2*)(host + t.twtd), (float2*)(host + t.twtf), n);
+  double2* pred = (double2*)(host + t.pred);
+  float2* pref = (float2*)(host + t.pref);
+  for (int k = 0; k < n; ++k) {
+    const double a = -M_PI * (double)k / n;
+    pred[k].x = std::cos(a); pred[k].y = std::sin(a);
+    pref[k].x = (float)pred[k].x; pref[k].y = (float)pred[k].y;
   }
   if (g.var_a) {
-    double* ax = (double*)(host.data() + o_ax);
-    double* ay = (double*)(host.data() + o_ay);
-    double* dg = (double*)(host.data() + o_dg);
+    const size_t ne = (size_t)N * (N + 1);
+    double* ax = (double*)(host + t.ax);
+    double* ay = (double*)(host + t.ay);
+    double* dg = (double*)(host + t.dg);
     const double* axs = d->a_edges;
-    const double* ays = d->a_edges + (size_t)N * (N + 1);
+    const double* ays = d->a_edges + ne;
     for (size_t k = 0; k < ne; ++k) { ax[k] = g.c * axs[k]; ay[k] = g.c * ays[k]; }
     for (int j = 0; j < N; ++j)
       for (int i = 0; i < N; ++i)
         dg[j * N + i] = ax[j * (N + 1) + i] + ax[j * (N + 1) + i + 1] + ay[j * N + i] + ay[(j + 1) * N + i];
   }
+}
+
+// Point the Geom's table pointers into a device copy of the tables.
+void bind_tables(Geom& g, const TableLayout& t, unsigned char* tb) {
+  g.kap = (const double*)(tb + t.kap);
+  g.mu_d = (const double2*)(tb + t.mud); g.mu_f = (const float2*)(tb + t.muf);
+  g.twd_d = (const double2*)(tb + t.twdd); g.twd_f = (const float2*)(tb + t.twdf);
+  g.twt_d = (const double2*)(tb + t.twtd); g.twt_f = (const float2*)(tb + t.twtf);
+  g.pre_d = (const double2*)(tb + t.pred); g.pre_f = (const float2*)(tb + t.pref);
+  if (g.var_a) {
+    g.axs = (const double*)(tb + t.ax); g.ays = (const double*)(tb + t.ay); g.dgs = (const double*)(tb + t.dg);
+  }
+}
+
+}  // namespace pcb
+
+extern "C" {
+
+int pcb_create(const pcb_desc* d, pcb_problem** out) {
+  if (!d || !out) return PCB_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = validate_desc(d);
+  if (rc != PCB_OK) return rc;
+  pcb_problem* p = new (std::nothrow) pcb_problem();
+  if (!p) return PCB_ERR_OUT_OF_MEMORY;
+  p->desc = *d;
+  p->desc.a_edges = nullptr;
+  if (p->desc.mg_cycles <= 0) p->desc.mg_cycles = 2;
+  p->stream = (cudaStream_t)d->stream;
+  cudaGetDevice(&p->device);
+  Geom& g = p->g;
+  init_geom(d, g);
+  if (upload_constants() != cudaSuccess) { delete p; return PCB_ERR_CUDA; }
+  auto fail = [&](int code) { pcb_destroy(p); return code; };
+  TableLayout lay;
+  const size_t off_b = table_layout(g, lay);
+  std::vector<unsigned char> host(off_b, 0);
+  fill_tables(d, g, lay, host.data());
   if (cudaMalloc(&p->tables, off_b) != cudaSuccess) return fail(PCB_ERR_OUT_OF_MEMORY);
   p->bytes += off_b;
   if (cudaMemcpy(p->tables, host.data(), off_b, cudaMemcpyHostToDevice) != cudaSuccess) return fail(PCB_ERR_CUDA);
-  unsigned char* tb = (unsigned char*)p->tables;
-  g.kap = (const double*)(tb + o_kap);
-  g.mu_d = (const double2*)(tb + o_mud); g.mu_f = (const float2*)(tb + o_muf);
-  g.twd_d = (const double2*)(tb + o_twdd); g.twd_f = (const float2*)(tb + o_twdf);
-  g.twt_d = (const double2*)(tb + o_twtd); g.twt_f = (const float2*)(tb + o_twtf);
-  g.pre_d = (const double2*)(tb + o_pred); g.pre_f = (const float2*)(tb + o_pref);
-  if (g.var_a) {
-    g.axs = (const double*)(tb + o_ax); g.ays = (const double*)(tb + o_ay); g.dgs = (const double*)(tb + o_dg);
-  }
+  bind_tables(g, lay, (unsigned char*)p->tables);
   // ---- preconditioner scratch: 2mn values, FP64-sized so both precisions fit ----
   const size_t sbytes = (size_t)2 * g.mn * sizeof(double);
   if (cudaMalloc(&p->scratch, sbytes) != cudaSuccess) return fail(PCB_ERR_OUT_OF_MEMORY);
