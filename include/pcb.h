@@ -161,6 +161,28 @@ int pcb_solve(pcb_problem* p, const pcb_solve_opts* opts, const double* b_dev, d
 int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* opts, const double* b_host,
                    double* x_host, pcb_solve_info* info);
 
+/* ---- allocation-free preconditioner apply ---------------------------------------------- */
+/* The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory (code running where the device allocator is off limits, memory-capped or
+ * pre-partitioned processes, or plain C callers that want no handle to create and destroy).
+ * It computes y = P^{-1} x exactly like pcb_precond_apply, for a(x) = 1, without any
+ * cudaMalloc/cudaFree: the problem description, the spectral tables and the transform scratch
+ * live in one file-scope device array of PCB_NOALLOC_ARENA_BYTES that every GPU loading the
+ * library holds until the process exits.
+ *   desc       : as for pcb_create (a_edges must be NULL; desc->precision is ignored in favour of
+ *                `precision`); work is queued on desc->stream, the call does not wait for it.
+ *   x_dev/y_dev: caller-owned device buffers of 2*m*n FP64 values; they may be the same buffer.
+ * Errors: INVALID_ARG, UNSUPPORTED (as pcb_create, or variable a(x)), TOO_LARGE when the tables
+ * plus 2*m*n scratch values (4 bytes each for PCB_MIXED, 8 for PCB_FP64) exceed the arena (about
+ * 16.7 million unknowns mixed, 8.3 million FP64), CUDA.
+ * Every call shares the one array: calls whose GPU work overlaps (different streams, or several
+ * host threads) race on it; serialise them, e.g. on one stream.  The scratch needs no clearing
+ * between calls (each apply overwrites all of it).  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture. */
+#define PCB_NOALLOC_ARENA_BYTES (64ull * 1024ull * 1024ull)
+int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int precision, const double* x_dev,
+                              double* y_dev);
+
 /* ---- batches --------------------------------------------------------------------------- */
 /* Solve `count` independent problems (uneven N, n, theta, gamma allowed; all with the same
  * precision) with shared kernel launches: every launch of an iteration covers all unfinished

@@ -74,6 +74,7 @@ def load() -> ctypes.CDLL:
         "pcb_solve_host": (c_int, [P, POINTER(PcbSolveOpts), P, P, POINTER(PcbSolveInfo)]),
         "pcb_batch_solve": (c_int, [POINTER(c_void_p), c_int, POINTER(PcbSolveOpts), POINTER(c_void_p),
                                     POINTER(c_void_p), POINTER(PcbSolveInfo)]),
+        "pcb_precond_apply_noalloc": (c_int, [POINTER(PcbDesc), c_int, c_int, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -1,0 +1,59 @@
+"""The allocation-free preconditioner apply (pcb_precond_apply_noalloc) against the allocating
+entry point (pcb_precond_apply) through the C ABI, for callers that cannot use cudaMalloc.
+Collected last on purpose; passes alone in a fresh process and after the other tests."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+KIND = {"abs_ps": 1, "ps": 2, "pms": 3}
+PREC = {"fp64": 0, "mixed": 1}
+TOL = {"fp64": 1e-12, "mixed": 2e-6}       # same bounds as the oracle parity tests
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2406_00952_gb300 import _build, _lib
+    _build.build()
+    return _lib.load()
+
+
+def _desc(N, n, theta, gamma):
+    from paper_2406_00952_gb300 import _lib
+    s = torch.cuda.current_stream().cuda_stream
+    return _lib.PcbDesc(N, n, theta, 1.0, gamma, math.pi, None, 0, 2, ctypes.c_void_p(s))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_noalloc_matches_allocating_apply_two_calls_in_a_row(lib):
+    import paper_2406_00952_gb300 as P
+    cases = [(63, 64, 1.0, 1e-2, "abs_ps", "mixed", 1), (31, 16, 0.5, 1e-4, "ps", "fp64", 2),
+             (95, 32, 0.75, 1e-3, "pms", "mixed", 3)]
+    for N, n, theta, gamma, kind, prec, seed in cases:
+        size = 2 * N * N * n
+        x = torch.from_numpy(synth.random_vector(size, seed=seed)).cuda()
+        ref = P.Problem(N, n, theta, gamma).precond_apply(x, kind=kind, precision=prec).cpu().numpy()
+        d = _desc(N, n, theta, gamma)
+        for call in range(2):
+            y = torch.full((size,), float("nan"), dtype=torch.float64, device="cuda")
+            rc = lib.pcb_precond_apply_noalloc(ctypes.byref(d), KIND[kind], PREC[prec], x.data_ptr(), y.data_ptr())
+            assert rc == 0, rc
+            out = y.cpu().numpy()
+            assert np.all(np.isfinite(out))
+            assert _rel(out, ref) <= TOL[prec], (N, n, kind, prec, call, _rel(out, ref))
+
+
+def test_noalloc_rejects_sizes_beyond_the_arena(lib):
+    d = _desc(511, 512, 1.0, 1e-2)
+    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    assert lib.pcb_precond_apply_noalloc(ctypes.byref(d), 1, 1, x.data_ptr(), x.data_ptr()) == -9
+    assert lib.pcb_precond_apply_noalloc(None, 1, 1, x.data_ptr(), x.data_ptr()) == -1
