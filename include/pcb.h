@@ -79,7 +79,7 @@ typedef struct pcb_problem pcb_problem;   /* opaque, owned by the library */
 typedef struct {
   int N;                  /* interior points per side; N+1 must be 2^a * 3^b (DST radices),   */
                           /* N <= 511; variable a(x) needs N = 2^k - 1 (multigrid)             */
-  int n;                  /* time steps; a power of two, 2 <= n <= 1024                       */
+  int n;                  /* time steps; a power of two, 2 <= n <= 1024 (<= 512 with variable a)*/
   double theta;           /* 1/2 <= theta <= 1                                                 */
   double T;               /* horizon, > 0                                                      */
   double gamma;           /* regularisation, > 0                                               */

@@ -1,18 +1,556 @@
-// Multigrid preconditioner route for variable a(x) (Sec. 3.5, Step 2 with multigrid).
-#include "pcb_internal.cuh"
+// Multigrid preconditioner route for variable a(x) (paper Sec. 3.5, Step 2 by multigrid; Sec. 4).
+//
+// P_S^{-1} v: time DFT of both halves (zeta = pi scaling, packed as real/imaginary parts), then per
+// frequency slot r the 2x2 block G = [[mu_r, -alpha], [alpha, conj(mu_r)]] is decoupled with
+// Lemma 3.14 (G = W diag(D1, D2) W^{-1}, W = [[1, M], [M, 1]], D2 = conj(D1)); the two decoupled
+// components are solved with `cycles` V-cycles on (D1 I + tau K) -- the second as the conjugate of
+// a solve with a conjugated right-hand side -- then recoupled with W and transformed back.
+// P_MS^{-1} v (Eq. matrix_P_MS): the same pipeline with no coupling and the real shift
+// sigma_r = sqrt(|mu_r|^2 + alpha^2) for both halves.
+// Only slots r < n/2 are solved: slot n-1-r carries the conjugate system, whose solution is the
+// conjugate (this holds for any real-coefficient linear solver, the V-cycle included, because
+// W_{n-1-r} equals conj(W_r) with its columns swapped up to scaling).
+//
+// V-cycle (reading of an unspecified method): vertex-centred coarsening N -> (N-1)/2, coarse edge
+// coefficient = mean of the two fine edges it spans, full-weighting restriction, bilinear
+// prolongation, damped Jacobi (weight 4/5), nu1 = nu2 = 2, exact solve on the 1 x 1 grid, zero
+// initial guess; cycle c > 1 corrects with a V-cycle on the current residual.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fft_reg.cuh"
 
 namespace pcb {
 
-bool mg_available() { return false; }
-int mg_launch_count(int kind) { (void)kind; return 0; }
-size_t mg_workspace_bytes(const Geom& g) { (void)g; return 256; }
-cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host) {
-  (void)g; (void)ws; (void)a_edges_host;
-  return cudaSuccess;
+bool mg_available() { return true; }
+int mg_launch_count(int kind);
+
+static constexpr double kJacobiWeight = 0.8;
+static constexpr int kMaxLevels = 12;
+static constexpr int kNu = 2;
+static long long g_mg_launches = 0;   // kernel launches issued by the multigrid route
+
+struct MgLevel {
+  int N;                      // interior points per side
+  double* axs;                // tau/h_l^2 * ax  (N x (N+1))
+  double* ays;                // tau/h_l^2 * ay  ((N+1) x N)
+  double* dgs;                // sum of the four  (N x N)
+  float* axf; float* ayf; float* dgf;
+  void* a[3];                 // work arrays: n systems x N^2 complex (FP64-sized)
+};
+
+struct MgHost {
+  int nlev = 0;
+  int nsys = 0;               // systems = n (n/2 frequency slots x 2 right-hand sides)
+  MgLevel lev[kMaxLevels];
+  void* zfine = nullptr;      // outer solution (level 0)
+  void* xfine = nullptr;      // outer residual (level 0)
+  double2* tab_d = nullptr;   // per slot r < n/2: {shift, coupling M, 1/(1-M^2)} for P_S, then P_MS shift
+  float2* tab_f = nullptr;
+};
+
+// workspace registry: one MgHost per Geom (keyed by the workspace pointer)
+static std::vector<std::pair<const void*, MgHost>>& registry() {
+  static std::vector<std::pair<const void*, MgHost>> r;
+  return r;
 }
-cudaError_t launch_precond_mg(const Batch& B, int kind, int prec, int in_slot, int out_slot) {
-  (void)B; (void)kind; (void)prec; (void)in_slot; (void)out_slot;
-  return cudaErrorNotSupported;
+static MgHost* find_host(const void* ws) {
+  for (auto& e : registry())
+    if (e.first == ws) return &e.second;
+  return nullptr;
+}
+
+static int levels_for(int N) {
+  int l = 1;
+  while (N > 1) { N = (N - 1) / 2; ++l; }
+  return l;
+}
+
+size_t mg_workspace_bytes(const Geom& g) {
+  size_t b = 0;
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  int N = g.N;
+  const size_t nsys = (size_t)g.n;
+  for (int l = 0; l < levels_for(g.N); ++l) {
+    const size_t ne = (size_t)N * (N + 1), nn = (size_t)N * N;
+    b += up(ne * 8) * 2 + up(nn * 8) + up(ne * 4) * 2 + up(nn * 4);
+    b += 3 * up(nsys * nn * sizeof(double2));
+    if (l == 0) b += 2 * up(nsys * nn * sizeof(double2));
+    N = (N - 1) / 2;
+  }
+  b += up((size_t)g.n * 3 * sizeof(double2)) + up((size_t)g.n * 3 * sizeof(float2));
+  return b;
+}
+
+cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges) {
+  // this translation unit's copy of the register-FFT twiddle table
+  cudaError_t e0 = upload_w96();
+  if (e0 != cudaSuccess) return e0;
+  MgHost h;
+  h.nlev = levels_for(g.N);
+  if (h.nlev > kMaxLevels) return cudaErrorInvalidValue;
+  h.nsys = g.n;
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  unsigned char* p = (unsigned char*)ws;
+  // fine coefficients = tau/h^2 * a at the edges; coarser levels average the two fine edges each
+  // coarse edge spans and are rescaled with their own spacing
+  int N = g.N;
+  std::vector<double> ax(a_edges, a_edges + (size_t)N * (N + 1));
+  std::vector<double> ay(a_edges + (size_t)N * (N + 1), a_edges + 2 * (size_t)N * (N + 1));
+  std::vector<unsigned char> hostbuf;
+  for (int l = 0; l < h.nlev; ++l) {
+    MgLevel& L = h.lev[l];
+    L.N = N;
+    const double hl = 1.0 / (N + 1), s = g.tau / (hl * hl);
+    const size_t ne = (size_t)N * (N + 1), nn = (size_t)N * N;
+    std::vector<double> axs(ne), ays(ne), dgs(nn);
+    for (size_t k = 0; k < ne; ++k) { axs[k] = s * ax[k]; ays[k] = s * ay[k]; }
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i)
+        dgs[(size_t)j * N + i] = axs[(size_t)j * (N + 1) + i] + axs[(size_t)j * (N + 1) + i + 1] +
+                                 ays[(size_t)j * N + i] + ays[(size_t)(j + 1) * N + i];
+    std::vector<float> axf(ne), ayf(ne), dgf(nn);
+    for (size_t k = 0; k < ne; ++k) { axf[k] = (float)axs[k]; ayf[k] = (float)ays[k]; }
+    for (size_t k = 0; k < nn; ++k) dgf[k] = (float)dgs[k];
+    L.axs = (double*)p; cudaMemcpy(p, axs.data(), ne * 8, cudaMemcpyHostToDevice); p += up(ne * 8);
+    L.ays = (double*)p; cudaMemcpy(p, ays.data(), ne * 8, cudaMemcpyHostToDevice); p += up(ne * 8);
+    L.dgs = (double*)p; cudaMemcpy(p, dgs.data(), nn * 8, cudaMemcpyHostToDevice); p += up(nn * 8);
+    L.axf = (float*)p; cudaMemcpy(p, axf.data(), ne * 4, cudaMemcpyHostToDevice); p += up(ne * 4);
+    L.ayf = (float*)p; cudaMemcpy(p, ayf.data(), ne * 4, cudaMemcpyHostToDevice); p += up(ne * 4);
+    L.dgf = (float*)p; cudaMemcpy(p, dgf.data(), nn * 4, cudaMemcpyHostToDevice); p += up(nn * 4);
+    for (int k = 0; k < 3; ++k) { L.a[k] = p; p += up((size_t)h.nsys * nn * sizeof(double2)); }
+    if (l == 0) {
+      h.zfine = p; p += up((size_t)h.nsys * nn * sizeof(double2));
+      h.xfine = p; p += up((size_t)h.nsys * nn * sizeof(double2));
+    }
+    if (N == 1) break;
+    // coarse coefficients: coarse row J sits on fine row 2J+1 (0-based), coarse edge e spans fine
+    // edges 2e and 2e+1 (and symmetrically for the x2 edges)
+    const int Nc = (N - 1) / 2;
+    std::vector<double> axc((size_t)Nc * (Nc + 1)), ayc((size_t)Nc * (Nc + 1));
+    for (int J = 0; J < Nc; ++J)
+      for (int e = 0; e <= Nc; ++e)
+        axc[(size_t)J * (Nc + 1) + e] =
+            0.5 * (ax[(size_t)(2 * J + 1) * (N + 1) + 2 * e] + ax[(size_t)(2 * J + 1) * (N + 1) + 2 * e + 1]);
+    for (int e = 0; e <= Nc; ++e)
+      for (int I = 0; I < Nc; ++I)
+        ayc[(size_t)e * Nc + I] = 0.5 * (ay[(size_t)(2 * e) * N + 2 * I + 1] + ay[(size_t)(2 * e + 1) * N + 2 * I + 1]);
+    ax.swap(axc); ay.swap(ayc);
+    N = Nc;
+  }
+  // per-slot table from lambda(S_n) at the F-slots (same formula as the spectral tables)
+  const int n = g.n, half = n / 2;
+  std::vector<double2> td((size_t)half * 4);
+  std::vector<float2> tf((size_t)half * 4);
+  for (int r = 0; r < half; ++r) {
+    const double psi = -M_PI * (2.0 * r + 1.0) / n;
+    const double c = std::cos(psi), s = std::sin(psi);
+    const double f1r = 1.0 - c, f1i = -s;
+    double f2r = g.theta + (1.0 - g.theta) * c, f2i = (1.0 - g.theta) * s;
+    if (std::hypot(f2r, f2i) < 1e-14) { f2r = 1.0; f2i = 0.0; }
+    const double den = f2r * f2r + f2i * f2i;
+    const double mr = (f1r * f2r + f1i * f2i) / den, mi = (f1i * f2r - f1r * f2i) / den;
+    const double a = g.alpha;
+    const double sq = std::sqrt(mi * mi + a * a);
+    // Lemma 3.14 (principal root): D1 = Re mu + i sqrt(Im^2 mu + alpha^2); M = -(i/alpha)(sq - Im mu)
+    const double Mi = -(sq - mi) / a;                 // M = i * Mi (purely imaginary)
+    const double inv = 1.0 / (1.0 + Mi * Mi);         // 1/(1 - M^2) with M^2 = -Mi^2
+    td[4 * r + 0] = make_double2(mr, sq);             // D1
+    td[4 * r + 1] = make_double2(0.0, Mi);            // M
+    td[4 * r + 2] = make_double2(inv, 0.0);
+    td[4 * r + 3] = make_double2(std::sqrt(mr * mr + mi * mi + a * a), 0.0);   // P_MS shift sigma_r
+    for (int k = 0; k < 4; ++k) tf[4 * r + k] = make_float2((float)td[4 * r + k].x, (float)td[4 * r + k].y);
+  }
+  h.tab_d = (double2*)p; cudaMemcpy(p, td.data(), td.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  p += up(td.size() * sizeof(double2));
+  h.tab_f = (float2*)p; cudaMemcpy(p, tf.data(), tf.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  p += up(tf.size() * sizeof(float2));
+  if ((size_t)(p - (unsigned char*)ws) > mg_workspace_bytes(g)) return cudaErrorInvalidValue;
+  for (auto& e : registry())
+    if (e.first == ws) { e.second = h; return cudaGetLastError(); }
+  registry().push_back({ws, h});
+  g.mg = ws;
+  return cudaGetLastError();
+}
+
+void mg_release(const void* ws) {
+  auto& r = registry();
+  for (size_t k = 0; k < r.size(); ++k)
+    if (r[k].first == ws) { r.erase(r.begin() + k); return; }
+}
+
+// ------------------------------------------------------------------------------------------
+// kernels (one instance; thread per (system, grid point))
+// ------------------------------------------------------------------------------------------
+template <typename R> struct Coef;
+template <> struct Coef<float> {
+  static __device__ const float* ax(const MgLevel& L) { return L.axf; }
+  static __device__ const float* ay(const MgLevel& L) { return L.ayf; }
+  static __device__ const float* dg(const MgLevel& L) { return L.dgf; }
+};
+template <> struct Coef<double> {
+  static __device__ const double* ax(const MgLevel& L) { return L.axs; }
+  static __device__ const double* ay(const MgLevel& L) { return L.ays; }
+  static __device__ const double* dg(const MgLevel& L) { return L.dgs; }
+};
+
+// (tau K z) at point (i, j) of system b
+template <typename R>
+__device__ __forceinline__ cx<R> tauKz(const MgLevel& L, const cx<R>* __restrict__ z, int i, int j) {
+  const int N = L.N;
+  const R* ax = Coef<R>::ax(L) + (long long)j * (N + 1);
+  const R* ay = Coef<R>::ay(L);
+  const cx<R> c = z[j * N + i];
+  cx<R> s = mk<R>(0, 0);
+  if (i > 0) s = cadd(s, cscale(z[j * N + i - 1], ax[i]));
+  if (i < N - 1) s = cadd(s, cscale(z[j * N + i + 1], ax[i + 1]));
+  if (j > 0) s = cadd(s, cscale(z[(j - 1) * N + i], ay[(long long)j * N + i]));
+  if (j < N - 1) s = cadd(s, cscale(z[(j + 1) * N + i], ay[(long long)(j + 1) * N + i]));
+  const R d = Coef<R>::dg(L)[j * N + i];
+  return csub(cscale(c, d), s);
+}
+
+template <typename R>
+__device__ __forceinline__ cx<R> shift_of(const cx<R>* __restrict__ tab, int b, int kind) {
+  const int r = b >> 1;
+  return kind == 2 ? tab[4 * r + 0] : mk<R>(tab[4 * r + 3].x, (R)0);
+}
+
+// out = z + w (rhs - A z)/diag  (first: z = 0, so out = w rhs / diag)
+template <typename R>
+__global__ void k_mg_jacobi(MgLevel L, int nsys, const cx<R>* __restrict__ tab, int kind,
+                            const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z, cx<R>* __restrict__ out,
+                            int first, R w) {
+  const int N = L.N, nn = N * N;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nsys * nn) return;
+  const int b = (int)(idx / nn), pt = (int)(idx - (long long)b * nn);
+  const int j = pt / N, i = pt - j * N;
+  const cx<R> mu = shift_of<R>(tab, b, kind);
+  const cx<R> d = mk<R>(mu.x + Coef<R>::dg(L)[pt], mu.y);
+  const R dd = d.x * d.x + d.y * d.y;
+  const cx<R> dinv = mk<R>(d.x / dd, -d.y / dd);
+  const long long o = (long long)b * nn;
+  if (first) {
+    out[o + pt] = cscale(cmul(rhs[o + pt], dinv), w);
+    return;
+  }
+  const cx<R>* zb = z + o;
+  const cx<R> Az = cadd(cmul(mu, zb[pt]), tauKz<R>(L, zb, i, j));
+  out[o + pt] = cadd(zb[pt], cscale(cmul(csub(rhs[o + pt], Az), dinv), w));
+}
+
+// res = rhs - A z
+template <typename R>
+__global__ void k_mg_resid(MgLevel L, int nsys, const cx<R>* __restrict__ tab, int kind,
+                           const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z, cx<R>* __restrict__ res) {
+  const int N = L.N, nn = N * N;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nsys * nn) return;
+  const int b = (int)(idx / nn), pt = (int)(idx - (long long)b * nn);
+  const int j = pt / N, i = pt - j * N;
+  const cx<R> mu = shift_of<R>(tab, b, kind);
+  const long long o = (long long)b * nn;
+  const cx<R>* zb = z + o;
+  const cx<R> Az = cadd(cmul(mu, zb[pt]), tauKz<R>(L, zb, i, j));
+  res[o + pt] = csub(rhs[o + pt], Az);
+}
+
+// full weighting: coarse (I, J) <- fine 9-point neighbourhood of (2I+1, 2J+1) (0-based)
+template <typename R>
+__global__ void k_mg_restrict(int Nf, int nsys, const cx<R>* __restrict__ f, cx<R>* __restrict__ c) {
+  const int Nc = (Nf - 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nsys * nnc) return;
+  const int b = (int)(idx / nnc), pt = (int)(idx - (long long)b * nnc);
+  const int J = pt / Nc, I = pt - J * Nc;
+  const cx<R>* fb = f + (long long)b * nnf;
+  const int fi = 2 * I + 1, fj = 2 * J + 1;
+  auto at = [&](int ii, int jj) { return fb[jj * Nf + ii]; };
+  cx<R> s = cscale(at(fi, fj), (R)4);
+  s = cadd(s, cscale(cadd(cadd(at(fi - 1, fj), at(fi + 1, fj)), cadd(at(fi, fj - 1), at(fi, fj + 1))), (R)2));
+  s = cadd(s, cadd(cadd(at(fi - 1, fj - 1), at(fi + 1, fj - 1)), cadd(at(fi - 1, fj + 1), at(fi + 1, fj + 1))));
+  c[(long long)b * nnc + pt] = cscale(s, (R)(1.0 / 16.0));
+}
+
+// bilinear prolongation added to the fine solution
+template <typename R>
+__global__ void k_mg_prolong_add(int Nf, int nsys, const cx<R>* __restrict__ c, cx<R>* __restrict__ z) {
+  const int Nc = (Nf - 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nsys * nnf) return;
+  const int b = (int)(idx / nnf), pt = (int)(idx - (long long)b * nnf);
+  const int j = pt / Nf, i = pt - j * Nf;
+  const cx<R>* cb = c + (long long)b * nnc;
+  // fine 0-based index 2K+1 sits on coarse node K; even fine indices lie between coarse nodes
+  auto cv = [&](int I, int J) { return (I < 0 || J < 0 || I >= Nc || J >= Nc) ? mk<R>(0, 0) : cb[J * Nc + I]; };
+  cx<R> v;
+  const bool oi = i & 1, oj = j & 1;
+  if (oi && oj) v = cv(i >> 1, j >> 1);
+  else if (oi) v = cscale(cadd(cv(i >> 1, (j >> 1) - 1), cv(i >> 1, j >> 1)), (R)0.5);
+  else if (oj) v = cscale(cadd(cv((i >> 1) - 1, j >> 1), cv(i >> 1, j >> 1)), (R)0.5);
+  else v = cscale(cadd(cadd(cv((i >> 1) - 1, (j >> 1) - 1), cv(i >> 1, (j >> 1) - 1)),
+                       cadd(cv((i >> 1) - 1, j >> 1), cv(i >> 1, j >> 1))), (R)0.25);
+  z[(long long)b * nnf + pt] = cadd(z[(long long)b * nnf + pt], v);
+}
+
+// a += b  or  a = b (copy)
+template <typename R>
+__global__ void k_mg_axpy(long long len, const cx<R>* __restrict__ src, cx<R>* __restrict__ dst, int copy) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= len) return;
+  dst[idx] = copy ? src[idx] : cadd(dst[idx], src[idx]);
+}
+
+// ------------------------------------------------------------------------------------------
+// time passes around the multigrid
+// ------------------------------------------------------------------------------------------
+template <typename R> __device__ __forceinline__ const cx<R>* twt_(const Geom& g);
+template <> __device__ __forceinline__ const float2* twt_<float>(const Geom& g) { return g.twt_f; }
+template <> __device__ __forceinline__ const double2* twt_<double>(const Geom& g) { return g.twt_d; }
+template <typename R> __device__ __forceinline__ const cx<R>* pre_(const Geom& g);
+template <> __device__ __forceinline__ const float2* pre_<float>(const Geom& g) { return g.pre_f; }
+template <> __device__ __forceinline__ const double2* pre_<double>(const Geom& g) { return g.pre_d; }
+
+__host__ __device__ __forceinline__ int padded_len_mg(int len) { return (len + (len >> 5) + 1) | 1; }
+
+// Shared-memory radix-2 Stockham-free DFT of one column of length n by a single warp-group:
+// the time passes here handle one column per warp with the register/shuffle FFT.
+template <typename R, int Q>
+__device__ __forceinline__ void col_fft(cx<R>* line, int t, int P, const cx<R>* __restrict__ tw, bool inv) {
+  using T = cx<R>;
+  LaneStages<T, R> st;
+  lane_stages<T, R>(st, t, P, inv);
+  T x[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) x[q] = line[pidx(t + P * q)];
+  __syncwarp();
+  reg_dft<T, R, Q>(x, inv);
+#pragma unroll
+  for (int k1 = 1; k1 < Q; ++k1) {
+    T w = __ldg(&tw[t * k1]);
+    if (inv) w.y = -w.y;
+    x[pos<Q>(k1)] = cmul(x[pos<Q>(k1)], w);
+  }
+  lane_dif<T, R, Q>(x, P, st);
+  __syncwarp();
+  const int k2 = bitrev(t, P);
+#pragma unroll
+  for (int k1 = 0; k1 < Q; ++k1) line[pidx(k1 + Q * k2)] = x[pos<Q>(k1)];
+  __syncwarp();
+}
+
+// forward: v (FP64, 2 halves) -> right-hand sides of the n systems (slot r < n/2: 2r and 2r+1)
+template <typename R, int Q>
+__global__ void __launch_bounds__(256) k_mg_time_fwd(const Geom* __restrict__ G, const Slots* __restrict__ S,
+                                                     int in_slot, const cx<R>* __restrict__ tab, int kind,
+                                                     cx<R>* __restrict__ rhs, int cpw) {
+  using T = cx<R>;
+  const Geom& g = G[0];
+  const int n = g.n, m = g.m, ls = padded_len_mg(n);
+  const long long mn = g.mn;
+  const double* __restrict__ x = S[0].v[in_slot];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = (T*)smem_raw;
+  const int P = n / Q, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lpw = 32 / P;
+  const int t = lane % P;
+  const int cols_per_block = (blockDim.x >> 5) * lpw * cpw;
+  const int c0 = blockIdx.x * cols_per_block;
+  for (int e = threadIdx.x; e < cols_per_block * n; e += blockDim.x) {
+    const int tt = e / cols_per_block, l = e - tt * cols_per_block;
+    const int col = c0 + l;
+    T v = mk<R>(0, 0);
+    if (col < m) {
+      const long long a = (long long)tt * m + col;
+      v = cmul(mk<R>((R)x[a], (R)x[mn + a]), __ldg(&pre_<R>(g)[tt]));
+    }
+    tile[l * ls + pidx(tt)] = v;
+  }
+  __syncthreads();
+  const int half = n / 2;
+  for (int k = 0; k < cpw; ++k) {
+    const int l = (warp * cpw + k) * lpw + lane / P;
+    T* line = tile + l * ls;
+    col_fft<R, Q>(line, t, P, twt_<R>(g), false);
+    const int col = c0 + l;
+    if (col < m) {
+      for (int r = t; r < half; r += P) {
+        const T Cr = line[pidx(r)], Cq = cconj(line[pidx(n - 1 - r)]);
+        const T F1 = cscale(cadd(Cr, Cq), (R)0.5);
+        const T F2 = cmul_mi(cscale(csub(Cr, Cq), (R)0.5));
+        T T1 = F1, T2 = F2;
+        if (kind == 2) {   // W^{-1} [F1; F2], W = [[1, M], [M, 1]]
+          const T M = tab[4 * r + 1];
+          const R inv = tab[4 * r + 2].x;
+          T1 = cscale(csub(F1, cmul(M, F2)), inv);
+          T2 = cscale(csub(F2, cmul(M, F1)), inv);
+          T2 = cconj(T2);   // second component: solved as the conjugate system with D1
+        }
+        rhs[(long long)(2 * r) * m + col] = T1;
+        rhs[(long long)(2 * r + 1) * m + col] = T2;
+      }
+    }
+  }
+}
+
+// inverse: solutions of the n systems -> P^{-1} v (FP64, 2 halves)
+template <typename R, int Q>
+__global__ void __launch_bounds__(256) k_mg_time_inv(const Geom* __restrict__ G, const Slots* __restrict__ S,
+                                                     int out_slot, const cx<R>* __restrict__ tab, int kind,
+                                                     const cx<R>* __restrict__ z, int cpw) {
+  using T = cx<R>;
+  const Geom& g = G[0];
+  const int n = g.n, m = g.m, ls = padded_len_mg(n);
+  const long long mn = g.mn;
+  double* __restrict__ y = S[0].v[out_slot];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = (T*)smem_raw;
+  const int P = n / Q, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lpw = 32 / P;
+  const int t = lane % P;
+  const int cols_per_block = (blockDim.x >> 5) * lpw * cpw;
+  const int c0 = blockIdx.x * cols_per_block;
+  const int half = n / 2;
+  for (int e = threadIdx.x; e < cols_per_block * half; e += blockDim.x) {
+    const int r = e / cols_per_block, l = e - r * cols_per_block;
+    const int col = c0 + l;
+    T U1 = mk<R>(0, 0), U2 = mk<R>(0, 0);
+    if (col < m) {
+      const T Z1 = z[(long long)(2 * r) * m + col];
+      T Z2 = z[(long long)(2 * r + 1) * m + col];
+      if (kind == 2) {
+        Z2 = cconj(Z2);
+        const T M = tab[4 * r + 1];
+        U1 = cadd(Z1, cmul(M, Z2));
+        U2 = cadd(cmul(M, Z1), Z2);
+      } else {
+        U1 = Z1; U2 = Z2;
+      }
+    }
+    tile[l * ls + pidx(r)] = cadd(U1, cmul_pi(U2));
+    tile[l * ls + pidx(n - 1 - r)] = cadd(cconj(U1), cmul_pi(cconj(U2)));
+  }
+  __syncthreads();
+  for (int k = 0; k < cpw; ++k) {
+    const int l = (warp * cpw + k) * lpw + lane / P;
+    col_fft<R, Q>(tile + l * ls, t, P, twt_<R>(g), true);
+  }
+  __syncthreads();
+  const R sc = (R)1 / (R)n;
+  for (int e = threadIdx.x; e < cols_per_block * n; e += blockDim.x) {
+    const int tt = e / cols_per_block, l = e - tt * cols_per_block;
+    const int col = c0 + l;
+    if (col < m) {
+      const T v = cscale(cmul(tile[l * ls + pidx(tt)], cconj(__ldg(&pre_<R>(g)[tt]))), sc);
+      const long long a = (long long)tt * m + col;
+      y[a] = (double)v.x;
+      y[mn + a] = (double)v.y;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host orchestration
+// ------------------------------------------------------------------------------------------
+static unsigned blocks_for(long long len) { return (unsigned)((len + 255) / 256); }
+
+template <typename R>
+static void vcycle(const MgHost& h, const cx<R>* tab, int kind, int l, const cx<R>* rhs, cx<R>* z, cx<R>* spare,
+                   cudaStream_t st) {
+  const MgLevel& L = h.lev[l];
+  const long long len = (long long)h.nsys * L.N * L.N;
+  const R w = (R)kJacobiWeight;
+  if (L.N == 1) {   // exact solve on the single-unknown grid: z = rhs / diag
+    k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, nullptr, z, 1, (R)1);
+    g_mg_launches += 1;
+    return;
+  }
+  // pre-smoothing from zero: z1 = w D^{-1} rhs, then nu1-1 sweeps ping-ponging with `spare`
+  cx<R>* cur = z;
+  cx<R>* oth = spare;
+  k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, nullptr, cur, 1, w);
+  for (int s = 1; s < kNu; ++s) {
+    k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, cur, oth, 0, w);
+    std::swap(cur, oth);
+  }
+  // residual -> restrict to the coarse right-hand side
+  k_mg_resid<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, cur, oth);
+  const MgLevel& C = h.lev[l + 1];
+  const long long lenc = (long long)h.nsys * C.N * C.N;
+  cx<R>* crhs = (cx<R>*)C.a[0];
+  k_mg_restrict<R><<<blocks_for(lenc), 256, 0, st>>>(L.N, h.nsys, oth, crhs);
+  vcycle<R>(h, tab, kind, l + 1, crhs, (cx<R>*)C.a[1], (cx<R>*)C.a[2], st);
+  k_mg_prolong_add<R><<<blocks_for(len), 256, 0, st>>>(L.N, h.nsys, (const cx<R>*)C.a[1], cur);
+  for (int s = 0; s < kNu; ++s) {
+    k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, cur, oth, 0, w);
+    std::swap(cur, oth);
+  }
+  g_mg_launches += 2 * kNu + 3;
+  if (cur != z) { k_mg_axpy<R><<<blocks_for(len), 256, 0, st>>>(len, cur, z, 1); g_mg_launches += 1; }
+}
+
+template <typename R, int Q>
+static cudaError_t mg_apply(const Batch& B, const Geom& g, const MgHost& h, int kind, int cycles, int in_slot,
+                            int out_slot) {
+  using T = cx<R>;
+  cudaStream_t st = B.stream;
+  const T* tab = (const T*)(sizeof(R) == 4 ? (const void*)h.tab_f : (const void*)h.tab_d);
+  const MgLevel& F = h.lev[0];
+  const long long len = (long long)h.nsys * F.N * F.N;
+  T* r0 = (T*)F.a[0];
+  T* z0 = (T*)h.zfine;
+  T* x0 = (T*)h.xfine;
+  const int P = g.n / Q, lpw = 32 / P, cpw = 1;
+  const int cols = 8 * lpw * cpw;
+  const size_t smem = (size_t)cols * padded_len_mg(g.n) * sizeof(T);
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_mg_time_fwd<R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_mg_time_inv<R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    done = true;
+  }
+  const unsigned tb = (unsigned)((g.m + cols - 1) / cols);
+  k_mg_time_fwd<R, Q><<<tb, 256, smem, st>>>(B.G, B.S, in_slot, tab, kind, r0, cpw);
+  g_mg_launches += 2;
+  for (int c = 0; c < cycles; ++c) {
+    if (c == 0) {
+      vcycle<R>(h, tab, kind, 0, r0, z0, (T*)F.a[1], st);
+    } else {
+      k_mg_resid<R><<<blocks_for(len), 256, 0, st>>>(F, h.nsys, tab, kind, r0, z0, x0);
+      vcycle<R>(h, tab, kind, 0, x0, (T*)F.a[2], (T*)F.a[1], st);
+      k_mg_axpy<R><<<blocks_for(len), 256, 0, st>>>(len, (const T*)F.a[2], z0, 0);
+      g_mg_launches += 2;
+    }
+  }
+  k_mg_time_inv<R, Q><<<tb, 256, smem, st>>>(B.G, B.S, out_slot, tab, kind, z0, cpw);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t mg_dispatch(const Batch& B, const Geom& g, const MgHost& h, int kind, int cycles, int in_slot,
+                               int out_slot) {
+  switch (g.time_q) {
+    case 1: return mg_apply<R, 1>(B, g, h, kind, cycles, in_slot, out_slot);
+    case 2: return mg_apply<R, 2>(B, g, h, kind, cycles, in_slot, out_slot);
+    case 4: return mg_apply<R, 4>(B, g, h, kind, cycles, in_slot, out_slot);
+    case 8: return mg_apply<R, 8>(B, g, h, kind, cycles, in_slot, out_slot);
+    case 16: return mg_apply<R, 16>(B, g, h, kind, cycles, in_slot, out_slot);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int mg_launch_count(int kind) { (void)kind; return 0; }
+long long mg_launch_total() { return g_mg_launches; }
+
+cudaError_t launch_precond_mg(const Batch& B, const Geom& g, int kind, int prec, int cycles, int in_slot,
+                              int out_slot) {
+  if (B.count != 1 || !g.mg) return cudaErrorInvalidValue;
+  const MgHost* h = find_host(g.mg);
+  if (!h) return cudaErrorInvalidValue;
+  if (kind != PCB_PREC_PS && kind != PCB_PREC_PMS) return cudaErrorInvalidValue;
+  return prec == PCB_MIXED ? mg_dispatch<float>(B, g, *h, kind, cycles, in_slot, out_slot)
+                           : mg_dispatch<double>(B, g, *h, kind, cycles, in_slot, out_slot);
 }
 
 }  // namespace pcb

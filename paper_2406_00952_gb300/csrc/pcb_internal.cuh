@@ -80,6 +80,7 @@ struct Geom {
   const double* ays;              //        tau/h^2 * ay  ((N+1) x N)
   const double* dgs;              //        tau/h^2 * (sum of the 4 edge coefficients) (N x N)
   void* scratch;                  // preconditioner workspace: 2mn values of the apply's Real type
+  const void* mg;                 // multigrid workspace (variable a), else null
 };
 
 // per-instance Krylov scalars (MINRES and GMRES share the struct)

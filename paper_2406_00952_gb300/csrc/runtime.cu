@@ -16,7 +16,10 @@
 namespace pcb {
 // launchers defined in the other translation units
 cudaError_t launch_precond_fast(const Batch& B, int kind, int prec, int in_slot, int out_slot);
-cudaError_t launch_precond_mg(const Batch& B, int kind, int prec, int in_slot, int out_slot);
+cudaError_t launch_precond_mg(const Batch& B, const Geom& g, int kind, int prec, int cycles, int in_slot,
+                              int out_slot);
+void mg_release(const void* ws);
+long long mg_launch_total();
 cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi);
 cudaError_t launch_rhs(const Geom& g, cudaStream_t st, int op, const double* gs, const double* fs, const double* y0,
                        double* b);
@@ -247,6 +250,7 @@ void pcb_destroy(pcb_problem* p) {
   cudaStreamSynchronize(p->stream);
   cudaFree(p->tables);
   cudaFree(p->scratch);
+  if (p->mgws) mg_release(p->mgws);
   cudaFree(p->mgws);
   cudaFree(p->vec_minres);
   cudaFree(p->vec_mixed);
@@ -284,6 +288,7 @@ int validate_desc(const pcb_desc* d) {
   if (!q_supported(dst_Q(d->N)) || !q_supported(time_Q(d->n))) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges && !pow2(d->N + 1)) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges && !mg_available()) return PCB_ERR_UNSUPPORTED;
+  if (d->a_edges && d->n > 512) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges) {
     const long long ne = 2LL * d->N * (d->N + 1);
     for (long long k = 0; k < ne; ++k)
@@ -492,10 +497,10 @@ struct SolveCfg {
   bool check_true;      // FP64 route: keep iterating if the true residual check fails
 };
 
-static int apply_precond(const Batch& B, bool var_a, int kind, int prec, int in_slot, int out_slot) {
+static int apply_precond(const pcb_problem* p, const Batch& B, int kind, int prec, int in_slot, int out_slot) {
   cudaError_t e;
   if (kind == PCB_PREC_NONE) e = launch_axpby(B, AX_COPY, in_slot, out_slot, -1);
-  else if (var_a) e = launch_precond_mg(B, kind, prec, in_slot, out_slot);
+  else if (p->g.var_a) e = launch_precond_mg(B, p->g, kind, prec, p->desc.mg_cycles, in_slot, out_slot);
   else e = launch_precond_fast(B, kind, prec, in_slot, out_slot);
   return e == cudaSuccess ? PCB_OK : cuda_status(e);
 }
@@ -521,9 +526,10 @@ static int P_precond(pcb_problem* p, const Batch& B, int kind, int prec, int in_
   cudaEvent_t a = nullptr, b = nullptr;
   const bool ev = p->prof && ev_pair(p->ev_prec, p->ev_prec_used, a, b);
   if (ev) cudaEventRecord(a, B.stream);
-  const int rc = apply_precond(B, va, kind, prec, in_slot, out_slot);
+  const long long mg0 = mg_launch_total();
+  const int rc = apply_precond(p, B, kind, prec, in_slot, out_slot);
   if (ev) cudaEventRecord(b, B.stream);
-  p->launches += precond_launch_count(va, kind);
+  p->launches += va ? (mg_launch_total() - mg0) : precond_launch_count(va, kind);
   p->prec_applies += 1;
   return rc;
 }
@@ -829,7 +835,7 @@ int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_d
   p->hS.v[SL_UOUT] = y_dev;
   int rc;
   if ((rc = upload_slots(p))) return rc;
-  return apply_precond(p->B, p->g.var_a != 0, kind, precision, SL_UIN, SL_UOUT);
+  return apply_precond(p, p->B, kind, precision, SL_UIN, SL_UOUT);
 }
 
 int pcb_recover(pcb_problem* p, const double* x_dev, double* y_dev, double* p_dev) {

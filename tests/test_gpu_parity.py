@@ -181,3 +181,47 @@ def test_errors_are_reported_not_raised_in_kernels(P):
     z = torch.zeros(gp.size, dtype=torch.float64, device="cuda")
     x, info = gp.solve(z)
     assert info["relres"] == 0.0 and float(x.abs().max()) == 0.0
+
+
+# ---------------------------------------------------------------- variable a(x): multigrid route
+MG_SHAPES = [(1, 4, 0.5, 1e-2), (3, 2, 1.0, 1e-3), (7, 8, 0.5, 1e-4), (15, 16, 1.0, 1e-2), (31, 32, 0.5, 1e-4),
+             (63, 64, 0.5, 1e-6), (127, 8, 0.75, 1e-2)]
+
+
+@pytest.mark.parametrize("shape", MG_SHAPES, ids=lambda s: "N%d-n%d-th%g-g%g" % s)
+@pytest.mark.parametrize("kind", ["ps", "pms"])
+def test_mg_precond_parity(P, shape, kind):
+    N, n, theta, gamma = shape
+    a = synth.variable_coefficient_edges(N)
+    prob = ds.Problem(N, n, theta, gamma, a_edges=a)
+    v = synth.random_vector(2 * prob.m * n, seed=300 + N + n)
+    ref = pc.apply_mg_ps_inv(prob, v, cycles=2) if kind == "ps" else pc.apply_pms_inv(prob, v, cycles=2)
+    gp = P.Problem(N, n, theta, gamma, a_edges=a, mg_cycles=2)
+    out64 = gp.precond_apply(dev(v), kind=kind, precision="fp64").cpu().numpy()
+    out32 = gp.precond_apply(dev(v), kind=kind, precision="mixed").cpu().numpy()
+    assert rel(out64, ref) <= 1e-12, rel(out64, ref)
+    assert rel(out32, ref) <= 5e-6, rel(out32, ref)
+
+
+def test_variable_a_matvec_and_fgmres(P):
+    """Variable coefficient, Crank-Nicolson: matvec parity, same-algorithm FGMRES iterates, and
+    convergence of the FP64 and mixed solves to 1e-8 (the config-2 method at a small size)."""
+    N, n = 31, 32
+    a = synth.variable_coefficient_edges(N)
+    prob = ds.Problem(N, n, 0.5, 1e-4, a_edges=a)
+    g = synth.random_target(N, n, seed=2); f = synth.manufactured_source(N, n)
+    v = synth.random_vector(2 * prob.m * n, seed=9)
+    gp = P.Problem(N, n, 0.5, 1e-4, a_edges=a, precision="fp64")
+    assert rel(gp.matvec(dev(v), op="Ahat").cpu().numpy(), op.matvec_A_hat(prob, v)) <= 1e-13
+    assert rel(gp.matvec(dev(v), op="A").cpu().numpy(), op.matvec_A(prob, v)) <= 1e-13
+    b = ds.rhs_gmres(prob, g, f)
+    xo, _ = kr.fgmres(lambda z: op.matvec_A_hat(prob, z), b, lambda r: pc.apply_mg_ps_inv(prob, r), fixed_iterations=4)
+    x, info = gp.solve(dev(b), method="fgmres", precond="ps", fixed_iterations=4)
+    assert rel(x.cpu().numpy(), xo) <= 1e-10
+    x, info = gp.solve(dev(b), tol=1e-8)
+    assert info["method"] == 3 and info["relres"] <= 1e-8
+    xs, io = kr.fgmres(lambda z: op.matvec_A_hat(prob, z), b, lambda r: pc.apply_mg_ps_inv(prob, r), tol=1e-12)
+    assert rel(x.cpu().numpy(), xs) <= 1e-6
+    gm = P.Problem(N, n, 0.5, 1e-4, a_edges=a, precision="mixed")
+    xm, im = gm.solve(dev(b), tol=1e-8)
+    assert im["relres"] <= 1e-8 and rel(xm.cpu().numpy(), xs) <= 1e-6
