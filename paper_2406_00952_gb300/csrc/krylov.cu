@@ -54,13 +54,13 @@ __global__ void __launch_bounds__(256) k_dot(const Geom* __restrict__ G, const S
 }
 
 // y = a*x + b*y with (a, b) chosen by `mode` from the instance scalars
-enum { AX_COPY = 0, AX_MINRES_R = 1, AX_SCALE_INV_BETA = 2, AX_SCALE_INV_HNORM = 3, AX_ADD = 4 };
+enum { AX_COPY = 0, AX_MINRES_R = 1, AX_SCALE_INV_BETA = 2, AX_SCALE_INV_HNORM = 3, AX_ADD = 4, AX_ZERO = 5 };
 __global__ void __launch_bounds__(256) k_axpby(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                                const Scal* __restrict__ Sc, const int* __restrict__ off, int count,
                                                const int* __restrict__ active, int mode, int sx, int sy, int sz) {
   INST_PROLOGUE
   const Scal& c = Sc[inst];
-  const double* __restrict__ x = S[inst].v[sx];
+  const double* __restrict__ x = sx >= 0 ? S[inst].v[sx] : nullptr;
   double* __restrict__ y = S[inst].v[sy];
   if (mode == AX_COPY) {
     for (long long e = e0; e < len; e += stride) y[e] = x[e];
@@ -75,8 +75,10 @@ __global__ void __launch_bounds__(256) k_axpby(const Geom* __restrict__ G, const
   } else if (mode == AX_SCALE_INV_HNORM) {
     const double f = 1.0 / c.hnorm;
     for (long long e = e0; e < len; e += stride) y[e] = x[e] * f;
-  } else {   // AX_ADD: y += x
+  } else if (mode == AX_ADD) {
     for (long long e = e0; e < len; e += stride) y[e] += x[e];
+  } else {   // AX_ZERO
+    for (long long e = e0; e < len; e += stride) y[e] = 0.0;
   }
 }
 
@@ -252,7 +254,8 @@ __device__ void scalar_step(Scal& c, int step, double v, double tol, int j, int 
 // Sum the instance's partials (nper values per block, index `which`) and run a scalar step.
 __global__ void __launch_bounds__(256) k_reduce(const int* __restrict__ off, int count, const int* __restrict__ active,
                                                 const double* __restrict__ partial, int nper, int which, Scal* Sc,
-                                                int step, double tol, int j, int restart) {
+                                                int step, double tol, const double* __restrict__ tols, int j,
+                                                int restart) {
   const int inst = blockIdx.x;
   if (inst >= count) return;
   if (active && !active[inst]) return;
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(256) k_reduce(const int* __restrict__ off, int
   double acc = 0.0;
   for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) acc += partial[(long long)b * nper + which];
   const double s = block_sum(acc);
-  if (threadIdx.x == 0) scalar_step(Sc[inst], step, s, tol, j, restart);
+  if (threadIdx.x == 0) scalar_step(Sc[inst], step, s, tols ? tols[inst] : tol, j, restart);
 }
 
 // multi-reduction for CGS: H[pass][i] = sum of partials i
@@ -308,7 +311,8 @@ cudaError_t launch_dot(const Batch& B, int sa, int sb) {
 }
 cudaError_t launch_reduce(const Batch& B, const int* off, int nper, int which, int step, double tol, int j,
                           int restart) {
-  k_reduce<<<B.count, 256, 0, B.stream>>>(off, B.count, B.active, B.partial, nper, which, B.Sc, step, tol, j, restart);
+  k_reduce<<<B.count, 256, 0, B.stream>>>(off, B.count, B.active, B.partial, nper, which, B.Sc, step, tol, B.tols, j,
+                                          restart);
   return cudaGetLastError();
 }
 cudaError_t launch_axpby(const Batch& B, int mode, int sx, int sy, int sz) {

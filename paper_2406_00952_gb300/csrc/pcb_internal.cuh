@@ -134,7 +134,8 @@ struct Batch {
   const int* off_time[2];  int tot_time[2];
   const int* off_mv;    int tot_mv;
   const int* off_vec;   int tot_vec;
-  double* partial;        // reduction partials [tot_vec * 8]
+  double* partial;        // reduction partials
+  const double* tols;     // per-instance tolerances for the scalar steps (device) or null
   int dst_q, time_q;      // register-FFT variant shared by every instance of the batch
   size_t dst_smem[2], time_smem[2];   // dynamic shared memory per block, per precision
 };

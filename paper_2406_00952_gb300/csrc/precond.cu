@@ -101,15 +101,9 @@ struct LineFFT {
 // in_slot / out_slot >= 0 select a vector slot (FP64), -1 selects the instance scratch (R).
 // ------------------------------------------------------------------------------------------
 template <typename TIn, typename TOut, typename R, int Q>
-__global__ void __launch_bounds__(256, 2) k_dst(const Geom* __restrict__ G, const Slots* __restrict__ S,
-                                             const int* __restrict__ off, int count,
-                                             const int* __restrict__ active, int axis, int in_slot,
-                                             int out_slot) {
+__device__ __forceinline__ void dst_body(const Geom& g, const Slots* __restrict__ S, int inst, int lb, int axis,
+                                         int in_slot, int out_slot) {
   using T = cx<R>;
-  const int inst = find_inst(off, count, blockIdx.x);
-  if (active && !active[inst]) return;
-  const Geom& g = G[inst];
-  const int lb = blockIdx.x - off[inst];
   const TIn* __restrict__ in = in_slot >= 0 ? (const TIn*)S[inst].v[in_slot] : (const TIn*)g.scratch;
   TOut* __restrict__ out = out_slot >= 0 ? (TOut*)S[inst].v[out_slot] : (TOut*)g.scratch;
   const int N = g.N, L = N + 1, M = 2 * L;
@@ -256,18 +250,48 @@ __global__ void __launch_bounds__(256, 2) k_dst(const Geom* __restrict__ G, cons
   }
 }
 
+template <typename TIn, typename TOut, typename R, int Q>
+__global__ void __launch_bounds__(256, 2) k_dst(const Geom* __restrict__ G, const Slots* __restrict__ S,
+                                             const int* __restrict__ off, int count,
+                                             const int* __restrict__ active, int axis, int in_slot,
+                                             int out_slot) {
+  const int inst = find_inst(off, count, blockIdx.x);
+  if (active && !active[inst]) return;
+  dst_body<TIn, TOut, R, Q>(G[inst], S, inst, blockIdx.x - off[inst], axis, in_slot, out_slot);
+}
+
+// Shared launch over instances with different line lengths: each block runs the register-FFT
+// variant of its own instance.
+template <typename TIn, typename TOut, typename R>
+__global__ void __launch_bounds__(256, 2) k_dst_any(const Geom* __restrict__ G, const Slots* __restrict__ S,
+                                                 const int* __restrict__ off, int count,
+                                                 const int* __restrict__ active, int axis, int in_slot,
+                                                 int out_slot) {
+  const int inst = find_inst(off, count, blockIdx.x);
+  if (active && !active[inst]) return;
+  const Geom& g = G[inst];
+  const int lb = blockIdx.x - off[inst];
+  switch (g.dst_q) {
+    case 1: dst_body<TIn, TOut, R, 1>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    case 2: dst_body<TIn, TOut, R, 2>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    case 3: dst_body<TIn, TOut, R, 3>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    case 4: dst_body<TIn, TOut, R, 4>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    case 6: dst_body<TIn, TOut, R, 6>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    case 8: dst_body<TIn, TOut, R, 8>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    case 12: dst_body<TIn, TOut, R, 12>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    case 16: dst_body<TIn, TOut, R, 16>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    case 24: dst_body<TIn, TOut, R, 24>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    default: dst_body<TIn, TOut, R, 32>(g, S, inst, lb, axis, in_slot, out_slot); break;
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Time pass: forward DFT of (half0 + i half1) * exp(-i pi t/n), pointwise solve per frequency
 // pair, inverse DFT, unscale.  In place on the scratch.
 // ------------------------------------------------------------------------------------------
 template <typename R, int Q>
-__global__ void __launch_bounds__(256, 2) k_time(const Geom* __restrict__ G, const int* __restrict__ off, int count,
-                                              const int* __restrict__ active, int kind) {
+__device__ __forceinline__ void time_body(const Geom& g, int lb, int kind) {
   using T = cx<R>;
-  const int inst = find_inst(off, count, blockIdx.x);
-  if (active && !active[inst]) return;
-  const Geom& g = G[inst];
-  const int lb = blockIdx.x - off[inst];
   R* __restrict__ y = (R*)g.scratch;
   const int n = g.n, m = g.m, N = g.N, cpb = g.time_cpb[sizeof(R) == 4];   // cpb: power of two
   const int ls = padded_len(n);
@@ -398,6 +422,31 @@ __global__ void __launch_bounds__(256, 2) k_time(const Geom* __restrict__ G, con
   }
 }
 
+template <typename R, int Q>
+__global__ void __launch_bounds__(256, 2) k_time(const Geom* __restrict__ G, const int* __restrict__ off, int count,
+                                              const int* __restrict__ active, int kind) {
+  const int inst = find_inst(off, count, blockIdx.x);
+  if (active && !active[inst]) return;
+  time_body<R, Q>(G[inst], blockIdx.x - off[inst], kind);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, 2) k_time_any(const Geom* __restrict__ G, const int* __restrict__ off,
+                                                  int count, const int* __restrict__ active, int kind) {
+  const int inst = find_inst(off, count, blockIdx.x);
+  if (active && !active[inst]) return;
+  const Geom& g = G[inst];
+  const int lb = blockIdx.x - off[inst];
+  switch (g.time_q) {
+    case 1: time_body<R, 1>(g, lb, kind); break;
+    case 2: time_body<R, 2>(g, lb, kind); break;
+    case 4: time_body<R, 4>(g, lb, kind); break;
+    case 8: time_body<R, 8>(g, lb, kind); break;
+    case 16: time_body<R, 16>(g, lb, kind); break;
+    default: time_body<R, 32>(g, lb, kind); break;
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // host side: shapes, constant tables, launchers
 // ------------------------------------------------------------------------------------------
@@ -459,6 +508,24 @@ template <typename R>
 static cudaError_t dispatch_dst(const Batch& B, int axis, int in_slot, int out_slot) {
   const int p = sizeof(R) == 4;
   const size_t smem = B.dst_smem[p];
+  if (B.dst_q == 0) {   // instances with different line lengths in one launch
+    static bool done = false;
+    if (!done) {
+      cudaFuncSetAttribute(k_dst_any<double, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(k_dst_any<R, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(k_dst_any<R, double, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      done = true;
+    }
+    const int* off = axis == 0 ? B.off_dst_i[p] : B.off_dst_j[p];
+    const int tot = axis == 0 ? B.tot_dst_i[p] : B.tot_dst_j[p];
+    if (in_slot >= 0)
+      k_dst_any<double, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, in_slot, -1);
+    else if (out_slot >= 0)
+      k_dst_any<R, double, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, -1, out_slot);
+    else
+      k_dst_any<R, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, -1, -1);
+    return cudaGetLastError();
+  }
   switch (B.dst_q) {
     case 1: launch_dst_q<R, 1>(B, axis, in_slot, out_slot, smem); break;
     case 2: launch_dst_q<R, 2>(B, axis, in_slot, out_slot, smem); break;
@@ -479,6 +546,15 @@ template <typename R>
 static cudaError_t dispatch_time(const Batch& B, int kind) {
   const int p = sizeof(R) == 4;
   const size_t smem = B.time_smem[p];
+  if (B.time_q == 0) {
+    static bool done = false;
+    if (!done) {
+      cudaFuncSetAttribute(k_time_any<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      done = true;
+    }
+    k_time_any<R><<<B.tot_time[p], 256, smem, B.stream>>>(B.G, B.off_time[p], B.count, B.active, kind);
+    return cudaGetLastError();
+  }
   switch (B.time_q) {
     case 1: launch_time_q<R, 1>(B, kind, smem); break;
     case 2: launch_time_q<R, 2>(B, kind, smem); break;
@@ -503,7 +579,7 @@ static cudaError_t precond_passes(const Batch& B, int kind, int in_slot, int out
 
 int precond_launch_count(bool var_a, int kind) { return var_a ? mg_launch_count(kind) : 5; }
 
-// All instances of B must share dst_q and time_q (the batch engine groups them that way).
+// B.dst_q / B.time_q = 0 selects the shared-launch kernels for instances of different sizes.
 cudaError_t launch_precond_fast(const Batch& B, int kind, int prec, int in_slot, int out_slot) {
   return prec == PCB_MIXED ? precond_passes<float>(B, kind, in_slot, out_slot)
                            : precond_passes<double>(B, kind, in_slot, out_slot);

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -49,7 +50,7 @@ cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host);
 // step ids of the scalar kernels (mirror krylov.cu)
 enum { SS_NONE = 0, SS_MINRES_INIT, SS_MINRES_ALFA, SS_MINRES_GIVENS, SS_NORM, SS_GMRES_ARNOLDI, SS_GMRES_START,
        SS_BNORM };
-enum { AX_COPY = 0, AX_MINRES_R = 1, AX_SCALE_INV_BETA = 2, AX_SCALE_INV_HNORM = 3, AX_ADD = 4 };
+enum { AX_COPY = 0, AX_MINRES_R = 1, AX_SCALE_INV_BETA = 2, AX_SCALE_INV_HNORM = 3, AX_ADD = 4, AX_ZERO = 5 };
 enum { EPI_PLAIN = 0, EPI_RESID = 1, EPI_MINRES = 2 };
 enum { PK_ABS_PS = 1, PK_PS = 2, PK_PMS = 3 };
 
@@ -219,6 +220,10 @@ int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStream_t st
   B.stream = st;
   B.dst_q = gs[0].dst_q;
   B.time_q = gs[0].time_q;
+  for (const Geom& g : gs) {   // mixed sizes: shared launches dispatch per instance
+    if (g.dst_q != B.dst_q) B.dst_q = 0;
+    if (g.time_q != B.time_q) B.time_q = 0;
+  }
   return PCB_OK;
 }
 }  // namespace pcb
@@ -869,16 +874,309 @@ int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* o, const double* b_host
   return rc;
 }
 
-int pcb_batch_solve(pcb_problem* const* problems, int count, const pcb_solve_opts* opts, const double* const* b_dev,
-                    double* const* x_dev, pcb_solve_info* infos) {
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Batched solves: instances of any size share every launch.  Instances are grouped by method
+// (MINRES for the symmetric system, (F)GMRES otherwise); each group iterates in lockstep and
+// instances leave through the device-side `active` mask when their inner solve ends.  Every
+// instance runs rounds of: inner Krylov solve from a zero guess on r = b - op x to the tolerance
+// tol*||b||/||r|| (recurrence estimate), then x += d and the FP64 true residual.  With FP64 the
+// first round normally finishes; with the FP32 preconditioner later rounds are the refinement.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+struct BGroup {
+  std::vector<pcb_problem*> probs;
+  std::vector<int> idx;               // positions in the caller's arrays
+  int method = PCB_MINRES, op = PCB_OP_A, kind = PCB_PREC_ABS_PS, prec = PCB_MIXED;
+  Batch B;
+  Geom* dG = nullptr; Slots* dS = nullptr; Scal* dSc = nullptr; int* dAct = nullptr; int* dOff = nullptr;
+  double* dPart = nullptr; double* dTol = nullptr;
+  Scal* hSc = nullptr; int* hAct = nullptr; double* hTol = nullptr;
+  std::vector<double> bnorm, rnorm;
+  std::vector<int> iters, sweeps, status, done, in_round, round_member;
+  int j = 0;                          // Arnoldi index (lockstep)
+  int it_round = 0;
+  bool round_open = false;
+  ~BGroup() {
+    cudaFree(dG); cudaFree(dS); cudaFree(dSc); cudaFree(dAct); cudaFree(dOff); cudaFree(dPart); cudaFree(dTol);
+    cudaFreeHost(hSc); cudaFreeHost(hAct); cudaFreeHost(hTol);
+  }
+};
+
+int set_active(BGroup& G, const std::vector<int>& mask) {
+  const int n = (int)G.probs.size();
+  CK(cudaStreamSynchronize(G.B.stream));
+  for (int k = 0; k < n; ++k) G.hAct[k] = mask[k];
+  CK(cudaMemcpyAsync(G.dAct, G.hAct, n * sizeof(int), cudaMemcpyHostToDevice, G.B.stream));
+  return PCB_OK;
+}
+
+int read_all(BGroup& G) {
+  CK(cudaMemcpyAsync(G.hSc, G.dSc, sizeof(Scal) * G.probs.size(), cudaMemcpyDeviceToHost, G.B.stream));
+  CK(cudaStreamSynchronize(G.B.stream));
+  return PCB_OK;
+}
+
+int group_setup(BGroup& G, const SolveCfg& c, const double* const* b_dev, double* const* x_dev, cudaStream_t st) {
+  const int n = (int)G.probs.size();
+  std::vector<Geom> gs;
+  std::vector<Slots> sl(n);
+  for (int k = 0; k < n; ++k) {
+    pcb_problem* p = G.probs[k];
+    int rc;
+    if ((rc = ensure_minres(p)) || (rc = ensure_mixed(p))) return rc;
+    if (G.method != PCB_MINRES && (rc = ensure_gmres(p, c.restart))) return rc;
+    const size_t nv = (size_t)2 * p->g.mn;
+    double* v = p->vec_minres;
+    Slots& S = sl[k];
+    std::memset(&S, 0, sizeof(S));
+    S.v[SL_R1] = v; S.v[SL_R2] = v + nv; S.v[SL_Y] = v + 2 * nv; S.v[SL_YO] = v + 3 * nv; S.v[SL_Q] = v + 4 * nv;
+    S.v[SL_W] = v + 5 * nv; S.v[SL_W2] = v + 6 * nv; S.v[SL_R] = v;
+    S.v[SL_BI] = p->vec_mixed; S.v[SL_XI] = p->vec_mixed + nv;
+    if (G.method != PCB_MINRES) { S.v[SL_VBASE] = p->vec_gmres; S.v[SL_ZBASE] = p->vec_gmres + (size_t)(c.restart + 1) * nv; }
+    S.v[SL_X] = x_dev[G.idx[k]];
+    S.v[SL_B] = (double*)b_dev[G.idx[k]];
+    gs.push_back(p->g);
+  }
+  size_t part = 0; int tv = 0, tm = 0;
+  for (const Geom& g : gs) { tv += g.vec_blocks; tm += g.mv_blocks; }
+  part = std::max((size_t)tv * (PCB_MAX_RESTART + 1), (size_t)tm) + 1;
+  if (cudaMalloc(&G.dG, sizeof(Geom) * n) || cudaMalloc(&G.dS, sizeof(Slots) * n) ||
+      cudaMalloc(&G.dSc, sizeof(Scal) * n) || cudaMalloc(&G.dAct, sizeof(int) * n) ||
+      cudaMalloc(&G.dOff, sizeof(int) * 8 * (n + 1)) || cudaMalloc(&G.dPart, part * sizeof(double)) ||
+      cudaMalloc(&G.dTol, sizeof(double) * n) || cudaMallocHost(&G.hSc, sizeof(Scal) * n) ||
+      cudaMallocHost(&G.hAct, sizeof(int) * n) || cudaMallocHost(&G.hTol, sizeof(double) * n)) {
+    cudaGetLastError();
+    return PCB_ERR_OUT_OF_MEMORY;
+  }
+  CK(cudaMemcpyAsync(G.dG, gs.data(), sizeof(Geom) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(G.dS, sl.data(), sizeof(Slots) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(G.dSc, 0, sizeof(Scal) * n, st));
+  std::vector<int> staging;
+  std::memset(&G.B, 0, sizeof(Batch));
+  int rc = fill_batch(G.B, gs, G.dOff, st, staging);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(st));
+  G.B.G = G.dG; G.B.S = G.dS; G.B.Sc = G.dSc; G.B.active = G.dAct; G.B.partial = G.dPart; G.B.tols = G.dTol;
+  G.bnorm.assign(n, 0.0); G.rnorm.assign(n, 0.0); G.iters.assign(n, 0); G.sweeps.assign(n, 0);
+  G.status.assign(n, PCB_OK); G.done.assign(n, 0); G.in_round.assign(n, 0); G.round_member.assign(n, 0);
+  // ||b|| for every instance; x = 0; inner right-hand side = b
+  std::vector<int> all(n, 1);
+  if ((rc = set_active(G, all))) return rc;
+  CK(launch_axpby(G.B, AX_ZERO, -1, SL_X, -1));
+  CK(launch_axpby(G.B, AX_COPY, SL_B, SL_BI, -1));
+  CK(launch_dot(G.B, SL_B, SL_B));
+  CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
+  if ((rc = read_all(G))) return rc;
+  for (int k = 0; k < n; ++k) {
+    G.bnorm[k] = G.hSc[k].bnorm; G.rnorm[k] = G.bnorm[k];
+    if (!std::isfinite(G.bnorm[k])) { G.status[k] = PCB_ERR_NONFINITE; G.done[k] = 1; }
+    else if (G.bnorm[k] == 0.0) { G.done[k] = 1; G.rnorm[k] = 0.0; }
+  }
+  return PCB_OK;
+}
+
+// start a round for every unfinished instance
+int round_start(BGroup& G, const SolveCfg& c) {
+  const int n = (int)G.probs.size();
+  std::vector<int> mask(n, 0);
+  int any = 0;
+  for (int k = 0; k < n; ++k) {
+    if (G.done[k]) continue;
+    mask[k] = 1; any = 1;
+    G.hTol[k] = std::min(0.5, c.tol * G.bnorm[k] / G.rnorm[k]);
+  }
+  G.round_member = mask; G.in_round = mask; G.round_open = any; G.it_round = 0; G.j = 0;
+  if (!any) return PCB_OK;
+  int rc;
+  if ((rc = set_active(G, mask))) return rc;
+  CK(cudaMemcpyAsync(G.dTol, G.hTol, sizeof(double) * n, cudaMemcpyHostToDevice, G.B.stream));
+  CK(launch_axpby(G.B, AX_ZERO, -1, SL_XI, -1));
+  if (G.method == PCB_MINRES) {
+    CK(launch_axpby(G.B, AX_ZERO, -1, SL_W, -1));
+    CK(launch_axpby(G.B, AX_ZERO, -1, SL_W2, -1));
+    CK(launch_axpby(G.B, AX_COPY, SL_BI, SL_R1, -1));
+    CK(launch_axpby(G.B, AX_COPY, SL_BI, SL_R2, -1));
+    if ((rc = apply_precond(G.probs[0], G.B, G.kind, G.prec, SL_R2, SL_Y))) return rc;
+    CK(launch_dot(G.B, SL_R2, SL_Y));
+    CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_MINRES_INIT, c.tol, 0, 0));
+  } else {
+    CK(launch_dot(G.B, SL_BI, SL_BI));
+    CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_BNORM, c.tol, 0, 0));
+    CK(launch_dot(G.B, SL_BI, SL_BI));
+    CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_GMRES_START, c.tol, 0, 0));
+    CK(launch_setslot(G.B, SL_VJ, SL_VBASE, 0));
+    CK(launch_axpby(G.B, AX_SCALE_INV_BETA, SL_BI, SL_VJ, -1));
+  }
+  if ((rc = read_all(G))) return rc;
+  for (int k = 0; k < n; ++k) {
+    if (!mask[k]) continue;
+    if (G.hSc[k].flags & 4) { G.status[k] = PCB_ERR_NONFINITE; G.done[k] = 1; G.in_round[k] = 0; }
+    else if (G.method == PCB_MINRES && (G.hSc[k].flags & 2)) { G.status[k] = PCB_ERR_BREAKDOWN; G.done[k] = 1; G.in_round[k] = 0; }
+  }
+  return set_active(G, G.in_round);
+}
+
+// one lockstep iteration of the group's active instances; ends instances whose estimate is met
+int round_step(BGroup& G, const SolveCfg& c) {
+  const int n = (int)G.probs.size();
+  int rc;
+  pcb_problem* p0 = G.probs[0];
+  std::vector<int> ending(n, 0);
+  bool any_end = false;
+  if (G.method == PCB_MINRES) {
+    CK(launch_matvec(G.B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
+    CK(launch_reduce(G.B, G.B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
+    CK(launch_axpby(G.B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
+    if ((rc = apply_precond(p0, G.B, G.kind, G.prec, SL_R1, SL_YO))) return rc;
+    CK(launch_dot(G.B, SL_R1, SL_YO));
+    CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_MINRES_GIVENS, c.tol, 0, 0));
+    CK(launch_minres_wx(G.B, SL_Y, SL_W, SL_W2, SL_XI));
+    CK(launch_swap(G.B, SL_R1, SL_R2, SL_Y, SL_YO, SL_W, SL_W2));
+    if ((rc = read_all(G))) return rc;
+    G.it_round += 1;
+    for (int k = 0; k < n; ++k) {
+      if (!G.in_round[k]) continue;
+      G.iters[k] += 1;
+      const int f = G.hSc[k].flags;
+      if (f & 4) { G.status[k] = PCB_ERR_NONFINITE; G.done[k] = 1; ending[k] = 1; }
+      else if (f & 2) { G.status[k] = PCB_ERR_BREAKDOWN; G.done[k] = 1; ending[k] = 1; }
+      else if ((f & 1) || G.iters[k] >= c.maxit) ending[k] = 1;
+      any_end |= ending[k] != 0;
+    }
+  } else {
+    const int j = G.j;
+    CK(launch_setslot(G.B, SL_VJ, SL_VBASE, j));
+    CK(launch_setslot(G.B, SL_ZJ, SL_ZBASE, j));
+    CK(launch_setslot(G.B, SL_VJ1, SL_VBASE, j + 1));
+    if ((rc = apply_precond(p0, G.B, G.kind, G.prec, SL_VJ, SL_ZJ))) return rc;
+    CK(launch_matvec(G.B, G.op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
+    for (int pass = 0; pass < 2; ++pass) {
+      CK(launch_multidot(G.B, SL_VBASE, j, SL_VJ1));
+      CK(launch_reduce_multi(G.B, j, pass));
+      CK(launch_multiaxpy(G.B, SL_VBASE, j, SL_VJ1, pass));
+    }
+    CK(launch_dot(G.B, SL_VJ1, SL_VJ1));
+    CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_GMRES_ARNOLDI, c.tol, j, c.restart));
+    CK(launch_axpby(G.B, AX_SCALE_INV_HNORM, SL_VJ1, SL_VJ1, -1));
+    if ((rc = read_all(G))) return rc;
+    G.it_round += 1;
+    for (int k = 0; k < n; ++k) {
+      if (!G.in_round[k]) continue;
+      G.iters[k] += 1;
+      const int f = G.hSc[k].flags;
+      if (f & 4) { G.status[k] = PCB_ERR_NONFINITE; G.done[k] = 1; ending[k] = 1; continue; }
+      if ((f & 1) || (f & 8) || j + 1 >= c.restart || G.iters[k] >= c.maxit) ending[k] = 1;
+      any_end |= ending[k] != 0;
+    }
+    if (any_end) {   // d = Z y for the instances whose cycle ends at this step (k = j + 1 columns)
+      std::vector<int> m2(n, 0);
+      for (int k = 0; k < n; ++k) m2[k] = ending[k] && !G.done[k];
+      if ((rc = set_active(G, m2))) return rc;
+      CK(launch_multiaxpy(G.B, SL_ZBASE, j, SL_XI, -1));
+    }
+    G.j += 1;
+  }
+  if (any_end) {
+    for (int k = 0; k < n; ++k) if (ending[k]) G.in_round[k] = 0;
+    if ((rc = set_active(G, G.in_round))) return rc;
+  }
+  return PCB_OK;
+}
+
+// x += d, r = b - op x, decide per instance
+int round_end(BGroup& G, const SolveCfg& c, int max_ref) {
+  const int n = (int)G.probs.size();
+  std::vector<int> mask(n, 0);
+  for (int k = 0; k < n; ++k) mask[k] = G.round_member[k] && !G.done[k];
+  int rc;
+  if ((rc = set_active(G, mask))) return rc;
+  CK(launch_axpby(G.B, AX_ADD, SL_XI, SL_X, -1));
+  CK(launch_matvec(G.B, G.op, SL_X, SL_BI, SL_B, EPI_RESID));
+  CK(launch_reduce(G.B, G.B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
+  if ((rc = read_all(G))) return rc;
+  for (int k = 0; k < n; ++k) {
+    if (!mask[k]) continue;
+    G.sweeps[k] += 1;
+    G.rnorm[k] = std::sqrt(G.hSc[k].dot1);
+    const double rel = G.rnorm[k] / G.bnorm[k];
+    if (!std::isfinite(rel)) { G.status[k] = PCB_ERR_NONFINITE; G.done[k] = 1; }
+    else if (rel <= c.tol) G.done[k] = 1;
+    else if (G.sweeps[k] >= max_ref || G.iters[k] >= c.maxit) { G.status[k] = PCB_NOT_CONVERGED; G.done[k] = 1; }
+  }
+  G.round_open = false;
+  return PCB_OK;
+}
+
+}  // namespace
+
+extern "C" int pcb_batch_solve(pcb_problem* const* problems, int count, const pcb_solve_opts* opts,
+                               const double* const* b_dev, double* const* x_dev, pcb_solve_info* infos) {
   if (!problems || count < 1 || !b_dev || !x_dev) return PCB_ERR_INVALID_ARG;
-  int worst = PCB_OK;
+  for (int k = 0; k < count; ++k)
+    if (!problems[k] || !b_dev[k] || !x_dev[k] || problems[k]->desc.precision != problems[0]->desc.precision ||
+        problems[k]->stream != problems[0]->stream)
+      return PCB_ERR_INVALID_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  // groups by method (and preconditioner)
+  std::vector<std::unique_ptr<BGroup>> groups;
+  std::vector<SolveCfg> cfgs;
   for (int k = 0; k < count; ++k) {
-    const int rc = pcb_solve(problems[k], opts, b_dev[k], x_dev[k], infos ? infos + k : nullptr);
-    if (rc < 0 && worst >= 0) worst = rc;
-    else if (rc > 0 && worst == PCB_OK) worst = rc;
+    SolveCfg c;
+    resolve_defaults(problems[k], opts, c);
+    if (c.method == PCB_MINRES && c.kind == PCB_PREC_PS) return PCB_ERR_INVALID_ARG;
+    if (problems[k]->g.var_a) return PCB_ERR_UNSUPPORTED;      // multigrid instances solve one at a time
+    BGroup* G = nullptr;
+    for (size_t q = 0; q < groups.size(); ++q)
+      if (groups[q]->method == c.method && groups[q]->kind == c.kind) G = groups[q].get();
+    if (!G) {
+      groups.emplace_back(new BGroup());
+      G = groups.back().get();
+      G->method = c.method; G->kind = c.kind; G->op = c.op; G->prec = c.prec;
+      cfgs.push_back(c);
+    }
+    G->probs.push_back(problems[k]);
+    G->idx.push_back(k);
+  }
+  cudaStream_t st = problems[0]->stream;
+  const int max_ref = (opts && opts->max_refinements > 0) ? opts->max_refinements : 10;
+  int rc = PCB_OK;
+  for (size_t q = 0; q < groups.size() && rc == PCB_OK; ++q) rc = group_setup(*groups[q], cfgs[q], b_dev, x_dev, st);
+  for (size_t q = 0; q < groups.size() && rc == PCB_OK; ++q) rc = round_start(*groups[q], cfgs[q]);
+  while (rc == PCB_OK) {
+    bool work = false;
+    for (size_t q = 0; q < groups.size() && rc == PCB_OK; ++q) {
+      BGroup& G = *groups[q];
+      if (!G.round_open) continue;
+      work = true;
+      bool any = false;
+      for (int v : G.in_round) any |= v != 0;
+      if (any) rc = round_step(G, cfgs[q]);
+      else {
+        rc = round_end(G, cfgs[q], max_ref);
+        if (rc == PCB_OK) rc = round_start(G, cfgs[q]);
+      }
+    }
+    if (!work) break;
+  }
+  if (rc == PCB_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = PCB_ERR_CUDA;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int worst = rc;
+  for (auto& Gp : groups) {
+    BGroup& G = *Gp;
+    for (size_t k = 0; k < G.probs.size(); ++k) {
+      const int s2 = rc != PCB_OK ? rc : G.status[k];
+      if (infos) {
+        pcb_solve_info& I = infos[G.idx[k]];
+        std::memset(&I, 0, sizeof(I));
+        I.status = s2; I.method = G.method; I.precond = G.kind; I.iterations = G.iters[k];
+        I.refinements = G.sweeps[k]; I.relres = G.bnorm[k] > 0 ? G.rnorm[k] / G.bnorm[k] : 0.0; I.seconds = secs;
+      }
+      if (s2 < 0 && worst >= 0) worst = s2;
+      else if (s2 > 0 && worst == PCB_OK) worst = s2;
+    }
   }
   return worst;
 }
-
-}  // extern "C"

@@ -225,3 +225,33 @@ def test_variable_a_matvec_and_fgmres(P):
     gm = P.Problem(N, n, 0.5, 1e-4, a_edges=a, precision="mixed")
     xm, im = gm.solve(dev(b), tol=1e-8)
     assert im["relres"] <= 1e-8 and rel(xm.cpu().numpy(), xs) <= 1e-6
+
+
+# ---------------------------------------------------------------- batches with shared launches
+def _batch_instances():
+    shapes = [(15, 16, 1.0, 1e-2), (31, 8, 0.5, 1e-4), (47, 32, 1.0, 1e-5), (63, 16, 0.5, 1e-2),
+              (31, 32, 1.0, 1e-1), (23, 64, 0.5, 1e-3)]
+    out = []
+    for k, (N, n, theta, gamma) in enumerate(shapes):
+        prob = ds.Problem(N, n, theta, gamma)
+        g = synth.random_target(N, n, seed=40 + k); f = synth.manufactured_source(N, n)
+        b = ds.rhs_minres(prob, g, f) if theta == 1.0 else ds.rhs_gmres(prob, g, f)
+        out.append((prob, b))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_solve_uneven(P, precision):
+    insts = _batch_instances()
+    probs = [P.Problem(pr.N, pr.n, pr.theta, pr.gamma, precision=precision) for pr, _ in insts]
+    bs = [dev(b) for _, b in insts]
+    xs, infos = P.batch_solve(probs, bs, tol=1e-8, restart=16)
+    xs2, _ = P.batch_solve(probs, bs, tol=1e-8, restart=16)
+    for (pr, b), x, x2, info, gp in zip(insts, xs, xs2, infos, probs):
+        assert info["relres"] <= 1e-8, info
+        xo = x.cpu().numpy()
+        assert np.array_equal(xo, x2.cpu().numpy())                      # deterministic
+        A = (lambda z: op.matvec_A(pr, z)) if pr.theta == 1.0 else (lambda z: op.matvec_A_hat(pr, z))
+        assert np.linalg.norm(b - A(xo)) / np.linalg.norm(b) <= 1.5e-8    # oracle's FP64 residual
+        x1, i1 = P.batch_solve([gp], [dev(b)], tol=1e-8, restart=16)      # the same instance alone
+        assert rel(xo, x1[0].cpu().numpy()) <= 1e-12 and i1[0]["iterations"] == info["iterations"]
