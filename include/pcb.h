@@ -190,6 +190,47 @@ int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int precision, con
 int pcb_batch_solve(pcb_problem* const* problems, int count, const pcb_solve_opts* opts,
                     const double* const* b_dev, double* const* x_dev, pcb_solve_info* infos);
 
+/* ---- continuous-batching server -------------------------------------------------------- */
+/* Requests (independent control solves of any supported size) are queued with pcb_server_submit
+ * and advanced by pcb_server_step.  Each step retires finished requests (their solution is copied
+ * to the caller's host buffer), admits queued requests while a slot is free and the device bytes
+ * of the admitted requests stay within the budget, and advances every admitted request by one
+ * Krylov iteration (or one refinement transition) in launches shared by all admitted requests of
+ * the same method.  Krylov state stays on the device from admission to retirement.  Each request
+ * runs the same rounds as pcb_batch_solve, so its result does not depend on which other requests
+ * share the launches (reductions are per request and in a fixed order). */
+typedef struct pcb_server pcb_server;
+
+typedef struct {
+  long long budget_bytes; /* device bytes the admitted requests may hold in total (> 0)           */
+  int max_slots;          /* concurrent requests per method (1..256)                              */
+  int precision;          /* pcb_precision of every request                                       */
+  double tol;             /* target true relative residual; <= 0 => 1e-8                          */
+  int maxit;              /* Krylov iterations per request; <= 0 => 500                           */
+  int restart;            /* GMRES restart length; <= 0 => 16                                     */
+  void* stream;           /* cudaStream_t all server work is queued on                           */
+} pcb_server_opts;
+
+typedef struct {
+  long long tag;          /* caller's tag from pcb_server_submit                                  */
+  int status;             /* PCB_OK, PCB_NOT_CONVERGED or a negative error                         */
+  int iterations;         /* Krylov iterations                                                     */
+  int refinements;        /* refinement rounds                                                     */
+  double relres;          /* true FP64 relative residual                                          */
+} pcb_server_done;
+
+int pcb_server_create(const pcb_server_opts* opts, pcb_server** out);
+void pcb_server_destroy(pcb_server* s);
+/* Queue one request.  desc: as for pcb_create (a_edges must be NULL; precision and stream come from
+ * the server).  op_rhs_host: the 2*m*n right-hand side for the method pcb_create would pick (A for
+ * theta = 1, A_hat otherwise), host memory read when the request is admitted; x_host: 2*m*n host
+ * values written when it retires.  Both must stay valid until the request is reported done.
+ * Errors: INVALID_ARG, UNSUPPORTED, TOO_LARGE (the request alone exceeds the budget). */
+int pcb_server_submit(pcb_server* s, const pcb_desc* desc, const double* rhs_host, double* x_host, long long tag);
+/* One scheduling step (blocks while it runs).  Up to max_done retired requests are written to done[];
+ * *n_done, *n_active and *n_queued report the counts after the step. */
+int pcb_server_step(pcb_server* s, pcb_server_done* done, int max_done, int* n_done, int* n_active, int* n_queued);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,6 +41,16 @@ class PcbSolveInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class PcbServerOpts(ctypes.Structure):
+    _fields_ = [("budget_bytes", c_longlong), ("max_slots", c_int), ("precision", c_int), ("tol", c_double),
+                ("maxit", c_int), ("restart", c_int), ("stream", c_void_p)]
+
+
+class PcbServerDone(ctypes.Structure):
+    _fields_ = [("tag", c_longlong), ("status", c_int), ("iterations", c_int), ("refinements", c_int),
+                ("relres", c_double)]
+
+
 _lib = None
 
 
@@ -75,6 +85,11 @@ def load() -> ctypes.CDLL:
         "pcb_batch_solve": (c_int, [POINTER(c_void_p), c_int, POINTER(PcbSolveOpts), POINTER(c_void_p),
                                     POINTER(c_void_p), POINTER(PcbSolveInfo)]),
         "pcb_precond_apply_noalloc": (c_int, [POINTER(PcbDesc), c_int, c_int, P, P]),
+        "pcb_server_create": (c_int, [POINTER(PcbServerOpts), POINTER(c_void_p)]),
+        "pcb_server_destroy": (None, [P]),
+        "pcb_server_submit": (c_int, [P, POINTER(PcbDesc), P, P, c_longlong]),
+        "pcb_server_step": (c_int, [P, POINTER(PcbServerDone), c_int, POINTER(c_int), POINTER(c_int),
+                                    POINTER(c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

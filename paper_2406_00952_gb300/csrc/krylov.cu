@@ -106,9 +106,11 @@ __global__ void __launch_bounds__(256) k_minres_wx(const Geom* __restrict__ G, c
 
 // CGS: partial[blk*(PCB_MAX_RESTART+1) + i] = V_i . W,  i = 0..j
 __global__ void __launch_bounds__(256) k_multidot(const Geom* __restrict__ G, const Slots* __restrict__ S,
-                                                  const int* __restrict__ off, int count, const int* __restrict__ active,
-                                                  int svbase, int j, int sw, double* __restrict__ partial) {
+                                                  const Scal* __restrict__ Sc, const int* __restrict__ off, int count,
+                                                  const int* __restrict__ active, int svbase, int j, int sw,
+                                                  double* __restrict__ partial) {
   INST_PROLOGUE
+  if (j < 0) j = Sc[inst].j;   // each instance at its own Arnoldi index
   const double* __restrict__ V = S[inst].v[svbase];
   const double* __restrict__ W = S[inst].v[sw];
   double acc[PCB_MAX_RESTART + 1];
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const Geom* __restrict__ G, c
                                                    int pass) {
   INST_PROLOGUE
   const Scal& c = Sc[inst];
+  if (j < 0) j = pass >= 0 ? c.j : c.j - 1;   // per-instance index (after Arnoldi, c.j = columns)
   const double* __restrict__ V = S[inst].v[svbase];
   double* __restrict__ W = S[inst].v[sw];
   double coef[PCB_MAX_RESTART + 1];
@@ -198,7 +201,9 @@ __device__ void scalar_step(Scal& c, int step, double v, double tol, int j, int 
       break;
     }
     case SS_GMRES_START: {
-      // v = ||r||^2 ; beta = ||r|| ; g = (beta, 0, ...)
+      // v = ||r||^2 ; beta = ||r|| ; g = (beta, 0, ...); a new cycle clears the previous flags
+      c.flags = 0;
+      c.itn = 0;
       c.beta = sqrt(v);
       for (int i = 0; i <= PCB_MAX_RESTART; ++i) c.g[i] = 0.0;
       c.g[0] = c.beta;
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(256) k_reduce(const int* __restrict__ off, int
   double acc = 0.0;
   for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) acc += partial[(long long)b * nper + which];
   const double s = block_sum(acc);
-  if (threadIdx.x == 0) scalar_step(Sc[inst], step, s, tols ? tols[inst] : tol, j, restart);
+  if (threadIdx.x == 0) scalar_step(Sc[inst], step, s, tols ? tols[inst] : tol, j < 0 ? Sc[inst].j : j, restart);
 }
 
 // multi-reduction for CGS: H[pass][i] = sum of partials i
@@ -273,6 +278,7 @@ __global__ void __launch_bounds__(256) k_reduce_multi(const int* __restrict__ of
   const int inst = blockIdx.x;
   if (inst >= count) return;
   if (active && !active[inst]) return;
+  if (j < 0) j = Sc[inst].j;
   const int b0 = off[inst], b1 = off[inst + 1];
   for (int i = 0; i <= j; ++i) {
     double acc = 0.0;
@@ -295,11 +301,15 @@ __global__ void k_swap(Slots* S, int count, const int* __restrict__ active, int 
   if (a2 >= 0) { t = S[inst].v[a2]; S[inst].v[a2] = S[inst].v[b2]; S[inst].v[b2] = t; }
 }
 
-// set slot `dst` = slot `base` + k * 2mn  (GMRES basis addressing)
-__global__ void k_setslot(const Geom* __restrict__ G, Slots* S, int count, int dst, int base, int k) {
+// set slot `dst` = slot `base` + k * 2mn  (GMRES basis addressing); per_j: k is an offset from
+// the instance's own Arnoldi index
+__global__ void k_setslot(const Geom* __restrict__ G, Slots* S, const Scal* __restrict__ Sc, int count,
+                          const int* __restrict__ active, int dst, int base, int k, int per_j) {
   const int inst = blockIdx.x * blockDim.x + threadIdx.x;
   if (inst >= count) return;
-  S[inst].v[dst] = S[inst].v[base] + (long long)k * 2 * G[inst].mn;
+  if (active && !active[inst]) return;
+  const int kk = per_j ? Sc[inst].j + k : k;
+  S[inst].v[dst] = S[inst].v[base] + (long long)kk * 2 * G[inst].mn;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -324,7 +334,7 @@ cudaError_t launch_minres_wx(const Batch& B, int sy, int sw, int sw2, int sx) {
   return cudaGetLastError();
 }
 cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw) {
-  k_multidot<<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.off_vec, B.count, B.active, svbase, j, sw, B.partial);
+  k_multidot<<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, B.partial);
   return cudaGetLastError();
 }
 cudaError_t launch_reduce_multi(const Batch& B, int j, int pass) {
@@ -339,8 +349,8 @@ cudaError_t launch_swap(const Batch& B, int a0, int b0, int a1, int b1, int a2, 
   k_swap<<<(B.count + 63) / 64, 64, 0, B.stream>>>(B.S, B.count, B.active, a0, b0, a1, b1, a2, b2);
   return cudaGetLastError();
 }
-cudaError_t launch_setslot(const Batch& B, int dst, int base, int k) {
-  k_setslot<<<(B.count + 63) / 64, 64, 0, B.stream>>>(B.G, B.S, B.count, dst, base, k);
+cudaError_t launch_setslot(const Batch& B, int dst, int base, int k, int per_j) {
+  k_setslot<<<(B.count + 63) / 64, 64, 0, B.stream>>>(B.G, B.S, B.Sc, B.count, B.active, dst, base, k, per_j);
   return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw);
 cudaError_t launch_reduce_multi(const Batch& B, int j, int pass);
 cudaError_t launch_multiaxpy(const Batch& B, int svbase, int j, int sw, int pass);
 cudaError_t launch_swap(const Batch& B, int a0, int b0, int a1, int b1, int a2, int b2);
-cudaError_t launch_setslot(const Batch& B, int dst, int base, int k);
+cudaError_t launch_setslot(const Batch& B, int dst, int base, int k, int per_j = 0);
 size_t mg_workspace_bytes(const Geom& g);
 bool mg_available();
 int dst_Q(int N);
@@ -1180,3 +1180,412 @@ extern "C" int pcb_batch_solve(pcb_problem* const* problems, int count, const pc
   }
   return worst;
 }
+
+// ---------------------------------------------------------------------------------------------
+// Continuous-batching server: fixed slot tables (one per method) whose empty slots contribute no
+// blocks to the shared launches; requests join and leave between steps.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+enum { PH_FREE = 0, PH_START, PH_ITER, PH_END, PH_DONE };
+
+struct SrvReq {
+  pcb_desc desc;
+  const double* rhs;
+  double* x;
+  long long tag;
+};
+
+struct SrvSlot {
+  int phase = PH_FREE;
+  pcb_problem* p = nullptr;
+  SrvReq req;
+  double* b = nullptr;   // device copies (the problem's host-io staging)
+  double* x = nullptr;
+  double bnorm = 0, rnorm = 0;
+  int iters = 0, sweeps = 0, status = PCB_OK;
+  bool first = true;
+  long long bytes = 0;
+};
+
+struct SrvGroup {
+  int method = PCB_MINRES, op = PCB_OP_A, kind = PCB_PREC_ABS_PS;
+  int cap = 0;
+  std::vector<SrvSlot> slots;
+  std::vector<Geom> hG;
+  std::vector<Slots> hS;
+  Geom* dG = nullptr; Slots* dS = nullptr; Scal* dSc = nullptr; int* dAct = nullptr; int* dOff = nullptr;
+  double* dPart = nullptr; double* dTol = nullptr;
+  Scal* hSc = nullptr; int* hAct = nullptr; double* hTol = nullptr; Slots* hSpin = nullptr;
+  Batch B;
+  bool dirty = true;
+};
+
+}  // namespace
+
+struct pcb_server {
+  pcb_server_opts o;
+  cudaStream_t st;
+  long long used = 0;
+  std::vector<SrvReq> queue;   // FIFO
+  size_t qhead = 0;
+  SrvGroup grp[2];             // 0: MINRES (theta = 1), 1: GMRES
+  std::vector<pcb_server_done> done;
+};
+
+namespace {
+
+long long srv_estimate(const pcb_desc* d, int method, int restart) {
+  const long long mn = (long long)d->N * d->N * d->n;
+  const long long vec = 16 * mn;                         // one 2mn FP64 vector
+  long long nv = 1 + 7 + 2 + 2;                          // scratch + MINRES + refinement + staging
+  if (method != PCB_MINRES) nv += 2 * restart + 2;
+  return nv * vec + (4 << 20);
+}
+
+int srv_upload(SrvGroup& G, cudaStream_t st) {
+  const int n = G.cap;
+  if (G.dirty) {
+    CK(cudaStreamSynchronize(st));
+    std::vector<int> staging;
+    int rc = fill_batch(G.B, G.hG, G.dOff, st, staging);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(G.dG, G.hG.data(), sizeof(Geom) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    G.B.G = G.dG; G.B.S = G.dS; G.B.Sc = G.dSc; G.B.active = G.dAct; G.B.partial = G.dPart; G.B.tols = G.dTol;
+    G.dirty = false;
+  }
+  CK(cudaStreamSynchronize(st));
+  std::memcpy(G.hSpin, G.hS.data(), sizeof(Slots) * n);
+  CK(cudaMemcpyAsync(G.dS, G.hSpin, sizeof(Slots) * n, cudaMemcpyHostToDevice, st));
+  return PCB_OK;
+}
+
+int srv_mask(SrvGroup& G, cudaStream_t st, int phase, bool extra_first = false) {
+  CK(cudaStreamSynchronize(st));
+  int any = 0;
+  for (int k = 0; k < G.cap; ++k) {
+    const SrvSlot& s = G.slots[k];
+    G.hAct[k] = s.phase == phase && (!extra_first || s.first);
+    any |= G.hAct[k];
+  }
+  CK(cudaMemcpyAsync(G.dAct, G.hAct, sizeof(int) * G.cap, cudaMemcpyHostToDevice, st));
+  return any ? 1 : 0;
+}
+
+int srv_read(SrvGroup& G, cudaStream_t st) {
+  CK(cudaMemcpyAsync(G.hSc, G.dSc, sizeof(Scal) * G.cap, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PCB_OK;
+}
+
+int srv_group_step(pcb_server* S, SrvGroup& G) {
+  cudaStream_t st = S->st;
+  const double tol = S->o.tol;
+  const int prec = S->o.precision, restart = S->o.restart;
+  int rc;
+  pcb_problem* p0 = nullptr;
+  for (auto& s : G.slots) if (s.p) { p0 = s.p; break; }
+  if (!p0) return PCB_OK;
+  if ((rc = srv_upload(G, st))) return rc;
+  // ---- round end: x += d, r = b - op x
+  if ((rc = srv_mask(G, st, PH_END)) < 0) return rc;
+  if (rc == 1) {
+    CK(launch_axpby(G.B, AX_ADD, SL_XI, SL_X, -1));
+    CK(launch_matvec(G.B, G.op, SL_X, SL_BI, SL_B, EPI_RESID));
+    CK(launch_reduce(G.B, G.B.off_mv, 1, 0, SS_NORM, tol, 0, 0));
+    if ((rc = srv_read(G, st))) return rc;
+    for (int k = 0; k < G.cap; ++k) {
+      SrvSlot& s = G.slots[k];
+      if (s.phase != PH_END) continue;
+      s.sweeps += 1;
+      s.rnorm = std::sqrt(G.hSc[k].dot1);
+      const double rel = s.bnorm > 0 ? s.rnorm / s.bnorm : 0.0;
+      if (!std::isfinite(rel)) { s.status = PCB_ERR_NONFINITE; s.phase = PH_DONE; }
+      else if (rel <= tol) s.phase = PH_DONE;
+      else if (s.sweeps >= 10 || s.iters >= S->o.maxit) { s.status = PCB_NOT_CONVERGED; s.phase = PH_DONE; }
+      else s.phase = PH_START;
+    }
+  }
+  // ---- round start
+  if ((rc = srv_mask(G, st, PH_START, true)) < 0) return rc;
+  if (rc == 1) {   // first round: ||b||
+    CK(launch_dot(G.B, SL_B, SL_B));
+    CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_BNORM, tol, 0, 0));
+    if ((rc = srv_read(G, st))) return rc;
+    for (int k = 0; k < G.cap; ++k) {
+      SrvSlot& s = G.slots[k];
+      if (s.phase != PH_START || !s.first) continue;
+      s.bnorm = G.hSc[k].bnorm; s.rnorm = s.bnorm; s.first = false;
+      if (!std::isfinite(s.bnorm)) { s.status = PCB_ERR_NONFINITE; s.phase = PH_DONE; }
+      else if (s.bnorm == 0.0) { s.rnorm = 0.0; s.phase = PH_DONE; }
+    }
+  }
+  if ((rc = srv_mask(G, st, PH_START)) < 0) return rc;
+  if (rc == 1) {
+    for (int k = 0; k < G.cap; ++k)
+      if (G.slots[k].phase == PH_START) G.hTol[k] = std::min(0.5, tol * G.slots[k].bnorm / G.slots[k].rnorm);
+    CK(cudaMemcpyAsync(G.dTol, G.hTol, sizeof(double) * G.cap, cudaMemcpyHostToDevice, st));
+    CK(launch_axpby(G.B, AX_ZERO, -1, SL_XI, -1));
+    if (G.method == PCB_MINRES) {
+      CK(launch_axpby(G.B, AX_ZERO, -1, SL_W, -1));
+      CK(launch_axpby(G.B, AX_ZERO, -1, SL_W2, -1));
+      CK(launch_axpby(G.B, AX_COPY, SL_BI, SL_R1, -1));
+      CK(launch_axpby(G.B, AX_COPY, SL_BI, SL_R2, -1));
+      if ((rc = apply_precond(p0, G.B, G.kind, prec, SL_R2, SL_Y))) return rc;
+      CK(launch_dot(G.B, SL_R2, SL_Y));
+      CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_MINRES_INIT, tol, 0, 0));
+    } else {
+      CK(launch_dot(G.B, SL_BI, SL_BI));
+      CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_BNORM, tol, 0, 0));
+      CK(launch_dot(G.B, SL_BI, SL_BI));
+      CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_GMRES_START, tol, 0, 0));
+      CK(launch_setslot(G.B, SL_VJ, SL_VBASE, 0, 0));
+      CK(launch_axpby(G.B, AX_SCALE_INV_BETA, SL_BI, SL_VJ, -1));
+    }
+    if ((rc = srv_read(G, st))) return rc;
+    for (int k = 0; k < G.cap; ++k) {
+      SrvSlot& s = G.slots[k];
+      if (s.phase != PH_START) continue;
+      const int f = G.hSc[k].flags;
+      if (f & 4) { s.status = PCB_ERR_NONFINITE; s.phase = PH_DONE; }
+      else if (G.method == PCB_MINRES && (f & 2)) { s.status = PCB_ERR_BREAKDOWN; s.phase = PH_DONE; }
+      else s.phase = PH_ITER;
+    }
+    // device-side slot pointers may have been set by setslot: refresh the host mirror from the rule
+    for (int k = 0; k < G.cap; ++k)
+      if (G.method != PCB_MINRES && G.slots[k].phase == PH_ITER && G.slots[k].p) G.hS[k].v[SL_VJ] = G.hS[k].v[SL_VBASE];
+    if ((rc = srv_upload(G, st))) return rc;
+  }
+  // ---- one iteration
+  if ((rc = srv_mask(G, st, PH_ITER)) < 0) return rc;
+  if (rc == 1) {
+    std::vector<int> ending(G.cap, 0);
+    bool any_end = false;
+    if (G.method == PCB_MINRES) {
+      CK(launch_matvec(G.B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
+      CK(launch_reduce(G.B, G.B.off_mv, 1, 0, SS_MINRES_ALFA, tol, 0, 0));
+      CK(launch_axpby(G.B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
+      if ((rc = apply_precond(p0, G.B, G.kind, prec, SL_R1, SL_YO))) return rc;
+      CK(launch_dot(G.B, SL_R1, SL_YO));
+      CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_MINRES_GIVENS, tol, 0, 0));
+      CK(launch_minres_wx(G.B, SL_Y, SL_W, SL_W2, SL_XI));
+      if ((rc = srv_read(G, st))) return rc;
+      for (int k = 0; k < G.cap; ++k) {
+        SrvSlot& s = G.slots[k];
+        if (s.phase != PH_ITER) continue;
+        Slots& H = G.hS[k];
+        std::swap(H.v[SL_R1], H.v[SL_R2]); std::swap(H.v[SL_Y], H.v[SL_YO]); std::swap(H.v[SL_W], H.v[SL_W2]);
+        s.iters += 1;
+        const int f = G.hSc[k].flags;
+        if (f & 4) { s.status = PCB_ERR_NONFINITE; s.phase = PH_DONE; }
+        else if (f & 2) { s.status = PCB_ERR_BREAKDOWN; s.phase = PH_DONE; }
+        else if ((f & 1) || s.iters >= S->o.maxit) s.phase = PH_END;
+      }
+    } else {
+      for (int k = 0; k < G.cap; ++k) {
+        if (G.slots[k].phase != PH_ITER) continue;
+        const int j = G.hSc[k].j;
+        const size_t nv = (size_t)2 * G.hG[k].mn;
+        Slots& H = G.hS[k];
+        H.v[SL_VJ] = H.v[SL_VBASE] + (size_t)j * nv;
+        H.v[SL_ZJ] = H.v[SL_ZBASE] + (size_t)j * nv;
+        H.v[SL_VJ1] = H.v[SL_VBASE] + (size_t)(j + 1) * nv;
+      }
+      if ((rc = srv_upload(G, st))) return rc;
+      if ((rc = apply_precond(p0, G.B, G.kind, prec, SL_VJ, SL_ZJ))) return rc;
+      CK(launch_matvec(G.B, G.op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
+      for (int pass = 0; pass < 2; ++pass) {
+        CK(launch_multidot(G.B, SL_VBASE, -1, SL_VJ1));
+        CK(launch_reduce_multi(G.B, -1, pass));
+        CK(launch_multiaxpy(G.B, SL_VBASE, -1, SL_VJ1, pass));
+      }
+      CK(launch_dot(G.B, SL_VJ1, SL_VJ1));
+      CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_GMRES_ARNOLDI, tol, -1, restart));
+      CK(launch_axpby(G.B, AX_SCALE_INV_HNORM, SL_VJ1, SL_VJ1, -1));
+      if ((rc = srv_read(G, st))) return rc;
+      for (int k = 0; k < G.cap; ++k) {
+        SrvSlot& s = G.slots[k];
+        if (s.phase != PH_ITER) continue;
+        s.iters += 1;
+        const int f = G.hSc[k].flags;
+        if (f & 4) { s.status = PCB_ERR_NONFINITE; s.phase = PH_DONE; continue; }
+        if ((f & 1) || (f & 8) || G.hSc[k].j >= restart || s.iters >= S->o.maxit) { ending[k] = 1; any_end = true; }
+      }
+      if (any_end) {   // d = Z y for the requests whose cycle ends here
+        CK(cudaStreamSynchronize(st));
+        for (int k = 0; k < G.cap; ++k) G.hAct[k] = ending[k];
+        CK(cudaMemcpyAsync(G.dAct, G.hAct, sizeof(int) * G.cap, cudaMemcpyHostToDevice, st));
+        CK(launch_multiaxpy(G.B, SL_ZBASE, -1, SL_XI, -1));
+        for (int k = 0; k < G.cap; ++k) if (ending[k]) G.slots[k].phase = PH_END;
+      }
+    }
+  }
+  return PCB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pcb_server_create(const pcb_server_opts* o, pcb_server** out) {
+  if (!o || !out || o->budget_bytes <= 0 || o->max_slots < 1 || o->max_slots > 256 ||
+      (o->precision != PCB_FP64 && o->precision != PCB_MIXED))
+    return PCB_ERR_INVALID_ARG;
+  pcb_server* S = new (std::nothrow) pcb_server();
+  if (!S) return PCB_ERR_OUT_OF_MEMORY;
+  S->o = *o;
+  if (S->o.tol <= 0) S->o.tol = 1e-8;
+  if (S->o.maxit <= 0) S->o.maxit = 500;
+  if (S->o.restart <= 0) S->o.restart = 16;
+  S->o.restart = std::min(S->o.restart, PCB_MAX_RESTART);
+  S->st = (cudaStream_t)o->stream;
+  for (int q = 0; q < 2; ++q) {
+    SrvGroup& G = S->grp[q];
+    G.method = q == 0 ? PCB_MINRES : PCB_GMRES;
+    G.op = q == 0 ? PCB_OP_A : PCB_OP_AHAT;
+    G.kind = q == 0 ? PCB_PREC_ABS_PS : PCB_PREC_PS;
+    const int n = G.cap = o->max_slots;
+    G.slots.assign(n, SrvSlot());
+    Geom empty;
+    std::memset(&empty, 0, sizeof(empty));
+    G.hG.assign(n, empty);
+    Slots es;
+    std::memset(&es, 0, sizeof(es));
+    G.hS.assign(n, es);
+    const size_t part = (size_t)n * 2432 * (PCB_MAX_RESTART + 1) + 1;
+    if (cudaMalloc(&G.dG, sizeof(Geom) * n) || cudaMalloc(&G.dS, sizeof(Slots) * n) ||
+        cudaMalloc(&G.dSc, sizeof(Scal) * n) || cudaMalloc(&G.dAct, sizeof(int) * n) ||
+        cudaMalloc(&G.dOff, sizeof(int) * 8 * (n + 1)) || cudaMalloc(&G.dPart, part * sizeof(double)) ||
+        cudaMalloc(&G.dTol, sizeof(double) * n) || cudaMallocHost(&G.hSc, sizeof(Scal) * n) ||
+        cudaMallocHost(&G.hAct, sizeof(int) * n) || cudaMallocHost(&G.hTol, sizeof(double) * n) ||
+        cudaMallocHost(&G.hSpin, sizeof(Slots) * n)) {
+      cudaGetLastError();
+      pcb_server_destroy(S);
+      return PCB_ERR_OUT_OF_MEMORY;
+    }
+    cudaMemset(G.dSc, 0, sizeof(Scal) * n);
+    std::memset(&G.B, 0, sizeof(Batch));
+  }
+  *out = S;
+  return PCB_OK;
+}
+
+void pcb_server_destroy(pcb_server* S) {
+  if (!S) return;
+  cudaStreamSynchronize(S->st);
+  for (int q = 0; q < 2; ++q) {
+    SrvGroup& G = S->grp[q];
+    for (auto& s : G.slots) if (s.p) pcb_destroy(s.p);
+    cudaFree(G.dG); cudaFree(G.dS); cudaFree(G.dSc); cudaFree(G.dAct); cudaFree(G.dOff); cudaFree(G.dPart);
+    cudaFree(G.dTol); cudaFreeHost(G.hSc); cudaFreeHost(G.hAct); cudaFreeHost(G.hTol); cudaFreeHost(G.hSpin);
+  }
+  delete S;
+}
+
+int pcb_server_submit(pcb_server* S, const pcb_desc* d, const double* rhs, double* x, long long tag) {
+  if (!S || !d || !rhs || !x) return PCB_ERR_INVALID_ARG;
+  if (d->a_edges) return PCB_ERR_UNSUPPORTED;
+  pcb_desc dd = *d;
+  dd.precision = S->o.precision;
+  dd.stream = (void*)S->st;
+  const int rc = validate_desc(&dd);
+  if (rc != PCB_OK) return rc;
+  const int method = dd.theta == 1.0 ? PCB_MINRES : PCB_GMRES;
+  if (srv_estimate(&dd, method, S->o.restart) > S->o.budget_bytes) return PCB_ERR_TOO_LARGE;
+  S->queue.push_back(SrvReq{dd, rhs, x, tag});
+  return PCB_OK;
+}
+
+int pcb_server_step(pcb_server* S, pcb_server_done* done, int max_done, int* n_done, int* n_active, int* n_queued) {
+  if (!S) return PCB_ERR_INVALID_ARG;
+  int rc = PCB_OK;
+  // retire
+  for (int q = 0; q < 2; ++q) {
+    SrvGroup& G = S->grp[q];
+    for (int k = 0; k < G.cap; ++k) {
+      SrvSlot& s = G.slots[k];
+      if (s.phase != PH_DONE) continue;
+      const size_t vb = (size_t)2 * s.p->g.mn * sizeof(double);
+      if (cudaMemcpyAsync(s.req.x, s.x, vb, cudaMemcpyDeviceToHost, S->st) != cudaSuccess ||
+          cudaStreamSynchronize(S->st) != cudaSuccess)
+        return PCB_ERR_CUDA;
+      pcb_server_done r;
+      r.tag = s.req.tag; r.status = s.status; r.iterations = s.iters; r.refinements = s.sweeps;
+      r.relres = s.bnorm > 0 ? s.rnorm / s.bnorm : 0.0;
+      S->done.push_back(r);
+      S->used -= s.bytes;
+      pcb_destroy(s.p);
+      s = SrvSlot();
+      std::memset(&G.hG[k], 0, sizeof(Geom));
+      std::memset(&G.hS[k], 0, sizeof(Slots));
+      G.dirty = true;
+    }
+  }
+  // admit (FIFO; a request waits for a slot of its method and room in the budget)
+  while (S->qhead < S->queue.size()) {
+    SrvReq& r = S->queue[S->qhead];
+    const int q = r.desc.theta == 1.0 ? 0 : 1;
+    SrvGroup& G = S->grp[q];
+    int free_k = -1;
+    for (int k = 0; k < G.cap; ++k) if (G.slots[k].phase == PH_FREE) { free_k = k; break; }
+    const long long est = srv_estimate(&r.desc, G.method, S->o.restart);
+    if (free_k < 0 || S->used + est > S->o.budget_bytes) break;
+    pcb_problem* p = nullptr;
+    if ((rc = pcb_create(&r.desc, &p)) != PCB_OK) return rc;
+    SolveCfg c;
+    pcb_solve_opts so;
+    std::memset(&so, 0, sizeof(so));
+    so.restart = S->o.restart;
+    resolve_defaults(p, &so, c);
+    if ((rc = ensure_minres(p)) || (rc = ensure_mixed(p)) || (G.method != PCB_MINRES && (rc = ensure_gmres(p, S->o.restart)))) {
+      pcb_destroy(p);
+      return rc;
+    }
+    const size_t nv = (size_t)2 * p->g.mn;
+    if (!p->host_io) {
+      if (cudaMalloc(&p->host_io, 2 * nv * sizeof(double)) != cudaSuccess) { cudaGetLastError(); pcb_destroy(p); return PCB_ERR_OUT_OF_MEMORY; }
+      p->bytes += 2 * nv * sizeof(double);
+    }
+    SrvSlot& s = G.slots[free_k];
+    s = SrvSlot();
+    s.p = p; s.req = r; s.b = p->host_io; s.x = p->host_io + nv; s.phase = PH_START; s.first = true;
+    s.bytes = p->bytes;
+    S->used += s.bytes;
+    if (cudaMemcpyAsync(s.b, r.rhs, nv * sizeof(double), cudaMemcpyHostToDevice, S->st) != cudaSuccess ||
+        cudaMemsetAsync(s.x, 0, nv * sizeof(double), S->st) != cudaSuccess ||
+        cudaMemcpyAsync(p->vec_mixed, s.b, nv * sizeof(double), cudaMemcpyDeviceToDevice, S->st) != cudaSuccess)
+      return PCB_ERR_CUDA;
+    double* v = p->vec_minres;
+    Slots& H = G.hS[free_k];
+    std::memset(&H, 0, sizeof(H));
+    H.v[SL_R1] = v; H.v[SL_R2] = v + nv; H.v[SL_Y] = v + 2 * nv; H.v[SL_YO] = v + 3 * nv; H.v[SL_Q] = v + 4 * nv;
+    H.v[SL_W] = v + 5 * nv; H.v[SL_W2] = v + 6 * nv; H.v[SL_R] = v;
+    H.v[SL_BI] = p->vec_mixed; H.v[SL_XI] = p->vec_mixed + nv;
+    if (G.method != PCB_MINRES) { H.v[SL_VBASE] = p->vec_gmres; H.v[SL_ZBASE] = p->vec_gmres + (size_t)(S->o.restart + 1) * nv; }
+    H.v[SL_X] = s.x; H.v[SL_B] = s.b;
+    G.hG[free_k] = p->g;
+    G.dirty = true;
+    S->qhead += 1;
+  }
+  if (S->qhead > 4096 && S->qhead * 2 > S->queue.size()) {
+    S->queue.erase(S->queue.begin(), S->queue.begin() + S->qhead);
+    S->qhead = 0;
+  }
+  // advance every admitted request
+  for (int q = 0; q < 2 && rc == PCB_OK; ++q) rc = srv_group_step(S, S->grp[q]);
+  if (rc != PCB_OK) return rc;
+  int nd = 0;
+  while (nd < max_done && !S->done.empty()) {
+    done[nd++] = S->done.front();
+    S->done.erase(S->done.begin());
+  }
+  int act = 0;
+  for (int q = 0; q < 2; ++q) for (auto& s : S->grp[q].slots) act += s.phase != PH_FREE;
+  if (n_done) *n_done = nd;
+  if (n_active) *n_active = act;
+  if (n_queued) *n_queued = (int)(S->queue.size() - S->qhead);
+  return PCB_OK;
+}
+
+}  // extern "C"
