@@ -133,6 +133,8 @@ typedef struct {
   int fixed_iterations;   /* > 0: run exactly this many iterations (comparison runs)           */
   int profile;            /* != 0: time every preconditioner apply and matvec with CUDA events  */
                           /* recorded on the problem's stream (fills the *_ms fields of info)   */
+  double inner_floor;     /* mixed precision: an inner solve stops once its residual estimate is */
+                          /* below max(tol*||b||/||r||, inner_floor); <= 0 => no floor          */
 } pcb_solve_opts;
 
 typedef struct {

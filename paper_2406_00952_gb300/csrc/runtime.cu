@@ -499,6 +499,7 @@ static int ensure_gmres(pcb_problem* p, int restart) {
 struct SolveCfg {
   int op, prec, kind, method, maxit, restart, fixed;
   double tol;
+  double inner_floor;   // mixed precision: smallest inner tolerance
   bool check_true;      // FP64 route: keep iterating if the true residual check fails
 };
 
@@ -706,6 +707,7 @@ static void resolve_defaults(const pcb_problem* p, const pcb_solve_opts* o, Solv
   c.restart = (o && o->restart > 0) ? std::min(o->restart, PCB_MAX_RESTART) : 30;
   c.fixed = o ? o->fixed_iterations : 0;
   c.prec = p->desc.precision;
+  c.inner_floor = (o && o->inner_floor > 0) ? o->inner_floor : 0.0;
   const bool va = p->g.var_a != 0;
   if (c.method == PCB_METHOD_AUTO) {
     if (p->g.theta == 1.0) c.method = PCB_MINRES;
@@ -779,7 +781,7 @@ static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_d
     while (!conv && sweeps < max_ref && iters < c.maxit) {
       SolveCfg ci = c;
       ci.check_true = false;
-      ci.tol = std::min(0.5, c.tol * bnorm / rnorm);
+      ci.tol = std::min(0.5, std::max(c.tol * bnorm / rnorm, c.inner_floor));
       ci.maxit = c.maxit - iters;
       double rel_in; int it_in; bool cv_in;
       rc = run(ci, SL_BI, SL_XI, &rel_in, &it_in, &cv_in);
@@ -986,7 +988,7 @@ int round_start(BGroup& G, const SolveCfg& c) {
   for (int k = 0; k < n; ++k) {
     if (G.done[k]) continue;
     mask[k] = 1; any = 1;
-    G.hTol[k] = std::min(0.5, c.tol * G.bnorm[k] / G.rnorm[k]);
+    G.hTol[k] = std::min(0.5, std::max(c.tol * G.bnorm[k] / G.rnorm[k], c.inner_floor));
   }
   G.round_member = mask; G.in_round = mask; G.round_open = any; G.it_round = 0; G.j = 0;
   if (!any) return PCB_OK;
@@ -1324,7 +1326,8 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
   if ((rc = srv_mask(G, st, PH_START)) < 0) return rc;
   if (rc == 1) {
     for (int k = 0; k < G.cap; ++k)
-      if (G.slots[k].phase == PH_START) G.hTol[k] = std::min(0.5, tol * G.slots[k].bnorm / G.slots[k].rnorm);
+      if (G.slots[k].phase == PH_START)
+        G.hTol[k] = std::min(0.5, tol * G.slots[k].bnorm / G.slots[k].rnorm);
     CK(cudaMemcpyAsync(G.dTol, G.hTol, sizeof(double) * G.cap, cudaMemcpyHostToDevice, st));
     CK(launch_axpby(G.B, AX_ZERO, -1, SL_XI, -1));
     if (G.method == PCB_MINRES) {
