@@ -118,6 +118,17 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ off, int count,
   return lo;
 }
 
+// Instance selection of a preconditioner launch: instances with active[k] == 0 are skipped, and
+// when fam is set, so are instances whose kernel family fam[k] differs from want.
+struct Sel {
+  const int* active;
+  const int* fam;
+  int want;
+  __device__ __forceinline__ bool skip(int k) const {
+    return (active && !__ldg(active + k)) || (fam && __ldg(fam + k) != want);
+  }
+};
+
 // ------------------------------------------------------------------------------------------
 // host-side launch helpers (defined in runtime.cu)
 // ------------------------------------------------------------------------------------------
@@ -137,6 +148,17 @@ struct Batch {
   double* partial;        // reduction partials
   const double* tols;     // per-instance tolerances for the scalar steps (device) or null
   int dst_q, time_q;      // register-FFT variant shared by every instance of the batch
+  // FP32 kernel families: pipe_pd / pipe_pt > 0 is the lanes-per-line P of the pipelined DST /
+  // time kernels (precond_pipe.cu) shared by every instance with work, 0 means the kernels of
+  // precond.cu for all, -1 a mix: one launch per family present, each selecting its instances by
+  // fam_dst / fam_time (device arrays [count]: P, or 0).  fam_*_set: bit log2(P) (bit 0 for 0).
+  int pipe_pd, pipe_pt;
+  const int* fam_dst;
+  const int* fam_time;
+  int fam_dst_set, fam_time_set;
+  const int* filt;        // family filter of the launch being issued (null: none)
+  int filt_want;
+  Sel sel() const { Sel s; s.active = active; s.fam = filt; s.want = filt_want; return s; }
   size_t dst_smem[2], time_smem[2];   // dynamic shared memory per block, per precision
 };
 

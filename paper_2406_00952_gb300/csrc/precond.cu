@@ -253,10 +253,10 @@ __device__ __forceinline__ void dst_body(const Geom& g, const Slots* __restrict_
 template <typename TIn, typename TOut, typename R, int Q>
 __global__ void __launch_bounds__(256, 2) k_dst(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                              const int* __restrict__ off, int count,
-                                             const int* __restrict__ active, int axis, int in_slot,
+                                             Sel sel, int axis, int in_slot,
                                              int out_slot) {
   const int inst = find_inst(off, count, blockIdx.x);
-  if (active && !active[inst]) return;
+  if (sel.skip(inst)) return;
   dst_body<TIn, TOut, R, Q>(G[inst], S, inst, blockIdx.x - off[inst], axis, in_slot, out_slot);
 }
 
@@ -265,10 +265,10 @@ __global__ void __launch_bounds__(256, 2) k_dst(const Geom* __restrict__ G, cons
 template <typename TIn, typename TOut, typename R>
 __global__ void __launch_bounds__(256, 2) k_dst_any(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                                  const int* __restrict__ off, int count,
-                                                 const int* __restrict__ active, int axis, int in_slot,
+                                                 Sel sel, int axis, int in_slot,
                                                  int out_slot) {
   const int inst = find_inst(off, count, blockIdx.x);
-  if (active && !active[inst]) return;
+  if (sel.skip(inst)) return;
   const Geom& g = G[inst];
   const int lb = blockIdx.x - off[inst];
   switch (g.dst_q) {
@@ -424,17 +424,17 @@ __device__ __forceinline__ void time_body(const Geom& g, int lb, int kind) {
 
 template <typename R, int Q>
 __global__ void __launch_bounds__(256, 2) k_time(const Geom* __restrict__ G, const int* __restrict__ off, int count,
-                                              const int* __restrict__ active, int kind) {
+                                              Sel sel, int kind) {
   const int inst = find_inst(off, count, blockIdx.x);
-  if (active && !active[inst]) return;
+  if (sel.skip(inst)) return;
   time_body<R, Q>(G[inst], blockIdx.x - off[inst], kind);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(256, 2) k_time_any(const Geom* __restrict__ G, const int* __restrict__ off,
-                                                  int count, const int* __restrict__ active, int kind) {
+                                                  int count, Sel sel, int kind) {
   const int inst = find_inst(off, count, blockIdx.x);
-  if (active && !active[inst]) return;
+  if (sel.skip(inst)) return;
   const Geom& g = G[inst];
   const int lb = blockIdx.x - off[inst];
   switch (g.time_q) {
@@ -471,7 +471,11 @@ size_t time_smem_bytes(const Geom& g, int p) {
   return (size_t)g.time_cpb[p] * padded_len(g.n) * (p ? sizeof(float2) : sizeof(double2));
 }
 
-cudaError_t upload_constants() { return upload_w96(); }
+cudaError_t pipe_upload_constants();
+cudaError_t upload_constants() {
+  const cudaError_t e = upload_w96();
+  return e != cudaSuccess ? e : pipe_upload_constants();
+}
 
 template <typename R, int Q>
 static void launch_dst_q(const Batch& B, int axis, int in_slot, int out_slot, size_t smem) {
@@ -486,11 +490,11 @@ static void launch_dst_q(const Batch& B, int axis, int in_slot, int out_slot, si
   const int* off = axis == 0 ? B.off_dst_i[p] : B.off_dst_j[p];
   const int tot = axis == 0 ? B.tot_dst_i[p] : B.tot_dst_j[p];
   if (in_slot >= 0)
-    k_dst<double, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, in_slot, -1);
+    k_dst<double, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, in_slot, -1);
   else if (out_slot >= 0)
-    k_dst<R, double, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, -1, out_slot);
+    k_dst<R, double, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, out_slot);
   else
-    k_dst<R, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, -1, -1);
+    k_dst<R, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, -1);
 }
 
 template <typename R, int Q>
@@ -501,7 +505,7 @@ static void launch_time_q(const Batch& B, int kind, size_t smem) {
     cudaFuncSetAttribute(k_time<R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     done = true;
   }
-  k_time<R, Q><<<B.tot_time[p], 256, smem, B.stream>>>(B.G, B.off_time[p], B.count, B.active, kind);
+  k_time<R, Q><<<B.tot_time[p], 256, smem, B.stream>>>(B.G, B.off_time[p], B.count, B.sel(), kind);
 }
 
 template <typename R>
@@ -519,11 +523,11 @@ static cudaError_t dispatch_dst(const Batch& B, int axis, int in_slot, int out_s
     const int* off = axis == 0 ? B.off_dst_i[p] : B.off_dst_j[p];
     const int tot = axis == 0 ? B.tot_dst_i[p] : B.tot_dst_j[p];
     if (in_slot >= 0)
-      k_dst_any<double, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, in_slot, -1);
+      k_dst_any<double, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, in_slot, -1);
     else if (out_slot >= 0)
-      k_dst_any<R, double, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, -1, out_slot);
+      k_dst_any<R, double, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, out_slot);
     else
-      k_dst_any<R, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.active, axis, -1, -1);
+      k_dst_any<R, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, -1);
     return cudaGetLastError();
   }
   switch (B.dst_q) {
@@ -552,7 +556,7 @@ static cudaError_t dispatch_time(const Batch& B, int kind) {
       cudaFuncSetAttribute(k_time_any<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       done = true;
     }
-    k_time_any<R><<<B.tot_time[p], 256, smem, B.stream>>>(B.G, B.off_time[p], B.count, B.active, kind);
+    k_time_any<R><<<B.tot_time[p], 256, smem, B.stream>>>(B.G, B.off_time[p], B.count, B.sel(), kind);
     return cudaGetLastError();
   }
   switch (B.time_q) {
@@ -567,14 +571,50 @@ static cudaError_t dispatch_time(const Batch& B, int kind) {
   return cudaGetLastError();
 }
 
+cudaError_t pipe_dst_pass(const Batch& B, int axis, int in_slot, int out_slot);
+cudaError_t pipe_time_pass(const Batch& B, int kind);
+
+// FP32 passes take the pipelined kernels (precond_pipe.cu) for the instances whose line shapes
+// they cover; a batch that mixes kernel families runs one launch per family present.
+template <typename R>
+static cudaError_t dst_pass(const Batch& B, int axis, int in_slot, int out_slot) {
+  if (sizeof(R) == 8 || B.pipe_pd == 0) return dispatch_dst<R>(B, axis, in_slot, out_slot);
+  if (B.pipe_pd > 0) return pipe_dst_pass(B, axis, in_slot, out_slot);
+  Batch F = B;
+  F.filt = B.fam_dst;
+  for (int b = 0; b <= 5; ++b) {
+    if (!(B.fam_dst_set >> b & 1)) continue;
+    F.filt_want = b ? 1 << b : 0;
+    F.pipe_pd = F.filt_want;
+    const cudaError_t e = b ? pipe_dst_pass(F, axis, in_slot, out_slot) : dispatch_dst<R>(F, axis, in_slot, out_slot);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+template <typename R>
+static cudaError_t time_pass(const Batch& B, int kind) {
+  if (sizeof(R) == 8 || B.pipe_pt == 0) return dispatch_time<R>(B, kind);
+  if (B.pipe_pt > 0) return pipe_time_pass(B, kind);
+  Batch F = B;
+  F.filt = B.fam_time;
+  for (int b = 0; b <= 5; ++b) {
+    if (!(B.fam_time_set >> b & 1)) continue;
+    F.filt_want = b ? 1 << b : 0;
+    F.pipe_pt = F.filt_want;
+    const cudaError_t e = b ? pipe_time_pass(F, kind) : dispatch_time<R>(F, kind);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <typename R>
 static cudaError_t precond_passes(const Batch& B, int kind, int in_slot, int out_slot) {
   cudaError_t e;
-  if ((e = dispatch_dst<R>(B, 0, in_slot, -1)) != cudaSuccess) return e;
-  if ((e = dispatch_dst<R>(B, 1, -1, -1)) != cudaSuccess) return e;
-  if ((e = dispatch_time<R>(B, kind)) != cudaSuccess) return e;
-  if ((e = dispatch_dst<R>(B, 1, -1, -1)) != cudaSuccess) return e;
-  return dispatch_dst<R>(B, 0, -1, out_slot);
+  if ((e = dst_pass<R>(B, 0, in_slot, -1)) != cudaSuccess) return e;
+  if ((e = dst_pass<R>(B, 1, -1, -1)) != cudaSuccess) return e;
+  if ((e = time_pass<R>(B, kind)) != cudaSuccess) return e;
+  if ((e = dst_pass<R>(B, 1, -1, -1)) != cudaSuccess) return e;
+  return dst_pass<R>(B, 0, -1, out_slot);
 }
 
 int precond_launch_count(bool var_a, int kind) { return var_a ? mg_launch_count(kind) : 5; }

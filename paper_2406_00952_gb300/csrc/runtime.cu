@@ -43,6 +43,8 @@ bool q_supported(int Q);
 size_t dst_smem_bytes(const Geom& g, int p);
 size_t time_smem_bytes(const Geom& g, int p);
 int padded_len_host(int len);
+int pipe_dst_p(const Geom& g);
+int pipe_time_p(const Geom& g);
 cudaError_t upload_constants();
 struct TableLayout { size_t kap, mud, muf, twdd, twdf, twtd, twtf, pred, pref, ax, ay, dg, bytes; };
 cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host);
@@ -138,6 +140,7 @@ int round_down(int v, int q) { return std::max(q, (v / q) * q); }
 int pow2_floor(int v) { int p = 1; while (p * 2 <= v) p *= 2; return p; }
 
 void set_shapes(Geom& g) {
+  const int pd = pipe_dst_p(g), pt = pipe_time_p(g);   // pipelined FP32 passes: 256/P lines a tile
   const int lsd = padded_len_host(g.L), lst = padded_len_host(g.n);
   const int Pd = 2 * g.L / g.dst_q, Pt = g.n / g.time_q;
   const int lpwd = 32 / Pd, lpwt = 32 / Pt;
@@ -146,13 +149,16 @@ void set_shapes(Geom& g) {
     // powers of two (the kernels split thread indices with shifts) that are multiples of lpw
     // Q = 32 lines use one warp each plus a per-warp transpose scratch: 8 lines per block
     int lpb = g.dst_q == 32 ? 8 : std::max(lpwd, pow2_floor(std::min(256, std::max(1, budget[p] / lsd))));
+    if (p == 1 && pd) lpb = 256 / pd;
     g.dst_lpb[p] = lpb;
     int lpbj = std::max(lpwd, std::min(lpb, pow2_floor(std::max(1, g.N))));
+    if (p == 1 && pd) lpbj = 256 / pd;
     g.dst_lpb_j[p] = lpbj;
     g.dst_blocks_i[p] = (int)(((long long)g.n * g.N + lpb - 1) / lpb);
     g.dst_blocks_j[p] = g.n * ((g.N + lpbj - 1) / lpbj);
     int cpb = pow2_floor(std::min(256, std::max(1, budget[p] / lst)));
     cpb = std::max(lpwt, std::min(cpb, pow2_floor(std::max(1, g.m))));
+    if (p == 1 && pt) cpb = 256 / pt;
     g.time_cpb[p] = cpb;
     g.time_blocks[p] = (g.m + cpb - 1) / cpb;
   }
@@ -224,6 +230,24 @@ int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStream_t st
     if (g.dst_q != B.dst_q) B.dst_q = 0;
     if (g.time_q != B.time_q) B.time_q = 0;
   }
+  // FP32 kernel families (pipelined P or 0) of the instances with work (empty server slots have none)
+  const size_t fam_at = staging.size();
+  B.fam_dst_set = B.fam_time_set = 0;
+  for (const Geom& g : gs) staging.push_back(pipe_dst_p(g));
+  for (const Geom& g : gs) staging.push_back(pipe_time_p(g));
+  for (const Geom& g : gs) {
+    const int pd = pipe_dst_p(g), pt = pipe_time_p(g);
+    if (g.dst_blocks_i[1] > 0) B.fam_dst_set |= 1 << (pd ? __builtin_ctz(pd) : 0);
+    if (g.time_blocks[1] > 0) B.fam_time_set |= 1 << (pt ? __builtin_ctz(pt) : 0);
+  }
+  auto uniform = [](int set) { return __builtin_popcount(set) == 1 ? (set == 1 ? 0 : set) : (set ? -1 : 0); };
+  B.pipe_pd = uniform(B.fam_dst_set);
+  B.pipe_pt = uniform(B.fam_time_set);
+  B.fam_dst = doff + fam_at;
+  B.fam_time = doff + fam_at + count;
+  B.filt = nullptr;
+  B.filt_want = 0;
+  CK(cudaMemcpyAsync(doff + fam_at, staging.data() + fam_at, 2 * count * sizeof(int), cudaMemcpyHostToDevice, st));
   return PCB_OK;
 }
 }  // namespace pcb
@@ -437,7 +461,7 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
   }
   // ---- single-instance batch ----
   if (cudaMalloc(&p->dG, sizeof(Geom)) != cudaSuccess || cudaMalloc(&p->dS, sizeof(Slots)) != cudaSuccess ||
-      cudaMalloc(&p->dSc, sizeof(Scal)) != cudaSuccess || cudaMalloc(&p->doff, 8 * 2 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&p->dSc, sizeof(Scal)) != cudaSuccess || cudaMalloc(&p->doff, 10 * 2 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&p->partial, (size_t)g.vec_blocks * (PCB_MAX_RESTART + 2) * sizeof(double) +
                                   (size_t)std::max(g.mv_blocks, 1) * sizeof(double)) != cudaSuccess)
     return fail(PCB_ERR_OUT_OF_MEMORY);
@@ -947,7 +971,7 @@ int group_setup(BGroup& G, const SolveCfg& c, const double* const* b_dev, double
   part = std::max((size_t)tv * (PCB_MAX_RESTART + 1), (size_t)tm) + 1;
   if (cudaMalloc(&G.dG, sizeof(Geom) * n) || cudaMalloc(&G.dS, sizeof(Slots) * n) ||
       cudaMalloc(&G.dSc, sizeof(Scal) * n) || cudaMalloc(&G.dAct, sizeof(int) * n) ||
-      cudaMalloc(&G.dOff, sizeof(int) * 8 * (n + 1)) || cudaMalloc(&G.dPart, part * sizeof(double)) ||
+      cudaMalloc(&G.dOff, sizeof(int) * 10 * (n + 1)) || cudaMalloc(&G.dPart, part * sizeof(double)) ||
       cudaMalloc(&G.dTol, sizeof(double) * n) || cudaMallocHost(&G.hSc, sizeof(Scal) * n) ||
       cudaMallocHost(&G.hAct, sizeof(int) * n) || cudaMallocHost(&G.hTol, sizeof(double) * n)) {
     cudaGetLastError();
@@ -1459,7 +1483,7 @@ int pcb_server_create(const pcb_server_opts* o, pcb_server** out) {
     const size_t part = (size_t)n * 2432 * (PCB_MAX_RESTART + 1) + 1;
     if (cudaMalloc(&G.dG, sizeof(Geom) * n) || cudaMalloc(&G.dS, sizeof(Slots) * n) ||
         cudaMalloc(&G.dSc, sizeof(Scal) * n) || cudaMalloc(&G.dAct, sizeof(int) * n) ||
-        cudaMalloc(&G.dOff, sizeof(int) * 8 * (n + 1)) || cudaMalloc(&G.dPart, part * sizeof(double)) ||
+        cudaMalloc(&G.dOff, sizeof(int) * 10 * (n + 1)) || cudaMalloc(&G.dPart, part * sizeof(double)) ||
         cudaMalloc(&G.dTol, sizeof(double) * n) || cudaMallocHost(&G.hSc, sizeof(Scal) * n) ||
         cudaMallocHost(&G.hAct, sizeof(int) * n) || cudaMallocHost(&G.hTol, sizeof(double) * n) ||
         cudaMallocHost(&G.hSpin, sizeof(Slots) * n)) {
