@@ -137,36 +137,142 @@ __device__ __forceinline__ int table_inst(const int* __restrict__ off, int count
   return 0;
 }
 
-template <typename TIn> struct CxOf;
-template <> struct CxOf<float> { using T = float2; };
-template <> struct CxOf<double> { using T = double2; };
+// forward transform of an odd line (z_{M-s} = -z_s): as fwd2, but the exchange keeps only the
+// columns t <= P/2.  For t = P - t' (1 <= t' < P/2) the stage-1 outputs are redundant:
+//     V[P-t'][k1] = -W_P^{-t'} V[t'][32-k1]  (k1 != 0),   V[P-t'][0] = -V[t'][0],
+// with V[t][k1] = W_M^{t k1} sum_q z_{t+Pq} W_32^{q k1}, so readers rebuild them from the stored
+// half (shared memory per group: 32 rows x (P/2 + 1) columns).  wP[k] = W_P^k.
+template <int P>
+__device__ __forceinline__ void fwd_odd(float2* x, int t, float2* __restrict__ scr, const float2* __restrict__ tw2,
+                                        const float2* __restrict__ wP) {
+  constexpr int CW = P / 2 + 1;
+  reg_dft<float2, float, 32>(x, false);
+  if (t <= P / 2) {
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) {
+      float2 v = x[pos<32>(k1)];
+      if (k1) v = cmul(v, tw2[k1 * P + t]);
+      scr[k1 * CW + t] = v;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int a = 0; a < 32 / P; ++a) {
+    const int k1 = t + P * a;
+    const int k1m = (32 - k1) & 31;
+    const bool z0 = k1 == 0;
+#pragma unroll
+    for (int tt = 0; tt < P; ++tt) {
+      if (tt <= P / 2) {
+        x[a * P + tt] = scr[k1 * CW + tt];
+      } else {
+        const float2 sv = scr[k1m * CW + (P - tt)];
+        const float2 w = wP[tt];
+        float2 mlt;
+        mlt.x = z0 ? -1.f : -w.x;
+        mlt.y = z0 ? 0.f : -w.y;
+        x[a * P + tt] = cmul(sv, mlt);
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int a = 0; a < 32 / P; ++a) reg_dft<float2, float, P>(x + a * P, false);
+}
 
-__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
-__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <int P>
+__host__ __device__ constexpr int odd_scratch_per_warp() { return (32 / P) * 32 * (P / 2 + 1); }
+
+// DST-I tables: tw2 (M entries, see fwd2) and wP[k] = W_P^k = W_M^{32 k}
+template <int P>
+__device__ __forceinline__ void fill_dst_tables(float2* tw2, float2* wP, const float2* __restrict__ w) {
+  fill_twiddles<P>(tw2, nullptr, w);
+  for (int k = threadIdx.x; k < P; k += blockDim.x) wP[k] = __ldg(&w[32 * k]);
+}
 
 // ------------------------------------------------------------------------------------------
-// DST-I pass.  AXIS 0: lines along x1 (contiguous); AXIS 1: lines along x2 (stride N).
+// DST-I along x1 (contiguous lines of N = 16 P - 1 values).  Warps work independently: each
+// loads its line straight into registers (lane t needs x_{s-1}, s = t + P q: consecutive lanes,
+// consecutive addresses), transforms it and stores the result from registers (lane u holds
+// S_p, p = u + P j: again consecutive).  Tiles of LPB = 256 / P lines give the block offsets.
 // in_slot / out_slot >= 0: FP64 vector slot; -1: the FP32 scratch.
-// A tile is LPB = 256 / P lines; line length L - 1 = 16 P - 1 = N.
 // ------------------------------------------------------------------------------------------
-template <typename TIn, typename TOut, int P, int AXIS, int NS>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_dst_pipe(const Geom* __restrict__ G, const Slots* __restrict__ S, const int* __restrict__ off, int count,
+template <typename TIn, typename TOut, int P>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_dst_rows(const Geom* __restrict__ G, const Slots* __restrict__ S, const int* __restrict__ off, int count,
                Sel sel, int in_slot, int out_slot, int tot) {
+  constexpr int M = 32 * P, L = 16 * P, N = L - 1, LPB = kThreads / P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw2 = (float2*)smem_raw;
+  float2* wP = tw2 + M;
+  float2* scr_all = wP + P;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  fill_dst_tables<P>(tw2, wP, G[table_inst(off, count, sel)].twd_f);
+  __syncthreads();
+  float2* scr = scr_all + warp * odd_scratch_per_warp<P>() + (lane / P) * 32 * (P / 2 + 1);
+  const int t = lane % P;
+  const float sc = __frsqrt_rn((float)(2 * L));     // DST-I normalisation 0.5 sqrt(2/L)
+  const long long nvt = (long long)tot * kWarps;
+  for (long long vt = (long long)blockIdx.x * kWarps + warp; vt < nvt; vt += (long long)gridDim.x * kWarps) {
+    const int tile = (int)(vt / kWarps), w = (int)(vt % kWarps);
+    const int inst = find_inst(off, count, tile);
+    if (sel.skip(inst)) continue;
+    const Geom& g = G[inst];
+    const long long mn = g.mn;
+    const long long line = (long long)(tile - off[inst]) * LPB + w * (32 / P) + lane / P;
+    const bool lv = line < (long long)g.n * N;
+    const TIn* __restrict__ in = (in_slot >= 0 ? (const TIn*)S[inst].v[in_slot] : (const TIn*)g.scratch) +
+                                 (lv ? line : 0) * N;
+    // gather the odd extension: z_s = x_{s-1} (1 <= s <= N), -x_{M-s-1} (L < s < M), 0 else
+    float2 x[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int s = t + P * q;
+      const bool ok = lv && (q < 16 ? s > 0 : s > L);
+      const int idx = q < 16 ? s - 1 : M - s - 1;
+      float2 v = make_float2(0.f, 0.f);
+      if (ok) {
+        v.x = (float)in[idx];
+        v.y = (float)in[mn + idx];
+      }
+      if (q >= 16) { v.x = -v.x; v.y = -v.y; }
+      x[q] = v;
+    }
+    fwd_odd<P>(x, t, scr, tw2, wP);
+    if (lv) {
+      TOut* __restrict__ d = (out_slot >= 0 ? (TOut*)S[inst].v[out_slot] : (TOut*)g.scratch) + line * N;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int p = t + P * j;
+        const float2 Y = x[Two<P>::outreg(j)];
+        if (p >= 1) {
+          d[p - 1] = (TOut)(-Y.y * sc);
+          d[mn + p - 1] = (TOut)(Y.x * sc);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// DST-I along x2 (lines of stride N), FP32 scratch in place.  Tiles of LPB = 256 / P
+// consecutive x1 positions are staged through NS shared-memory stages with cp.async.
+// ------------------------------------------------------------------------------------------
+template <int P, int NS>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_dst_cols(const Geom* __restrict__ G, const int* __restrict__ off, int count, Sel sel, int tot) {
   constexpr int M = 32 * P, L = 16 * P, N = L - 1, LPB = kThreads / P;
   constexpr int PITCH = pitch_for<P>(N);
   constexpr int m = N * N;
-  constexpr int NBT = (N + LPB - 1) / LPB;       // x2-line tiles per time step
-  using CI = typename CxOf<TIn>::T;
+  constexpr int NBT = (N + LPB - 1) / LPB;       // tiles per time step
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw2 = (float2*)smem_raw;
-  float2* scr_all = tw2 + M;
-  CI* stages = (CI*)(scr_all + kWarps * kScrWarp);
+  float2* wP = tw2 + M;
+  float2* scr_all = wP + P;
+  float2* stages = scr_all + kWarps * odd_scratch_per_warp<P>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  fill_dst_tables<P>(tw2, wP, G[table_inst(off, count, sel)].twd_f);
 
-  fill_twiddles<P>(tw2, nullptr, G[table_inst(off, count, sel)].twd_f);
-
-  // issue the asynchronous loads of tile `tile` into stage `st`
   auto issue = [&](int tile, int st) {
     if (tile >= tot) return;
     const int inst = find_inst(off, count, tile);
@@ -174,30 +280,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const Geom& g = G[inst];
     const int lt = tile - off[inst];
     const long long mn = g.mn;
-    const TIn* in = in_slot >= 0 ? (const TIn*)S[inst].v[in_slot] : (const TIn*)g.scratch;
-    CI* buf = stages + (size_t)st * LPB * PITCH;
-    if (AXIS == 0) {
-      const long long nlines = (long long)g.n * N;
-      for (int l = warp; l < LPB; l += kWarps) {
-        const long long line = (long long)lt * LPB + l;
-        const bool lv = line < nlines;
-        const TIn* src = in + (lv ? line : 0) * N;
-        CI* d = buf + l * PITCH;
-        for (int q = lane; q < N; q += 32) {
-          cp_async<sizeof(TIn)>(&d[q].x, src + q, lv);
-          cp_async<sizeof(TIn)>(&d[q].y, src + mn + q, lv);
-        }
-      }
-    } else {
-      const int t0 = lt / NBT, i0 = (lt - t0 * NBT) * LPB;
-      const int l = tid % LPB;
-      const bool iv = i0 + l < N;
-      const TIn* src = in + (long long)t0 * m + (iv ? i0 + l : 0);
-      CI* d = buf + l * PITCH;
-      for (int q = tid / LPB; q < N; q += kThreads / LPB) {
-        cp_async<sizeof(TIn)>(&d[q].x, src + (long long)q * N, iv);
-        cp_async<sizeof(TIn)>(&d[q].y, src + mn + (long long)q * N, iv);
-      }
+    const int t0 = lt / NBT, i0 = (lt - t0 * NBT) * LPB;
+    const int l = tid % LPB;
+    const bool iv = i0 + l < N;
+    const float* src = (const float*)g.scratch + (long long)t0 * m + (iv ? i0 + l : 0);
+    float2* d = stages + (size_t)st * LPB * PITCH + l * PITCH;
+    for (int q = tid / LPB; q < N; q += kThreads / LPB) {
+      cp_async<4>(&d[q].x, src + q * N, iv);
+      cp_async<4>(&d[q].y, src + mn + q * N, iv);
     }
   };
 
@@ -206,8 +296,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     issue(blockIdx.x + s * gridDim.x, s);
     cp_commit();
   }
-  const float sc = __frsqrt_rn((float)(2 * L));     // DST-I normalisation 0.5 sqrt(2/L)
-  float2* scr = scr_all + warp * kScrWarp + (lane / P) * (32 * P + P);
+  const float sc = __frsqrt_rn((float)(2 * L));
+  float2* scr = scr_all + warp * odd_scratch_per_warp<P>() + (lane / P) * 32 * (P / 2 + 1);
   const int t = lane % P;
   const int lw = warp * (32 / P) + lane / P;      // this lane group's line within the tile
 
@@ -220,87 +310,75 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool on = !sel.skip(inst);
     const Geom& g = G[inst];
     const int lt = tile - off[inst];
-    const long long mn = g.mn;
-    CI* buf = stages + (size_t)st * LPB * PITCH;
-    bool lv;
-    long long line = 0;
-    int t0 = 0, i0 = 0;
-    if (AXIS == 0) {
-      line = (long long)lt * LPB + lw;
-      lv = on && line < (long long)g.n * N;
-    } else {
-      t0 = lt / NBT;
-      i0 = (lt - t0 * NBT) * LPB;
-      lv = on && i0 + lw < N;
-    }
+    const int t0 = lt / NBT, i0 = (lt - t0 * NBT) * LPB;
+    float2* buf = stages + (size_t)st * LPB * PITCH;
     if (on) {
-      // gather the odd extension: z_s = x_{s-1} (1 <= s <= N), -x_{M-s-1} (L < s < M), 0 else
-      const CI* ln = buf + lw * PITCH;
+      float2* ln = buf + lw * PITCH;
       float2 x[32];
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int s = t + P * q;
         float2 v;
         if (q < 16) {
-          v = to_f2(ln[s > 0 ? s - 1 : 0]);
+          v = ln[s > 0 ? s - 1 : 0];
           if (s == 0) v = make_float2(0.f, 0.f);
         } else {
-          v = to_f2(ln[s > L ? M - s - 1 : 0]);
+          v = ln[s > L ? M - s - 1 : 0];
           v.x = -v.x; v.y = -v.y;
           if (s == L) v = make_float2(0.f, 0.f);
         }
         x[q] = v;
       }
-      fwd2<P>(x, t, scr, tw2);
-      // outputs p = t + P j, 1 <= p <= N (j < 16): S_p = (i/2) sqrt(2/L) Y_p
-      if (AXIS == 0) {
-        if (lv) {
-          TOut* out = out_slot >= 0 ? (TOut*)S[inst].v[out_slot] : (TOut*)g.scratch;
-          TOut* d = out + line * N;
+      fwd_odd<P>(x, t, scr, tw2, wP);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int p = t + P * j;
-            const float2 Y = x[Two<P>::outreg(j)];
-            if (p >= 1) {
-              d[p - 1] = (TOut)(-Y.y * sc);
-              d[mn + p - 1] = (TOut)(Y.x * sc);
-            }
-          }
-        }
-      } else {
-        CI* lnw = buf + lw * PITCH;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int p = t + P * j;
-          const float2 Y = x[Two<P>::outreg(j)];
-          if (p >= 1) {
-            CI v;
-            v.x = -Y.y * sc;
-            v.y = Y.x * sc;
-            lnw[p - 1] = v;
-          }
+      for (int j = 0; j < 16; ++j) {
+        const int p = t + P * j;
+        const float2 Y = x[Two<P>::outreg(j)];
+        if (p >= 1) ln[p - 1] = make_float2(-Y.y * sc, Y.x * sc);
+      }
+    }
+    __syncthreads();
+    if (on) {
+      const long long mn = g.mn;
+      const int l = tid % LPB;
+      if (i0 + l < N) {
+        float* d = (float*)g.scratch + (long long)t0 * m + i0 + l;
+        const float2* srcl = buf + l * PITCH;
+        for (int q = tid / LPB; q < N; q += kThreads / LPB) {
+          const float2 v = srcl[q];
+          d[q * N] = v.x;
+          d[mn + q * N] = v.y;
         }
       }
     }
     __syncthreads();
-    if (AXIS == 1 && on) {
-      TOut* out = out_slot >= 0 ? (TOut*)S[inst].v[out_slot] : (TOut*)g.scratch;
-      const int l = tid % LPB;
-      if (i0 + l < N) {
-        TOut* d = out + (long long)t0 * m + i0 + l;
-        const CI* srcl = buf + l * PITCH;
-        for (int q = tid / LPB; q < N; q += kThreads / LPB) {
-          const CI v = srcl[q];
-          d[(long long)q * N] = (TOut)v.x;
-          d[mn + (long long)q * N] = (TOut)v.y;
-        }
-      }
-      __syncthreads();
-    }
     issue(tile + NS * gridDim.x, st);
     cp_commit();
   }
   cp_wait<0>();
+}
+
+// Pointwise solve at one F-slot r (Sec. 3.5): Cr = coefficient at r, Cq = conj(coefficient at n-1-r),
+// mr = lambda(S_n) at r, c = tau (kappa_i + kappa_j).  kind 1: |P_S|^-1 weight, 2: 2x2 solve of
+// P_S, 3: P_MS^-1 weight.
+__device__ __forceinline__ float2 pointwise(int kind, float2 Cr, float2 Cq, float2 mr, float c, float a2, float alpha) {
+  if (kind == PK_PS) {
+    const float2 lam = make_float2(mr.x + c, mr.y);
+    const float2 F1 = cscale(cadd(Cr, Cq), 0.5f);
+    const float2 F2 = cmul_mi(cscale(csub(Cr, Cq), 0.5f));
+    const float inv = 1.0f / (lam.x * lam.x + lam.y * lam.y + a2);
+    const float2 U1 = cscale(cadd(cmul(cconj(lam), F1), cscale(F2, alpha)), inv);
+    const float2 U2 = cscale(csub(cmul(lam, F2), cscale(F1, alpha)), inv);
+    return cadd(U1, cmul_pi(U2));
+  }
+  float w;
+  if (kind == PK_ABS_PS) {
+    const float lx = mr.x + c;
+    w = rsqrtf(lx * lx + mr.y * mr.y + a2);
+  } else {
+    w = 1.0f / (sqrtf(mr.x * mr.x + mr.y * mr.y + a2) + c);
+  }
+  return cscale(Cr, w);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -377,40 +455,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int jb = 31 - j;
-          float2 va = x[Two<P>::outreg(j)], vb = x[Two<P>::outreg(jb)];
+          const float2 va = x[Two<P>::outreg(j)], vb = x[Two<P>::outreg(jb)];
           float2 ra, rb;                       // partner's X at n-1-r for r = t+Pj and t+P jb
           ra.x = __shfl_xor_sync(0xffffffffu, vb.x, P - 1);
           ra.y = __shfl_xor_sync(0xffffffffu, vb.y, P - 1);
           rb.x = __shfl_xor_sync(0xffffffffu, va.x, P - 1);
           rb.y = __shfl_xor_sync(0xffffffffu, va.y, P - 1);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int jx = h ? jb : j;
-            const float2 Cr = h ? vb : va;
-            const float2 Cq = cconj(h ? rb : ra);
-            const float2 mr = __ldg(&mu[t + P * jx]);
-            const float2 lam = make_float2(mr.x + c, mr.y);
-            const float2 F1 = cscale(cadd(Cr, Cq), 0.5f);
-            const float2 F2 = cmul_mi(cscale(csub(Cr, Cq), 0.5f));
-            const float inv = 1.0f / (lam.x * lam.x + lam.y * lam.y + a2);
-            const float2 U1 = cscale(cadd(cmul(cconj(lam), F1), cscale(F2, alpha)), inv);
-            const float2 U2 = cscale(csub(cmul(lam, F2), cscale(F1, alpha)), inv);
-            x[Two<P>::outreg(jx)] = cadd(U1, cmul_pi(U2));
-          }
+          x[Two<P>::outreg(j)] = pointwise(PK_PS, va, cconj(ra), __ldg(&mu[t + P * j]), c, a2, alpha);
+          x[Two<P>::outreg(jb)] = pointwise(PK_PS, vb, cconj(rb), __ldg(&mu[t + P * jb]), c, a2, alpha);
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float2 mr = __ldg(&mu[t + P * j]);
-          float w;
-          if (kind == PK_ABS_PS) {
-            const float lx = mr.x + c;
-            w = rsqrtf(lx * lx + mr.y * mr.y + a2);
-          } else {
-            w = 1.0f / (sqrtf(mr.x * mr.x + mr.y * mr.y + a2) + c);
-          }
-          x[Two<P>::outreg(j)] = cscale(x[Two<P>::outreg(j)], w);
-        }
+        for (int j = 0; j < 32; ++j)
+          x[Two<P>::outreg(j)] = pointwise(kind, x[Two<P>::outreg(j)], x[Two<P>::outreg(j)], __ldg(&mu[t + P * j]), c,
+                                           a2, alpha);
       }
       inv2<P>(x, t, scr, tw3);
 #pragma unroll
@@ -438,20 +496,192 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------------------------------------
+// Time pass for n = 512 with one line per warp: lane t holds x[t + 32 q] (16 values).
+//   forward: 16-point register DFT over q, twiddle W_512^{t k1}, exchange through the line's own
+//   tile row (row k1, column t XOR k1), then lane (k1, h) = (u mod 16, u / 16) runs a 16-point
+//   DFT over t'' of V[2t''+h][k1] and one radix-2 step across lanes u, u^16:
+//       X[k1 + 16 k2 + 256 h] = G_0[k2] + (-1)^h W_32^{k2} G_1[k2].
+//   The partner slot n-1-r of r = k1 + 16 k2 + 256 h is lane u^31, register 15-k2.
+// Tiles of 8 columns, NS cp.async stages; two blocks per SM.
+// ------------------------------------------------------------------------------------------
+template <int NS>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_time512(const Geom* __restrict__ G, const int* __restrict__ off, int count, Sel sel, int kind, int tot) {
+  constexpr int n = 512, LPB = kWarps;
+  constexpr int PITCH = pitch_for<32>(n);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw1 = (float2*)smem_raw;        // [k1 * 32 + t] = W_512^{t k1}, k1 < 16
+  float2* tw32 = tw1 + n;                  // [h * 16 + k] = W_32^{h k}
+  float2* pre = tw32 + 32;                 // exp(-i pi t / n)
+  float2* mus = pre + n;                   // lambda(S_n) of the current instance
+  float2* stages = mus + n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    const Geom& g0 = G[table_inst(off, count, sel)];
+    const float2* __restrict__ w = g0.twt_f;
+    for (int k = tid; k < n; k += kThreads) {
+      tw1[k] = __ldg(&w[(k % 32) * (k / 32)]);
+      pre[k] = __ldg(&g0.pre_f[k]);
+    }
+    if (tid < 32) tw32[tid] = __ldg(&w[16 * (tid / 16) * (tid % 16)]);
+  }
+
+  auto issue = [&](int tile, int st) {
+    if (tile >= tot) return;
+    const int inst = find_inst(off, count, tile);
+    if (sel.skip(inst)) return;
+    const Geom& g = G[inst];
+    const int c0 = (tile - off[inst]) * LPB;
+    const int l = tid % LPB;
+    const bool cv = c0 + l < g.m;
+    const float* y = (const float*)g.scratch + (cv ? c0 + l : 0);
+    const long long m = g.m, mn = g.mn;
+    float2* d = stages + (size_t)st * LPB * PITCH + l * PITCH;
+    for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
+      cp_async<4>(&d[tt].x, y + tt * m, cv);
+      cp_async<4>(&d[tt].y, y + mn + tt * m, cv);
+    }
+  };
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    issue(blockIdx.x + s * gridDim.x, s);
+    cp_commit();
+  }
+  const int t = lane, k1 = lane & 15, h = lane >> 4;
+  const float sg = h ? -1.f : 1.f;
+  const float scale = 1.0f / (float)n;
+  int mu_inst = -1;
+
+  int it = 0;
+  for (int tile = blockIdx.x; tile < tot; tile += gridDim.x, ++it) {
+    const int st = it % NS;
+    cp_wait<NS - 1>();
+    __syncthreads();
+    const int inst = find_inst(off, count, tile);
+    const bool on = !sel.skip(inst);
+    const Geom& g = G[inst];
+    const int c0 = (tile - off[inst]) * LPB;
+    if (on && inst != mu_inst) {       // block-uniform
+      for (int k = tid; k < n; k += kThreads) mus[k] = __ldg(&g.mu_f[k]);
+      mu_inst = inst;
+      __syncthreads();
+    }
+    float2* buf = stages + (size_t)st * LPB * PITCH;
+    if (on) {
+      float2* ln = buf + warp * PITCH;
+      float2 x[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) x[q] = cmul(ln[t + 32 * q], pre[t + 32 * q]);
+      reg_dft<float2, float, 16>(x, false);
+      __syncwarp();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        float2 v = x[pos<16>(kk)];
+        if (kk) v = cmul(v, tw1[kk * 32 + t]);
+        ln[kk * 32 + (t ^ kk)] = v;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t2 = 0; t2 < 16; ++t2) x[t2] = ln[k1 * 32 + ((2 * t2 + h) ^ k1)];
+      reg_dft<float2, float, 16>(x, false);
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        float2 v = x[pos<16>(k2)];
+        if (k2) v = cmul(v, tw32[h * 16 + k2]);
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v.x, 16);
+        o.y = __shfl_xor_sync(0xffffffffu, v.y, 16);
+        x[pos<16>(k2)] = make_float2(fmaf(sg, v.x, o.x), fmaf(sg, v.y, o.y));
+      }
+      // pointwise solve at r = k1 + 16 k2 + 256 h
+      const int col = min(c0 + warp, g.m - 1);
+      const int jj = col / g.N, ii = col - jj * g.N;
+      const float c = (float)(g.tau * (__ldg(&g.kap[ii]) + __ldg(&g.kap[jj])));
+      const float a2 = (float)(g.alpha * g.alpha), alpha = (float)g.alpha;
+      if (kind == PK_PS) {
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) {
+          const int kb = 15 - k2;
+          const float2 va = x[pos<16>(k2)], vb = x[pos<16>(kb)];
+          float2 ra, rb;                    // the partner's coefficients at n-1-r
+          ra.x = __shfl_xor_sync(0xffffffffu, vb.x, 31);
+          ra.y = __shfl_xor_sync(0xffffffffu, vb.y, 31);
+          rb.x = __shfl_xor_sync(0xffffffffu, va.x, 31);
+          rb.y = __shfl_xor_sync(0xffffffffu, va.y, 31);
+          x[pos<16>(k2)] = pointwise(PK_PS, va, cconj(ra), mus[k1 + 16 * k2 + 256 * h], c, a2, alpha);
+          x[pos<16>(kb)] = pointwise(PK_PS, vb, cconj(rb), mus[k1 + 16 * kb + 256 * h], c, a2, alpha);
+        }
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2)
+          x[pos<16>(k2)] = pointwise(kind, x[pos<16>(k2)], x[pos<16>(k2)], mus[k1 + 16 * k2 + 256 * h], c, a2, alpha);
+      }
+      // inverse: undo the radix-2 step, W_32 twiddle, 16-point DFT over k2, exchange back,
+      // W_512 twiddle, 16-point DFT over k1, unscale
+      float2 z[16];
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const float2 v = x[pos<16>(k2)];
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v.x, 16);
+        o.y = __shfl_xor_sync(0xffffffffu, v.y, 16);
+        float2 a = make_float2(fmaf(sg, v.x, o.x), fmaf(sg, v.y, o.y));
+        if (k2) a = cmulc(a, tw32[h * 16 + k2]);
+        z[k2] = a;
+      }
+      reg_dft<float2, float, 16>(z, true);
+#pragma unroll
+      for (int t2 = 0; t2 < 16; ++t2) ln[k1 * 32 + ((2 * t2 + h) ^ k1)] = z[pos<16>(t2)];
+      __syncwarp();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        float2 v = ln[kk * 32 + (t ^ kk)];
+        if (kk) v = cmulc(v, tw1[kk * 32 + t]);
+        x[kk] = v;
+      }
+      reg_dft<float2, float, 16>(x, true);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) ln[t + 32 * q] = cscale(cmulc(x[pos<16>(q)], pre[t + 32 * q]), scale);
+    }
+    __syncthreads();
+    if (on) {
+      const int l = tid % LPB;
+      if (c0 + l < g.m) {
+        float* y = (float*)g.scratch + c0 + l;
+        const long long m = g.m, mn = g.mn;
+        const float2* srcl = buf + l * PITCH;
+        for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
+          const float2 v = srcl[tt];
+          y[tt * m] = v.x;
+          y[mn + tt * m] = v.y;
+        }
+      }
+    }
+    __syncthreads();
+    issue(tile + NS * gridDim.x, st);
+    cp_commit();
+  }
+  cp_wait<0>();
+}
+
+// ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
-constexpr int kNsDst = 3, kNsDstD = 2, kNsTime = 2;
+constexpr int kNsCols = 2, kNsTime = 2;
 
 template <int P>
-size_t dst_smem(int in_bytes, int ns) {
-  return (size_t)(32 * P + kWarps * kScrWarp) * sizeof(float2) +
-         (size_t)ns * (kThreads / P) * pitch_for<P>(16 * P - 1) * 2 * in_bytes;
+size_t dst_rows_smem() { return (size_t)(32 * P + P + kWarps * odd_scratch_per_warp<P>()) * sizeof(float2); }
+template <int P>
+size_t dst_cols_smem() {
+  return dst_rows_smem<P>() + (size_t)kNsCols * (kThreads / P) * pitch_for<P>(16 * P - 1) * sizeof(float2);
 }
 template <int P>
-size_t time_smem(int ns) {
+size_t time_smem() {
   return (size_t)(3 * 32 * P + kWarps * kScrWarp) * sizeof(float2) +
-         (size_t)ns * (kThreads / P) * pitch_for<P>(32 * P) * sizeof(float2);
+         (size_t)kNsTime * (kThreads / P) * pitch_for<P>(32 * P) * sizeof(float2);
 }
+size_t time512_smem() { return (size_t)(3 * 512 + 32 + kNsTime * kWarps * pitch_for<32>(512)) * sizeof(float2); }
 
 int sm_count() {
   static int n = 0;
@@ -464,57 +694,55 @@ int sm_count() {
   return n;
 }
 
-// blocks per SM of a persistent kernel (queried once per kernel)
-template <typename K>
-int resident_blocks(K kernel, size_t smem, int& cache) {
-  if (!cache) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem);
-    cache = std::max(1, occ) * sm_count();
-  }
-  return cache;
-}
-
-template <typename TIn, typename TOut, int P, int AXIS>
-cudaError_t launch_dst(const Batch& B, int in_slot, int out_slot) {
-  constexpr int NS = sizeof(TIn) == 8 ? kNsDstD : kNsDst;
-  auto kern = k_dst_pipe<TIn, TOut, P, AXIS, NS>;
-  const size_t smem = dst_smem<P>(sizeof(TIn), NS);
-  static int resident = 0;
-  const int* off = AXIS == 0 ? B.off_dst_i[1] : B.off_dst_j[1];
-  const int tot = AXIS == 0 ? B.tot_dst_i[1] : B.tot_dst_j[1];
+// Launch a persistent kernel: at most as many blocks as fit on the device at once (queried once
+// per kernel; `resident` caches the figure).
+template <typename K, typename... Args>
+cudaError_t launch_persistent(K kern, size_t smem, int tot, int& resident, cudaStream_t st, Args... args) {
   if (tot <= 0) return cudaSuccess;
   if (!resident) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    resident = std::max(1, occ) * sm_count();
   }
-  const int grid = std::min(tot, resident_blocks(kern, smem, resident));
-  kern<<<grid, kThreads, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), in_slot, out_slot, tot);
+  kern<<<std::min(tot, resident), kThreads, smem, st>>>(args...);
   return cudaGetLastError();
+}
+
+template <typename TIn, typename TOut, int P>
+cudaError_t launch_rows(const Batch& B, int in_slot, int out_slot) {
+  static int resident = 0;
+  return launch_persistent(k_dst_rows<TIn, TOut, P>, dst_rows_smem<P>(), B.tot_dst_i[1], resident, B.stream, B.G,
+                           (const Slots*)B.S, B.off_dst_i[1], B.count, B.sel(), in_slot, out_slot, B.tot_dst_i[1]);
+}
+
+template <int P>
+cudaError_t launch_cols(const Batch& B) {
+  static int resident = 0;
+  return launch_persistent(k_dst_cols<P, kNsCols>, dst_cols_smem<P>(), B.tot_dst_j[1], resident, B.stream, B.G,
+                           B.off_dst_j[1], B.count, B.sel(), B.tot_dst_j[1]);
 }
 
 template <int P>
 cudaError_t launch_time(const Batch& B, int kind) {
-  auto kern = k_time_pipe<P, kNsTime>;
-  const size_t smem = time_smem<P>(kNsTime);
   static int resident = 0;
-  const int tot = B.tot_time[1];
-  if (tot <= 0) return cudaSuccess;
-  if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  if (P == 16) {
+    static int resident512 = 0;
+    return launch_persistent(k_time512<kNsTime>, time512_smem(), B.tot_time[1], resident512, B.stream, B.G,
+                             B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
   }
-  const int grid = std::min(tot, resident_blocks(kern, smem, resident));
-  kern<<<grid, kThreads, smem, B.stream>>>(B.G, B.off_time[1], B.count, B.sel(), kind, tot);
-  return cudaGetLastError();
+  return launch_persistent(k_time_pipe<P, kNsTime>, time_smem<P>(), B.tot_time[1], resident, B.stream, B.G,
+                           B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
 }
 
 template <int P>
 cudaError_t dst_pass_p(const Batch& B, int axis, int in_slot, int out_slot) {
-  if (axis == 0 && in_slot >= 0) return launch_dst<double, float, P, 0>(B, in_slot, -1);
-  if (axis == 0 && out_slot >= 0) return launch_dst<float, double, P, 0>(B, -1, out_slot);
-  if (axis == 0) return launch_dst<float, float, P, 0>(B, -1, -1);
-  return launch_dst<float, float, P, 1>(B, -1, -1);
+  if (axis == 1) return launch_cols<P>(B);
+  if (in_slot >= 0) return launch_rows<double, float, P>(B, in_slot, -1);
+  if (out_slot >= 0) return launch_rows<float, double, P>(B, -1, out_slot);
+  return launch_rows<float, float, P>(B, -1, -1);
 }
 
 }  // namespace
@@ -533,6 +761,10 @@ int pipe_time_p(const Geom& g) {
   const int P = g.n / 32;
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
+// spatial columns per tile of the pipelined time pass (n = 512: one line per warp)
+int pipe_time_cols(int n) { return n == 512 ? kWarps : kThreads / (n / 32); }
+// lines per tile of the pipelined DST passes
+int pipe_dst_lines(int L) { return kThreads / (2 * L / 32); }
 
 cudaError_t pipe_upload_constants() { return upload_w96(); }
 

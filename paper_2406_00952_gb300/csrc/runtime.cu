@@ -45,6 +45,8 @@ size_t time_smem_bytes(const Geom& g, int p);
 int padded_len_host(int len);
 int pipe_dst_p(const Geom& g);
 int pipe_time_p(const Geom& g);
+int pipe_time_cols(int n);
+int pipe_dst_lines(int L);
 cudaError_t upload_constants();
 struct TableLayout { size_t kap, mud, muf, twdd, twdf, twtd, twtf, pred, pref, ax, ay, dg, bytes; };
 cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host);
@@ -149,16 +151,16 @@ void set_shapes(Geom& g) {
     // powers of two (the kernels split thread indices with shifts) that are multiples of lpw
     // Q = 32 lines use one warp each plus a per-warp transpose scratch: 8 lines per block
     int lpb = g.dst_q == 32 ? 8 : std::max(lpwd, pow2_floor(std::min(256, std::max(1, budget[p] / lsd))));
-    if (p == 1 && pd) lpb = 256 / pd;
+    if (p == 1 && pd) lpb = pipe_dst_lines(g.L);
     g.dst_lpb[p] = lpb;
     int lpbj = std::max(lpwd, std::min(lpb, pow2_floor(std::max(1, g.N))));
-    if (p == 1 && pd) lpbj = 256 / pd;
+    if (p == 1 && pd) lpbj = pipe_dst_lines(g.L);
     g.dst_lpb_j[p] = lpbj;
     g.dst_blocks_i[p] = (int)(((long long)g.n * g.N + lpb - 1) / lpb);
     g.dst_blocks_j[p] = g.n * ((g.N + lpbj - 1) / lpbj);
     int cpb = pow2_floor(std::min(256, std::max(1, budget[p] / lst)));
     cpb = std::max(lpwt, std::min(cpb, pow2_floor(std::max(1, g.m))));
-    if (p == 1 && pt) cpb = 256 / pt;
+    if (p == 1 && pt) cpb = pipe_time_cols(g.n);
     g.time_cpb[p] = cpb;
     g.time_blocks[p] = (g.m + cpb - 1) / cpb;
   }
