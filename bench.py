@@ -129,7 +129,7 @@ def profile_traffic():
             if line.startswith("traffic_bytes_per_apply:"):
                 traffic = float(line.split(":", 1)[1].strip())
         h = hashlib.sha256()
-        for f in ("fft_reg.cuh", "precond.cu", "pcb_internal.cuh"):
+        for f in ("fft_reg.cuh", "precond.cu", "precond_pipe.cu", "pcb_internal.cuh"):
             h.update(open(os.path.join(ROOT, "paper_2406_00952_gb300", "csrc", f), "rb").read())
         return traffic if (want == h.hexdigest() and traffic) else None
     except Exception:
