@@ -29,7 +29,6 @@ cudaError_t upload_constants();
 size_t dst_smem_bytes(const Geom& g, int p);
 size_t time_smem_bytes(const Geom& g, int p);
 cudaError_t launch_precond_fast(const Batch& B, int kind, int prec, int in_slot, int out_slot);
-int pipe_dst_p(const Geom& g);
 int pipe_time_p(const Geom& g);
 }  // namespace pcb
 
@@ -118,7 +117,7 @@ extern "C" int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int pre
   }
   B.dst_q = g.dst_q;
   B.time_q = g.time_q;
-  B.pipe_pd = pipe_dst_p(g);
+  B.pipe_pd = 0;               // the pipelined DST passes need two FP32 scratch buffers; the arena has one
   B.pipe_pt = pipe_time_p(g);
   // (copies from pageable host memory return once the source has been staged, so the host buffers
   // above may be reused as soon as cudaMemcpyAsync returns)

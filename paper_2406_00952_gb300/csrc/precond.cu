@@ -571,22 +571,25 @@ static cudaError_t dispatch_time(const Batch& B, int kind) {
   return cudaGetLastError();
 }
 
-cudaError_t pipe_dst_pass(const Batch& B, int axis, int in_slot, int out_slot);
+cudaError_t pipe_dst_pass(const Batch& B, int stage, int in_slot, int out_slot);
 cudaError_t pipe_time_pass(const Batch& B, int kind);
 
 // FP32 passes take the pipelined kernels (precond_pipe.cu) for the instances whose line shapes
-// they cover; a batch that mixes kernel families runs one launch per family present.
+// they cover; a batch that mixes kernel families runs one launch per family present.  `stage` is
+// the pass number (1, 2, 4 or 5); the kernels of this file run passes 1 and 5 along x1 and
+// passes 2 and 4 along x2.
 template <typename R>
-static cudaError_t dst_pass(const Batch& B, int axis, int in_slot, int out_slot) {
+static cudaError_t dst_pass(const Batch& B, int stage, int in_slot, int out_slot) {
+  const int axis = (stage == 1 || stage == 5) ? 0 : 1;
   if (sizeof(R) == 8 || B.pipe_pd == 0) return dispatch_dst<R>(B, axis, in_slot, out_slot);
-  if (B.pipe_pd > 0) return pipe_dst_pass(B, axis, in_slot, out_slot);
+  if (B.pipe_pd > 0) return pipe_dst_pass(B, stage, in_slot, out_slot);
   Batch F = B;
   F.filt = B.fam_dst;
   for (int b = 0; b <= 5; ++b) {
     if (!(B.fam_dst_set >> b & 1)) continue;
     F.filt_want = b ? 1 << b : 0;
     F.pipe_pd = F.filt_want;
-    const cudaError_t e = b ? pipe_dst_pass(F, axis, in_slot, out_slot) : dispatch_dst<R>(F, axis, in_slot, out_slot);
+    const cudaError_t e = b ? pipe_dst_pass(F, stage, in_slot, out_slot) : dispatch_dst<R>(F, axis, in_slot, out_slot);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -610,11 +613,11 @@ static cudaError_t time_pass(const Batch& B, int kind) {
 template <typename R>
 static cudaError_t precond_passes(const Batch& B, int kind, int in_slot, int out_slot) {
   cudaError_t e;
-  if ((e = dst_pass<R>(B, 0, in_slot, -1)) != cudaSuccess) return e;
-  if ((e = dst_pass<R>(B, 1, -1, -1)) != cudaSuccess) return e;
+  if ((e = dst_pass<R>(B, 1, in_slot, -1)) != cudaSuccess) return e;
+  if ((e = dst_pass<R>(B, 2, -1, -1)) != cudaSuccess) return e;
   if ((e = time_pass<R>(B, kind)) != cudaSuccess) return e;
-  if ((e = dst_pass<R>(B, 1, -1, -1)) != cudaSuccess) return e;
-  return dst_pass<R>(B, 0, -1, out_slot);
+  if ((e = dst_pass<R>(B, 4, -1, -1)) != cudaSuccess) return e;
+  return dst_pass<R>(B, 5, -1, out_slot);
 }
 
 int precond_launch_count(bool var_a, int kind) { return var_a ? mg_launch_count(kind) : 5; }

@@ -191,169 +191,268 @@ __device__ __forceinline__ void fill_dst_tables(float2* tw2, float2* wP, const f
 }
 
 // ------------------------------------------------------------------------------------------
-// DST-I along x1 (contiguous lines of N = 16 P - 1 values).  Warps work independently: each
-// loads its line straight into registers (lane t needs x_{s-1}, s = t + P q: consecutive lanes,
-// consecutive addresses), transforms it and stores the result from registers (lane u holds
-// S_p, p = u + P j: again consecutive).  Tiles of LPB = 256 / P lines give the block offsets.
-// in_slot / out_slot >= 0: FP64 vector slot; -1: the FP32 scratch.
+// DST-I along x1 (contiguous lines of N = 16 P - 1 values).  Warps work independently, one line
+// at a time: the line's two halves are fetched with 16-byte cp.async copies into the warp's
+// shared-memory slot (the 16-byte aligned span that covers the line), gathered into registers,
+// and the copy of the warp's next line is issued before the line is transformed.  The result is
+// stored straight from registers (lane u holds S_p, p = u + P j: consecutive lanes, consecutive
+// addresses).  Tiles of LPB = 256 / P lines give the block offsets.
+// in_sel / out_sel >= 0: FP64 vector slot; -1 / -2: FP32 scratch buffer 0 / 1.
 // ------------------------------------------------------------------------------------------
+// vector of a pass: slot sel >= 0 of the instance (FP64), or FP32 scratch buffer -1 - sel (the
+// FP64-sized scratch holds two FP32 buffers of 2mn values)
+__device__ __forceinline__ void* buffer_of(const Geom& g, const Slots& s, int sel) {
+  return sel >= 0 ? (void*)s.v[sel] : (void*)((float*)g.scratch + (sel == -1 ? 0 : 2 * g.mn));
+}
+
+template <typename TIn>
+__host__ __device__ constexpr int row_slot_elems(int N) {   // per half: N values + both alignment tails
+  return ((N + 32 / (int)sizeof(TIn) + 16 / (int)sizeof(TIn) - 1) / (16 / (int)sizeof(TIn))) * (16 / (int)sizeof(TIn));
+}
+
 template <typename TIn, typename TOut, int P>
 __global__ void __launch_bounds__(kThreads, 2)
     k_dst_rows(const Geom* __restrict__ G, const Slots* __restrict__ S, const int* __restrict__ off, int count,
-               Sel sel, int in_slot, int out_slot, int tot) {
+               Sel sel, int in_sel, int out_sel, int tot) {
   constexpr int M = 32 * P, L = 16 * P, N = L - 1, LPB = kThreads / P;
+  constexpr int EPC = 16 / (int)sizeof(TIn);              // elements per 16-byte chunk
+  constexpr int SLOT = row_slot_elems<TIn>(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw2 = (float2*)smem_raw;
   float2* wP = tw2 + M;
   float2* scr_all = wP + P;
+  TIn* slots = (TIn*)(scr_all + kWarps * odd_scratch_per_warp<P>());
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   fill_dst_tables<P>(tw2, wP, G[table_inst(off, count, sel)].twd_f);
   __syncthreads();
   float2* scr = scr_all + warp * odd_scratch_per_warp<P>() + (lane / P) * 32 * (P / 2 + 1);
-  const int t = lane % P;
+  TIn* slot = slots + (size_t)warp * (32 / P) * 2 * SLOT;   // (32/P) lines x 2 halves
+  const int t = lane % P, grp = lane / P;
   const float sc = __frsqrt_rn((float)(2 * L));     // DST-I normalisation 0.5 sqrt(2/L)
   const long long nvt = (long long)tot * kWarps;
-  for (long long vt = (long long)blockIdx.x * kWarps + warp; vt < nvt; vt += (long long)gridDim.x * kWarps) {
+
+  // the warp's lines of work item vt (tile vt / 8, warp slot vt % 8): group k has line line0 + k
+  struct Item { int inst; long long line0; int nl; };    // nl: valid lines (0: nothing to do)
+  auto decode = [&](long long vt) {
+    Item it{0, 0, 0};
+    if (vt >= nvt) return it;
     const int tile = (int)(vt / kWarps), w = (int)(vt % kWarps);
-    const int inst = find_inst(off, count, tile);
-    if (sel.skip(inst)) continue;
-    const Geom& g = G[inst];
-    const long long mn = g.mn;
-    const long long line = (long long)(tile - off[inst]) * LPB + w * (32 / P) + lane / P;
-    const bool lv = line < (long long)g.n * N;
-    const TIn* __restrict__ in = (in_slot >= 0 ? (const TIn*)S[inst].v[in_slot] : (const TIn*)g.scratch) +
-                                 (lv ? line : 0) * N;
-    // gather the odd extension: z_s = x_{s-1} (1 <= s <= N), -x_{M-s-1} (L < s < M), 0 else
-    float2 x[32];
+    it.inst = find_inst(off, count, tile);
+    if (sel.skip(it.inst)) return it;
+    const long long nlines = (long long)G[it.inst].n * N;
+    it.line0 = (long long)(tile - off[it.inst]) * LPB + w * (32 / P);
+    it.nl = (int)min((long long)(32 / P), max(0LL, nlines - it.line0));
+    return it;
+  };
+  auto src_of = [&](const Item& it) { return (const TIn*)buffer_of(G[it.inst], S[it.inst], in_sel); };
+  // copy the 16-byte aligned spans covering the item's lines (both halves) into the slot
+  auto issue = [&](const Item& it) {
+    if (it.nl > 0) {
+      const TIn* in = src_of(it);
+      const long long mn = G[it.inst].mn;
+      for (int k = 0; k < it.nl; ++k) {
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const int s = t + P * q;
-      const bool ok = lv && (q < 16 ? s > 0 : s > L);
-      const int idx = q < 16 ? s - 1 : M - s - 1;
-      float2 v = make_float2(0.f, 0.f);
-      if (ok) {
-        v.x = (float)in[idx];
-        v.y = (float)in[mn + idx];
-      }
-      if (q >= 16) { v.x = -v.x; v.y = -v.y; }
-      x[q] = v;
-    }
-    fwd_odd<P>(x, t, scr, tw2, wP);
-    if (lv) {
-      TOut* __restrict__ d = (out_slot >= 0 ? (TOut*)S[inst].v[out_slot] : (TOut*)g.scratch) + line * N;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int p = t + P * j;
-        const float2 Y = x[Two<P>::outreg(j)];
-        if (p >= 1) {
-          d[p - 1] = (TOut)(-Y.y * sc);
-          d[mn + p - 1] = (TOut)(Y.x * sc);
+        for (int h = 0; h < 2; ++h) {
+          const TIn* base = in + h * mn + (it.line0 + k) * N;
+          const char* a0 = (const char*)((uintptr_t)base & ~(uintptr_t)15);
+          const char* a1 = (const char*)(((uintptr_t)(base + N) + 15) & ~(uintptr_t)15);
+          const int nch = (int)((a1 - a0) >> 4);
+          TIn* d = slot + (k * 2 + h) * SLOT;
+          for (int c = lane; c < nch; c += 32) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(d + c * EPC);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(a0 + 16 * c) : "memory");
+          }
         }
       }
     }
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// DST-I along x2 (lines of stride N), FP32 scratch in place.  Tiles of LPB = 256 / P
-// consecutive x1 positions are staged through NS shared-memory stages with cp.async.
-// ------------------------------------------------------------------------------------------
-template <int P, int NS>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_dst_cols(const Geom* __restrict__ G, const int* __restrict__ off, int count, Sel sel, int tot) {
-  constexpr int M = 32 * P, L = 16 * P, N = L - 1, LPB = kThreads / P;
-  constexpr int PITCH = pitch_for<P>(N);
-  constexpr int m = N * N;
-  constexpr int NBT = (N + LPB - 1) / LPB;       // tiles per time step
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tw2 = (float2*)smem_raw;
-  float2* wP = tw2 + M;
-  float2* scr_all = wP + P;
-  float2* stages = scr_all + kWarps * odd_scratch_per_warp<P>();
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  fill_dst_tables<P>(tw2, wP, G[table_inst(off, count, sel)].twd_f);
-
-  auto issue = [&](int tile, int st) {
-    if (tile >= tot) return;
-    const int inst = find_inst(off, count, tile);
-    if (sel.skip(inst)) return;
-    const Geom& g = G[inst];
-    const int lt = tile - off[inst];
-    const long long mn = g.mn;
-    const int t0 = lt / NBT, i0 = (lt - t0 * NBT) * LPB;
-    const int l = tid % LPB;
-    const bool iv = i0 + l < N;
-    const float* src = (const float*)g.scratch + (long long)t0 * m + (iv ? i0 + l : 0);
-    float2* d = stages + (size_t)st * LPB * PITCH + l * PITCH;
-    for (int q = tid / LPB; q < N; q += kThreads / LPB) {
-      cp_async<4>(&d[q].x, src + q * N, iv);
-      cp_async<4>(&d[q].y, src + mn + q * N, iv);
-    }
+    cp_commit();
   };
 
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    issue(blockIdx.x + s * gridDim.x, s);
-    cp_commit();
-  }
-  const float sc = __frsqrt_rn((float)(2 * L));
-  float2* scr = scr_all + warp * odd_scratch_per_warp<P>() + (lane / P) * 32 * (P / 2 + 1);
-  const int t = lane % P;
-  const int lw = warp * (32 / P) + lane / P;      // this lane group's line within the tile
-
-  int it = 0;
-  for (int tile = blockIdx.x; tile < tot; tile += gridDim.x, ++it) {
-    const int st = it % NS;
-    cp_wait<NS - 1>();
-    __syncthreads();
-    const int inst = find_inst(off, count, tile);
-    const bool on = !sel.skip(inst);
-    const Geom& g = G[inst];
-    const int lt = tile - off[inst];
-    const int t0 = lt / NBT, i0 = (lt - t0 * NBT) * LPB;
-    float2* buf = stages + (size_t)st * LPB * PITCH;
-    if (on) {
-      float2* ln = buf + lw * PITCH;
-      float2 x[32];
+  long long vt = (long long)blockIdx.x * kWarps + warp;
+  const long long stride = (long long)gridDim.x * kWarps;
+  Item cur = decode(vt);
+  issue(cur);
+  for (; vt < nvt; vt += stride) {
+    const Item nxt = decode(vt + stride);
+    cp_wait<0>();
+    __syncwarp();
+    const bool lv = grp < cur.nl;
+    float2 x[32];
+    if (cur.nl > 0) {
+      const TIn* in = src_of(cur);
+      const long long mn = G[cur.inst].mn;
+      const long long line = cur.line0 + (lv ? grp : 0);
+      const int o0 = (int)(((uintptr_t)(in + line * N) & 15) / sizeof(TIn));
+      const int o1 = (int)(((uintptr_t)(in + mn + line * N) & 15) / sizeof(TIn));
+      const TIn* s0 = slot + (lv ? grp : 0) * 2 * SLOT + o0;
+      const TIn* s1 = slot + ((lv ? grp : 0) * 2 + 1) * SLOT + o1;
+      // gather the odd extension: z_s = x_{s-1} (1 <= s <= N), -x_{M-s-1} (L < s < M), 0 else
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int s = t + P * q;
-        float2 v;
-        if (q < 16) {
-          v = ln[s > 0 ? s - 1 : 0];
-          if (s == 0) v = make_float2(0.f, 0.f);
-        } else {
-          v = ln[s > L ? M - s - 1 : 0];
-          v.x = -v.x; v.y = -v.y;
-          if (s == L) v = make_float2(0.f, 0.f);
-        }
+        const bool ok = lv && (q < 16 ? s > 0 : s > L);
+        const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
+        float2 v = make_float2((float)s0[idx], (float)s1[idx]);
+        if (!ok) v = make_float2(0.f, 0.f);
+        if (q >= 16) { v.x = -v.x; v.y = -v.y; }
         x[q] = v;
       }
+    }
+    __syncwarp();
+    issue(nxt);                          // the next line's copy overlaps this line's transform
+    if (cur.nl > 0) {
       fwd_odd<P>(x, t, scr, tw2, wP);
+      if (lv) {
+        const long long mn = G[cur.inst].mn;
+        TOut* __restrict__ d = (TOut*)buffer_of(G[cur.inst], S[cur.inst], out_sel) + (cur.line0 + grp) * N;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int p = t + P * j;
+          const float2 Y = x[Two<P>::outreg(j)];
+          if (p >= 1) {
+            d[p - 1] = (TOut)(-Y.y * sc);
+            d[mn + p - 1] = (TOut)(Y.x * sc);
+          }
+        }
+      }
+    }
+    cur = nxt;
+  }
+  cp_wait<0>();
+}
+
+// ------------------------------------------------------------------------------------------
+// DST-I of contiguous lines with a transposed result.  Tile (t0, r0) is the lines r0 .. r0+LPB-1
+// of time step t0 (each N contiguous values of the input buffer); the result of line r at index
+// p goes to out[t0 m + p N + r], i.e. the two spatial axes swap.  Passes 1 and 4 use it, so
+// that passes 2 and 5 find their lines contiguous as well:
+//   pass 1: x (x1 lines) -> buffer 0 with x2 lines contiguous; pass 2 transforms buffer 0 in place;
+//   pass 4: buffer 0 -> buffer 1 with x1 lines contiguous again; pass 5: buffer 1 -> y.
+// Each warp copies its next lines with cp.async while it transforms the current ones; a warp
+// parks its results in its own exchange block, and the block writes the tile out as LPB-wide
+// row segments.
+// ------------------------------------------------------------------------------------------
+template <int P>
+__host__ __device__ constexpr int rowsT_region() {   // complex elements per warp: exchange / parked results
+  return ((odd_scratch_per_warp<P>() + 11) / 16) * 16 + 4;
+}
+
+template <typename TIn, int P>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_dst_rowsT(const Geom* __restrict__ G, const Slots* __restrict__ S, const int* __restrict__ off, int count,
+                Sel sel, int in_sel, int out_sel, int tot) {
+  constexpr int M = 32 * P, L = 16 * P, N = L - 1, LPB = kThreads / P, A = 32 / P;
+  constexpr int m = N * N;
+  constexpr int NBT = (N + LPB - 1) / LPB;       // tiles per time step
+  constexpr int EPC = 16 / (int)sizeof(TIn);
+  constexpr int SLOT = row_slot_elems<TIn>(N);
+  constexpr int RS = rowsT_region<P>();
+  static_assert(A * N <= RS, "parked results must fit the exchange block");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw2 = (float2*)smem_raw;
+  float2* wP = tw2 + M;
+  float2* regions = wP + P;
+  TIn* slots = (TIn*)(regions + kWarps * RS);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  fill_dst_tables<P>(tw2, wP, G[table_inst(off, count, sel)].twd_f);
+  float2* region = regions + warp * RS;
+  float2* scr = region + (lane / P) * 32 * (P / 2 + 1);
+  TIn* slot = slots + (size_t)warp * A * 2 * SLOT;
+  const int t = lane % P, grp = lane / P;
+  const float sc = __frsqrt_rn((float)(2 * L));
+
+  struct Item { int inst; int t0, r0; int nl; };   // nl: valid lines of this warp (0: none)
+  auto decode = [&](int tile) {
+    Item it{0, 0, 0, 0};
+    if (tile >= tot) return it;
+    it.inst = find_inst(off, count, tile);
+    if (sel.skip(it.inst)) return it;
+    const int lt = tile - off[it.inst];
+    it.t0 = lt / NBT;
+    it.r0 = (lt - it.t0 * NBT) * LPB;
+    it.nl = max(0, min(A, N - (it.r0 + warp * A)));
+    return it;
+  };
+  auto line_ptr = [&](const Item& it, int k, int h) {
+    const TIn* in = (const TIn*)buffer_of(G[it.inst], S[it.inst], in_sel);
+    return in + h * G[it.inst].mn + (long long)it.t0 * m + (long long)(it.r0 + warp * A + k) * N;
+  };
+  auto issue = [&](const Item& it) {
+    for (int k = 0; k < it.nl; ++k) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const TIn* base = line_ptr(it, k, h);
+        const char* a0 = (const char*)((uintptr_t)base & ~(uintptr_t)15);
+        const char* a1 = (const char*)(((uintptr_t)(base + N) + 15) & ~(uintptr_t)15);
+        const int nch = (int)((a1 - a0) >> 4);
+        TIn* d = slot + (k * 2 + h) * SLOT;
+        for (int c = lane; c < nch; c += 32) {
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(d + c * EPC);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(a0 + 16 * c) : "memory");
+        }
+      }
+    }
+    cp_commit();
+  };
+
+  Item cur = decode(blockIdx.x);
+  issue(cur);
+  for (int tile = blockIdx.x; tile < tot; tile += gridDim.x) {
+    const Item nxt = decode(tile + gridDim.x);
+    const int inst = find_inst(off, count, tile);
+    const bool on = !sel.skip(inst);
+    cp_wait<0>();
+    __syncthreads();                               // tables (first tile) and all slots ready
+    const bool lv = grp < cur.nl;
+    float2 x[32];
+    if (on) {
+      const TIn* s0 = slot + (lv ? grp : 0) * 2 * SLOT;
+      const TIn* s1 = s0 + SLOT;
+      if (lv) {
+        s0 += (int)(((uintptr_t)line_ptr(cur, grp, 0) & 15) / sizeof(TIn));
+        s1 += (int)(((uintptr_t)line_ptr(cur, grp, 1) & 15) / sizeof(TIn));
+      }
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int s = t + P * q;
+        const bool ok = lv && (q < 16 ? s > 0 : s > L);
+        const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
+        float2 v = make_float2((float)s0[idx], (float)s1[idx]);
+        if (!ok) v = make_float2(0.f, 0.f);
+        if (q >= 16) { v.x = -v.x; v.y = -v.y; }
+        x[q] = v;
+      }
+    }
+    __syncwarp();
+    issue(nxt);
+    if (on) {
+      fwd_odd<P>(x, t, scr, tw2, wP);
+      __syncwarp();                                // exchange reads done: park the results
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int p = t + P * j;
         const float2 Y = x[Two<P>::outreg(j)];
-        if (p >= 1) ln[p - 1] = make_float2(-Y.y * sc, Y.x * sc);
+        if (p >= 1) region[grp * N + p - 1] = make_float2(-Y.y * sc, Y.x * sc);
       }
     }
     __syncthreads();
     if (on) {
-      const long long mn = g.mn;
+      const Geom& g = G[inst];
+      const int lt = tile - off[inst];
+      const int t0 = lt / NBT, r0 = (lt - t0 * NBT) * LPB;
       const int l = tid % LPB;
-      if (i0 + l < N) {
-        float* d = (float*)g.scratch + (long long)t0 * m + i0 + l;
-        const float2* srcl = buf + l * PITCH;
-        for (int q = tid / LPB; q < N; q += kThreads / LPB) {
-          const float2 v = srcl[q];
-          d[q * N] = v.x;
-          d[mn + q * N] = v.y;
+      if (r0 + l < N) {
+        float* d = (float*)buffer_of(g, S[inst], out_sel) + (long long)t0 * m + r0 + l;
+        const long long mn = g.mn;
+        const float2* src = regions + (l / A) * RS + (l % A) * N;
+        for (int p = tid / LPB; p < N; p += kThreads / LPB) {
+          const float2 v = src[p];
+          d[(long long)p * N] = v.x;
+          d[mn + (long long)p * N] = v.y;
         }
       }
     }
-    __syncthreads();
-    issue(tile + NS * gridDim.x, st);
-    cp_commit();
+    cur = nxt;
   }
   cp_wait<0>();
 }
@@ -668,13 +767,18 @@ __global__ void __launch_bounds__(kThreads, 2)
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
-constexpr int kNsCols = 2, kNsTime = 2;
+constexpr int kNsTime = 2;
 
 template <int P>
-size_t dst_rows_smem() { return (size_t)(32 * P + P + kWarps * odd_scratch_per_warp<P>()) * sizeof(float2); }
-template <int P>
-size_t dst_cols_smem() {
-  return dst_rows_smem<P>() + (size_t)kNsCols * (kThreads / P) * pitch_for<P>(16 * P - 1) * sizeof(float2);
+size_t dst_tables_smem() { return (size_t)(32 * P + P + kWarps * odd_scratch_per_warp<P>()) * sizeof(float2); }
+template <typename TIn, int P>
+size_t dst_rows_smem() {
+  return dst_tables_smem<P>() + (size_t)kThreads / P * 2 * row_slot_elems<TIn>(16 * P - 1) * sizeof(TIn);
+}
+template <typename TIn, int P>
+size_t dst_rowsT_smem() {
+  return (size_t)(32 * P + P + kWarps * rowsT_region<P>()) * sizeof(float2) +
+         (size_t)kThreads / P * 2 * row_slot_elems<TIn>(16 * P - 1) * sizeof(TIn);
 }
 template <int P>
 size_t time_smem() {
@@ -712,17 +816,17 @@ cudaError_t launch_persistent(K kern, size_t smem, int tot, int& resident, cudaS
 }
 
 template <typename TIn, typename TOut, int P>
-cudaError_t launch_rows(const Batch& B, int in_slot, int out_slot) {
+cudaError_t launch_rows(const Batch& B, int in_sel, int out_sel) {
   static int resident = 0;
-  return launch_persistent(k_dst_rows<TIn, TOut, P>, dst_rows_smem<P>(), B.tot_dst_i[1], resident, B.stream, B.G,
-                           (const Slots*)B.S, B.off_dst_i[1], B.count, B.sel(), in_slot, out_slot, B.tot_dst_i[1]);
+  return launch_persistent(k_dst_rows<TIn, TOut, P>, dst_rows_smem<TIn, P>(), B.tot_dst_i[1], resident, B.stream, B.G,
+                           (const Slots*)B.S, B.off_dst_i[1], B.count, B.sel(), in_sel, out_sel, B.tot_dst_i[1]);
 }
 
-template <int P>
-cudaError_t launch_cols(const Batch& B) {
+template <typename TIn, int P>
+cudaError_t launch_rowsT(const Batch& B, int in_sel, int out_sel) {
   static int resident = 0;
-  return launch_persistent(k_dst_cols<P, kNsCols>, dst_cols_smem<P>(), B.tot_dst_j[1], resident, B.stream, B.G,
-                           B.off_dst_j[1], B.count, B.sel(), B.tot_dst_j[1]);
+  return launch_persistent(k_dst_rowsT<TIn, P>, dst_rowsT_smem<TIn, P>(), B.tot_dst_j[1], resident, B.stream, B.G,
+                           (const Slots*)B.S, B.off_dst_j[1], B.count, B.sel(), in_sel, out_sel, B.tot_dst_j[1]);
 }
 
 template <int P>
@@ -737,12 +841,15 @@ cudaError_t launch_time(const Batch& B, int kind) {
                            B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
 }
 
+// pass `stage` (1, 2, 4, 5) of the FP32 apply; scratch buffers: -1 = buffer 0, -2 = buffer 1
 template <int P>
-cudaError_t dst_pass_p(const Batch& B, int axis, int in_slot, int out_slot) {
-  if (axis == 1) return launch_cols<P>(B);
-  if (in_slot >= 0) return launch_rows<double, float, P>(B, in_slot, -1);
-  if (out_slot >= 0) return launch_rows<float, double, P>(B, -1, out_slot);
-  return launch_rows<float, float, P>(B, -1, -1);
+cudaError_t dst_pass_p(const Batch& B, int stage, int in_slot, int out_slot) {
+  switch (stage) {
+    case 1: return launch_rowsT<double, P>(B, in_slot, -1);
+    case 2: return launch_rows<float, float, P>(B, -1, -1);
+    case 4: return launch_rowsT<float, P>(B, -1, -2);
+    default: return launch_rows<float, double, P>(B, -2, out_slot);
+  }
 }
 
 }  // namespace
@@ -768,14 +875,14 @@ int pipe_dst_lines(int L) { return kThreads / (2 * L / 32); }
 
 cudaError_t pipe_upload_constants() { return upload_w96(); }
 
-// One DST pass of the FP32 apply; B.pipe_pd is the common P of every instance.
-cudaError_t pipe_dst_pass(const Batch& B, int axis, int in_slot, int out_slot) {
+// DST pass `stage` of the FP32 apply; B.pipe_pd is the P shared by the instances it covers.
+cudaError_t pipe_dst_pass(const Batch& B, int stage, int in_slot, int out_slot) {
   switch (B.pipe_pd) {
-    case 2: return dst_pass_p<2>(B, axis, in_slot, out_slot);
-    case 4: return dst_pass_p<4>(B, axis, in_slot, out_slot);
-    case 8: return dst_pass_p<8>(B, axis, in_slot, out_slot);
-    case 16: return dst_pass_p<16>(B, axis, in_slot, out_slot);
-    case 32: return dst_pass_p<32>(B, axis, in_slot, out_slot);
+    case 2: return dst_pass_p<2>(B, stage, in_slot, out_slot);
+    case 4: return dst_pass_p<4>(B, stage, in_slot, out_slot);
+    case 8: return dst_pass_p<8>(B, stage, in_slot, out_slot);
+    case 16: return dst_pass_p<16>(B, stage, in_slot, out_slot);
+    case 32: return dst_pass_p<32>(B, stage, in_slot, out_slot);
     default: return cudaErrorInvalidValue;
   }
 }

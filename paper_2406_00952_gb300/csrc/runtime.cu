@@ -868,6 +868,11 @@ int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_d
   p->hS.v[SL_UOUT] = y_dev;
   int rc;
   if ((rc = upload_slots(p))) return rc;
+  if (((uintptr_t)x_dev & 15) && p->B.pipe_pd) {
+    Batch B = p->B;          // the pipelined x1-line pass reads its input in 16-byte copies
+    B.pipe_pd = 0;
+    return apply_precond(p, B, kind, precision, SL_UIN, SL_UOUT);
+  }
   return apply_precond(p, p->B, kind, precision, SL_UIN, SL_UOUT);
 }
 

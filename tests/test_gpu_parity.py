@@ -40,7 +40,8 @@ def dev(x):
 
 SHAPES = [(1, 2, 1.0, 1.0), (2, 4, 0.5, 1e-2), (15, 16, 1.0, 1e-2), (31, 8, 0.5, 1e-4), (47, 32, 1.0, 1e-6),
           (63, 64, 0.5, 1e-2), (95, 128, 0.75, 1e-3), (127, 4, 1.0, 1e-1), (191, 32, 0.5, 1e-5),
-          (511, 4, 1.0, 1e-2), (3, 1024, 0.5, 1e-3), (383, 2, 1.0, 1e-6), (5, 512, 1.0, 1e-2)]
+          (511, 4, 1.0, 1e-2), (3, 1024, 0.5, 1e-3), (383, 2, 1.0, 1e-6), (5, 512, 1.0, 1e-2),
+          (255, 16, 1.0, 1e-2), (31, 512, 0.5, 1e-3), (15, 256, 1.0, 1e-4)]
 ORACLE = {"abs_ps": pc.apply_abs_ps_inv, "ps": pc.apply_ps_inv, "pms": pc.apply_pms_inv}
 
 
@@ -60,6 +61,22 @@ def test_precond_parity(P, shape, kind):
     t = dev(v)
     gp.precond_apply(t, out=t, kind=kind, precision="fp64")
     assert rel(t.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(511, 4, 1.0, 1e-2), (63, 64, 0.5, 1e-2)], ids=lambda s: "N%d-n%d" % s[:2])
+def test_precond_misaligned_input(P, shape):
+    # a user input that is not 16-byte aligned takes the per-instance x1-line kernel
+    N, n, theta, gamma = shape
+    prob = ds.Problem(N, n, theta, gamma)
+    v = synth.random_vector(2 * prob.m * n, seed=300 + N)
+    ref = pc.apply_abs_ps_inv(prob, v)
+    gp = P.Problem(N, n, theta, gamma, precision="mixed")
+    buf = torch.zeros(v.size + 1, dtype=torch.float64, device="cuda")
+    buf[1:] = dev(v)
+    xin = buf[1:]
+    assert xin.data_ptr() % 16 == 8
+    out = gp.precond_apply(xin, kind="abs_ps", precision="mixed").cpu().numpy()
+    assert rel(out, ref) <= 2e-6, rel(out, ref)
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "N%d-n%d-th%g-g%g" % s)
