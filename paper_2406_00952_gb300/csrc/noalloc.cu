@@ -29,7 +29,6 @@ cudaError_t upload_constants();
 size_t dst_smem_bytes(const Geom& g, int p);
 size_t time_smem_bytes(const Geom& g, int p);
 cudaError_t launch_precond_fast(const Batch& B, int kind, int prec, int in_slot, int out_slot);
-int pipe_time_p(const Geom& g);
 }  // namespace pcb
 
 using namespace pcb;
@@ -72,6 +71,10 @@ extern "C" int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int pre
 
   Geom g;
   init_geom(desc, g);
+  // the arena holds one FP32 scratch buffer of 2mn values: unpadded layout, kernels of precond.cu
+  g.lr = g.N;
+  g.mp = g.m;
+  g.time_blocks[1] = (g.m + g.time_cpb[1] - 1) / g.time_cpb[1];
   TableLayout lay;
   const size_t tab = table_layout(g, lay);
   const size_t real = precision == PCB_MIXED ? sizeof(float) : sizeof(double);
@@ -117,8 +120,8 @@ extern "C" int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int pre
   }
   B.dst_q = g.dst_q;
   B.time_q = g.time_q;
-  B.pipe_pd = 0;               // the pipelined DST passes need two FP32 scratch buffers; the arena has one
-  B.pipe_pt = pipe_time_p(g);
+  B.pipe_pd = 0;
+  B.pipe_pt = 0;
   // (copies from pageable host memory return once the source has been staged, so the host buffers
   // above may be reused as soon as cudaMemcpyAsync returns)
   const cudaError_t e = launch_precond_fast(B, kind, precision, 0, 1);

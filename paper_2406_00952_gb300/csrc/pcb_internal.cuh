@@ -54,6 +54,11 @@ struct Geom {
   double theta, tau, gamma, alpha, h, sqrt_gamma;
   double c;                       // tau / h^2
   int var_a;                      // 0: a = 1; 1: coefficient tables below
+  // FP32 scratch layout of the pipelined passes: rows of lr values (lr = L when the pipelined DST
+  // runs, so that row segments are 32-byte aligned; else N), time slices of mp = N lr values;
+  // buffer b, half h, time t, row r, index i at (float*)scratch + (2b + h) n mp + t mp + r lr + i
+  int lr;
+  long long mp;
   // launch shapes (blocks of each pass for this instance)
   // launch shapes of the preconditioner passes, index 0 = FP64 apply, 1 = FP32 apply
   int dst_lpb[2];                 // lines per block of the x1-line DST pass

@@ -199,10 +199,24 @@ __device__ __forceinline__ void fill_dst_tables(float2* tw2, float2* wP, const f
 // addresses).  Tiles of LPB = 256 / P lines give the block offsets.
 // in_sel / out_sel >= 0: FP64 vector slot; -1 / -2: FP32 scratch buffer 0 / 1.
 // ------------------------------------------------------------------------------------------
-// vector of a pass: slot sel >= 0 of the instance (FP64), or FP32 scratch buffer -1 - sel (the
-// FP64-sized scratch holds two FP32 buffers of 2mn values)
-__device__ __forceinline__ void* buffer_of(const Geom& g, const Slots& s, int sel) {
-  return sel >= 0 ? (void*)s.v[sel] : (void*)((float*)g.scratch + (sel == -1 ? 0 : 2 * g.mn));
+// Layout of the vector a pass reads or writes: slot sel >= 0 of the instance (FP64, rows of N,
+// slices of m, halves of mn values) or FP32 scratch buffer -1 - sel (rows of lr, slices of mp,
+// halves of n mp values).  Element (half h, time t, row r, index i) sits at
+// base + h hs + t ts + r rs + i.
+struct View {
+  void* base;
+  long long hs, ts;
+  int rs;
+};
+__device__ __forceinline__ View view_of(const Geom& g, const Slots& s, int sel) {
+  View v;
+  if (sel >= 0) {
+    v.base = s.v[sel]; v.hs = g.mn; v.ts = g.m; v.rs = g.N;
+  } else {
+    v.hs = (long long)g.n * g.mp; v.ts = g.mp; v.rs = g.lr;
+    v.base = (float*)g.scratch + (sel == -1 ? 0 : 2 * v.hs);
+  }
+  return v;
 }
 
 template <typename TIn>
@@ -244,16 +258,16 @@ __global__ void __launch_bounds__(kThreads, 2)
     it.nl = (int)min((long long)(32 / P), max(0LL, nlines - it.line0));
     return it;
   };
-  auto src_of = [&](const Item& it) { return (const TIn*)buffer_of(G[it.inst], S[it.inst], in_sel); };
+  // line l = t N + r of the item's instance: offset t ts + r rs in a view
+  auto line_off = [&](const View& v, long long l) { return (l / N) * v.ts + (l % N) * v.rs; };
   // copy the 16-byte aligned spans covering the item's lines (both halves) into the slot
   auto issue = [&](const Item& it) {
     if (it.nl > 0) {
-      const TIn* in = src_of(it);
-      const long long mn = G[it.inst].mn;
+      const View v = view_of(G[it.inst], S[it.inst], in_sel);
       for (int k = 0; k < it.nl; ++k) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const TIn* base = in + h * mn + (it.line0 + k) * N;
+          const TIn* base = (const TIn*)v.base + h * v.hs + line_off(v, it.line0 + k);
           const char* a0 = (const char*)((uintptr_t)base & ~(uintptr_t)15);
           const char* a1 = (const char*)(((uintptr_t)(base + N) + 15) & ~(uintptr_t)15);
           const int nch = (int)((a1 - a0) >> 4);
@@ -279,11 +293,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     const bool lv = grp < cur.nl;
     float2 x[32];
     if (cur.nl > 0) {
-      const TIn* in = src_of(cur);
-      const long long mn = G[cur.inst].mn;
-      const long long line = cur.line0 + (lv ? grp : 0);
-      const int o0 = (int)(((uintptr_t)(in + line * N) & 15) / sizeof(TIn));
-      const int o1 = (int)(((uintptr_t)(in + mn + line * N) & 15) / sizeof(TIn));
+      const View v = view_of(G[cur.inst], S[cur.inst], in_sel);
+      const TIn* in = (const TIn*)v.base + line_off(v, cur.line0 + (lv ? grp : 0));
+      const int o0 = (int)(((uintptr_t)in & 15) / sizeof(TIn));
+      const int o1 = (int)(((uintptr_t)(in + v.hs) & 15) / sizeof(TIn));
       const TIn* s0 = slot + (lv ? grp : 0) * 2 * SLOT + o0;
       const TIn* s1 = slot + ((lv ? grp : 0) * 2 + 1) * SLOT + o1;
       // gather the odd extension: z_s = x_{s-1} (1 <= s <= N), -x_{M-s-1} (L < s < M), 0 else
@@ -303,15 +316,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (cur.nl > 0) {
       fwd_odd<P>(x, t, scr, tw2, wP);
       if (lv) {
-        const long long mn = G[cur.inst].mn;
-        TOut* __restrict__ d = (TOut*)buffer_of(G[cur.inst], S[cur.inst], out_sel) + (cur.line0 + grp) * N;
+        const View v = view_of(G[cur.inst], S[cur.inst], out_sel);
+        TOut* __restrict__ d = (TOut*)v.base + line_off(v, cur.line0 + grp);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int p = t + P * j;
           const float2 Y = x[Two<P>::outreg(j)];
           if (p >= 1) {
             d[p - 1] = (TOut)(-Y.y * sc);
-            d[mn + p - 1] = (TOut)(Y.x * sc);
+            d[v.hs + p - 1] = (TOut)(Y.x * sc);
           }
         }
       }
@@ -342,7 +355,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     k_dst_rowsT(const Geom* __restrict__ G, const Slots* __restrict__ S, const int* __restrict__ off, int count,
                 Sel sel, int in_sel, int out_sel, int tot) {
   constexpr int M = 32 * P, L = 16 * P, N = L - 1, LPB = kThreads / P, A = 32 / P;
-  constexpr int m = N * N;
   constexpr int NBT = (N + LPB - 1) / LPB;       // tiles per time step
   constexpr int EPC = 16 / (int)sizeof(TIn);
   constexpr int SLOT = row_slot_elems<TIn>(N);
@@ -374,21 +386,34 @@ __global__ void __launch_bounds__(kThreads, 2)
     return it;
   };
   auto line_ptr = [&](const Item& it, int k, int h) {
-    const TIn* in = (const TIn*)buffer_of(G[it.inst], S[it.inst], in_sel);
-    return in + h * G[it.inst].mn + (long long)it.t0 * m + (long long)(it.r0 + warp * A + k) * N;
+    const View v = view_of(G[it.inst], S[it.inst], in_sel);
+    return (const TIn*)v.base + h * v.hs + it.t0 * v.ts + (long long)(it.r0 + warp * A + k) * v.rs;
   };
+  // The 16-byte aligned span of a line is copied in 16-byte pieces.  Where that span would
+  // leave the vector (a caller's buffer that is not 16-byte aligned), the line is copied value by
+  // value to the same slot positions instead.
   auto issue = [&](const Item& it) {
-    for (int k = 0; k < it.nl; ++k) {
+    if (it.nl > 0) {
+      const View v = view_of(G[it.inst], S[it.inst], in_sel);
+      const char* lo = (const char*)v.base;
+      const char* hi = lo + 2 * v.hs * (long long)sizeof(TIn);
+      for (int k = 0; k < it.nl; ++k) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const TIn* base = line_ptr(it, k, h);
-        const char* a0 = (const char*)((uintptr_t)base & ~(uintptr_t)15);
-        const char* a1 = (const char*)(((uintptr_t)(base + N) + 15) & ~(uintptr_t)15);
-        const int nch = (int)((a1 - a0) >> 4);
-        TIn* d = slot + (k * 2 + h) * SLOT;
-        for (int c = lane; c < nch; c += 32) {
-          const unsigned sa = (unsigned)__cvta_generic_to_shared(d + c * EPC);
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(a0 + 16 * c) : "memory");
+        for (int h = 0; h < 2; ++h) {
+          const TIn* base = line_ptr(it, k, h);
+          const char* a0 = (const char*)((uintptr_t)base & ~(uintptr_t)15);
+          const char* a1 = (const char*)(((uintptr_t)(base + N) + 15) & ~(uintptr_t)15);
+          TIn* d = slot + (k * 2 + h) * SLOT;
+          if (a0 >= lo && a1 <= hi) {
+            const int nch = (int)((a1 - a0) >> 4);
+            for (int c = lane; c < nch; c += 32) {
+              const unsigned sa = (unsigned)__cvta_generic_to_shared(d + c * EPC);
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(a0 + 16 * c) : "memory");
+            }
+          } else {
+            TIn* de = d + (((uintptr_t)base & 15) / sizeof(TIn));
+            for (int e = lane; e < N; e += 32) cp_async<sizeof(TIn)>(de + e, base + e, true);
+          }
         }
       }
     }
@@ -442,13 +467,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int t0 = lt / NBT, r0 = (lt - t0 * NBT) * LPB;
       const int l = tid % LPB;
       if (r0 + l < N) {
-        float* d = (float*)buffer_of(g, S[inst], out_sel) + (long long)t0 * m + r0 + l;
-        const long long mn = g.mn;
+        const View ov = view_of(g, S[inst], out_sel);
+        float* d = (float*)ov.base + t0 * ov.ts + r0 + l;
         const float2* src = regions + (l / A) * RS + (l % A) * N;
         for (int p = tid / LPB; p < N; p += kThreads / LPB) {
           const float2 v = src[p];
-          d[(long long)p * N] = v.x;
-          d[mn + (long long)p * N] = v.y;
+          d[(long long)p * ov.rs] = v.x;
+          d[ov.hs + (long long)p * ov.rs] = v.y;
         }
       }
     }
@@ -508,9 +533,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const Geom& g = G[inst];
     const int c0 = (tile - off[inst]) * LPB;
     const int l = tid % LPB;
-    const bool cv = c0 + l < g.m;
+    const bool cv = c0 + l < g.mp;
     const float* y = (const float*)g.scratch + (cv ? c0 + l : 0);
-    const long long m = g.m, mn = g.mn;
+    const long long m = g.mp, mn = (long long)g.n * g.mp;
     float2* d = stages + (size_t)st * LPB * PITCH + l * PITCH;
     for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
       cp_async<4>(&d[tt].x, y + tt * m, cv);
@@ -545,8 +570,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int q = 0; q < 32; ++q) x[q] = cmul(ln[t + P * q], pre[t + P * q]);
       fwd2<P>(x, t, scr, tw2);
       // pointwise solve at r = t + P j; the partner n-1-r is lane P-1-t, register 31-j
-      const int col = min(c0 + lw, g.m - 1);
-      const int jj = col / g.N, ii = col - jj * g.N;
+      const long long col = min((long long)(c0 + lw), g.mp - 1);   // padded columns compute junk
+      const int jj = (int)(col / g.lr), ii = min((int)(col - (long long)jj * g.lr), g.N - 1);
       const float c = (float)(g.tau * (__ldg(&g.kap[ii]) + __ldg(&g.kap[jj])));
       const float a2 = (float)(g.alpha * g.alpha), alpha = (float)g.alpha;
       const float2* __restrict__ mu = g.mu_f;
@@ -576,9 +601,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (on) {
       const int l = tid % LPB;
-      if (c0 + l < g.m) {
+      if (c0 + l < g.mp) {
         float* y = (float*)g.scratch + c0 + l;
-        const long long m = g.m, mn = g.mn;
+        const long long m = g.mp, mn = (long long)g.n * g.mp;
         const float2* srcl = buf + l * PITCH;
         for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
           const float2 v = srcl[tt];
@@ -632,9 +657,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     const Geom& g = G[inst];
     const int c0 = (tile - off[inst]) * LPB;
     const int l = tid % LPB;
-    const bool cv = c0 + l < g.m;
+    const bool cv = c0 + l < g.mp;
     const float* y = (const float*)g.scratch + (cv ? c0 + l : 0);
-    const long long m = g.m, mn = g.mn;
+    const long long m = g.mp, mn = (long long)g.n * g.mp;
     float2* d = stages + (size_t)st * LPB * PITCH + l * PITCH;
     for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
       cp_async<4>(&d[tt].x, y + tt * m, cv);
@@ -693,8 +718,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         x[pos<16>(k2)] = make_float2(fmaf(sg, v.x, o.x), fmaf(sg, v.y, o.y));
       }
       // pointwise solve at r = k1 + 16 k2 + 256 h
-      const int col = min(c0 + warp, g.m - 1);
-      const int jj = col / g.N, ii = col - jj * g.N;
+      const long long col = min((long long)(c0 + warp), g.mp - 1);  // padded columns compute junk
+      const int jj = (int)(col / g.lr), ii = min((int)(col - (long long)jj * g.lr), g.N - 1);
       const float c = (float)(g.tau * (__ldg(&g.kap[ii]) + __ldg(&g.kap[jj])));
       const float a2 = (float)(g.alpha * g.alpha), alpha = (float)g.alpha;
       if (kind == PK_PS) {
@@ -746,9 +771,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     if (on) {
       const int l = tid % LPB;
-      if (c0 + l < g.m) {
+      if (c0 + l < g.mp) {
         float* y = (float*)g.scratch + c0 + l;
-        const long long m = g.m, mn = g.mn;
+        const long long m = g.mp, mn = (long long)g.n * g.mp;
         const float2* srcl = buf + l * PITCH;
         for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
           const float2 v = srcl[tt];
@@ -856,8 +881,9 @@ cudaError_t dst_pass_p(const Batch& B, int stage, int in_slot, int out_slot) {
 
 // P of the pipelined passes for an instance (0: not eligible): DST lines of 2L = 32 P points,
 // time lines of n = 32 P points, P a power of two in [2, 32]; the constant-coefficient route only.
+int pipe_time_p(const Geom& g);
 int pipe_dst_p(const Geom& g) {
-  if (g.var_a) return 0;
+  if (g.var_a || !pipe_time_p(g)) return 0;      // the padded scratch layout needs the pipelined time pass
   const int M = 2 * g.L;
   if (M % 32) return 0;
   const int P = M / 32;

@@ -143,6 +143,8 @@ int pow2_floor(int v) { int p = 1; while (p * 2 <= v) p *= 2; return p; }
 
 void set_shapes(Geom& g) {
   const int pd = pipe_dst_p(g), pt = pipe_time_p(g);   // pipelined FP32 passes: 256/P lines a tile
+  g.lr = pd ? g.L : g.N;
+  g.mp = (long long)g.N * g.lr;
   const int lsd = padded_len_host(g.L), lst = padded_len_host(g.n);
   const int Pd = 2 * g.L / g.dst_q, Pt = g.n / g.time_q;
   const int lpwd = 32 / Pd, lpwt = 32 / Pt;
@@ -162,7 +164,7 @@ void set_shapes(Geom& g) {
     cpb = std::max(lpwt, std::min(cpb, pow2_floor(std::max(1, g.m))));
     if (p == 1 && pt) cpb = pipe_time_cols(g.n);
     g.time_cpb[p] = cpb;
-    g.time_blocks[p] = (g.m + cpb - 1) / cpb;
+    g.time_blocks[p] = (int)(((p == 1 && pt ? g.mp : (long long)g.m) + cpb - 1) / cpb);
   }
   const int ncb = (g.m + 255) / 256;
   if (g.theta == 1.0) {
@@ -451,7 +453,8 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
   if (cudaMemcpy(p->tables, host.data(), off_b, cudaMemcpyHostToDevice) != cudaSuccess) return fail(PCB_ERR_CUDA);
   bind_tables(g, lay, (unsigned char*)p->tables);
   // ---- preconditioner scratch: 2mn values, FP64-sized so both precisions fit ----
-  const size_t sbytes = (size_t)2 * g.mn * sizeof(double);
+  // (the pipelined FP32 passes keep two buffers of padded rows in it: 16 n N lr bytes)
+  const size_t sbytes = std::max<size_t>((size_t)2 * g.mn * sizeof(double), (size_t)16 * g.n * g.N * (size_t)g.lr);
   if (cudaMalloc(&p->scratch, sbytes) != cudaSuccess) return fail(PCB_ERR_OUT_OF_MEMORY);
   p->bytes += sbytes;
   g.scratch = p->scratch;
@@ -868,11 +871,6 @@ int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_d
   p->hS.v[SL_UOUT] = y_dev;
   int rc;
   if ((rc = upload_slots(p))) return rc;
-  if (((uintptr_t)x_dev & 15) && p->B.pipe_pd) {
-    Batch B = p->B;          // the pipelined x1-line pass reads its input in 16-byte copies
-    B.pipe_pd = 0;
-    return apply_precond(p, B, kind, precision, SL_UIN, SL_UOUT);
-  }
   return apply_precond(p, p->B, kind, precision, SL_UIN, SL_UOUT);
 }
 
