@@ -45,6 +45,8 @@ def args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--serve-window", type=float, default=0.25,
+                    help="seconds of the serving trace replayed for the serving figures (0: skip)")
     ap.add_argument("--small", action="store_true", help="N=255, n=256 instead (quick checks only)")
     return ap.parse_args()
 
@@ -314,6 +316,23 @@ def main():
         e2e = {"value": len(W["gammas"]) * a.e2e_steps * world / dt, "unit": "solves/s",
                "h2d_bytes_per_step": nb * len(W["gammas"]), "d2h_bytes_per_step": nb * len(W["gammas"])}
 
+    # serving: a window of the Poisson request trace (uneven grids, 5% at N=511 n=512), served by the
+    # continuous-batching server in mixed precision, against single FP64 solves in arrival order
+    serving = None
+    if rank == 0 and a.serve_window > 0:
+        from paper_2406_00952_gb300 import serve
+        trace = synth.serving_trace(duration_s=a.serve_window)
+        reqs = serve.build_requests(trace)
+        torch.cuda.synchronize()
+        srv = serve.run(reqs, budget_bytes=150 << 30, max_slots=32, precision="mixed")
+        base = serve.one_at_a_time(reqs, precision="fp64")
+        serving = {"trace": f"Poisson 200/s, first {a.serve_window:g} s ({len(reqs)} requests, "
+                            f"{sum(r.N == 511 for r in reqs)} at N=511 n=512), HBM budget 150 GB",
+                   "solves_per_s": srv["solves_per_s"], "p50_latency_s": srv["p50_latency_s"],
+                   "p99_latency_s": srv["p99_latency_s"], "max_relres": srv["max_relres"], "failed": srv["failed"],
+                   "fp64_one_at_a_time": {k: base[k] for k in ("solves_per_s", "p50_latency_s", "p99_latency_s")}}
+        del reqs
+
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
         dt, it_o = cpu_baseline(W)
@@ -341,6 +360,7 @@ def main():
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": sum(i["launches"] for i in infos),
+            "serving": serving,
         }
         print(json.dumps(line))
     if world > 1:
