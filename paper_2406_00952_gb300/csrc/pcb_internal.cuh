@@ -54,8 +54,8 @@ struct Geom {
   double theta, tau, gamma, alpha, h, sqrt_gamma;
   double c;                       // tau / h^2
   int var_a;                      // 0: a = 1; 1: coefficient tables below
-  // FP32 scratch layout of the pipelined passes: rows of lr values (lr = L when the pipelined DST
-  // runs, so that row segments are 32-byte aligned; else N), time slices of mp = N lr values;
+  // FP32 scratch layout of the pipelined passes: rows of lr values (lr = L + 16 when the pipelined
+  // DST runs: 64-byte aligned rows, stride off a power of two; else N), slices of mp = N lr values;
   // buffer b, half h, time t, row r, index i at (float*)scratch + (2b + h) n mp + t mp + r lr + i
   int lr;
   long long mp;

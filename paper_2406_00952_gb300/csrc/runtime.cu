@@ -143,7 +143,7 @@ int pow2_floor(int v) { int p = 1; while (p * 2 <= v) p *= 2; return p; }
 
 void set_shapes(Geom& g) {
   const int pd = pipe_dst_p(g), pt = pipe_time_p(g);   // pipelined FP32 passes: 256/P lines a tile
-  g.lr = pd ? g.L : g.N;
+  g.lr = pd ? g.L + 16 : g.N;      // + 16: rows stay 64-byte aligned, stride off a power of two
   g.mp = (long long)g.N * g.lr;
   const int lsd = padded_len_host(g.L), lst = padded_len_host(g.n);
   const int Pd = 2 * g.L / g.dst_q, Pt = g.n / g.time_q;
