@@ -49,6 +49,41 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a * conj(b)
   return c;
 }
 
+// FP64 <-> FP32 conversions with integer operations.  The conversion instructions run on the FP64
+// pipe, which is narrow on this GPU and became the bottleneck of the passes that read or write
+// the FP64 vectors.  IEEE-754 binary64 -> binary32, round to nearest even: for results in the
+// normal FP32 range the rounded value is the top 31 bits of (exponent - 896, mantissa >> 29)
+// plus one when the dropped 29 bits exceed half, or equal half and the kept value is odd (a
+// carry into the exponent gives the right next binade, or infinity).  Zeros keep their sign;
+// the rare remaining cases (FP32 subnormals, overflow, infinities, NaN) use the instruction.
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ah = hi & 0x7fffffffu, e = ah >> 20;
+  if (e - 897u <= 253u) {
+    const unsigned m = (ah << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    const unsigned rnd = (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & m & 1u);
+    return __uint_as_float(((m - (896u << 23)) + rnd) | (hi & 0x80000000u));
+  }
+  if ((ah | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+  return __double2float_rn(x);
+}
+// binary32 -> binary64 (exact): exponent rebiased by 896, mantissa moved up by 29 bits
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned b = __float_as_uint(f), e = (b >> 23) & 0xffu;
+  if (e - 1u < 254u) {
+    const unsigned hi = (b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(b << 29));
+  }
+  if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return (double)f;
+}
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(double v) { return d2f(v); }
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ double from_f32<double>(float v) { return f2d(v); }
+
 // ------------------------------------------------------------------------------------------
 // two-stage line FFT, M = 32 P
 // ------------------------------------------------------------------------------------------
@@ -305,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int s = t + P * q;
         const bool ok = lv && (q < 16 ? s > 0 : s > L);
         const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
-        float2 v = make_float2((float)s0[idx], (float)s1[idx]);
+        float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
         if (!ok) v = make_float2(0.f, 0.f);
         if (q >= 16) { v.x = -v.x; v.y = -v.y; }
         x[q] = v;
@@ -323,8 +358,8 @@ __global__ void __launch_bounds__(kThreads, 2)
           const int p = t + P * j;
           const float2 Y = x[Two<P>::outreg(j)];
           if (p >= 1) {
-            d[p - 1] = (TOut)(-Y.y * sc);
-            d[v.hs + p - 1] = (TOut)(Y.x * sc);
+            d[p - 1] = from_f32<TOut>(-Y.y * sc);
+            d[v.hs + p - 1] = from_f32<TOut>(Y.x * sc);
           }
         }
       }
@@ -442,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int s = t + P * q;
         const bool ok = lv && (q < 16 ? s > 0 : s > L);
         const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
-        float2 v = make_float2((float)s0[idx], (float)s1[idx]);
+        float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
         if (!ok) v = make_float2(0.f, 0.f);
         if (q >= 16) { v.x = -v.x; v.y = -v.y; }
         x[q] = v;
