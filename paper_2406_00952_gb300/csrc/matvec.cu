@@ -71,27 +71,6 @@ __device__ __forceinline__ double epi_apply(const Epi& e, double o, const double
   return v;
 }
 
-// Deferred MINRES direction/solution update of the previous iteration, fused into the product
-// (the product is FP64-ALU bound, the update HBM bound): for every index e it owns, a thread does
-//   w_new = (y/oldb - oldeps*w2 - delta*w)/gamma -> w2[e] ;  x[e] += phi*w_new
-// with the same operations in the same order as the separate update kernel.
-struct Wx {
-  const double* y;
-  const double* w;
-  double* w2;
-  double* x;
-  double iv, ig, oe, de, phi;
-};
-
-__device__ __forceinline__ void wx_apply(const Wx& u, long long e) {
-  double t = u.y[e] * u.iv;
-  t = fma(u.oe, u.w2[e], t);
-  t = fma(u.de, u.w[e], t);
-  t *= u.ig;
-  u.w2[e] = t;
-  u.x[e] = fma(u.phi, t, u.x[e]);
-}
-
 __device__ __forceinline__ Epi make_epi(int kind, const Scal* sc) {
   Epi e; e.kind = kind; e.s = 1.0; e.c = 0.0; e.ds = 1.0;
   if (kind == EPI_MINRES) {
@@ -106,7 +85,7 @@ __device__ __forceinline__ Epi make_epi(int kind, const Scal* sc) {
 __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                                 Scal* __restrict__ Sc, const int* __restrict__ off, int count,
                                                 const int* __restrict__ active, int op, int x_slot, int out_slot,
-                                                int aux_slot, int epi_kind, double* __restrict__ partial, int4 wxs) {
+                                                int aux_slot, int epi_kind, double* __restrict__ partial) {
   const int inst = find_inst(off, count, blockIdx.x);
   if (active && !active[inst]) return;
   const Geom& g = G[inst];
@@ -115,13 +94,6 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
   double* __restrict__ out = S[inst].v[out_slot];
   const double* __restrict__ aux = aux_slot >= 0 ? S[inst].v[aux_slot] : nullptr;
   const Epi e = make_epi(epi_kind, Sc + inst);
-  const bool do_wx = wxs.x >= 0;        // wxs = (y, w, w2, x) slots of the deferred MINRES update
-  Wx wu;
-  if (do_wx) {
-    const Scal& c = Sc[inst];
-    wu.y = S[inst].v[wxs.x]; wu.w = S[inst].v[wxs.y]; wu.w2 = S[inst].v[wxs.z]; wu.x = S[inst].v[wxs.w];
-    wu.iv = 1.0 / c.oldb; wu.ig = 1.0 / c.gamma; wu.oe = -c.oldeps; wu.de = -c.delta; wu.phi = c.phi;
-  }
   const int N = g.N, m = g.m, n = g.n;
   const long long mn = g.mn;
   const double* __restrict__ x1 = x;
@@ -156,7 +128,6 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
         oTT = fma(alpha, x1c, oTT);
         out[offT + a] = epi_apply(e, oT, aux, x, offT + a, part);
         out[offTT + a] = epi_apply(e, oTT, aux, x, offTT + a, part);
-        if (do_wx) { wx_apply(wu, a); wx_apply(wu, mn + a); }
         x1prev = x1c;
       }
     }
@@ -176,7 +147,6 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
           double oT = (z - zprev) + tauK(g, u1, i, j, col);
           oT = fma(-alpha, x2[a], oT);
           out[offT + a] = epi_apply(e, oT, aux, x, offT + a, part);
-          if (do_wx) wx_apply(wu, offT + a);
           zprev = z;
         }
       } else {
@@ -189,7 +159,6 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
           double oTT = (u - unext) + tauK(g, u2, i, j, col);
           oTT = fma(alpha, x1[a], oTT);
           out[offTT + a] = epi_apply(e, oTT, aux, x, offTT + a, part);
-          if (do_wx) wx_apply(wu, offTT + a);
           unext = u;
         }
       }
@@ -201,9 +170,9 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
   }
 }
 
-cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi, int4 wx) {
+cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi) {
   k_matvec<<<B.tot_mv, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_mv, B.count, B.active, op, x_slot, out_slot,
-                                           aux_slot, epi, B.partial, wx);
+                                           aux_slot, epi, B.partial);
   return cudaGetLastError();
 }
 

@@ -21,8 +21,7 @@ cudaError_t launch_precond_mg(const Batch& B, const Geom& g, int kind, int prec,
                               int out_slot);
 void mg_release(const void* ws);
 long long mg_launch_total();
-cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi,
-                          int4 wx = make_int4(-1, -1, -1, -1));
+cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi);
 cudaError_t launch_rhs(const Geom& g, cudaStream_t st, int op, const double* gs, const double* fs, const double* y0,
                        double* b);
 cudaError_t launch_recover(const Geom& g, cudaStream_t st, const double* x, double* y, double* p);
@@ -570,12 +569,11 @@ static int P_precond(pcb_problem* p, const Batch& B, int kind, int prec, int in_
   return rc;
 }
 
-static cudaError_t P_matvec(pcb_problem* p, const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi,
-                            int4 wx = make_int4(-1, -1, -1, -1)) {
+static cudaError_t P_matvec(pcb_problem* p, const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi) {
   cudaEvent_t a = nullptr, b = nullptr;
   const bool ev = p->prof && ev_pair(p->ev_mv, p->ev_mv_used, a, b);
   if (ev) cudaEventRecord(a, B.stream);
-  const cudaError_t e = launch_matvec(B, op, x_slot, out_slot, aux_slot, epi, wx);
+  const cudaError_t e = launch_matvec(B, op, x_slot, out_slot, aux_slot, epi);
   if (ev) cudaEventRecord(b, B.stream);
   p->launches += 1;
   p->matvecs += 1;
@@ -624,39 +622,24 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   if (hs->bnorm == 0.0 || !hs->active) { *conv_out = true; *relres_out = 0.0; return PCB_OK; }
   const int limit = c.fixed > 0 ? c.fixed : c.maxit;
   bool checking = false;
-  // The direction/solution update of iteration k (w_k, x += phi_k w_k) is deferred into the
-  // product of iteration k+1, which reads y_k from slot YO; `flush` applies a pending update on
-  // its own (before x is used and at the end).
-  bool pending = false;
-  auto flush = [&]() -> cudaError_t {
-    if (!pending) return cudaSuccess;
-    cudaError_t e = LC(p) launch_minres_wx(B, SL_YO, SL_W, SL_W2, s_x);
-    if (e == cudaSuccess) e = LC(p) launch_swap(B, SL_W, SL_W2, -1, -1, -1, -1);
-    std::swap(p->hS.v[SL_W], p->hS.v[SL_W2]);
-    pending = false;
-    return e;
-  };
   for (int it = 0; it < limit; ++it) {
-    const bool fused = pending;
-    CK(P_matvec(p, B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES,
-                fused ? make_int4(SL_YO, SL_W, SL_W2, s_x) : make_int4(-1, -1, -1, -1)));
+    CK(P_matvec(p, B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
     CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
     CK(LC(p) launch_axpby(B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
     if ((rc = P_precond(p, B, c.kind, c.prec, SL_R1, SL_YO))) return rc;
     CK(LC(p) launch_dot(B, SL_R1, SL_YO));
     CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_MINRES_GIVENS, c.tol, 0, 0));
-    CK(LC(p) launch_swap(B, SL_R1, SL_R2, SL_Y, SL_YO, fused ? SL_W : -1, SL_W2));
+    CK(LC(p) launch_minres_wx(B, SL_Y, SL_W, SL_W2, s_x));
+    CK(LC(p) launch_swap(B, SL_R1, SL_R2, SL_Y, SL_YO, SL_W, SL_W2));
     std::swap(p->hS.v[SL_R1], p->hS.v[SL_R2]);
     std::swap(p->hS.v[SL_Y], p->hS.v[SL_YO]);
-    if (fused) std::swap(p->hS.v[SL_W], p->hS.v[SL_W2]);
-    pending = true;
+    std::swap(p->hS.v[SL_W], p->hS.v[SL_W2]);
     if ((rc = read_scal(B, hs, 1))) return rc;
     *it_out = it + 1;
     if (hs->flags & 4) return PCB_ERR_NONFINITE;
     if (hs->flags & 2) return PCB_ERR_BREAKDOWN;
     if (c.fixed > 0) continue;
     if ((hs->flags & 1) || checking) {
-      CK(flush());
       CK(P_matvec(p, B, PCB_OP_A, s_x, SL_Q, s_b, EPI_RESID));
       CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
       if ((rc = read_scal(B, hs, 1))) return rc;
@@ -667,7 +650,6 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
       checking = true;
     }
   }
-  CK(flush());
   CK(P_matvec(p, B, PCB_OP_A, s_x, SL_Q, s_b, EPI_RESID));
   CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_NORM, c.tol, 0, 0));
   if ((rc = read_scal(B, hs, 1))) return rc;
