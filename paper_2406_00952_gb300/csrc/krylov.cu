@@ -93,12 +93,14 @@ __global__ void __launch_bounds__(256) k_minres_wx(const Geom* __restrict__ G, c
   const double* __restrict__ w = S[inst].v[sw];
   double* __restrict__ w2 = S[inst].v[sw2];
   double* __restrict__ x = S[inst].v[sx];
-  const double iv = 1.0 / c.oldb, ig = 1.0 / c.gamma, oe = -c.oldeps, de = -c.delta, phi = c.phi;
+  // the 1/gamma scale is folded into the three coefficients: four FP64 operations per value (the
+  // kernel sits at the FP64 instruction limit as much as at the HBM limit)
+  const double ig = 1.0 / c.gamma;
+  const double cy = ig / c.oldb, c2 = -c.oldeps * ig, c1 = -c.delta * ig, phi = c.phi;
   for (long long e = e0; e < len; e += stride) {
-    double t = y[e] * iv;
-    t = fma(oe, w2[e], t);
-    t = fma(de, w[e], t);
-    t *= ig;
+    double t = y[e] * cy;
+    t = fma(c2, w2[e], t);
+    t = fma(c1, w[e], t);
     w2[e] = t;
     x[e] = fma(phi, t, x[e]);
   }
