@@ -79,6 +79,26 @@ def test_precond_misaligned_input(P, shape):
     assert rel(out, ref) <= 2e-6, rel(out, ref)
 
 
+def test_precond_special_values(P):
+    # exact zeros (both signs) and values outside the FP32 normal range take the conversion
+    # fallbacks of the first and last pass; an all-zero input gives an exactly zero output
+    N, n = 63, 64
+    prob = ds.Problem(N, n, 1.0, 1e-2)
+    v = synth.random_vector(2 * prob.m * n, seed=400)
+    rng = np.random.default_rng(401)
+    idx = rng.choice(v.size, v.size // 10, replace=False)
+    v[idx[0::4]] = 0.0
+    v[idx[1::4]] = -0.0
+    v[idx[2::4]] = 1e-310 * np.sign(rng.standard_normal(idx[2::4].size))
+    v[idx[3::4]] = 1e-40 * np.sign(rng.standard_normal(idx[3::4].size))
+    gp = P.Problem(N, n, 1.0, 1e-2, precision="mixed")
+    out = gp.precond_apply(dev(v), kind="abs_ps", precision="mixed").cpu().numpy()
+    assert np.all(np.isfinite(out))
+    assert rel(out, pc.apply_abs_ps_inv(prob, v)) <= 2e-6
+    z = gp.precond_apply(dev(np.zeros_like(v)), kind="abs_ps", precision="mixed").cpu().numpy()
+    assert np.all(z == 0.0)
+
+
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "N%d-n%d-th%g-g%g" % s)
 @pytest.mark.parametrize("opname", ["A", "Ahat"])
 def test_matvec_parity(P, shape, opname):
