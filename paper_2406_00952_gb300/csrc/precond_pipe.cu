@@ -1,20 +1,26 @@
 // Pipelined FP32 preconditioner passes for power-of-two line lengths (paper Sec. 3.5).
 //
-// The same five passes as precond.cu (DST-I along x1, DST-I along x2, time DFT + pointwise solve
-// + inverse time DFT, DST-I along x2, DST-I along x1), organised to hide memory latency:
-//   * Persistent blocks (one per SM, eight warps) walk the tiles of a pass.  The input of each
-//     tile is fetched with asynchronous copies (cp.async) into one of NS shared-memory stages, so
-//     the loads of the next tiles are in flight while the current tile is transformed.
+// The same five passes as precond.cu: DST-I along x1, DST-I along x2, time DFT + pointwise
+// solve + inverse time DFT, DST-I along x2, DST-I along x1.  They are organised for this GPU as
+// follows.
 //   * A line of length M = 32 P (2 <= P <= 32) is transformed by P lanes holding 32 values each,
-//     as a two-stage FFT: with s = t + P q and k = k1 + 32 k2,
+//     as a two-stage FFT.  With s = t + P q and k = k1 + 32 k2,
 //         X[k1 + 32 k2] = sum_t W_P^{t k2} W_M^{t k1} sum_q x[t + P q] W_32^{q k1},
-//     i.e. a 32-point register DFT per lane, the twiddle W_M^{t k1}, an exchange through a per-warp
-//     shared-memory block (XOR-swizzled, free of bank conflicts) and 32/P register DFTs of size P.
-//     Lane t starts with x[t + P q] and ends with X[u + P j] (u = t): both cyclic with stride P, so
-//     contiguous lines load and store with coalesced accesses and no bit reversal.  The inverse
-//     runs the same steps in reverse order.
-// Scratch layout and the value of every pass are those of precond.cu, so the two implementations
-// can be mixed pass by pass.
+//     that is a 32-point register DFT per lane, the twiddle W_M^{t k1}, an exchange through a
+//     per-warp shared-memory block (XOR-swizzled, free of bank conflicts) and 32/P register DFTs
+//     of size P.  Lane t starts with x[t + P q] and ends with X[u + P j] (u = t).  Both orders
+//     are cyclic with stride P, so contiguous lines load and store coalesced, with no bit
+//     reversal.  The inverse runs the same steps in reverse order.
+//   * Every DST pass reads contiguous lines.  Passes 1 and 4 write their result transposed
+//     (the two spatial axes swap), so the x2 lines of pass 2 and the x1 lines of pass 5 are
+//     contiguous too.  Each warp copies its next line with 16-byte cp.async copies while it
+//     transforms the current one.
+//   * The FP32 scratch holds two buffers whose rows are padded to 64-byte boundaries (Geom::lr,
+//     Geom::mp): x -> buffer 0 (transposed) -> in place -> time pass in place -> buffer 1
+//     (transposed back) -> y.
+//   * The time pass stages tiles of spatial columns with cp.async (one line per warp for n = 512).
+// Two 256-thread blocks run per SM (128 registers, at most about 110 KB of shared memory).  An
+// instance takes these kernels for all of its DST passes or for none; see pipe_dst_p.
 #include <algorithm>
 
 #include "fft_reg.cuh"
@@ -661,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 //   DFT over t'' of V[2t''+h][k1] and one radix-2 step across lanes u, u^16:
 //       X[k1 + 16 k2 + 256 h] = G_0[k2] + (-1)^h W_32^{k2} G_1[k2].
 //   The partner slot n-1-r of r = k1 + 16 k2 + 256 h is lane u^31, register 15-k2.
-// Tiles of 8 columns, NS cp.async stages; two blocks per SM.
+// Tiles of 8 columns come in through NS cp.async stages; two blocks run per SM.
 // ------------------------------------------------------------------------------------------
 template <int NS>
 __global__ void __launch_bounds__(kThreads, 2)
