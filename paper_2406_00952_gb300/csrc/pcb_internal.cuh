@@ -134,6 +134,17 @@ struct Sel {
   }
 };
 
+// family code <-> bit of Batch::fam_*_set: 0 -> 0, P -> log2 P, P + 64 -> log2 P + 6
+__host__ __device__ inline int fam_index(int code) {
+  if (!code) return 0;
+  int b = 0;
+  while ((2 << b) <= (code & 63)) ++b;
+  return b + ((code & 64) ? 6 : 0);
+}
+__host__ __device__ inline int fam_code(int index) {
+  return index == 0 ? 0 : index < 6 ? (1 << index) : ((1 << (index - 6)) | 64);
+}
+
 // ------------------------------------------------------------------------------------------
 // host-side launch helpers (defined in runtime.cu)
 // ------------------------------------------------------------------------------------------
@@ -153,10 +164,11 @@ struct Batch {
   double* partial;        // reduction partials
   const double* tols;     // per-instance tolerances for the scalar steps (device) or null
   int dst_q, time_q;      // register-FFT variant shared by every instance of the batch
-  // FP32 kernel families: pipe_pd / pipe_pt > 0 is the lanes-per-line P of the pipelined DST /
-  // time kernels (precond_pipe.cu) shared by every instance with work, 0 means the kernels of
+  // FP32 kernel families: pipe_pd / pipe_pt > 0 is the family code of the pipelined DST / time
+  // kernels (precond_pipe.cu) shared by every instance with work: the lanes per line P, plus 64
+  // when pass 2 hands the time pass contiguous time lines (n = 512).  0 means the kernels of
   // precond.cu for all, -1 a mix: one launch per family present, each selecting its instances by
-  // fam_dst / fam_time (device arrays [count]: P, or 0).  fam_*_set: bit log2(P) (bit 0 for 0).
+  // fam_dst / fam_time (device arrays [count] of codes).  fam_*_set: bit fam_index(code).
   int pipe_pd, pipe_pt;
   const int* fam_dst;
   const int* fam_time;

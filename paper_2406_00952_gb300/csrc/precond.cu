@@ -585,9 +585,9 @@ static cudaError_t dst_pass(const Batch& B, int stage, int in_slot, int out_slot
   if (B.pipe_pd > 0) return pipe_dst_pass(B, stage, in_slot, out_slot);
   Batch F = B;
   F.filt = B.fam_dst;
-  for (int b = 0; b <= 5; ++b) {
+  for (int b = 0; b < 12; ++b) {
     if (!(B.fam_dst_set >> b & 1)) continue;
-    F.filt_want = b ? 1 << b : 0;
+    F.filt_want = fam_code(b);
     F.pipe_pd = F.filt_want;
     const cudaError_t e = b ? pipe_dst_pass(F, stage, in_slot, out_slot) : dispatch_dst<R>(F, axis, in_slot, out_slot);
     if (e != cudaSuccess) return e;
@@ -600,9 +600,9 @@ static cudaError_t time_pass(const Batch& B, int kind) {
   if (B.pipe_pt > 0) return pipe_time_pass(B, kind);
   Batch F = B;
   F.filt = B.fam_time;
-  for (int b = 0; b <= 5; ++b) {
+  for (int b = 0; b < 12; ++b) {
     if (!(B.fam_time_set >> b & 1)) continue;
-    F.filt_want = b ? 1 << b : 0;
+    F.filt_want = fam_code(b);
     F.pipe_pt = F.filt_want;
     const cudaError_t e = b ? pipe_time_pass(F, kind) : dispatch_time<R>(F, kind);
     if (e != cudaSuccess) return e;

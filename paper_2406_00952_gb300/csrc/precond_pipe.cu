@@ -391,7 +391,11 @@ __host__ __device__ constexpr int rowsT_region() {   // complex elements per war
   return ((odd_scratch_per_warp<P>() + 11) / 16) * 16 + 4;
 }
 
-template <typename TIn, int P>
+// MODE 1 (pass 2 when the time lines are 512 long): tile (r, t0) is the lines (t0 + l, r) of the
+// rows r of LPB consecutive time steps, and the result goes to the time-major layout of scratch
+// buffer 1, value (half h, spatial point r N + p, time t) at h n m + (r N + p) n + t, so that the
+// time pass reads contiguous time lines.
+template <typename TIn, int P, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
     k_dst_rowsT(const Geom* __restrict__ G, const Slots* __restrict__ S, const int* __restrict__ off, int count,
                 Sel sel, int in_sel, int out_sel, int tot) {
@@ -421,14 +425,23 @@ __global__ void __launch_bounds__(kThreads, 2)
     it.inst = find_inst(off, count, tile);
     if (sel.skip(it.inst)) return it;
     const int lt = tile - off[it.inst];
-    it.t0 = lt / NBT;
-    it.r0 = (lt - it.t0 * NBT) * LPB;
-    it.nl = max(0, min(A, N - (it.r0 + warp * A)));
+    if (MODE == 0) {
+      it.t0 = lt / NBT;
+      it.r0 = (lt - it.t0 * NBT) * LPB;
+      it.nl = max(0, min(A, N - (it.r0 + warp * A)));
+    } else {
+      const int ntt = G[it.inst].n / LPB;        // tiles per row
+      it.r0 = lt / ntt;
+      it.t0 = (lt - it.r0 * ntt) * LPB;
+      it.nl = max(0, min(A, G[it.inst].n - (it.t0 + warp * A)));
+    }
     return it;
   };
   auto line_ptr = [&](const Item& it, int k, int h) {
     const View v = view_of(G[it.inst], S[it.inst], in_sel);
-    return (const TIn*)v.base + h * v.hs + it.t0 * v.ts + (long long)(it.r0 + warp * A + k) * v.rs;
+    if (MODE == 0)
+      return (const TIn*)v.base + h * v.hs + it.t0 * v.ts + (long long)(it.r0 + warp * A + k) * v.rs;
+    return (const TIn*)v.base + h * v.hs + (it.t0 + warp * A + k) * v.ts + (long long)it.r0 * v.rs;
   };
   // The 16-byte aligned span of a line is copied in 16-byte pieces.  Where that span would
   // leave the vector (a caller's buffer that is not 16-byte aligned), the line is copied value by
@@ -502,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
     __syncthreads();
-    if (on) {
+    if (on && MODE == 0) {
       const Geom& g = G[inst];
       const int lt = tile - off[inst];
       const int t0 = lt / NBT, r0 = (lt - t0 * NBT) * LPB;
@@ -515,6 +528,19 @@ __global__ void __launch_bounds__(kThreads, 2)
           const float2 v = src[p];
           d[(long long)p * ov.rs] = v.x;
           d[ov.hs + (long long)p * ov.rs] = v.y;
+        }
+      }
+    } else if (on) {
+      const Geom& g = G[inst];
+      const int l = tid % LPB;
+      if (cur.t0 + l < g.n) {
+        const long long hs = (long long)g.n * g.m;
+        float* d = (float*)g.scratch + 2LL * g.n * g.mp + (long long)cur.r0 * N * g.n + cur.t0 + l;
+        const float2* src = regions + (l / A) * RS + (l % A) * N;
+        for (int p = tid / LPB; p < N; p += kThreads / LPB) {
+          const float2 v = src[p];
+          d[(long long)p * g.n] = v.x;
+          d[hs + (long long)p * g.n] = v.y;
         }
       }
     }
@@ -669,7 +695,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 //   The partner slot n-1-r of r = k1 + 16 k2 + 256 h is lane u^31, register 15-k2.
 // Tiles of 8 columns come in through NS cp.async stages; two blocks run per SM.
 // ------------------------------------------------------------------------------------------
-template <int NS>
+// MODE 0: tiles of 8 spatial columns of buffer 0 (any layout), strided loads, result in place.
+// MODE 1: tiles of 8 spatial points (r, p0 .. p0+7) of the time-major buffer 1 (contiguous time
+// lines, 16-byte copies), result written to buffer 0 in the row layout of pass 4 (value
+// (t, r, p) at t mp + r lr + p): row segments of 8 values.
+template <int NS, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
     k_time512(const Geom* __restrict__ G, const int* __restrict__ off, int count, Sel sel, int kind, int tot) {
   constexpr int n = 512, LPB = kWarps;
@@ -696,15 +726,32 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int inst = find_inst(off, count, tile);
     if (sel.skip(inst)) return;
     const Geom& g = G[inst];
-    const int c0 = (tile - off[inst]) * LPB;
-    const int l = tid % LPB;
-    const bool cv = c0 + l < g.mp;
-    const float* y = (const float*)g.scratch + (cv ? c0 + l : 0);
-    const long long m = g.mp, mn = (long long)g.n * g.mp;
-    float2* d = stages + (size_t)st * LPB * PITCH + l * PITCH;
-    for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
-      cp_async<4>(&d[tt].x, y + tt * m, cv);
-      cp_async<4>(&d[tt].y, y + mn + tt * m, cv);
+    if (MODE == 0) {
+      const int c0 = (tile - off[inst]) * LPB;
+      const int l = tid % LPB;
+      const bool cv = c0 + l < g.mp;
+      const float* y = (const float*)g.scratch + (cv ? c0 + l : 0);
+      const long long m = g.mp, mn = (long long)g.n * g.mp;
+      float2* d = stages + (size_t)st * LPB * PITCH + l * PITCH;
+      for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
+        cp_async<4>(&d[tt].x, y + tt * m, cv);
+        cp_async<4>(&d[tt].y, y + mn + tt * m, cv);
+      }
+    } else {
+      // each warp copies its own time line: re[512] then im[512] (raw floats) into its tile row
+      const int lt = tile - off[inst], nbs = (g.N + LPB - 1) / LPB;
+      const int r = lt / nbs, p = (lt - r * nbs) * LPB + warp;
+      if (p < g.N) {
+        const float* y = (const float*)g.scratch + 2LL * g.n * g.mp + ((long long)r * g.N + p) * n;
+        const long long hs = (long long)g.n * g.m;
+        float* d = (float*)(stages + (size_t)st * LPB * PITCH + warp * PITCH);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          for (int c = lane; c < n / 4; c += 32) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(d + h * n + 4 * c);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(y + h * hs + 4 * c) : "memory");
+          }
+      }
     }
   };
 #pragma unroll
@@ -735,8 +782,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (on) {
       float2* ln = buf + warp * PITCH;
       float2 x[16];
+      if (MODE == 0) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) x[q] = cmul(ln[t + 32 * q], pre[t + 32 * q]);
+        for (int q = 0; q < 16; ++q) x[q] = cmul(ln[t + 32 * q], pre[t + 32 * q]);
+      } else {
+        const float* raw = (const float*)ln;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) x[q] = cmul(make_float2(raw[t + 32 * q], raw[n + t + 32 * q]), pre[t + 32 * q]);
+      }
       reg_dft<float2, float, 16>(x, false);
       __syncwarp();
 #pragma unroll
@@ -759,8 +812,16 @@ __global__ void __launch_bounds__(kThreads, 2)
         x[pos<16>(k2)] = make_float2(fmaf(sg, v.x, o.x), fmaf(sg, v.y, o.y));
       }
       // pointwise solve at r = k1 + 16 k2 + 256 h
-      const long long col = min((long long)(c0 + warp), g.mp - 1);  // padded columns compute junk
-      const int jj = (int)(col / g.lr), ii = min((int)(col - (long long)jj * g.lr), g.N - 1);
+      int jj, ii;
+      if (MODE == 0) {
+        const long long col = min((long long)(c0 + warp), g.mp - 1);  // padded columns compute junk
+        jj = (int)(col / g.lr);
+        ii = min((int)(col - (long long)jj * g.lr), g.N - 1);
+      } else {
+        const int lt = tile - off[inst], nbs = (g.N + LPB - 1) / LPB;
+        jj = lt / nbs;
+        ii = min((lt - jj * nbs) * LPB + warp, g.N - 1);               // points past N compute junk
+      }
       const float c = (float)(g.tau * (__ldg(&g.kap[ii]) + __ldg(&g.kap[jj])));
       const float a2 = (float)(g.alpha * g.alpha), alpha = (float)g.alpha;
       if (kind == PK_PS) {
@@ -810,10 +871,24 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int q = 0; q < 16; ++q) ln[t + 32 * q] = cscale(cmulc(x[pos<16>(q)], pre[t + 32 * q]), scale);
     }
     __syncthreads();
-    if (on) {
+    if (on && MODE == 0) {
       const int l = tid % LPB;
       if (c0 + l < g.mp) {
         float* y = (float*)g.scratch + c0 + l;
+        const long long m = g.mp, mn = (long long)g.n * g.mp;
+        const float2* srcl = buf + l * PITCH;
+        for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
+          const float2 v = srcl[tt];
+          y[tt * m] = v.x;
+          y[mn + tt * m] = v.y;
+        }
+      }
+    } else if (on) {
+      const int l = tid % LPB;
+      const int lt = tile - off[inst], nbs = (g.N + LPB - 1) / LPB;
+      const int r = lt / nbs, p = (lt - r * nbs) * LPB + l;
+      if (p < g.N) {
+        float* y = (float*)g.scratch + (long long)r * g.lr + p;
         const long long m = g.mp, mn = (long long)g.n * g.mp;
         const float2* srcl = buf + l * PITCH;
         for (int tt = tid / LPB; tt < n; tt += kThreads / LPB) {
@@ -888,32 +963,41 @@ cudaError_t launch_rows(const Batch& B, int in_sel, int out_sel) {
                            (const Slots*)B.S, B.off_dst_i[1], B.count, B.sel(), in_sel, out_sel, B.tot_dst_i[1]);
 }
 
-template <typename TIn, int P>
+template <typename TIn, int P, int MODE>
 cudaError_t launch_rowsT(const Batch& B, int in_sel, int out_sel) {
   static int resident = 0;
-  return launch_persistent(k_dst_rowsT<TIn, P>, dst_rowsT_smem<TIn, P>(), B.tot_dst_j[1], resident, B.stream, B.G,
-                           (const Slots*)B.S, B.off_dst_j[1], B.count, B.sel(), in_sel, out_sel, B.tot_dst_j[1]);
+  // MODE 0 tiles: (time step, LPB rows) -> dst_j offsets; MODE 1 tiles: (row, LPB time steps),
+  // as many as the contiguous-line tiles -> dst_i offsets
+  const int* off = MODE == 0 ? B.off_dst_j[1] : B.off_dst_i[1];
+  const int tot = MODE == 0 ? B.tot_dst_j[1] : B.tot_dst_i[1];
+  return launch_persistent(k_dst_rowsT<TIn, P, MODE>, dst_rowsT_smem<TIn, P>(), tot, resident, B.stream, B.G,
+                           (const Slots*)B.S, off, B.count, B.sel(), in_sel, out_sel, tot);
 }
 
 template <int P>
-cudaError_t launch_time(const Batch& B, int kind) {
+cudaError_t launch_time(const Batch& B, int kind, bool time_major = false) {
   static int resident = 0;
   if (P == 16) {
-    static int resident512 = 0;
-    return launch_persistent(k_time512<kNsTime>, time512_smem(), B.tot_time[1], resident512, B.stream, B.G,
+    static int resident512[2] = {0, 0};
+    if (time_major)
+      return launch_persistent(k_time512<kNsTime, 1>, time512_smem(), B.tot_time[1], resident512[1], B.stream, B.G,
+                               B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
+    return launch_persistent(k_time512<kNsTime, 0>, time512_smem(), B.tot_time[1], resident512[0], B.stream, B.G,
                              B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
   }
   return launch_persistent(k_time_pipe<P, kNsTime>, time_smem<P>(), B.tot_time[1], resident, B.stream, B.G,
                            B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
 }
 
-// pass `stage` (1, 2, 4, 5) of the FP32 apply; scratch buffers: -1 = buffer 0, -2 = buffer 1
+// pass `stage` (1, 2, 4, 5) of the FP32 apply; scratch buffers: -1 = buffer 0, -2 = buffer 1.
+// time_major: pass 2 writes time-major lines to buffer 1 and the time pass writes buffer 0 back
+// in the row layout, so pass 4 finds its input where it would otherwise be.
 template <int P>
-cudaError_t dst_pass_p(const Batch& B, int stage, int in_slot, int out_slot) {
+cudaError_t dst_pass_p(const Batch& B, int stage, int in_slot, int out_slot, bool time_major) {
   switch (stage) {
-    case 1: return launch_rowsT<double, P>(B, in_slot, -1);
-    case 2: return launch_rows<float, float, P>(B, -1, -1);
-    case 4: return launch_rowsT<float, P>(B, -1, -2);
+    case 1: return launch_rowsT<double, P, 0>(B, in_slot, -1);
+    case 2: return time_major ? launch_rowsT<float, P, 1>(B, -1, -2) : launch_rows<float, float, P>(B, -1, -1);
+    case 4: return launch_rowsT<float, P, 0>(B, -1, -2);
     default: return launch_rows<float, double, P>(B, -2, out_slot);
   }
 }
@@ -935,6 +1019,15 @@ int pipe_time_p(const Geom& g) {
   const int P = g.n / 32;
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
+// family codes: P, plus 64 when pass 2 writes time-major lines for the n = 512 time pass
+int pipe_dst_code(const Geom& g) {
+  const int p = pipe_dst_p(g);
+  return p ? (p | (g.n == 512 ? 64 : 0)) : 0;
+}
+int pipe_time_code(const Geom& g) {
+  const int p = pipe_time_p(g);
+  return p ? (p | (pipe_dst_p(g) && g.n == 512 ? 64 : 0)) : 0;
+}
 // spatial columns per tile of the pipelined time pass (n = 512: one line per warp)
 int pipe_time_cols(int n) { return n == 512 ? kWarps : kThreads / (n / 32); }
 // lines per tile of the pipelined DST passes
@@ -944,22 +1037,24 @@ cudaError_t pipe_upload_constants() { return upload_w96(); }
 
 // DST pass `stage` of the FP32 apply; B.pipe_pd is the P shared by the instances it covers.
 cudaError_t pipe_dst_pass(const Batch& B, int stage, int in_slot, int out_slot) {
-  switch (B.pipe_pd) {
-    case 2: return dst_pass_p<2>(B, stage, in_slot, out_slot);
-    case 4: return dst_pass_p<4>(B, stage, in_slot, out_slot);
-    case 8: return dst_pass_p<8>(B, stage, in_slot, out_slot);
-    case 16: return dst_pass_p<16>(B, stage, in_slot, out_slot);
-    case 32: return dst_pass_p<32>(B, stage, in_slot, out_slot);
+  const bool tm = B.pipe_pd & 64;
+  switch (B.pipe_pd & 63) {
+    case 2: return dst_pass_p<2>(B, stage, in_slot, out_slot, tm);
+    case 4: return dst_pass_p<4>(B, stage, in_slot, out_slot, tm);
+    case 8: return dst_pass_p<8>(B, stage, in_slot, out_slot, tm);
+    case 16: return dst_pass_p<16>(B, stage, in_slot, out_slot, tm);
+    case 32: return dst_pass_p<32>(B, stage, in_slot, out_slot, tm);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t pipe_time_pass(const Batch& B, int kind) {
-  switch (B.pipe_pt) {
+  const bool tm = B.pipe_pt & 64;
+  switch (B.pipe_pt & 63) {
     case 2: return launch_time<2>(B, kind);
     case 4: return launch_time<4>(B, kind);
     case 8: return launch_time<8>(B, kind);
-    case 16: return launch_time<16>(B, kind);
+    case 16: return launch_time<16>(B, kind, tm);
     case 32: return launch_time<32>(B, kind);
     default: return cudaErrorInvalidValue;
   }

@@ -45,6 +45,8 @@ size_t time_smem_bytes(const Geom& g, int p);
 int padded_len_host(int len);
 int pipe_dst_p(const Geom& g);
 int pipe_time_p(const Geom& g);
+int pipe_dst_code(const Geom& g);
+int pipe_time_code(const Geom& g);
 int pipe_time_cols(int n);
 int pipe_dst_lines(int L);
 cudaError_t upload_constants();
@@ -165,6 +167,7 @@ void set_shapes(Geom& g) {
     if (p == 1 && pt) cpb = pipe_time_cols(g.n);
     g.time_cpb[p] = cpb;
     g.time_blocks[p] = (int)(((p == 1 && pt ? g.mp : (long long)g.m) + cpb - 1) / cpb);
+    if (p == 1 && (pipe_time_code(g) & 64)) g.time_blocks[p] = g.N * ((g.N + cpb - 1) / cpb);   // rows of points
   }
   const int ncb = (g.m + 255) / 256;
   if (g.theta == 1.0) {
@@ -237,14 +240,15 @@ int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStream_t st
   // FP32 kernel families (pipelined P or 0) of the instances with work (empty server slots have none)
   const size_t fam_at = staging.size();
   B.fam_dst_set = B.fam_time_set = 0;
-  for (const Geom& g : gs) staging.push_back(pipe_dst_p(g));
-  for (const Geom& g : gs) staging.push_back(pipe_time_p(g));
+  for (const Geom& g : gs) staging.push_back(pipe_dst_code(g));
+  for (const Geom& g : gs) staging.push_back(pipe_time_code(g));
   for (const Geom& g : gs) {
-    const int pd = pipe_dst_p(g), pt = pipe_time_p(g);
-    if (g.dst_blocks_i[1] > 0) B.fam_dst_set |= 1 << (pd ? __builtin_ctz(pd) : 0);
-    if (g.time_blocks[1] > 0) B.fam_time_set |= 1 << (pt ? __builtin_ctz(pt) : 0);
+    if (g.dst_blocks_i[1] > 0) B.fam_dst_set |= 1 << fam_index(pipe_dst_code(g));
+    if (g.time_blocks[1] > 0) B.fam_time_set |= 1 << fam_index(pipe_time_code(g));
   }
-  auto uniform = [](int set) { return __builtin_popcount(set) == 1 ? (set == 1 ? 0 : set) : (set ? -1 : 0); };
+  auto uniform = [](int set) {
+    return __builtin_popcount(set) == 1 ? fam_code(__builtin_ctz(set)) : (set ? -1 : 0);
+  };
   B.pipe_pd = uniform(B.fam_dst_set);
   B.pipe_pt = uniform(B.fam_time_set);
   B.fam_dst = doff + fam_at;
