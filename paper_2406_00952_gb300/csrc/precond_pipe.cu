@@ -491,9 +491,22 @@ __global__ void __launch_bounds__(kThreads, 2)
         s0 += (int)(((uintptr_t)line_ptr(cur, grp, 0) & 15) / sizeof(TIn));
         s1 += (int)(((uintptr_t)line_ptr(cur, grp, 1) & 15) / sizeof(TIn));
       }
+      // FP64 input: each value is read and converted once; the mirrored half (q >= 16) comes from
+      // the lane holding it: -x_{M-s-1} with s = t + P q is lane P - t's value at q' = 31 - q
+      // (lane 0: its own value at 32 - q)
+      constexpr bool kShuffleMirror = sizeof(TIn) == 8;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int s = t + P * q;
+        if (kShuffleMirror && q >= 16) {
+          const float2 a = x[31 - q];
+          float2 v;
+          v.x = __shfl_sync(0xffffffffu, a.x, (P - t) & (P - 1), P);
+          v.y = __shfl_sync(0xffffffffu, a.y, (P - t) & (P - 1), P);
+          if (t == 0) v = q > 16 ? x[32 - q] : make_float2(0.f, 0.f);
+          x[q] = make_float2(-v.x, -v.y);
+          continue;
+        }
         const bool ok = lv && (q < 16 ? s > 0 : s > L);
         const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
         float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
