@@ -354,7 +354,14 @@ def main():
                          "frac": achieved / hbm, "traffic": profile_traffic(), "kernel": "precond apply |P_S|^-1 (FP32)",
                          "alg_bytes_per_launch": alg_bytes, "avg_ms": pms / applies, "peak_kind": peak_kind},
             "kernels": {"precond_ms_share": pms / ms, "matvec_ms_share": mvms / ms, "matvec_avg_ms": mvms / mvs,
-                        "matvec_alg_gbs": mv_ach},
+                        "matvec_alg_gbs": mv_ach,
+                        # the product (with the MINRES epilogue) is bound by FP64 issue: 10 FP64
+                        # operations per unknown against the nominal FP64 rate of 1.25 TFLOP/s,
+                        # i.e. 625 G FMA-class instructions/s
+                        "matvec_roofline": {"bound": "alu", "unit": "G FP64 ops/s",
+                                            "achieved": 10.0 * unknowns / (mvms / mvs / 1e3) / 1e9,
+                                            "peak": 625.0,
+                                            "frac": 10.0 * unknowns / (mvms / mvs / 1e3) / 1e9 / 625.0}},
             "fp64_gpu": fp64,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -65,7 +65,7 @@ def test_precond_parity(P, shape, kind):
 
 @pytest.mark.parametrize("shape", [(511, 4, 1.0, 1e-2), (63, 64, 0.5, 1e-2)], ids=lambda s: "N%d-n%d" % s[:2])
 def test_precond_misaligned_input(P, shape):
-    # a user input that is not 16-byte aligned takes the per-instance x1-line kernel
+    # a caller input that is not 16-byte aligned: the first pass copies its lines value by value
     N, n, theta, gamma = shape
     prob = ds.Problem(N, n, theta, gamma)
     v = synth.random_vector(2 * prob.m * n, seed=300 + N)
@@ -265,9 +265,8 @@ def test_variable_a_matvec_and_fgmres(P):
 
 
 # ---------------------------------------------------------------- batches with shared launches
-def _batch_instances():
-    shapes = [(15, 16, 1.0, 1e-2), (31, 8, 0.5, 1e-4), (47, 32, 1.0, 1e-5), (63, 16, 0.5, 1e-2),
-              (31, 32, 1.0, 1e-1), (23, 64, 0.5, 1e-3)]
+def _batch_instances(shapes=((15, 16, 1.0, 1e-2), (31, 8, 0.5, 1e-4), (47, 32, 1.0, 1e-5), (63, 16, 0.5, 1e-2),
+                             (31, 32, 1.0, 1e-1), (23, 64, 0.5, 1e-3))):
     out = []
     for k, (N, n, theta, gamma) in enumerate(shapes):
         prob = ds.Problem(N, n, theta, gamma)
@@ -277,9 +276,17 @@ def _batch_instances():
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_solve_uneven(P, precision):
-    insts = _batch_instances()
+# instances of every FP32 kernel family: pipelined DST with the time-major hand-off (N = 31,
+# n = 512), pipelined DST with P = 2 and P = 4, per-instance DST with a pipelined time pass
+# (N = 15, n = 64), and per-instance kernels throughout (N = 47, n = 32)
+FAMILY_SHAPES = ((31, 512, 1.0, 1e-2), (31, 128, 0.5, 1e-3), (63, 64, 1.0, 1e-4), (15, 64, 1.0, 1e-2),
+                 (47, 32, 0.5, 1e-3))
+
+
+@pytest.mark.parametrize("precision,shapes", [("fp64", None), ("mixed", None), ("mixed", FAMILY_SHAPES)],
+                         ids=["fp64", "mixed", "mixed-families"])
+def test_batch_solve_uneven(P, precision, shapes):
+    insts = _batch_instances(shapes) if shapes else _batch_instances()
     probs = [P.Problem(pr.N, pr.n, pr.theta, pr.gamma, precision=precision) for pr, _ in insts]
     bs = [dev(b) for _, b in insts]
     xs, infos = P.batch_solve(probs, bs, tol=1e-8, restart=16)
