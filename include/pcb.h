@@ -83,7 +83,9 @@ typedef struct {
   double theta;           /* 1/2 <= theta <= 1                                                 */
   double T;               /* horizon, > 0                                                      */
   double gamma;           /* regularisation, > 0                                               */
-  double zeta;            /* omega = exp(i zeta); this build supports zeta = pi (skew-circulant)*/
+  double zeta;            /* omega = exp(i zeta), Sec. 2; pi (skew-circulant) runs the fastest */
+                          /* kernels, other values (0: circulant) run per-instance kernels;   */
+                          /* variable a(x) needs zeta = pi                                     */
   const double* a_edges;  /* host; NULL => a(x) = 1; else 2*N*(N+1) values of a at cell-edge   */
                           /* midpoints: first ax[j][e] (N rows of N+1; x1-edge between nodes   */
                           /* e and e+1 of row j+1), then ay[e][i] (N+1 rows of N)              */
@@ -94,8 +96,10 @@ typedef struct {
 
 /* Validate the descriptor, compute the spectral tables (Sec. 3.5: lambda_k(S_n), the eigenvalues
  * of -L, twiddle tables) and allocate the workspaces.  Errors: INVALID_ARG, UNSUPPORTED
- * (zeta != pi, N+1 not 2^a 3^b, n not a power of two, N > 511, variable a with N != 2^k - 1),
- * OUT_OF_MEMORY, CUDA.  Remark 1's singular S^(2) cannot occur for the supported (zeta, n). */
+ * (N+1 not 2^a 3^b, n not a power of two, N > 511, variable a with N != 2^k - 1 or zeta != pi),
+ * OUT_OF_MEMORY, CUDA.  A zero eigenvalue of S^(2) (Remark 1, e.g. theta = 1/2, zeta = 0) is
+ * replaced by 1.  For zeta other than 0 and pi the preconditioners are complex; applied to real
+ * vectors they return the real part (a real symmetric positive definite operator for |P_S|). */
 int pcb_create(const pcb_desc* desc, pcb_problem** out);
 void pcb_destroy(pcb_problem* p);
 const char* pcb_status_str(int status);

@@ -52,6 +52,8 @@ struct Geom {
   int L, M;                       // L = N+1 (DST-I order), M = 2L (extended FFT length)
   long long mn;                   // m*n (one half of the all-at-once vector)
   double theta, tau, gamma, alpha, h, sqrt_gamma;
+  double zeta;                    // omega = exp(i zeta)
+  int zeta_pi;                    // 1 when zeta = pi: the two halves share one complex time line
   double c;                       // tau / h^2
   int var_a;                      // 0: a = 1; 1: coefficient tables below
   // FP32 scratch layout of the pipelined passes: rows of lr values (lr = L + 16 when the pipelined

@@ -289,8 +289,122 @@ __global__ void __launch_bounds__(256, 2) k_dst_any(const Geom* __restrict__ G, 
 // Time pass: forward DFT of (half0 + i half1) * exp(-i pi t/n), pointwise solve per frequency
 // pair, inverse DFT, unscale.  In place on the scratch.
 // ------------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------------
+// Time pass for a general zeta (omega = exp(i zeta), Sec. 3.5 with the circulant zeta = 0 and any
+// other choice of Sec. 2).  Slot r of the DFT of x_t exp(-i zeta t/n) has frequency
+// psi_r = -(zeta + 2 pi r)/n; unlike zeta = pi, the transform of a real series has no conjugate
+// partner slot, so each half runs as its own complex line: forward DFT of v_h(t) exp(-i zeta t/n),
+// the per-slot solve on (V_1, V_2) at each r, inverse DFT, unscale, real part (reading A12:
+// the operator applied to real vectors is Re(P^-1)).
+// ------------------------------------------------------------------------------------------
+template <typename R, int Q>
+__device__ __forceinline__ void time_body_general(const Geom& g, int lb, int kind) {
+  using T = cx<R>;
+  R* __restrict__ y = (R*)g.scratch;
+  const int n = g.n, m = g.m, N = g.N, cpb = g.time_cpb[sizeof(R) == 4];
+  const int ls = padded_len(n);
+  const long long mn = g.mn;
+  const int c0 = lb * cpb;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = (T*)smem_raw;                        // line 2l + h: column c0 + l, half h
+  const T* __restrict__ pr = pre<R>(g);
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  const int nl = 2 * cpb;
+  for (int e = tid; e < cpb * n; e += nthr) {
+    const int l = e % cpb, t = e / cpb;
+    const int col = c0 + l;
+    const bool cv = col < m;
+    const long long a = (long long)t * m + (cv ? col : 0);
+    const T w = __ldg(&pr[t]);
+    const R v0 = cv ? y[a] : (R)0, v1 = cv ? y[mn + a] : (R)0;
+    tile[(2 * l) * ls + pidx(t)] = mk<R>(v0 * w.x, v0 * w.y);
+    tile[(2 * l + 1) * ls + pidx(t)] = mk<R>(v1 * w.x, v1 * w.y);
+  }
+  __syncthreads();
+  const int P = n / Q;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  const int lpw = 32 / P;
+  const int t = lane % P;
+  const T* __restrict__ tw = twt<R>(g);
+  T twq[Q < 32 ? Q : 1];
+  if constexpr (Q < 32) {
+#pragma unroll
+    for (int k1 = 0; k1 < Q; ++k1) twq[k1] = __ldg(&tw[t * k1]);
+  }
+  const int k2 = bitrev(t, P);
+  for (int dir = 0; dir < 2; ++dir) {            // 0: forward, 1: inverse
+    LaneStages<T, R> st;
+    lane_stages<T, R>(st, t, P, dir == 1);
+    for (int lbase = warp * lpw; lbase < nl; lbase += nw * lpw) {
+      const int l = lbase + lane / P;
+      const bool lv = l < nl;
+      T* line = tile + (lv ? l : 0) * ls;
+      LineFFT<T, R, Q> f;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) f.x[q] = lv ? line[pidx(t + P * q)] : mk<R>(0, 0);
+      __syncwarp();
+      f.run(t, P, st, tw, twq, line, dir == 1);
+      __syncwarp();
+      if (lv) {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) line[pidx(LineFFT<T, R, Q>::owned(j, t, k2))] = f.value(j);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (dir == 1) break;
+    // per-slot solve of the pair (V_1, V_2) at slot r of column c0 + l
+    const T* __restrict__ mu = mutab<R>(g);
+    const R alpha = (R)g.alpha, a2 = (R)(g.alpha * g.alpha);
+    for (int e = tid; e < cpb * n; e += nthr) {
+      const int l = e / n, r = e - l * n;
+      const int col = min(c0 + l, m - 1);
+      const int jj = col / N, ii = col - jj * N;
+      const R c = (R)(g.tau * (__ldg(&g.kap[ii]) + __ldg(&g.kap[jj])));
+      const T mr = __ldg(&mu[r]);
+      T* p1 = tile + (2 * l) * ls + pidx(r);
+      T* p2 = tile + (2 * l + 1) * ls + pidx(r);
+      const T V1 = *p1, V2 = *p2;
+      if (kind == PK_PS) {
+        // [[lam, -alpha], [alpha, conj(lam)]] [U1; U2] = [V1; V2], lam = lambda_r + c
+        const T lam = mk<R>(mr.x + c, mr.y);
+        const R inv = (R)1 / (lam.x * lam.x + lam.y * lam.y + a2);
+        *p1 = cscale(cadd(cmul(cconj(lam), V1), cscale(V2, alpha)), inv);
+        *p2 = cscale(csub(cmul(lam, V2), cscale(V1, alpha)), inv);
+      } else {
+        R w;
+        if (kind == PK_ABS_PS) {
+          const R lx = mr.x + c;
+          w = rsqrt_<R>(lx * lx + mr.y * mr.y + a2);
+        } else {
+          w = (R)1 / (sqrt(mr.x * mr.x + mr.y * mr.y + a2) + c);
+        }
+        *p1 = cscale(V1, w);
+        *p2 = cscale(V2, w);
+      }
+    }
+    __syncthreads();
+  }
+  const R sc = (R)1 / (R)n;
+  for (int e = tid; e < cpb * n; e += nthr) {
+    const int l = e % cpb, tt = e / cpb;
+    const int col = c0 + l;
+    if (col < m) {
+      const T w = __ldg(&pr[tt]);
+      const T z0 = tile[(2 * l) * ls + pidx(tt)], z1 = tile[(2 * l + 1) * ls + pidx(tt)];
+      const long long a = (long long)tt * m + col;
+      y[a] = (z0.x * w.x + z0.y * w.y) * sc;        // Re(z conj(w)) / n
+      y[mn + a] = (z1.x * w.x + z1.y * w.y) * sc;
+    }
+  }
+}
+
 template <typename R, int Q>
 __device__ __forceinline__ void time_body(const Geom& g, int lb, int kind) {
+  if (!g.zeta_pi) {
+    time_body_general<R, Q>(g, lb, kind);
+    return;
+  }
   using T = cx<R>;
   R* __restrict__ y = (R*)g.scratch;
   const int n = g.n, m = g.m, N = g.N, cpb = g.time_cpb[sizeof(R) == 4];   // cpb: power of two
@@ -468,7 +582,8 @@ size_t dst_smem_bytes(const Geom& g, int p) {
 }
 int padded_len_host(int len) { return padded_len(len); }
 size_t time_smem_bytes(const Geom& g, int p) {
-  return (size_t)g.time_cpb[p] * padded_len(g.n) * (p ? sizeof(float2) : sizeof(double2));
+  // general zeta: two complex lines per spatial column
+  return (size_t)(g.zeta_pi ? 1 : 2) * g.time_cpb[p] * padded_len(g.n) * (p ? sizeof(float2) : sizeof(double2));
 }
 
 cudaError_t pipe_upload_constants();

@@ -1028,7 +1028,7 @@ int pipe_dst_p(const Geom& g) {
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
 int pipe_time_p(const Geom& g) {
-  if (g.var_a || g.n % 32) return 0;
+  if (g.var_a || !g.zeta_pi || g.n % 32) return 0;   // general zeta: per-instance kernels
   const int P = g.n / 32;
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }

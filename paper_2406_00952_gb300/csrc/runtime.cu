@@ -316,8 +316,8 @@ int validate_desc(const pcb_desc* d) {
       (d->precision != PCB_FP64 && d->precision != PCB_MIXED) || !std::isfinite(d->zeta) ||
       !std::isfinite(d->gamma) || !std::isfinite(d->T))
     return PCB_ERR_INVALID_ARG;
-  // supported: zeta = pi, n a power of two <= 1024, N+1 = 2^a 3^b with N <= 511
-  if (std::fabs(d->zeta - M_PI) > 1e-12) return PCB_ERR_UNSUPPORTED;
+  // supported: any zeta (multigrid route: zeta = pi), n a power of two <= 1024, N+1 = 2^a 3^b with N <= 511
+  if (d->a_edges && std::fabs(d->zeta - M_PI) > 1e-12) return PCB_ERR_UNSUPPORTED;
   if (!pow2(d->n) || d->n > 1024) return PCB_ERR_UNSUPPORTED;
   if (d->N > 511) return PCB_ERR_UNSUPPORTED;
   FftPlan pd, pt;
@@ -342,6 +342,8 @@ void init_geom(const pcb_desc* d, Geom& g) {
   g.theta = d->theta; g.tau = d->T / d->n; g.gamma = d->gamma; g.alpha = g.tau / std::sqrt(d->gamma);
   g.h = 1.0 / (d->N + 1); g.sqrt_gamma = std::sqrt(d->gamma); g.c = g.tau / (g.h * g.h);
   g.var_a = d->a_edges ? 1 : 0;
+  g.zeta = d->zeta;
+  g.zeta_pi = std::fabs(d->zeta - M_PI) <= 1e-12 ? 1 : 0;
   make_plan(g.M, g.pdst);
   make_plan(g.n, g.ptime);
   g.dst_q = dst_Q(g.N);
@@ -372,11 +374,12 @@ void fill_tables(const pcb_desc* d, const Geom& g, const TableLayout& t, unsigne
     const double s = std::sin(q * M_PI * g.h / 2.0);
     kap[q - 1] = 4.0 / (g.h * g.h) * s * s;
   }
-  // lambda(S_n) at F-slot r: psi_r = -pi (2r+1)/n, f1/f2 with f1 = 1 - e^{i psi}, f2 = theta + (1-theta) e^{i psi}
+  // lambda(S_n) at F-slot r: psi_r = -(zeta + 2 pi r)/n (zeta = pi: -pi (2r+1)/n), f1/f2 with
+  // f1 = 1 - e^{i psi}, f2 = theta + (1-theta) e^{i psi}
   double2* mud = (double2*)(host + t.mud);
   float2* muf = (float2*)(host + t.muf);
   for (int r = 0; r < n; ++r) {
-    const double psi = -M_PI * (2.0 * r + 1.0) / n;
+    const double psi = g.zeta_pi ? -M_PI * (2.0 * r + 1.0) / n : -(g.zeta + 2.0 * M_PI * r) / n;
     const double c = std::cos(psi), s = std::sin(psi);
     const double f1r = 1.0 - c, f1i = -s;
     double f2r = g.theta + (1.0 - g.theta) * c, f2i = (1.0 - g.theta) * s;
@@ -398,7 +401,7 @@ void fill_tables(const pcb_desc* d, const Geom& g, const TableLayout& t, unsigne
   double2* pred = (double2*)(host + t.pred);
   float2* pref = (float2*)(host + t.pref);
   for (int k = 0; k < n; ++k) {
-    const double a = -M_PI * (double)k / n;
+    const double a = (g.zeta_pi ? -M_PI : -g.zeta) * (double)k / n;   // exp(-i zeta t / n)
     pred[k].x = std::cos(a); pred[k].y = std::sin(a);
     pref[k].x = (float)pred[k].x; pref[k].y = (float)pred[k].y;
   }

@@ -31,9 +31,14 @@ def test_create_rejects_invalid_descriptors_without_touching_the_gpu():
         d = _lib.PcbDesc(b["N"], b["n"], b["theta"], 1.0, b["gamma"], 3.141592653589793, None, 0, 2, None)
         h = ctypes.c_void_p()
         assert lib.pcb_create(ctypes.byref(d), ctypes.byref(h)) == -1
-    # unsupported: zeta != pi, n not a power of two, N+1 not 2^a 3^b
-    for N, n, z in ((3, 4, 0.0), (3, 6, 3.141592653589793), (4, 4, 3.141592653589793)):
+    # unsupported: n not a power of two, N+1 not 2^a 3^b
+    for N, n, z in ((3, 6, 3.141592653589793), (4, 4, 3.141592653589793)):
         d = _lib.PcbDesc(N, n, 1.0, 1.0, 1e-2, z, None, 0, 2, None)
         h = ctypes.c_void_p()
         assert lib.pcb_create(ctypes.byref(d), ctypes.byref(h)) == -2
+    # unsupported: variable a(x) with zeta != pi (the multigrid route pairs conjugate slots)
+    a = (ctypes.c_double * (2 * 3 * 4))(*([1.0] * 24))
+    d = _lib.PcbDesc(3, 4, 1.0, 1.0, 1e-2, 0.4, a, 0, 2, None)
+    h = ctypes.c_void_p()
+    assert lib.pcb_create(ctypes.byref(d), ctypes.byref(h)) == -2
     assert lib.pcb_create(None, None) == -1

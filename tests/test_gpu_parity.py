@@ -79,6 +79,44 @@ def test_precond_misaligned_input(P, shape):
     assert rel(out, ref) <= 2e-6, rel(out, ref)
 
 
+ZETA_SHAPES = [(15, 16, 1.0, 1e-2, 0.0), (31, 64, 0.5, 1e-3, 0.4), (63, 32, 1.0, 1e-4, 2.0),
+               (47, 512, 1.0, 1e-2, 1.0), (23, 1024, 0.5, 1e-2, 0.0)]
+
+
+@pytest.mark.parametrize("shape", ZETA_SHAPES, ids=lambda s: "N%d-n%d-th%g-g%g-z%g" % s)
+@pytest.mark.parametrize("kind", ["abs_ps", "ps", "pms"])
+def test_precond_parity_general_zeta(P, shape, kind):
+    # omega = exp(i zeta) other than -1 (zeta = 0: circulant): two complex time lines per point,
+    # the real part of the complex operator (reading A12)
+    N, n, theta, gamma, zeta = shape
+    prob = ds.Problem(N, n, theta, gamma, zeta=zeta)
+    v = synth.random_vector(2 * prob.m * n, seed=500 + N + n)
+    ref = ORACLE[kind](prob, v)
+    gp = P.Problem(N, n, theta, gamma, zeta=zeta, precision="fp64")
+    out64 = gp.precond_apply(dev(v), kind=kind, precision="fp64").cpu().numpy()
+    out32 = gp.precond_apply(dev(v), kind=kind, precision="mixed").cpu().numpy()
+    assert rel(out64, ref) <= 1e-12, rel(out64, ref)
+    assert rel(out32, ref) <= 2e-6, rel(out32, ref)
+
+
+@pytest.mark.parametrize("zeta", [0.0, 0.4])
+def test_same_algorithm_iterates_general_zeta(P, zeta):
+    """MINRES-|P_S| with omega = exp(i zeta): oracle and GPU iterates after 3 and 8 steps (FP64)."""
+    inst = synth.config0()
+    prob = ds.Problem(inst.N, inst.n, 1.0, inst.gamma, zeta=zeta)
+    b = ds.rhs_minres(prob, inst.g, inst.f)
+    for k in (3, 8):
+        xo, _ = _oracle_solve(prob, b, "minres", "abs_ps", 1e-10, fixed=k)
+        gp = P.Problem(inst.N, inst.n, 1.0, inst.gamma, zeta=zeta, precision="fp64")
+        x, info = gp.solve(dev(b), method="minres", precond="abs_ps", fixed_iterations=k)
+        assert info["iterations"] == k
+        assert rel(x.cpu().numpy(), xo) <= 1e-10, rel(x.cpu().numpy(), xo)
+    gm = P.Problem(inst.N, inst.n, 1.0, inst.gamma, zeta=zeta, precision="mixed")
+    x, info = gm.solve(dev(b), tol=1e-8)
+    assert info["relres"] <= 1e-8
+    assert np.linalg.norm(b - op.matvec_A(prob, x.cpu().numpy())) / np.linalg.norm(b) <= 1.5e-8
+
+
 def test_precond_special_values(P):
     # exact zeros (both signs) and values outside the FP32 normal range take the conversion
     # fallbacks of the first and last pass; an all-zero input gives an exactly zero output
