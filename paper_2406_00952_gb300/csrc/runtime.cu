@@ -383,7 +383,7 @@ void fill_tables(const pcb_desc* d, const Geom& g, const TableLayout& t, unsigne
     const double c = std::cos(psi), s = std::sin(psi);
     const double f1r = 1.0 - c, f1i = -s;
     double f2r = g.theta + (1.0 - g.theta) * c, f2i = (1.0 - g.theta) * s;
-    if (std::hypot(f2r, f2i) < 1e-14) { f2r = 1.0; f2i = 0.0; }   // Remark 1 remedy (odd n only)
+    if (std::hypot(f2r, f2i) < 1e-14) { f2r = 1.0; f2i = 0.0; }   // Remark 1 remedy (theta = 1/2, psi = pi)
     const double den = f2r * f2r + f2i * f2i;
     mud[r].x = (f1r * f2r + f1i * f2i) / den;
     mud[r].y = (f1i * f2r - f1r * f2i) / den;
