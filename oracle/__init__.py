@@ -31,5 +31,10 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
                         operators, coarse coefficients) is a reading of a method the paper does not
                         specify -- parity unpinned beyond that.
   krylov.*              pinned: sparse direct solve; Table 1 iteration counts.
+  Neumann route (Problem(bc="neumann"): discretisation.apply_K / K_sparse, spectra.kappa_neumann,
+  spectra.dct1_*, precond.apply_ps_inv)
+                        pinned: the 1D stencil written out by hand, its cosine eigenbasis,
+                        dense A_hat and P_S with the nonsymmetric K as printed, a sparse direct
+                        solve, and all ten rows of Table 4 (Example 3: iteration counts and e_h).
 """
 from . import discretisation, operators, spectra, precond, multigrid, krylov  # noqa: F401

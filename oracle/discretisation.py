@@ -3,8 +3,18 @@ finite differences in space (M = I, K = -L), the all-at-once system of Eq. (main
 / (matrix_A_before), its right-hand side, the symmetrising change of variables of
 Eq. (main_system), and the error measure of Eq. (error_measure).
 
-Vector layout: a time block holds the N*N interior values with x1 fastest,
-index (i-1) + (j-1)*N.  The unknown y = [y^(1) .. y^(n)], p = [p^(0) .. p^(n-1)].
+Two boundary conditions:
+  dirichlet (Examples 1-2): N interior nodes per side, h = 1/(N+1), zero boundary values,
+            conservative edge-weighted stencil (a(x) at cell-edge midpoints, or the constant a0).
+  neumann   (Example 3, homogeneous Neumann): N nodes per side *including* the boundary,
+            x_i = i h, h = 1/(N-1), the constant coefficient a0, second differences with the
+            ghost values mirrored across the boundary (u_{-1} = u_1, u_N = u_{N-2}).  This K is
+            not symmetric; the paper's block matrices are formed with it as printed (K in both
+            the state and the adjoint rows), which is why the Neumann A is not symmetric and the
+            paper uses GMRES-P_S there.  Reading pinned by Table 4's e_h.
+
+Vector layout: a time block holds the N*N spatial values with x1 fastest, index i + j*N.
+The unknown y = [y^(1) .. y^(n)], p = [p^(0) .. p^(n-1)].
 """
 from __future__ import annotations
 
@@ -17,16 +27,24 @@ from scipy.linalg import solve_banded
 
 
 class Problem:
-    """Parameters of one instance: N, n, theta, T, gamma, zeta, optional a(x) edge values."""
+    """Parameters of one instance: N, n, theta, T, gamma, zeta, optional a(x) edge values,
+    boundary condition bc ("dirichlet" or "neumann") and constant coefficient a0 (used when
+    a_edges is None)."""
 
-    def __init__(self, N, n, theta, gamma, T=1.0, zeta=math.pi, a_edges=None):
+    def __init__(self, N, n, theta, gamma, T=1.0, zeta=math.pi, a_edges=None, bc="dirichlet", a0=1.0):
         self.N, self.n = int(N), int(n)
         self.theta, self.gamma, self.T, self.zeta = float(theta), float(gamma), float(T), float(zeta)
         self.a_edges = None if a_edges is None else np.asarray(a_edges, dtype=np.float64)
+        if bc not in ("dirichlet", "neumann"):
+            raise ValueError("bc must be 'dirichlet' or 'neumann'")
+        if bc == "neumann" and (a_edges is not None or self.N < 3):
+            raise ValueError("neumann takes a constant coefficient and N >= 3")
+        self.bc, self.a0 = bc, float(a0)
 
     @classmethod
     def from_instance(cls, inst):
-        return cls(inst.N, inst.n, inst.theta, inst.gamma, inst.T, inst.zeta, inst.a_edges)
+        return cls(inst.N, inst.n, inst.theta, inst.gamma, inst.T, inst.zeta, inst.a_edges,
+                   getattr(inst, "bc", "dirichlet"), getattr(inst, "a0", 1.0))
 
     @property
     def m(self):
@@ -34,7 +52,7 @@ class Problem:
 
     @property
     def h(self):
-        return 1.0 / (self.N + 1)
+        return 1.0 / (self.N - 1) if self.bc == "neumann" else 1.0 / (self.N + 1)
 
     @property
     def tau(self):
@@ -50,7 +68,7 @@ class Problem:
         ay[e, i] couples nodes (i+1, e)-(i+1, e+1), shape (N+1, N).  a = 1 when not given."""
         N = self.N
         if self.a_edges is None:
-            return np.ones((N, N + 1)), np.ones((N + 1, N))
+            return self.a0 * np.ones((N, N + 1)), self.a0 * np.ones((N + 1, N))
         ax = self.a_edges[: N * (N + 1)].reshape(N, N + 1)
         ay = self.a_edges[N * (N + 1):].reshape(N + 1, N)
         return ax, ay
@@ -61,9 +79,17 @@ class Problem:
 # ----------------------------------------------------------------------------------------
 
 def apply_K(prob: Problem, u: np.ndarray) -> np.ndarray:
-    """K u for u of shape (..., N*N): conservative 5-point stencil with zero Dirichlet data,
-    (K u)_ij = sum over the four edges of a_edge (u_ij - u_neighbour) / h^2."""
+    """K u for u of shape (..., N*N).  Dirichlet: conservative 5-point stencil with zero boundary
+    data, (K u)_ij = sum over the four edges of a_edge (u_ij - u_neighbour) / h^2.  Neumann:
+    a0 (4 u_ij - sum of the four neighbours) / h^2 with mirrored ghost values."""
     N = prob.N
+    if prob.bc == "neumann":
+        U = u.reshape(u.shape[:-1] + (N, N))
+        # mirror: padded index 0 holds u_1, padded index N+1 holds u_{N-2}
+        P = np.pad(U, [(0, 0)] * (U.ndim - 2) + [(1, 1), (1, 1)], mode="reflect")
+        c = P[..., 1:-1, 1:-1]
+        nb = P[..., 1:-1, :-2] + P[..., 1:-1, 2:] + P[..., :-2, 1:-1] + P[..., 2:, 1:-1]
+        return (prob.a0 * (4.0 * c - nb) / prob.h ** 2).reshape(u.shape)
     ax, ay = prob.edges()
     U = u.reshape(u.shape[:-1] + (N, N))             # [..., j, i]
     P = np.zeros(u.shape[:-1] + (N + 2, N + 2), dtype=u.dtype)
@@ -79,6 +105,22 @@ def apply_K(prob: Problem, u: np.ndarray) -> np.ndarray:
 def K_sparse(prob: Problem) -> sp.csr_matrix:
     """K as a sparse m x m matrix, assembled entry by entry from the same stencil definition."""
     N = prob.N
+    if prob.bc == "neumann":
+        c = prob.a0 / prob.h ** 2
+        rows, cols, vals = [], [], []
+        for j in range(N):
+            for i in range(N):
+                r = i + j * N
+                rows.append(r); cols.append(r); vals.append(4.0 * c)
+                # a missing neighbour is the mirror image of the one across the node
+                for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                    ii, jj = i + di, j + dj
+                    if ii < 0 or ii > N - 1:
+                        ii = i - di
+                    if jj < 0 or jj > N - 1:
+                        jj = j - dj
+                    rows.append(r); cols.append(ii + jj * N); vals.append(-c)
+        return sp.csr_matrix((vals, (rows, cols)), shape=(N * N, N * N))
     ax, ay = prob.edges()
     h2 = prob.h ** 2
     rows, cols, vals = [], [], []

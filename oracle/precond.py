@@ -11,7 +11,14 @@ Fast routes (any size):
                      per-frequency 2x2 block, multigrid on (mu_k I + tau K) for both components.
 Both halves use the same unitary Q = (F D / sqrt(n)) (x) (S_N (x) S_N)  [reading of the second
 diagonal block of U, U~ in Sec. 3.5: S is normal, so S*S = SS* and the two blocks of |P_S| agree].
-For zeta in {0, pi} the operators are real on real vectors; the output is the real part.
+For zeta in {0, pi} the operators are real on real vectors; for other zeta the applied operator
+is the real part of the complex one.
+
+Neumann (Example 3): K is not symmetric, and P_S is formed as printed with K in both diagonal
+blocks, [[calS, -alpha I], [alpha I, S_n^* (x) I + tau I (x) K]] (the paper's Sec. 1 formulas with
+K_m in place, as for A).  Both blocks are diagonalised by (F D) (x) V^{-1} (x) V^{-1} with V the
+scaled DCT-I basis (spectra.py), so apply_ps_inv runs the same per-mode 2x2 solve.  |P_S| and P_MS
+belong to MINRES, which the nonsymmetric A excludes; they are not defined for Neumann here.
 
 Dense routes (tiny sizes): the matrices exactly as Eqs. (matrix_S), (matrix_P_GMRES), (matrix_P),
 (matrix_P_MS), (abs_ideal_matrix_H) define them.
@@ -33,22 +40,34 @@ def _halves(prob, v):
 
 
 def _forward(prob, x):
-    """Q-transform up to scaling: time (F D) then 2D DST; x (n, m) real -> complex (n, m)."""
-    return spc.dst2(spc.time_forward(x, prob.zeta), prob.N)
+    """Q-transform up to scaling: time (F D) then the 2D spatial transform (DST-I, or the scaled
+    DCT-I basis for Neumann); x (n, m) real -> complex (n, m)."""
+    return spc.space_forward(spc.time_forward(x, prob.zeta), prob.N, prob.bc)
 
 
 def _inverse(prob, w):
-    return spc.time_inverse(spc.dst2(w, prob.N), prob.zeta)
+    return spc.time_inverse(spc.space_inverse(w, prob.N, prob.bc), prob.zeta)
+
+
+def _kappa2d(prob):
+    """a0 (kappa_p + kappa_q): eigenvalues of K (constant coefficient)."""
+    return prob.a0 * spc.kappa2d(prob.N, prob.bc)
 
 
 def _modes(prob):
     """lambda_k(S_n) + tau (kappa_p + kappa_q), shape (n, m)."""
     lam = spc.lam_Sn(prob.n, prob.theta, prob.zeta)
-    return lam[:, None] + prob.tau * spc.kappa2d(prob.N).reshape(1, -1)
+    return lam[:, None] + prob.tau * _kappa2d(prob).reshape(1, -1)
+
+
+def _no_neumann(prob):
+    if prob.bc == "neumann":
+        raise ValueError("|P_S| and P_MS are MINRES preconditioners; the Neumann A is not symmetric")
 
 
 def apply_abs_ps_inv(prob, v):
     """|P_S|^{-1} v (a = 1)."""
+    _no_neumann(prob)
     W = 1.0 / np.sqrt(np.abs(_modes(prob)) ** 2 + prob.alpha ** 2)
     out = []
     for x in _halves(prob, v):
@@ -80,6 +99,7 @@ def apply_pms_inv(prob, v, cycles=None):
     """P_MS^{-1} v: time transform, per frequency (sigma_k I + tau K)^{-1}, inverse transform
     (three steps in Sec. 3.5).  a = 1 and cycles None: exact DST solve; otherwise `cycles`
     multigrid V-cycles."""
+    _no_neumann(prob)
     sig = sigma_ms(prob)
     out = []
     for x in _halves(prob, v):
@@ -87,8 +107,8 @@ def apply_pms_inv(prob, v, cycles=None):
         if cycles is None:
             if prob.a_edges is not None:
                 raise ValueError("exact P_MS solve needs a = 1; pass cycles for variable a")
-            W = 1.0 / (sig[:, None] + prob.tau * spc.kappa2d(prob.N).reshape(1, -1))
-            Z = spc.dst2(W * spc.dst2(X, prob.N), prob.N)
+            W = 1.0 / (sig[:, None] + prob.tau * _kappa2d(prob).reshape(1, -1))
+            Z = spc.space_inverse(W * spc.space_forward(X, prob.N, prob.bc), prob.N, prob.bc)
         else:
             ax, ay = prob.edges()
             levels = mg.hierarchy(prob.N, ax, ay, prob.tau)
@@ -154,24 +174,40 @@ def dense_calS(prob):
     return np.kron(dense_Sn(prob), np.eye(prob.m)) + prob.tau * np.kron(np.eye(prob.n), dense_K(prob))
 
 
+def dense_calS_second(prob):
+    """Second diagonal block of P_S: calS^* = S_n^* (x) I + tau I (x) K^T; with the Neumann K the
+    printed formula keeps K itself, S_n^* (x) I + tau I (x) K (equal for symmetric K)."""
+    K = dense_K(prob)
+    return (np.kron(dense_Sn(prob).conj().T, np.eye(prob.m))
+            + prob.tau * np.kron(np.eye(prob.n), K if prob.bc == "neumann" else K.T))
+
+
 def dense_T(prob):
     Bn = B1_dense(prob.n) @ np.linalg.inv(B2_dense(prob.n, prob.theta))
     return np.kron(Bn, np.eye(prob.m)) + prob.tau * np.kron(np.eye(prob.n), dense_K(prob))
 
 
+def dense_T_second(prob):
+    """The adjoint-row block T^T = B_n^T (x) I + tau I (x) K^T; the Neumann K enters as printed,
+    B_n^T (x) I + tau I (x) K (equal for symmetric K)."""
+    Bn = B1_dense(prob.n) @ np.linalg.inv(B2_dense(prob.n, prob.theta))
+    K = dense_K(prob)
+    return np.kron(Bn.T, np.eye(prob.m)) + prob.tau * np.kron(np.eye(prob.n), K if prob.bc == "neumann" else K.T)
+
+
 def dense_A(prob):
     T = dense_T(prob); a = prob.alpha; I = np.eye(T.shape[0])
-    return np.block([[a * I, T.T], [T, -a * I]])
+    return np.block([[a * I, dense_T_second(prob)], [T, -a * I]])
 
 
 def dense_A_hat(prob):
     T = dense_T(prob); a = prob.alpha; I = np.eye(T.shape[0])
-    return np.block([[T, -a * I], [a * I, T.T]])
+    return np.block([[T, -a * I], [a * I, dense_T_second(prob)]])
 
 
 def dense_P_S(prob):
     S = dense_calS(prob); a = prob.alpha; I = np.eye(S.shape[0])
-    return np.block([[S, -a * I], [a * I, S.conj().T]])
+    return np.block([[S, -a * I], [a * I, dense_calS_second(prob)]])
 
 
 def _sqrtm_herm(H):

@@ -12,7 +12,14 @@ f((zeta + 2 pi k)/n) re-indexed k -> -k (mod n).
 
 Spatial factor (Sec. 3.5): for a = 1, K = -L_m = (S_N (x) S_N) diag(kappa_p + kappa_q) (S_N (x) S_N),
 S_N[i, p] = sqrt(2/(N+1)) sin(i p pi/(N+1)) (orthogonal, symmetric, involutory),
-kappa_p = (4/h^2) sin^2(p pi h / 2).
+kappa_p = (4/h^2) sin^2(p pi h / 2).  A constant coefficient a0 scales kappa.
+
+Neumann (Example 3, the "minimal modification" of Sec. 1 with a cosine transform in place of the
+sine transform): the mirrored second difference on N nodes (h = 1/(N-1)) is K1 = W^{-1} K1s with
+W = diag(1/2, 1, .., 1, 1/2) and K1s symmetric, so W^{1/2} K1 W^{-1/2} is symmetric and is
+diagonalised by the orthonormal DCT-I matrix C (C = C^T = C^{-1}):
+    K1 = V diag(kappa) V^{-1},  V = W^{-1/2} C,  V^{-1} = C W^{1/2},
+    kappa_k = (4/h^2) sin^2(k pi / (2 (N-1))), k = 0..N-1.
 """
 from __future__ import annotations
 
@@ -73,9 +80,16 @@ def kappa(N):
     return (4.0 / h ** 2) * np.sin(p * math.pi * h / 2.0) ** 2
 
 
-def kappa2d(N):
+def kappa_neumann(N):
+    """Eigenvalues of the 1D mirrored (Neumann) second-difference matrix, k = 0..N-1, h = 1/(N-1)."""
+    h = 1.0 / (N - 1)
+    k = np.arange(N)
+    return (4.0 / h ** 2) * np.sin(k * math.pi / (2.0 * (N - 1))) ** 2
+
+
+def kappa2d(N, bc="dirichlet"):
     """kappa_p + kappa_q laid out [q, p] (x1-mode p fastest), matching the spatial vector layout."""
-    k = kappa(N)
+    k = kappa_neumann(N) if bc == "neumann" else kappa(N)
     return k[None, :] + k[:, None]
 
 
@@ -106,3 +120,36 @@ def dst2(u, N):
     U = scipy.fft.dst(U, type=1, axis=-1, norm="ortho")
     U = scipy.fft.dst(U, type=1, axis=-2, norm="ortho")
     return U.reshape(u.shape)
+
+
+def _wsqrt(N):
+    w = np.ones(N)
+    w[0] = w[-1] = math.sqrt(0.5)
+    return w
+
+
+def dct1_forward2(u, N):
+    """(V^{-1} (x) V^{-1}) u = (C (x) C)(W^{1/2} (x) W^{1/2}) u for u of shape (..., N*N)."""
+    w = _wsqrt(N)
+    U = u.reshape(u.shape[:-1] + (N, N)) * w[:, None] * w[None, :]
+    U = scipy.fft.dct(U, type=1, axis=-1, norm="ortho")
+    U = scipy.fft.dct(U, type=1, axis=-2, norm="ortho")
+    return U.reshape(u.shape)
+
+
+def dct1_inverse2(v, N):
+    """(V (x) V) v = (W^{-1/2} (x) W^{-1/2})(C (x) C) v."""
+    w = _wsqrt(N)
+    V = v.reshape(v.shape[:-1] + (N, N))
+    V = scipy.fft.dct(V, type=1, axis=-1, norm="ortho")
+    V = scipy.fft.dct(V, type=1, axis=-2, norm="ortho")
+    return (V / w[:, None] / w[None, :]).reshape(v.shape)
+
+
+def space_forward(u, N, bc="dirichlet"):
+    """Spatial eigenbasis coordinates: S_N (x) S_N (Dirichlet) or V^{-1} (x) V^{-1} (Neumann)."""
+    return dct1_forward2(u, N) if bc == "neumann" else dst2(u, N)
+
+
+def space_inverse(v, N, bc="dirichlet"):
+    return dct1_inverse2(v, N) if bc == "neumann" else dst2(v, N)

@@ -90,6 +90,24 @@ def example1_data(N: int, n: int, T: float = 1.0):
     return y.copy(), (2.0 * math.pi ** 2 - 1.0) * y, y, np.zeros_like(y)
 
 
+def neumann_grid(N: int) -> tuple[np.ndarray, np.ndarray]:
+    """Node coordinates x1[j, i], x2[j, i] (i fastest) of the Neumann grid: N nodes per side
+    including the boundary, x = i h, h = 1/(N-1)."""
+    x = np.arange(N) / (N - 1)
+    x2, x1 = np.meshgrid(x, x, indexing="ij")
+    return x1, x2
+
+
+def example3_data(N: int, n: int, a0: float = 1e-3, T: float = 1.0):
+    """Example 3 of the paper's numerical section (homogeneous Neumann, constant a = a0):
+    f = (8 pi^2 a0 - 1) e^{-t} cos(2 pi x1) cos(2 pi x2), g = e^{-t} cos cos, exact y = g, p = 0.
+    Returns (g, f, y_exact, p_exact), each (n+1, N*N), on neumann_grid(N)."""
+    x1, x2 = neumann_grid(N)
+    s = (np.cos(2.0 * math.pi * x1) * np.cos(2.0 * math.pi * x2)).reshape(1, -1)
+    y = np.exp(-times(n, T))[:, None] * s
+    return y.copy(), (8.0 * math.pi ** 2 * a0 - 1.0) * y, y, np.zeros_like(y)
+
+
 def variable_coefficient_edges(N: int, fn=None) -> np.ndarray:
     """a(x) at cell-edge midpoints, flattened as [ax (N rows x (N+1)), ay ((N+1) rows x N)].
 

@@ -1,0 +1,129 @@
+"""Pins of the oracle's Neumann route (Example 3, Table 4) against what the paper and the
+mathematics fix (no GPU): the mirrored stencil's structure, the DCT-I eigenbasis of the 1D
+operator written from the cosine formula, dense constructions of A_hat and P_S with the
+nonsymmetric K as printed, a sparse direct solve, and Table 4's iteration counts and errors.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import discretisation as ds
+from oracle import krylov as kr
+from oracle import operators as op
+from oracle import precond as pc
+from oracle import spectra as spc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(4242)
+
+
+def _K1_by_hand(N, h):
+    """1D mirrored second difference written out: rows 0 and N-1 see their one neighbour twice."""
+    K = np.zeros((N, N))
+    for i in range(N):
+        K[i, i] = 2.0
+        for j in (i - 1, i + 1):
+            jj = j if 0 <= j < N else 2 * i - j
+            K[i, jj] -= 1.0
+    return K / h ** 2
+
+
+@pytest.mark.parametrize("N", [3, 4, 7, 9, 17])
+def test_neumann_stencil_structure(N):
+    prob = ds.Problem(N, 2, 1.0, 1e-2, bc="neumann", a0=0.37)
+    K = ds.K_sparse(prob).toarray()
+    K1 = _K1_by_hand(N, prob.h)
+    assert np.abs(K - 0.37 * (np.kron(np.eye(N), K1) + np.kron(K1, np.eye(N)))).max() < 1e-9 * np.abs(K).max()
+    assert np.abs(K @ np.ones(N * N)).max() < 1e-9 * np.abs(K).max()          # constants in the kernel
+    w = np.ones(N); w[0] = w[-1] = 0.5
+    W = np.kron(w, w)
+    assert np.abs(W[:, None] * K - (W[:, None] * K).T).max() < 1e-9 * np.abs(K).max()   # W K symmetric
+    assert np.abs(K - K.T).max() > 0                                          # K itself is not
+    u = rng.standard_normal((3, N * N))
+    assert np.abs(ds.apply_K(prob, u) - (K @ u.T).T).max() < 1e-10 * np.abs(K).max()
+
+
+@pytest.mark.parametrize("N", [3, 5, 8, 17, 33])
+def test_neumann_cosine_eigenbasis(N):
+    """K1 cos(pi i k/(N-1)) = kappa_k cos(pi i k/(N-1)) with kappa_k = (4/h^2) sin^2(pi k/(2(N-1)))."""
+    h = 1.0 / (N - 1)
+    K1 = _K1_by_hand(N, h)
+    i = np.arange(N)
+    V = np.cos(np.pi * np.outer(i, i) / (N - 1))
+    kap = spc.kappa_neumann(N)
+    assert np.abs(K1 @ V - V * kap[None, :]).max() < 1e-10 * np.abs(K1).max()
+    assert kap[0] == 0.0 and np.all(np.diff(kap) > 0)
+
+
+@pytest.mark.parametrize("N", [3, 6, 9, 16])
+def test_neumann_fast_transforms(N):
+    """The 2D fast pair diagonalises the stencil and inverts itself."""
+    prob = ds.Problem(N, 2, 1.0, 1e-2, bc="neumann")
+    u = rng.standard_normal((2, N * N))
+    fwd = spc.space_forward(u, N, "neumann")
+    assert np.abs(spc.space_inverse(fwd, N, "neumann") - u).max() < 1e-12 * np.abs(u).max()
+    lhs = spc.space_forward(ds.apply_K(prob, u), N, "neumann")
+    rhs = spc.kappa2d(N, "neumann").reshape(1, -1) * fwd
+    assert np.abs(lhs - rhs).max() < 1e-9 * np.abs(rhs).max()
+
+
+@pytest.mark.parametrize("N,n", [(3, 4), (4, 6), (5, 8)])
+@pytest.mark.parametrize("theta,zeta", [(1.0, math.pi), (0.5, math.pi), (1.0, 0.0), (0.75, 1.1), (0.5, 2.3)])
+def test_neumann_ps_and_matvec_vs_dense(N, n, theta, zeta):
+    prob = ds.Problem(N, n, theta, 1e-3, zeta=zeta, bc="neumann", a0=0.2)
+    v = rng.standard_normal(2 * prob.m * prob.n)
+    P = pc.dense_P_S(prob)
+    w = pc.apply_ps_inv(prob, v, real=False)
+    assert np.abs(P @ w - v).max() < 1e-11 * np.abs(v).max()
+    exact = np.linalg.solve(P, v)
+    assert np.abs(pc.apply_ps_inv(prob, v) - exact.real).max() < 1e-10 * np.abs(exact).max()
+    Ah = pc.dense_A_hat(prob)
+    assert np.abs(op.matvec_A_hat(prob, v) - Ah @ v).max() < 1e-10 * np.abs(Ah).max()
+    A = pc.dense_A(prob)
+    assert np.abs(op.matvec_A(prob, v) - A @ v).max() < 1e-10 * np.abs(A).max()
+    assert np.abs(A - A.T).max() > 1e-6            # the Neumann A is not symmetric (Sec. 4)
+    with pytest.raises(ValueError):
+        pc.apply_abs_ps_inv(prob, v)
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_neumann_gmres_vs_direct(theta):
+    N, n = 9, 8
+    prob = ds.Problem(N, n, theta, 1e-3, bc="neumann", a0=1e-2)
+    g, f, ye, _ = synth.example3_data(N, n, a0=1e-2)
+    yd, pd = ds.solve_direct(prob, g, f, ye[0])
+    x, info = kr.fgmres(lambda z: op.matvec_A_hat(prob, z), ds.rhs_gmres(prob, g, f, ye[0]),
+                        lambda r: pc.apply_ps_inv(prob, r), tol=1e-12)
+    assert info.converged
+    y, p = ds.recover(prob, x)
+    assert np.abs(y - yd).max() < 1e-9 * np.abs(yd).max()
+    assert np.abs(p - pd).max() < 1e-9 * max(np.abs(pd).max(), 1e-300)
+
+
+def _table4():
+    rows = []
+    with open(os.path.join(GOLDEN, "table4_example3_cn.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                g, k, dof, it, eh = line.split()
+                rows.append((float(g), int(k), int(dof), int(it), float(eh)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _table4(), ids=lambda r: f"g{r[0]:g}-h2^-{r[1]}")
+def test_table4_example3(row):
+    """GMRES-P_S on Example 3: iteration counts and e_h as printed in Table 4."""
+    gamma, k, dof, it, eh_printed = row
+    N = n = 2 ** k
+    assert 2 * N * N * n == dof
+    prob = ds.Problem(N, n, 0.5, gamma, bc="neumann", a0=1e-3)
+    g, f, ye, pe = synth.example3_data(N, n)
+    x, info = kr.fgmres(lambda z: op.matvec_A_hat(prob, z), ds.rhs_gmres(prob, g, f, ye[0]),
+                        lambda r: pc.apply_ps_inv(prob, r), tol=1e-8)
+    assert info.converged and info.iterations == it
+    y, p = ds.recover(prob, x)
+    eh = ds.error_eh(prob, y, p, ye, pe)
+    assert abs(eh - eh_printed) / eh_printed < 0.01, (eh, eh_printed)      # printed to 3 digits
