@@ -71,14 +71,24 @@ enum pcb_precond {
 
 enum pcb_method { PCB_METHOD_AUTO = 0, PCB_MINRES = 1, PCB_GMRES = 2, PCB_FGMRES = 3 };
 /* AUTO: MINRES with |P_S| (theta = 1, a = 1) or P_MS (a variable, theta = 1); GMRES with P_S
- * (theta < 1, a = 1); FGMRES with multigrid P_S (a variable, theta < 1). */
+ * (theta < 1, a = 1, and every Neumann problem); FGMRES with multigrid P_S (a variable,
+ * theta < 1). */
+
+enum pcb_bc { PCB_BC_DIRICHLET = 0, PCB_BC_NEUMANN = 1 };
+/* DIRICHLET (Sec. 1, Examples 1-2): N interior nodes per side, h = 1/(N+1), zero boundary values.
+ * NEUMANN (Sec. 4, Example 3, homogeneous Neumann): N nodes per side including the boundary,
+ *   x_i = i h, h = 1/(N-1); K = a (4 u - sum of neighbours)/h^2 with the missing neighbour of a
+ *   boundary node mirrored across it.  This K is not symmetric and enters A and P_S as printed
+ *   (K in both diagonal blocks), so A is not symmetric: GMRES with P_S only.  The spatial
+ *   transform is the DCT-I of order N-1 in place of the DST-I. */
 
 /* ---- problem --------------------------------------------------------------------------- */
 typedef struct pcb_problem pcb_problem;   /* opaque, owned by the library */
 
 typedef struct {
-  int N;                  /* interior points per side; N+1 must be 2^a * 3^b (DST radices),   */
-                          /* N <= 511; variable a(x) needs N = 2^k - 1 (multigrid)             */
+  int N;                  /* points per side.  Dirichlet: interior points, N+1 = 2^a * 3^b      */
+                          /* (DST radices), N <= 511; variable a(x) needs N = 2^k - 1          */
+                          /* (multigrid).  Neumann: all nodes, N-1 = 2^a * 3^b, 3 <= N <= 513  */
   int n;                  /* time steps; a power of two, 2 <= n <= 1024 (<= 512 with variable a)*/
   double theta;           /* 1/2 <= theta <= 1                                                 */
   double T;               /* horizon, > 0                                                      */
@@ -92,12 +102,15 @@ typedef struct {
   int precision;          /* pcb_precision                                                     */
   int mg_cycles;          /* V-cycles per shifted solve when a(x) varies; <= 0 => 2            */
   void* stream;           /* cudaStream_t the problem's work is queued on; NULL = default      */
+  int bc;                 /* pcb_bc; 0 = Dirichlet                                             */
+  double a_const;         /* constant a(x) when a_edges is NULL; <= 0 => 1.  Neumann requires   */
+                          /* a_edges = NULL                                                    */
 } pcb_desc;
 
 /* Validate the descriptor, compute the spectral tables (Sec. 3.5: lambda_k(S_n), the eigenvalues
  * of -L, twiddle tables) and allocate the workspaces.  Errors: INVALID_ARG, UNSUPPORTED
- * (N+1 not 2^a 3^b, n not a power of two, N > 511, variable a with N != 2^k - 1 or zeta != pi),
- * OUT_OF_MEMORY, CUDA.  A zero eigenvalue of S^(2) (Remark 1, e.g. theta = 1/2, zeta = 0) is
+ * (N+1 not 2^a 3^b, n not a power of two, N > 511, variable a with N != 2^k - 1 or zeta != pi;
+ * Neumann with N-1 not 2^a 3^b, N < 3 or N > 513, or with a_edges), OUT_OF_MEMORY, CUDA.  A zero eigenvalue of S^(2) (Remark 1, e.g. theta = 1/2, zeta = 0) is
  * replaced by 1.  For zeta other than 0 and pi the preconditioners are complex; applied to real
  * vectors they return the real part (a real symmetric positive definite operator for |P_S|). */
 int pcb_create(const pcb_desc* desc, pcb_problem** out);
@@ -119,7 +132,8 @@ int pcb_matvec(pcb_problem* p, int op, const double* x_dev, double* y_dev);
 
 /* y = P^{-1} x for kind = pcb_precond, computed in `precision` (pcb_precision).
  * x_dev and y_dev may be the same buffer.  Uses the problem's scratch workspace, so calls on
- * one problem are serialised by its stream. */
+ * one problem are serialised by its stream.  UNSUPPORTED: |P_S| with variable a(x); |P_S| and
+ * P_MS for Neumann problems (MINRES preconditioners; the Neumann A is not symmetric). */
 int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_dev, double* y_dev);
 
 /* Undo the symmetrising change of variables of Eq. (main_system):
@@ -157,7 +171,8 @@ typedef struct {
 } pcb_solve_info;
 
 /* Solve op x = b from a zero initial guess, op = A for MINRES and A_hat for (F)GMRES.
- * b_dev, x_dev: device, 2*m*n each; info may be NULL.  Blocks until the solve ends. */
+ * b_dev, x_dev: device, 2*m*n each; info may be NULL.  Blocks until the solve ends.
+ * Neumann problems take GMRES with P_S (AUTO); MINRES or another preconditioner is UNSUPPORTED. */
 int pcb_solve(pcb_problem* p, const pcb_solve_opts* opts, const double* b_dev, double* x_dev,
               pcb_solve_info* info);
 

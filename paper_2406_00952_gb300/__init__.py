@@ -20,6 +20,7 @@ OPS = {"A": 0, "Ahat": 1}
 PRECONDS = {None: 0, "none": 0, "abs_ps": 1, "ps": 2, "pms": 3}
 METHODS = {"auto": 0, "minres": 1, "gmres": 2, "fgmres": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+BCS = {"dirichlet": 0, "neumann": 1}
 
 
 def _ptr(t: torch.Tensor | None, numel: int | None = None) -> int | None:
@@ -39,10 +40,12 @@ def _opts(method="auto", precond=None, tol=1e-8, maxit=500, restart=30, max_refi
 
 
 class Problem:
-    """One control problem on the current CUDA device and stream (C-ABI pcb_create)."""
+    """One control problem on the current CUDA device and stream (C-ABI pcb_create).
+    bc="neumann" selects Example 3's homogeneous Neumann grid (N nodes per side including the
+    boundary); a is the constant coefficient when a_edges is None."""
 
     def __init__(self, N, n, theta, gamma, T=1.0, zeta=math.pi, a_edges=None, precision="fp64", mg_cycles=2,
-                 stream: torch.cuda.Stream | None = None):
+                 stream: torch.cuda.Stream | None = None, bc="dirichlet", a=1.0):
         self.lib = _lib.load()
         self.N, self.n, self.theta, self.gamma, self.T = int(N), int(n), float(theta), float(gamma), float(T)
         self.m = self.N * self.N
@@ -55,7 +58,7 @@ class Problem:
             self._a = np.ascontiguousarray(a_edges, dtype=np.float64)
             ap = self._a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         d = PcbDesc(self.N, self.n, self.theta, self.T, self.gamma, float(zeta), ap, PRECISIONS[precision],
-                    int(mg_cycles), ctypes.c_void_p(self.stream.cuda_stream))
+                    int(mg_cycles), ctypes.c_void_p(self.stream.cuda_stream), BCS[bc], float(a))
         h = ctypes.c_void_p()
         check("pcb_create", self.lib.pcb_create(ctypes.byref(d), ctypes.byref(h)))
         self.h = h

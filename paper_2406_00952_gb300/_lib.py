@@ -22,7 +22,7 @@ STATUS = {0: "ok", 1: "not converged", -1: "invalid argument", -2: "unsupported"
 class PcbDesc(ctypes.Structure):
     _fields_ = [("N", c_int), ("n", c_int), ("theta", c_double), ("T", c_double), ("gamma", c_double),
                 ("zeta", c_double), ("a_edges", POINTER(c_double)), ("precision", c_int),
-                ("mg_cycles", c_int), ("stream", c_void_p)]
+                ("mg_cycles", c_int), ("stream", c_void_p), ("bc", c_int), ("a_const", c_double)]
 
 
 class PcbSolveOpts(ctypes.Structure):

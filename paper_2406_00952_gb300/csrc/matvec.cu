@@ -5,8 +5,10 @@
 // B_n x is applied per spatial column as the bidiagonal recurrence z_t = (x_t - (1-theta) z_{t-1})/theta
 // followed by z_t - z_{t-1}; B_n^T x marches backward.  For theta = 1 (B_n = B^(1)) there is no
 // recurrence and one fused pass over (t, x) reads x once and writes both output halves.
-// K is the 5-point stencil (a = 1: (4u - sum of neighbours)/h^2; variable a: conservative
-// edge-weighted form).  Epilogues fuse the Krylov updates that consume the product.
+// K is the 5-point stencil (constant a: a (4u - sum of neighbours)/h^2; variable a: conservative
+// edge-weighted form).  A neighbour outside the grid is 0 (Dirichlet) or the mirror image of the
+// neighbour across the node (Neumann, Example 3: u_{-1} = u_1, u_N = u_{N-2}).  Epilogues fuse the
+// Krylov updates that consume the product.
 #include "pcb_internal.cuh"
 
 namespace pcb {
@@ -17,10 +19,18 @@ enum { EPI_PLAIN = 0, EPI_RESID = 1, EPI_MINRES = 2 };
 __device__ __forceinline__ double tauK(const Geom& g, const double* __restrict__ u, int i, int j, int col) {
   const int N = g.N;
   const double uc = u[col];
-  const double l = i > 0 ? u[col - 1] : 0.0;
-  const double r = i < N - 1 ? u[col + 1] : 0.0;
-  const double d = j > 0 ? u[col - N] : 0.0;
-  const double t = j < N - 1 ? u[col + N] : 0.0;
+  double l, r, d, t;
+  if (g.bc == PCB_BC_NEUMANN) {      // N >= 3: the mirrored neighbour always exists
+    l = u[i > 0 ? col - 1 : col + 1];
+    r = u[i < N - 1 ? col + 1 : col - 1];
+    d = u[j > 0 ? col - N : col + N];
+    t = u[j < N - 1 ? col + N : col - N];
+  } else {
+    l = i > 0 ? u[col - 1] : 0.0;
+    r = i < N - 1 ? u[col + 1] : 0.0;
+    d = j > 0 ? u[col - N] : 0.0;
+    t = j < N - 1 ? u[col + N] : 0.0;
+  }
   if (!g.var_a) {
     const double s = (l + r) + (d + t);
     return fma(-g.c, s, 4.0 * g.c * uc);
@@ -119,6 +129,12 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
     const int col = cb * 256 + threadIdx.x;
     if (col < m) {
       const int j = col / N, i = col - j * N;
+      // neighbour offsets; at a Neumann boundary the missing one is the mirrored neighbour, at a
+      // Dirichlet boundary it is masked to zero below
+      const bool neu = g.bc == PCB_BC_NEUMANN;
+      const int oL = i > 0 ? -1 : (neu ? 1 : 0), oR = i < N - 1 ? 1 : (neu ? -1 : 0);
+      const int oD = j > 0 ? -N : (neu ? N : 0), oU = j < N - 1 ? N : (neu ? -N : 0);
+      const bool zL = oL == 0, zR = oR == 0, zD = oD == 0, zU = oU == 0;
       const int t0 = tc * g.mv_tchunk;
       const int t1 = min(n, t0 + g.mv_tchunk);
       double s1prev = t0 > 0 ? sg * x1[(long long)(t0 - 1) * m + col] : 0.0;
@@ -129,10 +145,10 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
         const double* u2 = x2 + (long long)t * m;
         const double x1c = u1[col], x2c = u2[col];
         const double x2n = t + 1 < n ? x2[a + m] : 0.0;
-        const double nb1 = ((i > 0 ? u1[col - 1] : 0.0) + (i < N - 1 ? u1[col + 1] : 0.0)) +
-                           ((j > 0 ? u1[col - N] : 0.0) + (j < N - 1 ? u1[col + N] : 0.0));
-        const double nb2 = ((i > 0 ? u2[col - 1] : 0.0) + (i < N - 1 ? u2[col + 1] : 0.0)) +
-                           ((j > 0 ? u2[col - N] : 0.0) + (j < N - 1 ? u2[col + N] : 0.0));
+        const double nb1 = ((zL ? 0.0 : u1[col + oL]) + (zR ? 0.0 : u1[col + oR])) +
+                           ((zD ? 0.0 : u1[col + oD]) + (zU ? 0.0 : u1[col + oU]));
+        const double nb2 = ((zL ? 0.0 : u2[col + oL]) + (zR ? 0.0 : u2[col + oR])) +
+                           ((zD ? 0.0 : u2[col + oD]) + (zU ? 0.0 : u2[col + oU]));
         const double s1 = sg * x1c, s2n = sg * x2n;
         double vT = fma(-sga, x2c, s1 - s1prev);
         vT = fma(sgc, fma(4.0, x1c, -nb1), vT);

@@ -68,6 +68,7 @@ extern "C" int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int pre
   int rc = validate_desc(desc);
   if (rc != PCB_OK) return rc;
   if (desc->a_edges) return PCB_ERR_UNSUPPORTED;     // the multigrid route needs its own workspace
+  if (desc->bc == PCB_BC_NEUMANN && kind != PCB_PREC_PS) return PCB_ERR_UNSUPPORTED;   // GMRES route only
 
   Geom g;
   init_geom(desc, g);

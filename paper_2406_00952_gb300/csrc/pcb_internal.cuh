@@ -49,12 +49,13 @@ struct FftPlan {
 
 struct Geom {
   int N, n, m;                    // m = N*N
-  int L, M;                       // L = N+1 (DST-I order), M = 2L (extended FFT length)
+  int L, M;                       // L = N+1 (DST-I order; Neumann: N-1, DCT-I order), M = 2L (extended FFT length)
+  int bc;                         // PCB_BC_DIRICHLET or PCB_BC_NEUMANN (mirrored stencil, DCT-I transform)
   long long mn;                   // m*n (one half of the all-at-once vector)
   double theta, tau, gamma, alpha, h, sqrt_gamma;
   double zeta;                    // omega = exp(i zeta)
   int zeta_pi;                    // 1 when zeta = pi: the two halves share one complex time line
-  double c;                       // tau / h^2
+  double c;                       // tau a / h^2 (a: the constant coefficient)
   int var_a;                      // 0: a = 1; 1: coefficient tables below
   // FP32 scratch layout of the pipelined passes: rows of lr values (lr = L + 16 when the pipelined
   // DST runs: 64-byte aligned rows, stride off a power of two; else N), slices of mp = N lr values;
@@ -74,7 +75,8 @@ struct Geom {
   int vec_blocks;                 // blocks of the vector kernels over 2mn
   FftPlan pdst, ptime;
   // tables (device)
-  const double* kap;              // N: eigenvalues kappa_p of the 1D second difference
+  const double* kap;              // N: eigenvalues a kappa_p of the 1D second difference (Dirichlet p = 1..N,
+                                  //    Neumann k = 0..N-1)
   const double2* mu_d;            // n: lambda(S_n) at F-slot r (FP64)
   const float2* mu_f;
   const double2* twd_d;           // M: exp(-2 pi i k / M)

@@ -97,18 +97,23 @@ struct LineFFT {
 };
 
 // ------------------------------------------------------------------------------------------
-// DST-I pass along x1 (axis 0) or x2 (axis 1), both halves at once.
+// Spatial pass along x1 (axis 0) or x2 (axis 1), both halves at once: the orthonormal DST-I of
+// order L = N+1 (Dirichlet), or for Neumann the scaled DCT-I pair of order L = N-1, forward
+// (inv = 0: u -> C W^{1/2} u) or inverse (inv = 1: v -> W^{-1/2} C v), with C the orthonormal
+// DCT-I and W = diag(1/2, 1, .., 1, 1/2).  Both come from one length-2L FFT of the line's
+// extension: odd (Y_p = -2i DST(x)_p) or even (Y_k = 2 sum_i w_i x_i cos(pi i k / L)).
 // in_slot / out_slot >= 0 select a vector slot (FP64), -1 selects the instance scratch (R).
 // ------------------------------------------------------------------------------------------
 template <typename TIn, typename TOut, typename R, int Q>
 __device__ __forceinline__ void dst_body(const Geom& g, const Slots* __restrict__ S, int inst, int lb, int axis,
-                                         int in_slot, int out_slot) {
+                                         int in_slot, int out_slot, int inv) {
   using T = cx<R>;
   const TIn* __restrict__ in = in_slot >= 0 ? (const TIn*)S[inst].v[in_slot] : (const TIn*)g.scratch;
   TOut* __restrict__ out = out_slot >= 0 ? (TOut*)S[inst].v[out_slot] : (TOut*)g.scratch;
-  const int N = g.N, L = N + 1, M = 2 * L;
+  const int N = g.N, L = g.L, M = g.M;
+  const bool neu = g.bc == PCB_BC_NEUMANN;
   const int lpb = axis == 0 ? g.dst_lpb[sizeof(R) == 4] : g.dst_lpb_j[sizeof(R) == 4];   // power of two
-  const int ls = padded_len(L);
+  const int ls = padded_len(N + 1);          // element q of a line at padded index q + 1
   const long long mn = g.mn;
   const int m = g.m;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -192,7 +197,8 @@ __device__ __forceinline__ void dst_body(const Geom& g, const Slots* __restrict_
     for (int k1 = 0; k1 < Q; ++k1) twq[k1] = __ldg(&tw[t * k1]);
   }
   T* wscr = tile + lpb * ls + warp * (32 * 33);
-  const R sc = (R)(0.5 * sqrt(2.0 / (double)L));
+  const R sc = (R)(0.5 * sqrt(2.0 / (double)L));      // orthonormal scale of both DST-I and DCT-I
+  const R rt2 = (R)1.4142135623730951, irt2 = (R)0.7071067811865476;
   const int k2 = bitrev(t, P);
   for (int lbase = warp * lpw; lbase < lpb; lbase += nw * lpw) {
     const int l = lbase + lane / P;
@@ -204,8 +210,16 @@ __device__ __forceinline__ void dst_body(const Geom& g, const Slots* __restrict_
       const int s = t + P * q;
       T v = mk<R>(0, 0);
       if (lv) {
-        if (s > 0 && s < L) v = line[pidx(s)];
-        else if (s > L) { v = line[pidx(M - s)]; v.x = -v.x; v.y = -v.y; }
+        if (neu) {
+          // even extension of element j = s (s <= L) or 2L - s; the inverse enters W^{-1/2} v
+          const int j = s <= L ? s : M - s;
+          v = line[pidx(j + 1)];
+          if (inv && (j == 0 || j == L)) v = cscale(v, rt2);
+        } else if (s > 0 && s < L) {
+          v = line[pidx(s)];
+        } else if (s > L) {
+          v = line[pidx(M - s)]; v.x = -v.x; v.y = -v.y;
+        }
       }
       f.x[q] = v;
     }
@@ -214,7 +228,14 @@ __device__ __forceinline__ void dst_body(const Geom& g, const Slots* __restrict_
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
       const int p = LineFFT<T, R, Q>::owned(j, t, k2);
-      if (lv && p >= 1 && p <= N) {
+      if (neu) {
+        // a real line's even extension has a real transform: both halves stay in place; the
+        // forward pass applies W^{1/2} to the two end modes
+        if (lv && p <= L) {
+          const R fct = (!inv && (p == 0 || p == L)) ? sc * irt2 : sc;
+          line[pidx(p + 1)] = cscale(f.value(j), fct);
+        }
+      } else if (lv && p >= 1 && p <= N) {
         const T Y = f.value(j);
         line[pidx(p)] = mk<R>(-Y.y * sc, Y.x * sc);
       }
@@ -254,10 +275,10 @@ template <typename TIn, typename TOut, typename R, int Q>
 __global__ void __launch_bounds__(256, 2) k_dst(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                              const int* __restrict__ off, int count,
                                              Sel sel, int axis, int in_slot,
-                                             int out_slot) {
+                                             int out_slot, int inv) {
   const int inst = find_inst(off, count, blockIdx.x);
   if (sel.skip(inst)) return;
-  dst_body<TIn, TOut, R, Q>(G[inst], S, inst, blockIdx.x - off[inst], axis, in_slot, out_slot);
+  dst_body<TIn, TOut, R, Q>(G[inst], S, inst, blockIdx.x - off[inst], axis, in_slot, out_slot, inv);
 }
 
 // Shared launch over instances with different line lengths: each block runs the register-FFT
@@ -266,22 +287,22 @@ template <typename TIn, typename TOut, typename R>
 __global__ void __launch_bounds__(256, 2) k_dst_any(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                                  const int* __restrict__ off, int count,
                                                  Sel sel, int axis, int in_slot,
-                                                 int out_slot) {
+                                                 int out_slot, int inv) {
   const int inst = find_inst(off, count, blockIdx.x);
   if (sel.skip(inst)) return;
   const Geom& g = G[inst];
   const int lb = blockIdx.x - off[inst];
   switch (g.dst_q) {
-    case 1: dst_body<TIn, TOut, R, 1>(g, S, inst, lb, axis, in_slot, out_slot); break;
-    case 2: dst_body<TIn, TOut, R, 2>(g, S, inst, lb, axis, in_slot, out_slot); break;
-    case 3: dst_body<TIn, TOut, R, 3>(g, S, inst, lb, axis, in_slot, out_slot); break;
-    case 4: dst_body<TIn, TOut, R, 4>(g, S, inst, lb, axis, in_slot, out_slot); break;
-    case 6: dst_body<TIn, TOut, R, 6>(g, S, inst, lb, axis, in_slot, out_slot); break;
-    case 8: dst_body<TIn, TOut, R, 8>(g, S, inst, lb, axis, in_slot, out_slot); break;
-    case 12: dst_body<TIn, TOut, R, 12>(g, S, inst, lb, axis, in_slot, out_slot); break;
-    case 16: dst_body<TIn, TOut, R, 16>(g, S, inst, lb, axis, in_slot, out_slot); break;
-    case 24: dst_body<TIn, TOut, R, 24>(g, S, inst, lb, axis, in_slot, out_slot); break;
-    default: dst_body<TIn, TOut, R, 32>(g, S, inst, lb, axis, in_slot, out_slot); break;
+    case 1: dst_body<TIn, TOut, R, 1>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
+    case 2: dst_body<TIn, TOut, R, 2>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
+    case 3: dst_body<TIn, TOut, R, 3>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
+    case 4: dst_body<TIn, TOut, R, 4>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
+    case 6: dst_body<TIn, TOut, R, 6>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
+    case 8: dst_body<TIn, TOut, R, 8>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
+    case 12: dst_body<TIn, TOut, R, 12>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
+    case 16: dst_body<TIn, TOut, R, 16>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
+    case 24: dst_body<TIn, TOut, R, 24>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
+    default: dst_body<TIn, TOut, R, 32>(g, S, inst, lb, axis, in_slot, out_slot, inv); break;
   }
 }
 
@@ -566,8 +587,7 @@ __global__ void __launch_bounds__(256, 2) k_time_any(const Geom* __restrict__ G,
 // ------------------------------------------------------------------------------------------
 static int largest_pow2_divisor(int v) { return v & (-v); }
 
-int dst_Q(int N) {
-  const int M = 2 * (N + 1);
+int dst_Q(int M) {
   const int P = std::min(32, largest_pow2_divisor(M));
   return M / P;
 }
@@ -593,7 +613,7 @@ cudaError_t upload_constants() {
 }
 
 template <typename R, int Q>
-static void launch_dst_q(const Batch& B, int axis, int in_slot, int out_slot, size_t smem) {
+static void launch_dst_q(const Batch& B, int axis, int in_slot, int out_slot, int inv, size_t smem) {
   const int p = sizeof(R) == 4;
   static bool done = false;
   if (!done) {
@@ -605,11 +625,11 @@ static void launch_dst_q(const Batch& B, int axis, int in_slot, int out_slot, si
   const int* off = axis == 0 ? B.off_dst_i[p] : B.off_dst_j[p];
   const int tot = axis == 0 ? B.tot_dst_i[p] : B.tot_dst_j[p];
   if (in_slot >= 0)
-    k_dst<double, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, in_slot, -1);
+    k_dst<double, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, in_slot, -1, inv);
   else if (out_slot >= 0)
-    k_dst<R, double, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, out_slot);
+    k_dst<R, double, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, out_slot, inv);
   else
-    k_dst<R, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, -1);
+    k_dst<R, R, R, Q><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, -1, inv);
 }
 
 template <typename R, int Q>
@@ -624,7 +644,7 @@ static void launch_time_q(const Batch& B, int kind, size_t smem) {
 }
 
 template <typename R>
-static cudaError_t dispatch_dst(const Batch& B, int axis, int in_slot, int out_slot) {
+static cudaError_t dispatch_dst(const Batch& B, int axis, int in_slot, int out_slot, int inv) {
   const int p = sizeof(R) == 4;
   const size_t smem = B.dst_smem[p];
   if (B.dst_q == 0) {   // instances with different line lengths in one launch
@@ -638,24 +658,24 @@ static cudaError_t dispatch_dst(const Batch& B, int axis, int in_slot, int out_s
     const int* off = axis == 0 ? B.off_dst_i[p] : B.off_dst_j[p];
     const int tot = axis == 0 ? B.tot_dst_i[p] : B.tot_dst_j[p];
     if (in_slot >= 0)
-      k_dst_any<double, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, in_slot, -1);
+      k_dst_any<double, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, in_slot, -1, inv);
     else if (out_slot >= 0)
-      k_dst_any<R, double, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, out_slot);
+      k_dst_any<R, double, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, out_slot, inv);
     else
-      k_dst_any<R, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, -1);
+      k_dst_any<R, R, R><<<tot, 256, smem, B.stream>>>(B.G, B.S, off, B.count, B.sel(), axis, -1, -1, inv);
     return cudaGetLastError();
   }
   switch (B.dst_q) {
-    case 1: launch_dst_q<R, 1>(B, axis, in_slot, out_slot, smem); break;
-    case 2: launch_dst_q<R, 2>(B, axis, in_slot, out_slot, smem); break;
-    case 3: launch_dst_q<R, 3>(B, axis, in_slot, out_slot, smem); break;
-    case 4: launch_dst_q<R, 4>(B, axis, in_slot, out_slot, smem); break;
-    case 6: launch_dst_q<R, 6>(B, axis, in_slot, out_slot, smem); break;
-    case 8: launch_dst_q<R, 8>(B, axis, in_slot, out_slot, smem); break;
-    case 12: launch_dst_q<R, 12>(B, axis, in_slot, out_slot, smem); break;
-    case 16: launch_dst_q<R, 16>(B, axis, in_slot, out_slot, smem); break;
-    case 24: launch_dst_q<R, 24>(B, axis, in_slot, out_slot, smem); break;
-    case 32: launch_dst_q<R, 32>(B, axis, in_slot, out_slot, smem); break;
+    case 1: launch_dst_q<R, 1>(B, axis, in_slot, out_slot, inv, smem); break;
+    case 2: launch_dst_q<R, 2>(B, axis, in_slot, out_slot, inv, smem); break;
+    case 3: launch_dst_q<R, 3>(B, axis, in_slot, out_slot, inv, smem); break;
+    case 4: launch_dst_q<R, 4>(B, axis, in_slot, out_slot, inv, smem); break;
+    case 6: launch_dst_q<R, 6>(B, axis, in_slot, out_slot, inv, smem); break;
+    case 8: launch_dst_q<R, 8>(B, axis, in_slot, out_slot, inv, smem); break;
+    case 12: launch_dst_q<R, 12>(B, axis, in_slot, out_slot, inv, smem); break;
+    case 16: launch_dst_q<R, 16>(B, axis, in_slot, out_slot, inv, smem); break;
+    case 24: launch_dst_q<R, 24>(B, axis, in_slot, out_slot, inv, smem); break;
+    case 32: launch_dst_q<R, 32>(B, axis, in_slot, out_slot, inv, smem); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -696,7 +716,8 @@ cudaError_t pipe_time_pass(const Batch& B, int kind);
 template <typename R>
 static cudaError_t dst_pass(const Batch& B, int stage, int in_slot, int out_slot) {
   const int axis = (stage == 1 || stage == 5) ? 0 : 1;
-  if (sizeof(R) == 8 || B.pipe_pd == 0) return dispatch_dst<R>(B, axis, in_slot, out_slot);
+  const int inv = stage >= 4;          // passes 4 and 5 run the inverse transform (DCT-I pair)
+  if (sizeof(R) == 8 || B.pipe_pd == 0) return dispatch_dst<R>(B, axis, in_slot, out_slot, inv);
   if (B.pipe_pd > 0) return pipe_dst_pass(B, stage, in_slot, out_slot);
   Batch F = B;
   F.filt = B.fam_dst;
@@ -704,7 +725,7 @@ static cudaError_t dst_pass(const Batch& B, int stage, int in_slot, int out_slot
     if (!(B.fam_dst_set >> b & 1)) continue;
     F.filt_want = fam_code(b);
     F.pipe_pd = F.filt_want;
-    const cudaError_t e = b ? pipe_dst_pass(F, stage, in_slot, out_slot) : dispatch_dst<R>(F, axis, in_slot, out_slot);
+    const cudaError_t e = b ? pipe_dst_pass(F, stage, in_slot, out_slot) : dispatch_dst<R>(F, axis, in_slot, out_slot, inv);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

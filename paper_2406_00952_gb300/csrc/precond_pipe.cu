@@ -1021,7 +1021,8 @@ cudaError_t dst_pass_p(const Batch& B, int stage, int in_slot, int out_slot, boo
 // time lines of n = 32 P points, P a power of two in [2, 32]; the constant-coefficient route only.
 int pipe_time_p(const Geom& g);
 int pipe_dst_p(const Geom& g) {
-  if (g.var_a || !pipe_time_p(g)) return 0;      // the padded scratch layout needs the pipelined time pass
+  // the padded scratch layout needs the pipelined time pass; the DCT-I (Neumann) runs in precond.cu
+  if (g.var_a || g.bc == PCB_BC_NEUMANN || !pipe_time_p(g)) return 0;
   const int M = 2 * g.L;
   if (M % 32) return 0;
   const int P = M / 32;

@@ -316,13 +316,18 @@ int validate_desc(const pcb_desc* d) {
       (d->precision != PCB_FP64 && d->precision != PCB_MIXED) || !std::isfinite(d->zeta) ||
       !std::isfinite(d->gamma) || !std::isfinite(d->T))
     return PCB_ERR_INVALID_ARG;
-  // supported: any zeta (multigrid route: zeta = pi), n a power of two <= 1024, N+1 = 2^a 3^b with N <= 511
+  if (d->bc != PCB_BC_DIRICHLET && d->bc != PCB_BC_NEUMANN) return PCB_ERR_INVALID_ARG;
+  if (!std::isfinite(d->a_const)) return PCB_ERR_INVALID_ARG;
+  const bool neu = d->bc == PCB_BC_NEUMANN;
+  // supported: any zeta (multigrid route: zeta = pi), n a power of two <= 1024; Dirichlet
+  // N+1 = 2^a 3^b with N <= 511, Neumann N-1 = 2^a 3^b with 3 <= N <= 513 and constant a
   if (d->a_edges && std::fabs(d->zeta - M_PI) > 1e-12) return PCB_ERR_UNSUPPORTED;
   if (!pow2(d->n) || d->n > 1024) return PCB_ERR_UNSUPPORTED;
-  if (d->N > 511) return PCB_ERR_UNSUPPORTED;
+  if (neu ? (d->N < 3 || d->N > 513 || d->a_edges) : d->N > 511) return PCB_ERR_UNSUPPORTED;
+  const int M = neu ? 2 * (d->N - 1) : 2 * (d->N + 1);
   FftPlan pd, pt;
-  if (!make_plan(2 * (d->N + 1), pd) || !make_plan(d->n, pt)) return PCB_ERR_UNSUPPORTED;
-  if (!q_supported(dst_Q(d->N)) || !q_supported(time_Q(d->n))) return PCB_ERR_UNSUPPORTED;
+  if (!make_plan(M, pd) || !make_plan(d->n, pt)) return PCB_ERR_UNSUPPORTED;
+  if (!q_supported(dst_Q(M)) || !q_supported(time_Q(d->n))) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges && !pow2(d->N + 1)) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges && !mg_available()) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges && d->n > 512) return PCB_ERR_UNSUPPORTED;
@@ -337,16 +342,20 @@ int validate_desc(const pcb_desc* d) {
 // Scalar fields, FFT plans and launch shapes of a validated descriptor (no device work).
 void init_geom(const pcb_desc* d, Geom& g) {
   std::memset(&g, 0, sizeof(g));
-  g.N = d->N; g.n = d->n; g.m = d->N * d->N; g.L = d->N + 1; g.M = 2 * (d->N + 1);
+  g.bc = d->bc == PCB_BC_NEUMANN ? PCB_BC_NEUMANN : PCB_BC_DIRICHLET;
+  const bool neu = g.bc == PCB_BC_NEUMANN;
+  g.N = d->N; g.n = d->n; g.m = d->N * d->N; g.L = neu ? d->N - 1 : d->N + 1; g.M = 2 * g.L;
   g.mn = (long long)g.m * g.n;
   g.theta = d->theta; g.tau = d->T / d->n; g.gamma = d->gamma; g.alpha = g.tau / std::sqrt(d->gamma);
-  g.h = 1.0 / (d->N + 1); g.sqrt_gamma = std::sqrt(d->gamma); g.c = g.tau / (g.h * g.h);
+  g.h = 1.0 / g.L; g.sqrt_gamma = std::sqrt(d->gamma);
+  const double a0 = d->a_const > 0.0 ? d->a_const : 1.0;
+  g.c = a0 * g.tau / (g.h * g.h);
   g.var_a = d->a_edges ? 1 : 0;
   g.zeta = d->zeta;
   g.zeta_pi = std::fabs(d->zeta - M_PI) <= 1e-12 ? 1 : 0;
   make_plan(g.M, g.pdst);
   make_plan(g.n, g.ptime);
-  g.dst_q = dst_Q(g.N);
+  g.dst_q = dst_Q(g.M);
   g.time_q = time_Q(g.n);
   set_shapes(g);
 }
@@ -370,9 +379,12 @@ void fill_tables(const pcb_desc* d, const Geom& g, const TableLayout& t, unsigne
   const int N = g.N, n = g.n, M = g.M;
   std::memset(host, 0, t.bytes);
   double* kap = (double*)(host + t.kap);
-  for (int q = 1; q <= N; ++q) {
-    const double s = std::sin(q * M_PI * g.h / 2.0);
-    kap[q - 1] = 4.0 / (g.h * g.h) * s * s;
+  const double a0 = d->a_const > 0.0 && !d->a_edges ? d->a_const : 1.0;
+  for (int q = 0; q < N; ++q) {
+    // Dirichlet mode q+1 of the DST-I, Neumann mode q of the DCT-I: a (4/h^2) sin^2(k pi / (2L))
+    const int k = g.bc == PCB_BC_NEUMANN ? q : q + 1;
+    const double s = std::sin(k * M_PI / (2.0 * g.L));
+    kap[q] = a0 * 4.0 / (g.h * g.h) * s * s;
   }
   // lambda(S_n) at F-slot r: psi_r = -(zeta + 2 pi r)/n (zeta = pi: -pi (2r+1)/n), f1/f2 with
   // f1 = 1 - e^{i psi}, f2 = theta + (1-theta) e^{i psi}
@@ -746,7 +758,7 @@ static void resolve_defaults(const pcb_problem* p, const pcb_solve_opts* o, Solv
   c.inner_floor = (o && o->inner_floor > 0) ? o->inner_floor : 0.0;
   const bool va = p->g.var_a != 0;
   if (c.method == PCB_METHOD_AUTO) {
-    if (p->g.theta == 1.0) c.method = PCB_MINRES;
+    if (p->g.theta == 1.0 && p->g.bc != PCB_BC_NEUMANN) c.method = PCB_MINRES;
     else c.method = va ? PCB_FGMRES : PCB_GMRES;
     if (c.kind == PCB_PREC_NONE) {
       if (c.method == PCB_MINRES) c.kind = va ? PCB_PREC_PMS : PCB_PREC_ABS_PS;
@@ -762,6 +774,7 @@ static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_d
   resolve_defaults(p, o, c);
   if (c.method == PCB_MINRES && (c.kind == PCB_PREC_PS)) return PCB_ERR_INVALID_ARG;   // P_S is not SPD
   if (c.kind == PCB_PREC_ABS_PS && p->g.var_a) return PCB_ERR_UNSUPPORTED;
+  if (p->g.bc == PCB_BC_NEUMANN && (c.method == PCB_MINRES || c.kind != PCB_PREC_PS)) return PCB_ERR_UNSUPPORTED;
   int rc;
   if ((rc = ensure_minres(p))) return rc;
   const size_t nv = (size_t)2 * p->g.mn;
@@ -874,6 +887,7 @@ int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_d
   if (kind != PCB_PREC_ABS_PS && kind != PCB_PREC_PS && kind != PCB_PREC_PMS) return PCB_ERR_INVALID_ARG;
   if (precision != PCB_FP64 && precision != PCB_MIXED) return PCB_ERR_INVALID_ARG;
   if (kind == PCB_PREC_ABS_PS && p->g.var_a) return PCB_ERR_UNSUPPORTED;
+  if (kind != PCB_PREC_PS && p->g.bc == PCB_BC_NEUMANN) return PCB_ERR_UNSUPPORTED;
   p->hS.v[SL_UIN] = (double*)x_dev;
   p->hS.v[SL_UOUT] = y_dev;
   int rc;
@@ -1166,6 +1180,8 @@ extern "C" int pcb_batch_solve(pcb_problem* const* problems, int count, const pc
     resolve_defaults(problems[k], opts, c);
     if (c.method == PCB_MINRES && c.kind == PCB_PREC_PS) return PCB_ERR_INVALID_ARG;
     if (problems[k]->g.var_a) return PCB_ERR_UNSUPPORTED;      // multigrid instances solve one at a time
+    if (problems[k]->g.bc == PCB_BC_NEUMANN && (c.method == PCB_MINRES || c.kind != PCB_PREC_PS))
+      return PCB_ERR_UNSUPPORTED;
     BGroup* G = nullptr;
     for (size_t q = 0; q < groups.size(); ++q)
       if (groups[q]->method == c.method && groups[q]->kind == c.kind) G = groups[q].get();
@@ -1530,7 +1546,7 @@ int pcb_server_submit(pcb_server* S, const pcb_desc* d, const double* rhs, doubl
   dd.stream = (void*)S->st;
   const int rc = validate_desc(&dd);
   if (rc != PCB_OK) return rc;
-  const int method = dd.theta == 1.0 ? PCB_MINRES : PCB_GMRES;
+  const int method = dd.theta == 1.0 && dd.bc != PCB_BC_NEUMANN ? PCB_MINRES : PCB_GMRES;
   if (srv_estimate(&dd, method, S->o.restart) > S->o.budget_bytes) return PCB_ERR_TOO_LARGE;
   S->queue.push_back(SrvReq{dd, rhs, x, tag});
   return PCB_OK;
@@ -1564,7 +1580,7 @@ int pcb_server_step(pcb_server* S, pcb_server_done* done, int max_done, int* n_d
   // admit (FIFO; a request waits for a slot of its method and room in the budget)
   while (S->qhead < S->queue.size()) {
     SrvReq& r = S->queue[S->qhead];
-    const int q = r.desc.theta == 1.0 ? 0 : 1;
+    const int q = r.desc.theta == 1.0 && r.desc.bc != PCB_BC_NEUMANN ? 0 : 1;
     SrvGroup& G = S->grp[q];
     int free_k = -1;
     for (int k = 0; k < G.cap; ++k) if (G.slots[k].phase == PH_FREE) { free_k = k; break; }

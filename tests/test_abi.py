@@ -41,4 +41,13 @@ def test_create_rejects_invalid_descriptors_without_touching_the_gpu():
     d = _lib.PcbDesc(3, 4, 1.0, 1.0, 1e-2, 0.4, a, 0, 2, None)
     h = ctypes.c_void_p()
     assert lib.pcb_create(ctypes.byref(d), ctypes.byref(h)) == -2
+    # Neumann: N-1 must be 2^a 3^b (DCT-I radices), 3 <= N <= 513, no a_edges; bc outside the enum
+    for N in (2, 6, 514, 1025):
+        d = _lib.PcbDesc(N, 4, 0.5, 1.0, 1e-2, 3.141592653589793, None, 0, 2, None, 1, 1e-3)
+        assert lib.pcb_create(ctypes.byref(d), ctypes.byref(h)) == -2, N
+    a = (ctypes.c_double * (2 * 3 * 4))(*([1.0] * 24))
+    d = _lib.PcbDesc(3, 4, 0.5, 1.0, 1e-2, 3.141592653589793, a, 0, 2, None, 1, 0.0)
+    assert lib.pcb_create(ctypes.byref(d), ctypes.byref(h)) == -2
+    d = _lib.PcbDesc(5, 4, 0.5, 1.0, 1e-2, 3.141592653589793, None, 0, 2, None, 2, 1.0)
+    assert lib.pcb_create(ctypes.byref(d), ctypes.byref(h)) == -1
     assert lib.pcb_create(None, None) == -1
