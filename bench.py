@@ -48,6 +48,7 @@ def args():
     ap.add_argument("--serve-window", type=float, default=0.25,
                     help="seconds of the serving trace replayed for the serving figures (0: skip)")
     ap.add_argument("--small", action="store_true", help="N=255, n=256 instead (quick checks only)")
+    ap.add_argument("--no-neumann", action="store_true", help="skip the Example 3 (Neumann) figures")
     return ap.parse_args()
 
 
@@ -206,6 +207,42 @@ def reference_arm(a, W, rank, world):
     print(json.dumps(line))
 
 
+def neumann_figures(P, synth, np, torch, stream, steps):
+    """Mixed and FP64 GMRES-P_S on Example 3 (N = 257 nodes, n = 256), timed with CUDA events after
+    one warm-up solve; e_h against the exact solution; the FP32 P_S apply against the HBM roofline."""
+    N = 257; n = 256; gam = 1e-2
+    g, f, ye, pe = synth.example3_data(N, n)
+    out = {"workload": f"Example 3 Neumann N={N} nodes (h=1/256) n={n} CN a=1e-3 gamma={gam:g}",
+           "unknowns": 2 * N * N * n}
+    gd = torch.from_numpy(g.ravel()).cuda(); fd = torch.from_numpy(f.ravel()).cuda()
+    y0 = torch.from_numpy(np.ascontiguousarray(ye[0])).cuda()
+    hbm, _ = peaks()
+    for prec in ("mixed", "fp64"):
+        pr = P.Problem(N, n, 0.5, gam, precision=prec, stream=stream, bc="neumann", a=1e-3)
+        b = pr.assemble_rhs(gd, fd, y0, op="Ahat")
+        x = pr._empty()
+        pr.solve(b, x, tol=1e-8)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [pr.solve(b, x, tol=1e-8, profile=True)[1] for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        y, p = pr.recover(x)
+        ey = y.cpu().numpy().reshape(n, -1) - ye[1:]
+        ep = p.cpu().numpy().reshape(n, -1) - pe[:-1]
+        eh = float((np.sqrt((ey ** 2).sum(1) + (ep ** 2).sum(1)) / (N - 1)).max())
+        applies = sum(i["precond_applies"] for i in infos); pms = sum(i["precond_ms"] for i in infos)
+        out[prec] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iterations": infos[-1]["iterations"],
+                     "relres": infos[-1]["relres"], "e_h": eh, "precond_avg_ms": pms / applies}
+        if prec == "mixed":
+            ach = 16.0 * out["unknowns"] / (pms / applies / 1e3) / 1e9
+            out["precond_roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                       "frac": ach / hbm, "kernel": "P_S^-1 apply, DCT-I passes (FP32)"}
+        pr.close(); del b, x, y, p
+    return out
+
+
 def main():
     a = args()
     rank = int(os.environ.get("RANK", 0)); world = int(os.environ.get("WORLD_SIZE", 1))
@@ -333,6 +370,12 @@ def main():
                    "fp64_one_at_a_time": {k: base[k] for k in ("solves_per_s", "p50_latency_s", "p99_latency_s")}}
         del reqs
 
+    # Example 3 (homogeneous Neumann, a = 1e-3, Crank-Nicolson, gamma = 1e-2) at the size of
+    # Table 4's finest row: 257 nodes per side (h = 1/256), n = 256, GMRES-P_S with the DCT-I passes
+    neumann = None
+    if rank == 0 and not a.no_neumann:
+        neumann = neumann_figures(P, synth, np, torch, stream, a.steps)
+
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
         dt, it_o = cpu_baseline(W)
@@ -368,6 +411,7 @@ def main():
             "clocks": clocks,
             "gpu_launches": sum(i["launches"] for i in infos),
             "serving": serving,
+            "neumann": neumann,
         }
         print(json.dumps(line))
     if world > 1:

@@ -106,7 +106,10 @@ __global__ void __launch_bounds__(256) k_minres_wx(const Geom* __restrict__ G, c
   }
 }
 
-// CGS: partial[blk*(PCB_MAX_RESTART+1) + i] = V_i . W,  i = 0..j
+// CGS: partial[blk*(PCB_MAX_RESTART+1) + i] = V_i . W,  i = 0..j.  JB >= j + 1 bounds the unrolled
+// basis loop: the host picks the smallest of 2, 4, 8, 16, 33 that covers the Arnoldi index, so an
+// early step does not pay for 33 predicated basis vectors per element.
+template <int JB>
 __global__ void __launch_bounds__(256) k_multidot(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                                   const Scal* __restrict__ Sc, const int* __restrict__ off, int count,
                                                   const int* __restrict__ active, int svbase, int j, int sw,
@@ -115,17 +118,17 @@ __global__ void __launch_bounds__(256) k_multidot(const Geom* __restrict__ G, co
   if (j < 0) j = Sc[inst].j;   // each instance at its own Arnoldi index
   const double* __restrict__ V = S[inst].v[svbase];
   const double* __restrict__ W = S[inst].v[sw];
-  double acc[PCB_MAX_RESTART + 1];
+  double acc[JB];
 #pragma unroll
-  for (int i = 0; i <= PCB_MAX_RESTART; ++i) acc[i] = 0.0;
+  for (int i = 0; i < JB; ++i) acc[i] = 0.0;
   for (long long e = e0; e < len; e += stride) {
     const double w = W[e];
 #pragma unroll
-    for (int i = 0; i <= PCB_MAX_RESTART; ++i)
+    for (int i = 0; i < JB; ++i)
       if (i <= j) acc[i] = fma(V[(long long)i * len + e], w, acc[i]);
   }
 #pragma unroll
-  for (int i = 0; i <= PCB_MAX_RESTART; ++i) {
+  for (int i = 0; i < JB; ++i) {
     if (i > j) break;
     const double r = block_sum(acc[i]);
     if (threadIdx.x == 0) partial[(long long)blockIdx.x * (PCB_MAX_RESTART + 1) + i] = r;
@@ -133,6 +136,7 @@ __global__ void __launch_bounds__(256) k_multidot(const Geom* __restrict__ G, co
 }
 
 // W -= sum_i h_i V_i (coef from Scal.H[pass*(MAX+1) + i]) ; or X += sum_i y_i Z_i (pass = -1)
+template <int JB>
 __global__ void __launch_bounds__(256) k_multiaxpy(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                                    const Scal* __restrict__ Sc, const int* __restrict__ off, int count,
                                                    const int* __restrict__ active, int svbase, int j, int sw,
@@ -142,9 +146,9 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const Geom* __restrict__ G, c
   if (j < 0) j = pass >= 0 ? c.j : c.j - 1;   // per-instance index (after Arnoldi, c.j = columns)
   const double* __restrict__ V = S[inst].v[svbase];
   double* __restrict__ W = S[inst].v[sw];
-  double coef[PCB_MAX_RESTART + 1];
+  double coef[JB];
 #pragma unroll
-  for (int i = 0; i <= PCB_MAX_RESTART; ++i) {
+  for (int i = 0; i < JB; ++i) {
     double h = 0.0;
     if (i <= j) h = pass >= 0 ? -c.H[pass * (PCB_MAX_RESTART + 1) + i] : c.y[i];
     coef[i] = h;
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const Geom* __restrict__ G, c
   for (long long e = e0; e < len; e += stride) {
     double w = W[e];
 #pragma unroll
-    for (int i = 0; i <= PCB_MAX_RESTART; ++i)
+    for (int i = 0; i < JB; ++i)
       if (i <= j) w = fma(coef[i], V[(long long)i * len + e], w);
     W[e] = w;
   }
@@ -335,8 +339,22 @@ cudaError_t launch_minres_wx(const Batch& B, int sy, int sw, int sw2, int sx) {
   k_minres_wx<<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, sy, sw, sw2, sx);
   return cudaGetLastError();
 }
+// basis-loop bound for Arnoldi index j (j < 0: per-instance indices, any up to the maximum)
+static int basis_bound(int j) {
+  const int need = j < 0 ? PCB_MAX_RESTART + 1 : j + 1;
+  return need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : PCB_MAX_RESTART + 1;
+}
 cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw) {
-  k_multidot<<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, B.partial);
+#define PCB_MULTIDOT(JB) \
+  k_multidot<JB><<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, B.partial)
+  switch (basis_bound(j)) {
+    case 2: PCB_MULTIDOT(2); break;
+    case 4: PCB_MULTIDOT(4); break;
+    case 8: PCB_MULTIDOT(8); break;
+    case 16: PCB_MULTIDOT(16); break;
+    default: PCB_MULTIDOT(PCB_MAX_RESTART + 1); break;
+  }
+#undef PCB_MULTIDOT
   return cudaGetLastError();
 }
 cudaError_t launch_reduce_multi(const Batch& B, int j, int pass) {
@@ -344,7 +362,16 @@ cudaError_t launch_reduce_multi(const Batch& B, int j, int pass) {
   return cudaGetLastError();
 }
 cudaError_t launch_multiaxpy(const Batch& B, int svbase, int j, int sw, int pass) {
-  k_multiaxpy<<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, pass);
+#define PCB_MULTIAXPY(JB) \
+  k_multiaxpy<JB><<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, pass)
+  switch (basis_bound(j)) {
+    case 2: PCB_MULTIAXPY(2); break;
+    case 4: PCB_MULTIAXPY(4); break;
+    case 8: PCB_MULTIAXPY(8); break;
+    case 16: PCB_MULTIAXPY(16); break;
+    default: PCB_MULTIAXPY(PCB_MAX_RESTART + 1); break;
+  }
+#undef PCB_MULTIAXPY
   return cudaGetLastError();
 }
 cudaError_t launch_swap(const Batch& B, int a0, int b0, int a1, int b1, int a2, int b2) {
