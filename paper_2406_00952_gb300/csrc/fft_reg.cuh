@@ -169,9 +169,7 @@ __device__ __forceinline__ void lane_dif(T* x, int P, const LaneStages<T, R>& st
       T a;
       a.x = __shfl_xor_sync(0xffffffffu, v.x, d);
       a.y = __shfl_xor_sync(0xffffffffu, v.y, d);
-      a.x = fma(sg, v.x, a.x);
-      a.y = fma(sg, v.y, a.y);
-      x[q] = cmul(a, w);
+      x[q] = cmul(cfma_s(sg, v, a), w);
     }
   }
 }

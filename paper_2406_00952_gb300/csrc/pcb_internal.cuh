@@ -33,6 +33,17 @@ template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
 }
 template <typename T> __device__ __forceinline__ T cconj(T a) { a.y = -a.y; return a; }
 template <typename T, typename R> __device__ __forceinline__ T cscale(T a, R s) { a.x *= s; a.y *= s; return a; }
+// FP32 pairs: one packed instruction (f32x2, sm_100 and later) per complex add, subtract or real
+// scale; each lane rounds exactly like the scalar operation (a - b = fma(-1, b, a) is exact
+// before its single rounding)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(make_float2(-1.f, -1.f), b, a); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+// s * v + a for a real s
+template <typename T, typename R> __device__ __forceinline__ T cfma_s(R s, T v, T a) {
+  a.x = fma(s, v.x, a.x); a.y = fma(s, v.y, a.y); return a;
+}
+__device__ __forceinline__ float2 cfma_s(float s, float2 v, float2 a) { return __ffma2_rn(make_float2(s, s), v, a); }
 // a * (-i)
 template <typename T> __device__ __forceinline__ T cmul_mi(T a) { T c; c.x = a.y; c.y = -a.x; return c; }
 // a * (+i)

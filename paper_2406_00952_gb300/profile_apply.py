@@ -1,9 +1,11 @@
 """Profiling driver: runs a few preconditioner applies (or operator products) on one problem so a
 profiler can capture individual launches.
 
-    python -m paper_2406_00952_gb300.profile_apply N n [mixed|fp64] [abs_ps|ps|pms|matvec] [repeats]
+    python -m paper_2406_00952_gb300.profile_apply N n [mixed|fp64] [abs_ps|ps|pms|matvec] [repeats] [neumann]
 
 Each apply is five launches (x1-line DST, x2-line DST, time pass, x2-line DST, x1-line DST).
+With `neumann` the problem is Example 3's (N nodes per side with the boundary, a = 1e-3,
+Crank-Nicolson), whose applies run the DCT-I passes (kind ps).
 """
 from __future__ import annotations
 
@@ -21,7 +23,10 @@ def main(argv):
     prec = argv[2] if len(argv) > 2 else "mixed"
     kind = argv[3] if len(argv) > 3 else "abs_ps"
     reps = int(argv[4]) if len(argv) > 4 else 3
-    gp = P.Problem(N, n, 1.0, 1e-2, precision=prec)
+    if len(argv) > 5 and argv[5] == "neumann":
+        gp = P.Problem(N, n, 0.5, 1e-2, precision=prec, bc="neumann", a=1e-3)
+    else:
+        gp = P.Problem(N, n, 1.0, 1e-2, precision=prec)
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.randn(gp.size, dtype=torch.float64, device="cuda", generator=g)
     y = torch.empty_like(x)
