@@ -34,9 +34,10 @@ def _ptr(t: torch.Tensor | None, numel: int | None = None) -> int | None:
 
 
 def _opts(method="auto", precond=None, tol=1e-8, maxit=500, restart=30, max_refinements=10, fixed_iterations=0,
-          profile=False, inner_floor=0.0):
+          profile=False, inner_floor=0.0, graphs=True):
     return PcbSolveOpts(METHODS[method], PRECONDS[precond], float(tol), int(maxit), int(restart),
-                        int(max_refinements), int(fixed_iterations), int(bool(profile)), float(inner_floor))
+                        int(max_refinements), int(fixed_iterations), int(bool(profile)), float(inner_floor),
+                        int(not graphs))
 
 
 class Problem:

@@ -28,7 +28,7 @@ class PcbDesc(ctypes.Structure):
 class PcbSolveOpts(ctypes.Structure):
     _fields_ = [("method", c_int), ("precond", c_int), ("tol", c_double), ("maxit", c_int),
                 ("restart", c_int), ("max_refinements", c_int), ("fixed_iterations", c_int),
-                ("profile", c_int), ("inner_floor", c_double)]
+                ("profile", c_int), ("inner_floor", c_double), ("no_graphs", c_int)]
 
 
 class PcbSolveInfo(ctypes.Structure):

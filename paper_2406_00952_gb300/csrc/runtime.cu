@@ -98,6 +98,12 @@ struct pcb_problem {
   Slots* hSpin = nullptr;         // pinned staging for slot uploads
   Batch B;
   double* host_io = nullptr;      // device staging for pcb_solve_host (b, x)
+  // CUDA graph of one MINRES iteration (captured on a private stream, replayed on `stream`)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t git = nullptr;
+  int git_kind = -1, git_prec = -1, git_sx = -1;
+  long long git_launches = 0;
+  double* dtol = nullptr;         // device copy of the running tolerance read by the scalar steps
   // per-solve counters and optional event profiling
   long long launches = 0;
   int prec_applies = 0, matvecs = 0;
@@ -300,6 +306,9 @@ void pcb_destroy(pcb_problem* p) {
   cudaFreeHost(p->hSc);
   cudaFreeHost(p->hSpin);
   cudaFree(p->host_io);
+  if (p->git) cudaGraphExecDestroy(p->git);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  cudaFree(p->dtol);
   for (cudaEvent_t e : p->ev_prec) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev_mv) cudaEventDestroy(e);
   delete p;
@@ -549,6 +558,7 @@ struct SolveCfg {
   double tol;
   double inner_floor;   // mixed precision: smallest inner tolerance
   bool check_true;      // FP64 route: keep iterating if the true residual check fails
+  bool graphs;          // replay MINRES iterations from a captured CUDA graph
 };
 
 static int apply_precond(const pcb_problem* p, const Batch& B, int kind, int prec, int in_slot, int out_slot) {
@@ -617,6 +627,56 @@ static int read_scal(const Batch& B, Scal* host, int count) {
 
 // Single-instance MINRES on slot rhs -> slot x (both set by the caller).  Returns iterations via sc.
 #define LC(p) (++(p)->launches, 0) ? cudaSuccess :
+
+// One MINRES iteration's launches: product with the Lanczos epilogue, scalar steps, residual
+// update, preconditioner, inner product, direction/solution update, slot rotation.  Every kernel
+// takes its scalars and vector pointers from device memory (Scal, Slots, the tolerance in
+// B.tols), so one launch sequence serves every iteration and can be replayed from a graph.
+static int minres_iter_launches(pcb_problem* p, const Batch& B, const SolveCfg& c, int s_x) {
+  int rc;
+  CK(P_matvec(p, B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
+  CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
+  CK(LC(p) launch_axpby(B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
+  if ((rc = P_precond(p, B, c.kind, c.prec, SL_R1, SL_YO))) return rc;
+  CK(LC(p) launch_dot(B, SL_R1, SL_YO));
+  CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_MINRES_GIVENS, c.tol, 0, 0));
+  CK(LC(p) launch_minres_wx(B, SL_Y, SL_W, SL_W2, s_x));
+  CK(LC(p) launch_swap(B, SL_R1, SL_R2, SL_Y, SL_YO, SL_W, SL_W2));
+  return PCB_OK;
+}
+
+// Capture minres_iter_launches into p->git (on a private stream: the caller's may be the legacy
+// default stream, which cannot be captured).  Returns false when capture is not possible; the
+// caller then launches directly.  Counters are restored: the captured launches did not run.
+static bool capture_minres_iter(pcb_problem* p, const Batch& B, const SolveCfg& c, int s_x) {
+  if (p->git) { cudaGraphExecDestroy(p->git); p->git = nullptr; }
+  if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError(); p->cap_stream = nullptr; return false;
+  }
+  Batch Bc = B;
+  Bc.stream = p->cap_stream;
+  const long long l0 = p->launches;
+  const int a0 = p->prec_applies, m0 = p->matvecs;
+  if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError(); return false;
+  }
+  const int rc = minres_iter_launches(p, Bc, c, s_x);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+  p->git_launches = p->launches - l0;
+  p->launches = l0; p->prec_applies = a0; p->matvecs = m0;
+  if (rc != PCB_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return false;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&p->git, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) { p->git = nullptr; cudaGetLastError(); return false; }
+  p->git_kind = c.kind; p->git_prec = c.prec; p->git_sx = s_x;
+  return true;
+}
+
 static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Scal* hs, double* relres_out,
                          int* it_out, bool* conv_out) {
   const Batch& B = p->B;
@@ -641,15 +701,26 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   if (hs->bnorm == 0.0 || !hs->active) { *conv_out = true; *relres_out = 0.0; return PCB_OK; }
   const int limit = c.fixed > 0 ? c.fixed : c.maxit;
   bool checking = false;
+  // the iterations read the tolerance from the device, so a captured graph serves every sweep
+  if (!p->dtol && cudaMalloc(&p->dtol, sizeof(double)) != cudaSuccess) { cudaGetLastError(); p->dtol = nullptr; }
+  Batch Bt = B;
+  bool graph = c.graphs && !p->prof && !va && p->dtol;
+  if (p->dtol) {
+    CK(cudaMemcpyAsync(p->dtol, &c.tol, sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    Bt.tols = p->dtol;
+  }
   for (int it = 0; it < limit; ++it) {
-    CK(P_matvec(p, B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
-    CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
-    CK(LC(p) launch_axpby(B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
-    if ((rc = P_precond(p, B, c.kind, c.prec, SL_R1, SL_YO))) return rc;
-    CK(LC(p) launch_dot(B, SL_R1, SL_YO));
-    CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_MINRES_GIVENS, c.tol, 0, 0));
-    CK(LC(p) launch_minres_wx(B, SL_Y, SL_W, SL_W2, s_x));
-    CK(LC(p) launch_swap(B, SL_R1, SL_R2, SL_Y, SL_YO, SL_W, SL_W2));
+    // the first iteration runs directly (one-time kernel attribute setup happens there)
+    if (graph && it >= 1 && !(p->git && p->git_kind == c.kind && p->git_prec == c.prec && p->git_sx == s_x))
+      graph = capture_minres_iter(p, Bt, c, s_x);
+    if (graph && it >= 1) {
+      CK(cudaGraphLaunch(p->git, p->stream));
+      p->launches += p->git_launches;
+      p->prec_applies += 1;
+      p->matvecs += 1;
+    } else if ((rc = minres_iter_launches(p, Bt, c, s_x))) {
+      return rc;
+    }
     std::swap(p->hS.v[SL_R1], p->hS.v[SL_R2]);
     std::swap(p->hS.v[SL_Y], p->hS.v[SL_YO]);
     std::swap(p->hS.v[SL_W], p->hS.v[SL_W2]);
@@ -756,6 +827,7 @@ static void resolve_defaults(const pcb_problem* p, const pcb_solve_opts* o, Solv
   c.fixed = o ? o->fixed_iterations : 0;
   c.prec = p->desc.precision;
   c.inner_floor = (o && o->inner_floor > 0) ? o->inner_floor : 0.0;
+  c.graphs = !(o && o->no_graphs);
   const bool va = p->g.var_a != 0;
   if (c.method == PCB_METHOD_AUTO) {
     if (p->g.theta == 1.0 && p->g.bc != PCB_BC_NEUMANN) c.method = PCB_MINRES;

@@ -337,3 +337,21 @@ def test_batch_solve_uneven(P, precision, shapes):
         assert np.linalg.norm(b - A(xo)) / np.linalg.norm(b) <= 1.5e-8    # oracle's FP64 residual
         x1, i1 = P.batch_solve([gp], [dev(b)], tol=1e-8, restart=16)      # the same instance alone
         assert rel(xo, x1[0].cpu().numpy()) <= 1e-12 and i1[0]["iterations"] == info["iterations"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_minres_graph_replay_matches_direct_launches(P, precision):
+    """MINRES iterations replayed from the captured CUDA graph give the same iterates, bit for
+    bit, as launching each kernel directly, with the same iteration and launch counts; the
+    capture also works on the legacy default stream (it is taken on a private stream)."""
+    inst = synth.config0()
+    prob = ds.Problem(inst.N, inst.n, 1.0, inst.gamma)
+    b = dev(ds.rhs_minres(prob, inst.g, inst.f))
+    gp = P.Problem(inst.N, inst.n, 1.0, inst.gamma, precision=precision)
+    xd, idir = gp.solve(b, tol=1e-10, graphs=False)
+    xg, igr = gp.solve(b, tol=1e-10, graphs=True)
+    xg2, igr2 = gp.solve(b, tol=1e-10, graphs=True)            # replays the graph kept from the last solve
+    assert igr["iterations"] == idir["iterations"] == igr2["iterations"] > 1
+    assert igr["launches"] == idir["launches"] == igr2["launches"]
+    assert torch.equal(xd, xg) and torch.equal(xd, xg2)
+    assert igr["relres"] <= 1e-10
