@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import PRECISIONS, Problem, _lib
+from . import BCS, PRECISIONS, Problem, _lib
 from ._lib import PcbDesc, PcbServerDone, PcbServerOpts, check
 
 
@@ -55,8 +55,10 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, N, n, theta, gamma, rhs_host: torch.Tensor, x_host: torch.Tensor, tag: int, T=1.0):
-        d = PcbDesc(int(N), int(n), float(theta), float(T), float(gamma), math.pi, None, 0, 2, None)
+    def submit(self, N, n, theta, gamma, rhs_host: torch.Tensor, x_host: torch.Tensor, tag: int, T=1.0,
+               bc="dirichlet", a=1.0):
+        d = PcbDesc(int(N), int(n), float(theta), float(T), float(gamma), math.pi, None, 0, 2, None, BCS[bc],
+                    float(a))
         self._keep[tag] = (rhs_host, x_host)
         check("pcb_server_submit", self.lib.pcb_server_submit(self.h, ctypes.byref(d), rhs_host.data_ptr(),
                                                               x_host.data_ptr(), int(tag)))
@@ -84,6 +86,8 @@ class Request:
     gamma: float
     rhs: torch.Tensor          # pinned host, the system's right-hand side
     x: torch.Tensor = None     # pinned host output
+    bc: str = "dirichlet"      # "neumann": Example 3's grid, GMRES-P_S
+    a: float = 1.0             # constant coefficient
 
 
 def run(requests: list[Request], budget_bytes: int, max_slots: int = 32, precision: str = "mixed",
@@ -102,7 +106,7 @@ def run(requests: list[Request], budget_bytes: int, max_slots: int = 32, precisi
         now = time.perf_counter() - t0
         while nxt < len(pending) and pending[nxt].arrival_s <= now:
             r = pending[nxt]
-            srv.submit(r.N, r.n, r.theta, r.gamma, r.rhs, r.x, r.tag)
+            srv.submit(r.N, r.n, r.theta, r.gamma, r.rhs, r.x, r.tag, bc=r.bc, a=r.a)
             nxt += 1
         if active == 0 and queued == 0 and nxt < len(pending) and pending[nxt].arrival_s > now:
             time.sleep(min(0.001, pending[nxt].arrival_s - now))

@@ -63,3 +63,28 @@ def test_budget_admission_and_rejection(P):
         srv.submit(15, 16, 1.0, 1e-2, t, t.clone(), 0)
     assert "too large" in str(e.value)
     srv.close()
+
+
+def test_served_neumann_requests_beside_dirichlet(P):
+    """Neumann requests (Example 3's grid, GMRES-P_S with the DCT-I passes) served in the same
+    shared launches as Dirichlet ones; each equals the request solved alone."""
+    from paper_2406_00952_gb300 import serve
+    specs = [(33, 32, 1.0, 1e-3, "neumann", 1e-3), (31, 16, 1.0, 1e-2, "dirichlet", 1.0),
+             (17, 64, 0.5, 1e-5, "neumann", 0.1), (15, 32, 0.5, 1e-3, "dirichlet", 1.0)]
+    reqs = []
+    for k, (N, n, th, gm, bc, a) in enumerate(specs):
+        prob = ds.Problem(N, n, th, gm, bc=bc, a0=a)
+        g = synth.random_target(N, n, seed=90 + k); f = synth.manufactured_source(N, n)
+        gmres = th != 1.0 or bc == "neumann"
+        b = ds.rhs_gmres(prob, g, f) if gmres else ds.rhs_minres(prob, g, f)
+        reqs.append((serve.Request(k, 0.0, N, n, th, gm, torch.from_numpy(b).pin_memory(), bc=bc, a=a), prob, b, gmres))
+    res = serve.run([r for r, _, _, _ in reqs], budget_bytes=8 << 30, max_slots=4, precision="mixed")
+    assert res["failed"] == 0 and res["max_relres"] <= 1e-8
+    for r, prob, b, gmres in reqs:
+        x = r.x.numpy()
+        A = (lambda z: op.matvec_A_hat(prob, z)) if gmres else (lambda z: op.matvec_A(prob, z))
+        assert np.linalg.norm(b - A(x)) / np.linalg.norm(b) <= 1.5e-8
+        gp = P.Problem(r.N, r.n, r.theta, r.gamma, precision="mixed", bc=r.bc, a=r.a)
+        xa, ia = P.batch_solve([gp], [torch.from_numpy(b).cuda()], tol=1e-8, restart=16)
+        assert np.linalg.norm(xa[0].cpu().numpy() - x) <= 1e-12 * np.linalg.norm(x)
+        assert ia[0]["iterations"] == res["results"][r.tag].iterations

@@ -52,6 +52,22 @@ def test_noalloc_matches_allocating_apply_two_calls_in_a_row(lib):
             assert _rel(out, ref) <= TOL[prec], (N, n, kind, prec, call, _rel(out, ref))
 
 
+def test_noalloc_neumann_ps(lib):
+    """Example 3's Neumann grid through the allocation-free entry: the DCT-I passes; |P_S| refused."""
+    import paper_2406_00952_gb300 as P
+    from paper_2406_00952_gb300 import _lib
+    N, n = 33, 32
+    size = 2 * N * N * n
+    x = torch.from_numpy(synth.random_vector(size, seed=9)).cuda()
+    ref = P.Problem(N, n, 0.5, 1e-3, bc="neumann", a=1e-3).precond_apply(x, kind="ps", precision="mixed").cpu().numpy()
+    s = torch.cuda.current_stream().cuda_stream
+    d = _lib.PcbDesc(N, n, 0.5, 1.0, 1e-3, math.pi, None, 0, 2, ctypes.c_void_p(s), 1, 1e-3)
+    y = torch.full((size,), float("nan"), dtype=torch.float64, device="cuda")
+    assert lib.pcb_precond_apply_noalloc(ctypes.byref(d), KIND["ps"], PREC["mixed"], x.data_ptr(), y.data_ptr()) == 0
+    assert _rel(y.cpu().numpy(), ref) <= TOL["mixed"]
+    assert lib.pcb_precond_apply_noalloc(ctypes.byref(d), KIND["abs_ps"], PREC["mixed"], x.data_ptr(), y.data_ptr()) == -2
+
+
 def test_noalloc_rejects_sizes_beyond_the_arena(lib):
     d = _desc(511, 512, 1.0, 1e-2)
     x = torch.zeros(8, dtype=torch.float64, device="cuda")
