@@ -180,8 +180,9 @@ int pcb_solve(pcb_problem* p, const pcb_solve_opts* opts, const double* b_dev, d
               pcb_solve_info* info);
 
 /* Same solve through host buffers: copies b_host to the device, solves, copies x back
- * (device staging buffers are allocated on the first call and kept until pcb_destroy;
- * page-locked host buffers give the fastest copies). */
+ * (device staging buffers are allocated on the first call and kept until pcb_destroy).
+ * Page-locked host buffers are read and written by a copy kernel over the CPU-GPU link;
+ * pageable ones go through cudaMemcpyAsync.  info->launches counts the copy kernels. */
 int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* opts, const double* b_host,
                    double* x_host, pcb_solve_info* info);
 

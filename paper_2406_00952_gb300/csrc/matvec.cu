@@ -298,6 +298,29 @@ cudaError_t launch_rhs(const Geom& g, cudaStream_t st, int op, const double* gs,
   return cudaGetLastError();
 }
 
+// dst[0..n) = src[0..n) where one side is memory the device maps directly (page-locked host memory
+// over the coherent CPU-GPU link): SM loads and stores instead of a copy-engine transfer, which on
+// this system ran at 200 GB/s only some of the time (30-40 GB/s right after long kernel phases);
+// 16-byte accesses when both pointers are 16-byte aligned.
+__global__ void k_copy_mapped(const double* __restrict__ src, double* __restrict__ dst, long long n, int vec2) {
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long st = (long long)gridDim.x * blockDim.x;
+  if (vec2) {
+    const double2* s2 = (const double2*)src;
+    double2* d2 = (double2*)dst;
+    for (long long i = i0; i < n / 2; i += st) d2[i] = s2[i];
+    if (i0 == 0 && (n & 1)) dst[n - 1] = src[n - 1];
+  } else {
+    for (long long i = i0; i < n; i += st) dst[i] = src[i];
+  }
+}
+
+cudaError_t launch_copy_mapped(cudaStream_t st, const double* src, double* dst, long long n) {
+  const int vec2 = (((uintptr_t)src | (uintptr_t)dst) & 15) == 0;
+  k_copy_mapped<<<152 * 8, 256, 0, st>>>(src, dst, n, vec2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_recover(const Geom& g, cudaStream_t st, const double* x, double* y, double* p) {
   const int blocks = (2 * g.m + 127) / 128;
   k_recover<<<blocks, 128, 0, st>>>(g, x, y, p);

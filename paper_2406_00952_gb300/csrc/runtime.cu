@@ -25,6 +25,14 @@ cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int 
 cudaError_t launch_rhs(const Geom& g, cudaStream_t st, int op, const double* gs, const double* fs, const double* y0,
                        double* b);
 cudaError_t launch_recover(const Geom& g, cudaStream_t st, const double* x, double* y, double* p);
+cudaError_t launch_copy_mapped(cudaStream_t st, const double* src, double* dst, long long n);
+
+// device address of page-locked host memory the device maps, or null (pageable memory)
+static const void* mapped_ptr(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
 cudaError_t launch_dot(const Batch& B, int sa, int sb);
 cudaError_t launch_reduce(const Batch& B, const int* off, int nper, int which, int step, double tol, int j,
                           int restart);
@@ -989,12 +997,24 @@ int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* o, const double* b_host
   double* b = p->host_io;
   double* x = p->host_io + 2 * p->g.mn;
   int rc = PCB_OK;
-  if (cudaMemcpyAsync(b, b_host, vb, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) rc = PCB_ERR_CUDA;
-  if (rc == PCB_OK) rc = solve_impl(p, o, b, x, info);
-  if ((rc == PCB_OK || rc == PCB_NOT_CONVERGED) &&
-      cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+  // page-locked buffers move with a copy kernel, pageable ones with the runtime's copy
+  const double* bmap = (const double*)mapped_ptr(b_host);
+  double* xmap = (double*)mapped_ptr(x_host);
+  if (bmap) {
+    if (launch_copy_mapped(p->stream, bmap, b, 2 * p->g.mn) != cudaSuccess) rc = PCB_ERR_CUDA;
+  } else if (cudaMemcpyAsync(b, b_host, vb, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) {
     rc = PCB_ERR_CUDA;
+  }
+  if (rc == PCB_OK) rc = solve_impl(p, o, b, x, info);
+  if (rc == PCB_OK || rc == PCB_NOT_CONVERGED) {
+    if (xmap) {
+      if (launch_copy_mapped(p->stream, x, xmap, 2 * p->g.mn) != cudaSuccess) rc = PCB_ERR_CUDA;
+    } else if (cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess) {
+      rc = PCB_ERR_CUDA;
+    }
+  }
   if (cudaStreamSynchronize(p->stream) != cudaSuccess && rc == PCB_OK) rc = PCB_ERR_CUDA;
+  if (info) info->launches += (bmap ? 1 : 0) + (xmap ? 1 : 0);
   return rc;
 }
 

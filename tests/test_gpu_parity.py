@@ -355,3 +355,24 @@ def test_minres_graph_replay_matches_direct_launches(P, precision):
     assert igr["launches"] == idir["launches"] == igr2["launches"]
     assert torch.equal(xd, xg) and torch.equal(xd, xg2)
     assert igr["relres"] <= 1e-10
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_host_buffers(P, pinned):
+    """Host-buffer solve: page-locked buffers move with the copy kernel, pageable ones with the
+    runtime copy; both give the device solve's result bit for bit."""
+    N, n, theta, gamma = 31, 32, 1.0, 1e-3
+    prob = ds.Problem(N, n, theta, gamma)
+    g = synth.random_target(N, n, seed=31); f = synth.manufactured_source(N, n)
+    b = ds.rhs_minres(prob, g, f)
+    gp = P.Problem(N, n, theta, gamma, precision="mixed")
+    xd, idev = gp.solve(dev(b), tol=1e-8)
+    if pinned:
+        bh = torch.from_numpy(b).pin_memory()
+        xh, ih = gp.solve_host(bh, torch.full_like(bh, float("nan")).pin_memory(), tol=1e-8)
+        xh = xh.numpy()
+    else:
+        xh, ih = gp.solve_host(b.copy(), np.full_like(b, np.nan), tol=1e-8)
+    assert np.array_equal(xh, xd.cpu().numpy())
+    assert ih["iterations"] == idev["iterations"]
+    assert ih["launches"] == idev["launches"] + (2 if pinned else 0)
