@@ -33,6 +33,20 @@ static const void* mapped_ptr(const void* host) {
   if (cudaPointerGetAttributes(&a, host) != cudaSuccess) { cudaGetLastError(); return nullptr; }
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
+
+// n doubles between a host buffer and device memory: the copy kernel when the host side is
+// page-locked and mapped, cudaMemcpyAsync otherwise.  *kernels counts the copy kernels launched.
+static cudaError_t copy_host(double* dst, const double* src, size_t n, bool to_device, cudaStream_t st,
+                             long long* kernels) {
+  const void* map = mapped_ptr(to_device ? (const void*)src : (const void*)dst);
+  if (map) {
+    if (kernels) ++*kernels;
+    return to_device ? launch_copy_mapped(st, (const double*)map, dst, (long long)n)
+                     : launch_copy_mapped(st, src, (double*)map, (long long)n);
+  }
+  return cudaMemcpyAsync(dst, src, n * sizeof(double), to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
+                         st);
+}
 cudaError_t launch_dot(const Batch& B, int sa, int sb);
 cudaError_t launch_reduce(const Batch& B, const int* off, int nper, int which, int step, double tol, int j,
                           int restart);
@@ -998,23 +1012,14 @@ int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* o, const double* b_host
   double* x = p->host_io + 2 * p->g.mn;
   int rc = PCB_OK;
   // page-locked buffers move with a copy kernel, pageable ones with the runtime's copy
-  const double* bmap = (const double*)mapped_ptr(b_host);
-  double* xmap = (double*)mapped_ptr(x_host);
-  if (bmap) {
-    if (launch_copy_mapped(p->stream, bmap, b, 2 * p->g.mn) != cudaSuccess) rc = PCB_ERR_CUDA;
-  } else if (cudaMemcpyAsync(b, b_host, vb, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) {
-    rc = PCB_ERR_CUDA;
-  }
+  long long copies = 0;
+  if (copy_host(b, b_host, 2 * p->g.mn, true, p->stream, &copies) != cudaSuccess) rc = PCB_ERR_CUDA;
   if (rc == PCB_OK) rc = solve_impl(p, o, b, x, info);
-  if (rc == PCB_OK || rc == PCB_NOT_CONVERGED) {
-    if (xmap) {
-      if (launch_copy_mapped(p->stream, x, xmap, 2 * p->g.mn) != cudaSuccess) rc = PCB_ERR_CUDA;
-    } else if (cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess) {
-      rc = PCB_ERR_CUDA;
-    }
-  }
+  if ((rc == PCB_OK || rc == PCB_NOT_CONVERGED) &&
+      copy_host(x_host, x, 2 * p->g.mn, false, p->stream, &copies) != cudaSuccess)
+    rc = PCB_ERR_CUDA;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess && rc == PCB_OK) rc = PCB_ERR_CUDA;
-  if (info) info->launches += (bmap ? 1 : 0) + (xmap ? 1 : 0);
+  if (info) info->launches += copies;
   return rc;
 }
 
@@ -1654,7 +1659,7 @@ int pcb_server_step(pcb_server* S, pcb_server_done* done, int max_done, int* n_d
       SrvSlot& s = G.slots[k];
       if (s.phase != PH_DONE) continue;
       const size_t vb = (size_t)2 * s.p->g.mn * sizeof(double);
-      if (cudaMemcpyAsync(s.req.x, s.x, vb, cudaMemcpyDeviceToHost, S->st) != cudaSuccess ||
+      if (copy_host(s.req.x, s.x, vb / sizeof(double), false, S->st, nullptr) != cudaSuccess ||
           cudaStreamSynchronize(S->st) != cudaSuccess)
         return PCB_ERR_CUDA;
       pcb_server_done r;
@@ -1699,7 +1704,7 @@ int pcb_server_step(pcb_server* S, pcb_server_done* done, int max_done, int* n_d
     s.p = p; s.req = r; s.b = p->host_io; s.x = p->host_io + nv; s.phase = PH_START; s.first = true;
     s.bytes = p->bytes;
     S->used += s.bytes;
-    if (cudaMemcpyAsync(s.b, r.rhs, nv * sizeof(double), cudaMemcpyHostToDevice, S->st) != cudaSuccess ||
+    if (copy_host(s.b, r.rhs, nv, true, S->st, nullptr) != cudaSuccess ||
         cudaMemsetAsync(s.x, 0, nv * sizeof(double), S->st) != cudaSuccess ||
         cudaMemcpyAsync(p->vec_mixed, s.b, nv * sizeof(double), cudaMemcpyDeviceToDevice, S->st) != cudaSuccess)
       return PCB_ERR_CUDA;
