@@ -339,15 +339,16 @@ cudaError_t launch_minres_wx(const Batch& B, int sy, int sw, int sw2, int sx) {
   k_minres_wx<<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, sy, sw, sw2, sx);
   return cudaGetLastError();
 }
-// basis-loop bound for Arnoldi index j (j < 0: per-instance indices, any up to the maximum)
-static int basis_bound(int j) {
+// basis-loop bound for Arnoldi index j (j < 0: per-instance indices, at most jmax when jmax >= 0)
+static int basis_bound(int j, int jmax) {
+  if (j < 0) j = jmax;
   const int need = j < 0 ? PCB_MAX_RESTART + 1 : j + 1;
   return need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : PCB_MAX_RESTART + 1;
 }
-cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw) {
+cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw, int jmax) {
 #define PCB_MULTIDOT(JB) \
   k_multidot<JB><<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, B.partial)
-  switch (basis_bound(j)) {
+  switch (basis_bound(j, jmax)) {
     case 2: PCB_MULTIDOT(2); break;
     case 4: PCB_MULTIDOT(4); break;
     case 8: PCB_MULTIDOT(8); break;
@@ -361,10 +362,10 @@ cudaError_t launch_reduce_multi(const Batch& B, int j, int pass) {
   k_reduce_multi<<<B.count, 256, 0, B.stream>>>(B.off_vec, B.count, B.active, B.partial, j, pass, B.Sc);
   return cudaGetLastError();
 }
-cudaError_t launch_multiaxpy(const Batch& B, int svbase, int j, int sw, int pass) {
+cudaError_t launch_multiaxpy(const Batch& B, int svbase, int j, int sw, int pass, int jmax) {
 #define PCB_MULTIAXPY(JB) \
   k_multiaxpy<JB><<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, pass)
-  switch (basis_bound(j)) {
+  switch (basis_bound(j, jmax)) {
     case 2: PCB_MULTIAXPY(2); break;
     case 4: PCB_MULTIAXPY(4); break;
     case 8: PCB_MULTIAXPY(8); break;

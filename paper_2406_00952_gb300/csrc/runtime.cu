@@ -52,9 +52,10 @@ cudaError_t launch_reduce(const Batch& B, const int* off, int nper, int which, i
                           int restart);
 cudaError_t launch_axpby(const Batch& B, int mode, int sx, int sy, int sz);
 cudaError_t launch_minres_wx(const Batch& B, int sy, int sw, int sw2, int sx);
-cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw);
+// j < 0: each instance at its own Arnoldi index (from Scal), all of them <= jmax when jmax >= 0
+cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw, int jmax = -1);
 cudaError_t launch_reduce_multi(const Batch& B, int j, int pass);
-cudaError_t launch_multiaxpy(const Batch& B, int svbase, int j, int sw, int pass);
+cudaError_t launch_multiaxpy(const Batch& B, int svbase, int j, int sw, int pass, int jmax = -1);
 cudaError_t launch_swap(const Batch& B, int a0, int b0, int a1, int b1, int a2, int b2);
 cudaError_t launch_setslot(const Batch& B, int dst, int base, int k, int per_j = 0);
 size_t mg_workspace_bytes(const Geom& g);
@@ -1535,9 +1536,11 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
         else if ((f & 1) || s.iters >= S->o.maxit) s.phase = PH_END;
       }
     } else {
+      int jmax = 0;      // largest Arnoldi index among the iterating requests: bounds the basis loops
       for (int k = 0; k < G.cap; ++k) {
         if (G.slots[k].phase != PH_ITER) continue;
         const int j = G.hSc[k].j;
+        jmax = std::max(jmax, j);
         const size_t nv = (size_t)2 * G.hG[k].mn;
         Slots& H = G.hS[k];
         H.v[SL_VJ] = H.v[SL_VBASE] + (size_t)j * nv;
@@ -1548,9 +1551,9 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
       if ((rc = apply_precond(p0, G.B, G.kind, prec, SL_VJ, SL_ZJ))) return rc;
       CK(launch_matvec(G.B, G.op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
       for (int pass = 0; pass < 2; ++pass) {
-        CK(launch_multidot(G.B, SL_VBASE, -1, SL_VJ1));
+        CK(launch_multidot(G.B, SL_VBASE, -1, SL_VJ1, jmax));
         CK(launch_reduce_multi(G.B, -1, pass));
-        CK(launch_multiaxpy(G.B, SL_VBASE, -1, SL_VJ1, pass));
+        CK(launch_multiaxpy(G.B, SL_VBASE, -1, SL_VJ1, pass, jmax));
       }
       CK(launch_dot(G.B, SL_VJ1, SL_VJ1));
       CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_GMRES_ARNOLDI, tol, -1, restart));
@@ -1566,9 +1569,13 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
       }
       if (any_end) {   // d = Z y for the requests whose cycle ends here
         CK(cudaStreamSynchronize(st));
-        for (int k = 0; k < G.cap; ++k) G.hAct[k] = ending[k];
+        int jend = 0;    // the update uses columns 0 .. j-1 of each ending request
+        for (int k = 0; k < G.cap; ++k) {
+          G.hAct[k] = ending[k];
+          if (ending[k]) jend = std::max(jend, G.hSc[k].j - 1);
+        }
         CK(cudaMemcpyAsync(G.dAct, G.hAct, sizeof(int) * G.cap, cudaMemcpyHostToDevice, st));
-        CK(launch_multiaxpy(G.B, SL_ZBASE, -1, SL_XI, -1));
+        CK(launch_multiaxpy(G.B, SL_ZBASE, -1, SL_XI, -1, jend));
         for (int k = 0; k < G.cap; ++k) if (ending[k]) G.slots[k].phase = PH_END;
       }
     }
