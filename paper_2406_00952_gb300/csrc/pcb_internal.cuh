@@ -149,15 +149,22 @@ struct Sel {
   }
 };
 
-// family code <-> bit of Batch::fam_*_set: 0 -> 0, P -> log2 P, P + 64 -> log2 P + 6
+// family code <-> bit of Batch::fam_*_set: 0 -> 0, P -> log2 P, + 6 with flag 64 (time-major
+// hand-off), + 12 with flag 128 (DCT-I lines); at most kFamilies bits
+constexpr int kFamilies = 24;
 __host__ __device__ inline int fam_index(int code) {
   if (!code) return 0;
   int b = 0;
   while ((2 << b) <= (code & 63)) ++b;
-  return b + ((code & 64) ? 6 : 0);
+  return b + ((code & 64) ? 6 : 0) + ((code & 128) ? 12 : 0);
 }
 __host__ __device__ inline int fam_code(int index) {
-  return index == 0 ? 0 : index < 6 ? (1 << index) : ((1 << (index - 6)) | 64);
+  if (index == 0) return 0;
+  const int ev = index >= 12 ? 128 : 0;
+  if (ev) index -= 12;
+  const int tm = index >= 6 ? 64 : 0;
+  if (tm) index -= 6;
+  return (1 << index) | tm | ev;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -181,7 +188,7 @@ struct Batch {
   int dst_q, time_q;      // register-FFT variant shared by every instance of the batch
   // FP32 kernel families: pipe_pd / pipe_pt > 0 is the family code of the pipelined DST / time
   // kernels (precond_pipe.cu) shared by every instance with work: the lanes per line P, plus 64
-  // when pass 2 hands the time pass contiguous time lines (n = 512).  0 means the kernels of
+  // when pass 2 hands the time pass contiguous time lines (n = 512), plus 128 for DCT-I lines.  0 means the kernels of
   // precond.cu for all, -1 a mix: one launch per family present, each selecting its instances by
   // fam_dst / fam_time (device arrays [count] of codes).  fam_*_set: bit fam_index(code).
   int pipe_pd, pipe_pt;

@@ -721,7 +721,7 @@ static cudaError_t dst_pass(const Batch& B, int stage, int in_slot, int out_slot
   if (B.pipe_pd > 0) return pipe_dst_pass(B, stage, in_slot, out_slot);
   Batch F = B;
   F.filt = B.fam_dst;
-  for (int b = 0; b < 12; ++b) {
+  for (int b = 0; b < kFamilies; ++b) {
     if (!(B.fam_dst_set >> b & 1)) continue;
     F.filt_want = fam_code(b);
     F.pipe_pd = F.filt_want;
@@ -736,7 +736,7 @@ static cudaError_t time_pass(const Batch& B, int kind) {
   if (B.pipe_pt > 0) return pipe_time_pass(B, kind);
   Batch F = B;
   F.filt = B.fam_time;
-  for (int b = 0; b < 12; ++b) {
+  for (int b = 0; b < kFamilies; ++b) {
     if (!(B.fam_time_set >> b & 1)) continue;
     F.filt_want = fam_code(b);
     F.pipe_pt = F.filt_want;

@@ -182,8 +182,9 @@ __device__ __forceinline__ int table_inst(const int* __restrict__ off, int count
 // columns t <= P/2.  For t = P - t' (1 <= t' < P/2) the stage-1 outputs are redundant:
 //     V[P-t'][k1] = -W_P^{-t'} V[t'][32-k1]  (k1 != 0),   V[P-t'][0] = -V[t'][0],
 // with V[t][k1] = W_M^{t k1} sum_q z_{t+Pq} W_32^{q k1}, so readers rebuild them from the stored
-// half (shared memory per group: 32 rows x (P/2 + 1) columns).  wP[k] = W_P^k.
-template <int P>
+// half (shared memory per group: 32 rows x (P/2 + 1) columns).  wP[k] = W_P^k.  EV: an even line
+// (z_{M-s} = z_s, the DCT-I extension) has the same relation with the opposite sign.
+template <int P, bool EV = false>
 __device__ __forceinline__ void fwd_odd(float2* x, int t, float2* __restrict__ scr, const float2* __restrict__ tw2,
                                         const float2* __restrict__ wP) {
   constexpr int CW = P / 2 + 1;
@@ -209,9 +210,10 @@ __device__ __forceinline__ void fwd_odd(float2* x, int t, float2* __restrict__ s
       } else {
         const float2 sv = scr[k1m * CW + (P - tt)];
         const float2 w = wP[tt];
+        const float sgn = EV ? 1.f : -1.f;
         float2 mlt;
-        mlt.x = z0 ? -1.f : -w.x;
-        mlt.y = z0 ? 0.f : -w.y;
+        mlt.x = z0 ? sgn : sgn * w.x;
+        mlt.y = z0 ? 0.f : sgn * w.y;
         x[a * P + tt] = cmul(sv, mlt);
       }
     }
@@ -260,16 +262,24 @@ __device__ __forceinline__ View view_of(const Geom& g, const Slots& s, int sel) 
   return v;
 }
 
+// values per spatial line of the pipelined passes: DST-I lines hold N = L - 1 interior values, the
+// DCT-I lines of the Neumann grid N = L + 1 nodes (L = 16 P, the line FFT has M = 2 L points)
+template <int P, bool EV>
+__host__ __device__ constexpr int line_values() { return EV ? 16 * P + 1 : 16 * P - 1; }
+
 template <typename TIn>
 __host__ __device__ constexpr int row_slot_elems(int N) {   // per half: N values + both alignment tails
   return ((N + 32 / (int)sizeof(TIn) + 16 / (int)sizeof(TIn) - 1) / (16 / (int)sizeof(TIn))) * (16 / (int)sizeof(TIn));
 }
 
-template <typename TIn, typename TOut, int P>
+// EV: the DCT-I pair of the Neumann route instead (lines of N = L + 1 nodes, even extension);
+// inv = 1 selects the inverse of the pair (end values scaled by sqrt 2 on input), inv = 0 the
+// forward one (end modes scaled by sqrt 1/2 on output).
+template <typename TIn, typename TOut, int P, bool EV>
 __global__ void __launch_bounds__(kThreads, 2)
     k_dst_rows(const Geom* __restrict__ G, const Slots* __restrict__ S, const int* __restrict__ off, int count,
-               Sel sel, int in_sel, int out_sel, int tot) {
-  constexpr int M = 32 * P, L = 16 * P, N = L - 1, LPB = kThreads / P;
+               Sel sel, int in_sel, int out_sel, int tot, int inv) {
+  constexpr int M = 32 * P, L = 16 * P, N = line_values<P, EV>(), LPB = kThreads / P;
   constexpr int EPC = 16 / (int)sizeof(TIn);              // elements per 16-byte chunk
   constexpr int SLOT = row_slot_elems<TIn>(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -340,32 +350,56 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int o1 = (int)(((uintptr_t)(in + v.hs) & 15) / sizeof(TIn));
       const TIn* s0 = slot + (lv ? grp : 0) * 2 * SLOT + o0;
       const TIn* s1 = slot + ((lv ? grp : 0) * 2 + 1) * SLOT + o1;
-      // gather the odd extension: z_s = x_{s-1} (1 <= s <= N), -x_{M-s-1} (L < s < M), 0 else
+      // gather the odd extension: z_s = x_{s-1} (1 <= s <= N), -x_{M-s-1} (L < s < M), 0 else;
+      // EV: the even one, z_s = x_s (s <= L), x_{M-s} (L < s < M)
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int s = t + P * q;
-        const bool ok = lv && (q < 16 ? s > 0 : s > L);
-        const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
-        float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
-        if (!ok) v = make_float2(0.f, 0.f);
-        if (q >= 16) { v.x = -v.x; v.y = -v.y; }
-        x[q] = v;
+        if constexpr (EV) {
+          const int idx = q < 16 ? s : M - s;
+          float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
+          if (!lv) v = make_float2(0.f, 0.f);
+          if (inv && (s == 0 || s == L)) v = cscale(v, 1.41421356237309515f);
+          x[q] = v;
+        } else {
+          const bool ok = lv && (q < 16 ? s > 0 : s > L);
+          const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
+          float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
+          if (!ok) v = make_float2(0.f, 0.f);
+          if (q >= 16) { v.x = -v.x; v.y = -v.y; }
+          x[q] = v;
+        }
       }
     }
     __syncwarp();
     issue(nxt);                          // the next line's copy overlaps this line's transform
     if (cur.nl > 0) {
-      fwd_odd<P>(x, t, scr, tw2, wP);
+      fwd_odd<P, EV>(x, t, scr, tw2, wP);
       if (lv) {
         const View v = view_of(G[cur.inst], S[cur.inst], out_sel);
         TOut* __restrict__ d = (TOut*)v.base + line_off(v, cur.line0 + grp);
+        if constexpr (EV) {
+          // modes k = t + P j, j <= 16 (k = L only at lane 0); the real transform of each half
+          // stays in its own component
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int p = t + P * j;
-          const float2 Y = x[Two<P>::outreg(j)];
-          if (p >= 1) {
-            d[p - 1] = from_f32<TOut>(-Y.y * sc);
-            d[v.hs + p - 1] = from_f32<TOut>(Y.x * sc);
+          for (int j = 0; j <= 16; ++j) {
+            const int k = t + P * j;
+            if (k <= L) {
+              const float2 Y = x[Two<P>::outreg(j)];
+              const float f = (!inv && (k == 0 || k == L)) ? sc * 0.707106781186547524f : sc;
+              d[k] = from_f32<TOut>(Y.x * f);
+              d[v.hs + k] = from_f32<TOut>(Y.y * f);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int p = t + P * j;
+            const float2 Y = x[Two<P>::outreg(j)];
+            if (p >= 1) {
+              d[p - 1] = from_f32<TOut>(-Y.y * sc);
+              d[v.hs + p - 1] = from_f32<TOut>(Y.x * sc);
+            }
           }
         }
       }
@@ -395,11 +429,11 @@ __host__ __device__ constexpr int rowsT_region() {   // complex elements per war
 // rows r of LPB consecutive time steps, and the result goes to the time-major layout of scratch
 // buffer 1, value (half h, spatial point r N + p, time t) at h n m + (r N + p) n + t, so that the
 // time pass reads contiguous time lines.
-template <typename TIn, int P, int MODE>
+template <typename TIn, int P, int MODE, bool EV>
 __global__ void __launch_bounds__(kThreads, 2)
     k_dst_rowsT(const Geom* __restrict__ G, const Slots* __restrict__ S, const int* __restrict__ off, int count,
-                Sel sel, int in_sel, int out_sel, int tot) {
-  constexpr int M = 32 * P, L = 16 * P, N = L - 1, LPB = kThreads / P, A = 32 / P;
+                Sel sel, int in_sel, int out_sel, int tot, int inv) {
+  constexpr int M = 32 * P, L = 16 * P, N = line_values<P, EV>(), LPB = kThreads / P, A = 32 / P;
   constexpr int NBT = (N + LPB - 1) / LPB;       // tiles per time step
   constexpr int EPC = 16 / (int)sizeof(TIn);
   constexpr int SLOT = row_slot_elems<TIn>(N);
@@ -493,7 +527,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       // FP64 input: each value is read and converted once; the mirrored half (q >= 16) comes from
       // the lane holding it: -x_{M-s-1} with s = t + P q is lane P - t's value at q' = 31 - q
-      // (lane 0: its own value at 32 - q)
+      // (lane 0: its own value at 32 - q).  EV (even extension, x_{M-s} at s > L): the same lanes
+      // and registers without the sign; lane 0 at q = 16 holds x_L, read from the slot.
       constexpr bool kShuffleMirror = sizeof(TIn) == 8;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
@@ -503,28 +538,57 @@ __global__ void __launch_bounds__(kThreads, 2)
           float2 v;
           v.x = __shfl_sync(0xffffffffu, a.x, (P - t) & (P - 1), P);
           v.y = __shfl_sync(0xffffffffu, a.y, (P - t) & (P - 1), P);
-          if (t == 0) v = q > 16 ? x[32 - q] : make_float2(0.f, 0.f);
-          x[q] = make_float2(-v.x, -v.y);
+          if constexpr (EV) {
+            if (t == 0) {
+              v = q > 16 ? x[32 - q] : make_float2(to_f32(s0[L]), to_f32(s1[L]));
+              if (q == 16 && !lv) v = make_float2(0.f, 0.f);
+              if (q == 16 && inv) v = cscale(v, 1.41421356237309515f);
+            }
+            x[q] = v;
+          } else {
+            if (t == 0) v = q > 16 ? x[32 - q] : make_float2(0.f, 0.f);
+            x[q] = make_float2(-v.x, -v.y);
+          }
           continue;
         }
-        const bool ok = lv && (q < 16 ? s > 0 : s > L);
-        const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
-        float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
-        if (!ok) v = make_float2(0.f, 0.f);
-        if (q >= 16) { v.x = -v.x; v.y = -v.y; }
-        x[q] = v;
+        if constexpr (EV) {
+          const int idx = q < 16 ? s : M - s;
+          float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
+          if (!lv) v = make_float2(0.f, 0.f);
+          if (inv && (s == 0 || s == L)) v = cscale(v, 1.41421356237309515f);
+          x[q] = v;
+        } else {
+          const bool ok = lv && (q < 16 ? s > 0 : s > L);
+          const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
+          float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
+          if (!ok) v = make_float2(0.f, 0.f);
+          if (q >= 16) { v.x = -v.x; v.y = -v.y; }
+          x[q] = v;
+        }
       }
     }
     __syncwarp();
     issue(nxt);
     if (on) {
-      fwd_odd<P>(x, t, scr, tw2, wP);
+      fwd_odd<P, EV>(x, t, scr, tw2, wP);
       __syncwarp();                                // exchange reads done: park the results
+      if constexpr (EV) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int p = t + P * j;
-        const float2 Y = x[Two<P>::outreg(j)];
-        if (p >= 1) region[grp * N + p - 1] = make_float2(-Y.y * sc, Y.x * sc);
+        for (int j = 0; j <= 16; ++j) {
+          const int k = t + P * j;
+          if (k <= L) {
+            const float2 Y = x[Two<P>::outreg(j)];
+            const float f = (!inv && (k == 0 || k == L)) ? sc * 0.707106781186547524f : sc;
+            region[grp * N + k] = cscale(Y, f);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int p = t + P * j;
+          const float2 Y = x[Two<P>::outreg(j)];
+          if (p >= 1) region[grp * N + p - 1] = make_float2(-Y.y * sc, Y.x * sc);
+        }
       }
     }
     __syncthreads();
@@ -925,14 +989,14 @@ constexpr int kNsTime = 2;
 
 template <int P>
 size_t dst_tables_smem() { return (size_t)(32 * P + P + kWarps * odd_scratch_per_warp<P>()) * sizeof(float2); }
-template <typename TIn, int P>
+template <typename TIn, int P, bool EV>
 size_t dst_rows_smem() {
-  return dst_tables_smem<P>() + (size_t)kThreads / P * 2 * row_slot_elems<TIn>(16 * P - 1) * sizeof(TIn);
+  return dst_tables_smem<P>() + (size_t)kThreads / P * 2 * row_slot_elems<TIn>(line_values<P, EV>()) * sizeof(TIn);
 }
-template <typename TIn, int P>
+template <typename TIn, int P, bool EV>
 size_t dst_rowsT_smem() {
   return (size_t)(32 * P + P + kWarps * rowsT_region<P>()) * sizeof(float2) +
-         (size_t)kThreads / P * 2 * row_slot_elems<TIn>(16 * P - 1) * sizeof(TIn);
+         (size_t)kThreads / P * 2 * row_slot_elems<TIn>(line_values<P, EV>()) * sizeof(TIn);
 }
 template <int P>
 size_t time_smem() {
@@ -969,22 +1033,23 @@ cudaError_t launch_persistent(K kern, size_t smem, int tot, int& resident, cudaS
   return cudaGetLastError();
 }
 
-template <typename TIn, typename TOut, int P>
-cudaError_t launch_rows(const Batch& B, int in_sel, int out_sel) {
+template <typename TIn, typename TOut, int P, bool EV>
+cudaError_t launch_rows(const Batch& B, int in_sel, int out_sel, int inv) {
   static int resident = 0;
-  return launch_persistent(k_dst_rows<TIn, TOut, P>, dst_rows_smem<TIn, P>(), B.tot_dst_i[1], resident, B.stream, B.G,
-                           (const Slots*)B.S, B.off_dst_i[1], B.count, B.sel(), in_sel, out_sel, B.tot_dst_i[1]);
+  return launch_persistent(k_dst_rows<TIn, TOut, P, EV>, dst_rows_smem<TIn, P, EV>(), B.tot_dst_i[1], resident,
+                           B.stream, B.G, (const Slots*)B.S, B.off_dst_i[1], B.count, B.sel(), in_sel, out_sel,
+                           B.tot_dst_i[1], inv);
 }
 
-template <typename TIn, int P, int MODE>
-cudaError_t launch_rowsT(const Batch& B, int in_sel, int out_sel) {
+template <typename TIn, int P, int MODE, bool EV>
+cudaError_t launch_rowsT(const Batch& B, int in_sel, int out_sel, int inv) {
   static int resident = 0;
   // MODE 0 tiles: (time step, LPB rows) -> dst_j offsets; MODE 1 tiles: (row, LPB time steps),
   // as many as the contiguous-line tiles -> dst_i offsets
   const int* off = MODE == 0 ? B.off_dst_j[1] : B.off_dst_i[1];
   const int tot = MODE == 0 ? B.tot_dst_j[1] : B.tot_dst_i[1];
-  return launch_persistent(k_dst_rowsT<TIn, P, MODE>, dst_rowsT_smem<TIn, P>(), tot, resident, B.stream, B.G,
-                           (const Slots*)B.S, off, B.count, B.sel(), in_sel, out_sel, tot);
+  return launch_persistent(k_dst_rowsT<TIn, P, MODE, EV>, dst_rowsT_smem<TIn, P, EV>(), tot, resident, B.stream,
+                           B.G, (const Slots*)B.S, off, B.count, B.sel(), in_sel, out_sel, tot, inv);
 }
 
 template <int P>
@@ -1004,28 +1069,33 @@ cudaError_t launch_time(const Batch& B, int kind, bool time_major = false) {
 
 // pass `stage` (1, 2, 4, 5) of the FP32 apply; scratch buffers: -1 = buffer 0, -2 = buffer 1.
 // time_major: pass 2 writes time-major lines to buffer 1 and the time pass writes buffer 0 back
-// in the row layout, so pass 4 finds its input where it would otherwise be.
-template <int P>
+// in the row layout, so pass 4 finds its input where it would otherwise be.  EV: the Neumann
+// route's DCT-I pair, forward in passes 1-2 and inverse in passes 4-5.
+template <int P, bool EV>
 cudaError_t dst_pass_p(const Batch& B, int stage, int in_slot, int out_slot, bool time_major) {
+  const int inv = stage >= 4;
   switch (stage) {
-    case 1: return launch_rowsT<double, P, 0>(B, in_slot, -1);
-    case 2: return time_major ? launch_rowsT<float, P, 1>(B, -1, -2) : launch_rows<float, float, P>(B, -1, -1);
-    case 4: return launch_rowsT<float, P, 0>(B, -1, -2);
-    default: return launch_rows<float, double, P>(B, -2, out_slot);
+    case 1: return launch_rowsT<double, P, 0, EV>(B, in_slot, -1, inv);
+    case 2:
+      return time_major ? launch_rowsT<float, P, 1, EV>(B, -1, -2, inv) : launch_rows<float, float, P, EV>(B, -1, -1, inv);
+    case 4: return launch_rowsT<float, P, 0, EV>(B, -1, -2, inv);
+    default: return launch_rows<float, double, P, EV>(B, -2, out_slot, inv);
   }
 }
 
 }  // namespace
 
 // P of the pipelined passes for an instance (0: not eligible): DST lines of 2L = 32 P points,
-// time lines of n = 32 P points, P a power of two in [2, 32]; the constant-coefficient route only.
+// time lines of n = 32 P points, P a power of two in [2, 32] (Neumann's DCT-I lines: P >= 8);
+// the constant-coefficient route only.
 int pipe_time_p(const Geom& g);
 int pipe_dst_p(const Geom& g) {
-  // the padded scratch layout needs the pipelined time pass; the DCT-I (Neumann) runs in precond.cu
-  if (g.var_a || g.bc == PCB_BC_NEUMANN || !pipe_time_p(g)) return 0;
+  // the padded scratch layout needs the pipelined time pass
+  if (g.var_a || !pipe_time_p(g)) return 0;
   const int M = 2 * g.L;
   if (M % 32) return 0;
   const int P = M / 32;
+  if (g.bc == PCB_BC_NEUMANN && P < 8) return 0;
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
 int pipe_time_p(const Geom& g) {
@@ -1033,10 +1103,11 @@ int pipe_time_p(const Geom& g) {
   const int P = g.n / 32;
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
-// family codes: P, plus 64 when pass 2 writes time-major lines for the n = 512 time pass
+// family codes: P, plus 64 when pass 2 writes time-major lines for the n = 512 time pass, plus
+// 128 for the DCT-I lines of the Neumann route
 int pipe_dst_code(const Geom& g) {
   const int p = pipe_dst_p(g);
-  return p ? (p | (g.n == 512 ? 64 : 0)) : 0;
+  return p ? (p | (g.n == 512 ? 64 : 0) | (g.bc == PCB_BC_NEUMANN ? 128 : 0)) : 0;
 }
 int pipe_time_code(const Geom& g) {
   const int p = pipe_time_p(g);
@@ -1052,12 +1123,20 @@ cudaError_t pipe_upload_constants() { return upload_w96(); }
 // DST pass `stage` of the FP32 apply; B.pipe_pd is the P shared by the instances it covers.
 cudaError_t pipe_dst_pass(const Batch& B, int stage, int in_slot, int out_slot) {
   const bool tm = B.pipe_pd & 64;
+  if (B.pipe_pd & 128) {
+    switch (B.pipe_pd & 63) {
+      case 8: return dst_pass_p<8, true>(B, stage, in_slot, out_slot, tm);
+      case 16: return dst_pass_p<16, true>(B, stage, in_slot, out_slot, tm);
+      case 32: return dst_pass_p<32, true>(B, stage, in_slot, out_slot, tm);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (B.pipe_pd & 63) {
-    case 2: return dst_pass_p<2>(B, stage, in_slot, out_slot, tm);
-    case 4: return dst_pass_p<4>(B, stage, in_slot, out_slot, tm);
-    case 8: return dst_pass_p<8>(B, stage, in_slot, out_slot, tm);
-    case 16: return dst_pass_p<16>(B, stage, in_slot, out_slot, tm);
-    case 32: return dst_pass_p<32>(B, stage, in_slot, out_slot, tm);
+    case 2: return dst_pass_p<2, false>(B, stage, in_slot, out_slot, tm);
+    case 4: return dst_pass_p<4, false>(B, stage, in_slot, out_slot, tm);
+    case 8: return dst_pass_p<8, false>(B, stage, in_slot, out_slot, tm);
+    case 16: return dst_pass_p<16, false>(B, stage, in_slot, out_slot, tm);
+    case 32: return dst_pass_p<32, false>(B, stage, in_slot, out_slot, tm);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -37,11 +37,15 @@ def dev(x):
 
 
 # (N, n, theta, gamma, a, zeta): N - 1 = 2^a 3^b covers the register-FFT variants Q = 1 .. 32,
-# radix-3 lines (N = 25, 49, 97), the smallest grid and the largest (N = 513, a length-1024 line)
+# radix-3 lines (N = 25, 49, 97), the smallest grid and the largest (N = 513, a length-1024 line);
+# FP32 applies with 2(N-1) = 32 P (P = 8, 16, 32) and n = 64 ... 512 run the pipelined kernels
 SHAPES = [(3, 2, 1.0, 1.0, 1.0, PI), (5, 4, 0.5, 1e-2, 1e-3, PI), (17, 16, 0.5, 1e-2, 1e-3, PI),
           (33, 32, 1.0, 1e-4, 0.3, PI), (49, 8, 0.5, 1e-6, 1.0, PI), (65, 64, 0.5, 1e-3, 1e-3, 0.4),
           (97, 128, 1.0, 1e-2, 2.0, PI), (129, 512, 0.5, 1e-2, 1e-3, PI), (257, 32, 0.5, 1e-2, 1e-3, PI),
-          (513, 4, 0.5, 1e-2, 1e-3, PI), (25, 1024, 0.5, 1e-2, 1e-3, 0.0), (7, 256, 1.0, 1e-5, 1.0, PI)]
+          (513, 4, 0.5, 1e-2, 1e-3, PI), (25, 1024, 0.5, 1e-2, 1e-3, 0.0), (7, 256, 1.0, 1e-5, 1.0, PI),
+          # the pipelined DCT-I passes (2(N-1) = 32 P, P = 8, 16, 32; n = 512 with the time-major hand-off)
+          (257, 256, 0.5, 1e-2, 1e-3, PI), (513, 64, 1.0, 1e-4, 0.5, PI), (257, 512, 0.5, 1e-3, 1e-3, PI),
+          (129, 128, 1.0, 1e-6, 2.0, PI)]
 
 
 def _prob(s):
