@@ -651,10 +651,12 @@ __device__ __forceinline__ float2 pointwise(int kind, float2 Cr, float2 Cq, floa
 
 // ------------------------------------------------------------------------------------------
 // Time pass: forward DFT of (half0 + i half1) * exp(-i pi t/n), pointwise solve on the frequency
-// pairs (r, n-1-r), inverse DFT, unscale.  In place on the FP32 scratch; n = 32 P.
+// pairs (r, n-1-r), inverse DFT, unscale.  In place on the FP32 scratch; n = 32 P.  Each group
+// of P lanes exchanges through its own line's tile row (the line sits in registers meanwhile),
+// so a block holds the tables and NS tile stages only: two blocks per SM.
 // ------------------------------------------------------------------------------------------
 template <int P, int NS>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_time_pipe(const Geom* __restrict__ G, const int* __restrict__ off, int count, Sel sel, int kind, int tot) {
   constexpr int n = 32 * P, LPB = kThreads / P;
   constexpr int PITCH = pitch_for<P>(n);
@@ -662,8 +664,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float2* tw2 = (float2*)smem_raw;
   float2* tw3 = tw2 + n;
   float2* pre = tw3 + n;
-  float2* scr_all = pre + n;
-  float2* stages = scr_all + kWarps * kScrWarp;
+  float2* stages = pre + n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   const Geom& g0 = G[table_inst(off, count, sel)];
@@ -692,7 +693,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     issue(blockIdx.x + s * gridDim.x, s);
     cp_commit();
   }
-  float2* scr = scr_all + warp * kScrWarp + (lane / P) * (32 * P + P);
   const int t = lane % P;
   const int lw = warp * (32 / P) + lane / P;
   const float scale = 1.0f / (float)n;
@@ -712,7 +712,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       float2 x[32];
 #pragma unroll
       for (int q = 0; q < 32; ++q) x[q] = cmul(ln[t + P * q], pre[t + P * q]);
-      fwd2<P>(x, t, scr, tw2);
+      __syncwarp();                          // the group's row is free: it serves as exchange space
+      fwd2<P>(x, t, ln, tw2);
       // pointwise solve at r = t + P j; the partner n-1-r is lane P-1-t, register 31-j
       const long long col = min((long long)(c0 + lw), g.mp - 1);   // padded columns compute junk
       const int jj = (int)(col / g.lr), ii = min((int)(col - (long long)jj * g.lr), g.N - 1);
@@ -738,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           x[Two<P>::outreg(j)] = pointwise(kind, x[Two<P>::outreg(j)], x[Two<P>::outreg(j)], __ldg(&mu[t + P * j]), c,
                                            a2, alpha);
       }
-      inv2<P>(x, t, scr, tw3);
+      inv2<P>(x, t, ln, tw3);
 #pragma unroll
       for (int q = 0; q < 32; ++q) ln[t + P * q] = cscale(cmulc(x[pos<32>(q)], pre[t + P * q]), scale);
     }
@@ -986,6 +987,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // host side
 // ------------------------------------------------------------------------------------------
 constexpr int kNsTime = 2;
+constexpr int kNsTimePipe = 1;     // k_time_pipe: the second resident block hides the tile loads
 
 template <int P>
 size_t dst_tables_smem() { return (size_t)(32 * P + P + kWarps * odd_scratch_per_warp<P>()) * sizeof(float2); }
@@ -1000,8 +1002,8 @@ size_t dst_rowsT_smem() {
 }
 template <int P>
 size_t time_smem() {
-  return (size_t)(3 * 32 * P + kWarps * kScrWarp) * sizeof(float2) +
-         (size_t)kNsTime * (kThreads / P) * pitch_for<P>(32 * P) * sizeof(float2);
+  return (size_t)(3 * 32 * P) * sizeof(float2) +
+         (size_t)kNsTimePipe * (kThreads / P) * pitch_for<P>(32 * P) * sizeof(float2);
 }
 size_t time512_smem() { return (size_t)(3 * 512 + 32 + kNsTime * kWarps * pitch_for<32>(512)) * sizeof(float2); }
 
@@ -1063,7 +1065,7 @@ cudaError_t launch_time(const Batch& B, int kind, bool time_major = false) {
     return launch_persistent(k_time512<kNsTime, 0>, time512_smem(), B.tot_time[1], resident512[0], B.stream, B.G,
                              B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
   }
-  return launch_persistent(k_time_pipe<P, kNsTime>, time_smem<P>(), B.tot_time[1], resident, B.stream, B.G,
+  return launch_persistent(k_time_pipe<P, kNsTimePipe>, time_smem<P>(), B.tot_time[1], resident, B.stream, B.G,
                            B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
 }
 
