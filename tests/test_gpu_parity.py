@@ -41,7 +41,8 @@ def dev(x):
 SHAPES = [(1, 2, 1.0, 1.0), (2, 4, 0.5, 1e-2), (15, 16, 1.0, 1e-2), (31, 8, 0.5, 1e-4), (47, 32, 1.0, 1e-6),
           (63, 64, 0.5, 1e-2), (95, 128, 0.75, 1e-3), (127, 4, 1.0, 1e-1), (191, 32, 0.5, 1e-5),
           (511, 4, 1.0, 1e-2), (3, 1024, 0.5, 1e-3), (383, 2, 1.0, 1e-6), (5, 512, 1.0, 1e-2),
-          (255, 16, 1.0, 1e-2), (31, 512, 0.5, 1e-3), (15, 256, 1.0, 1e-4), (63, 512, 1.0, 1e-3)]
+          (255, 16, 1.0, 1e-2), (31, 512, 0.5, 1e-3), (15, 256, 1.0, 1e-4), (63, 512, 1.0, 1e-3),
+          (255, 256, 0.5, 1e-2), (127, 1024, 1.0, 1e-3)]
 ORACLE = {"abs_ps": pc.apply_abs_ps_inv, "ps": pc.apply_ps_inv, "pms": pc.apply_pms_inv}
 
 
