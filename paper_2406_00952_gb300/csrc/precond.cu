@@ -11,7 +11,9 @@
 // vector ride as real and imaginary parts of one complex line, and the DST-I of order L = N+1
 // comes from the length-2L FFT of the odd extension (Y_p = -2i * DST(x)_p).
 // The time pass packs the two halves the same way; for zeta = pi the F-slot r of a real series
-// and slot n-1-r are complex conjugates, which separates the halves per frequency pair.
+// and slot n-1-r are complex conjugates, which separates the halves per frequency pair (other
+// zeta: time_body_general, two complex lines per point).  Neumann problems (Example 3) take the
+// scaled DCT-I pair of order L = N-1 from the even extension in the same spatial passes.
 //
 // Each pass stages a tile of lines through padded shared memory (coalesced global access in both
 // directions); each line is transformed by a group of P <= 32 lanes holding Q values each

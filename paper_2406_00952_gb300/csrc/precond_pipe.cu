@@ -1,8 +1,8 @@
 // Pipelined FP32 preconditioner passes for power-of-two line lengths (paper Sec. 3.5).
 //
 // The same five passes as precond.cu: DST-I along x1, DST-I along x2, time DFT + pointwise
-// solve + inverse time DFT, DST-I along x2, DST-I along x1.  They are organised for this GPU as
-// follows.
+// solve + inverse time DFT, DST-I along x2, DST-I along x1 (for Neumann problems the DCT-I pair
+// of the even extension, template flag EV).  They are organised for this GPU as follows.
 //   * A line of length M = 32 P (2 <= P <= 32) is transformed by P lanes holding 32 values each,
 //     as a two-stage FFT.  With s = t + P q and k = k1 + 32 k2,
 //         X[k1 + 32 k2] = sum_t W_P^{t k2} W_M^{t k1} sum_q x[t + P q] W_32^{q k1},
