@@ -86,9 +86,25 @@ __device__ __forceinline__ double f2d(float f) {
 }
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(double v) { return d2f(v); }
+// The gather of pass 1 converts every kF2FEvery-th register of a line with the conversion
+// instruction and the rest with integer operations: both round to nearest even, and the mix
+// shares the work between the FP64 pipe and the integer pipe.
+constexpr int kF2FEvery = 2;
+__device__ __forceinline__ float to_f32_at(float v, int) { return v; }
+__device__ __forceinline__ float to_f32_at(double v, int q) {
+  return (kF2FEvery > 0 && q % kF2FEvery == kF2FEvery - 1) ? __double2float_rn(v) : d2f(v);
+}
 template <typename T> __device__ __forceinline__ T from_f32(float v);
 template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
 template <> __device__ __forceinline__ double from_f32<double>(float v) { return f2d(v); }
+// pass 5's FP64 results: every kF2DEvery-th register through the conversion instruction
+constexpr int kF2DEvery = 2;
+template <typename T> __device__ __forceinline__ T from_f32_at(float v, int j) {
+  if constexpr (sizeof(T) == 8) {
+    if (kF2DEvery > 0 && j % kF2DEvery == kF2DEvery - 1) return (double)v;
+  }
+  return from_f32<T>(v);
+}
 
 // ------------------------------------------------------------------------------------------
 // two-stage line FFT, M = 32 P
@@ -387,8 +403,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (k <= L) {
               const float2 Y = x[Two<P>::outreg(j)];
               const float f = (!inv && (k == 0 || k == L)) ? sc * 0.707106781186547524f : sc;
-              d[k] = from_f32<TOut>(Y.x * f);
-              d[v.hs + k] = from_f32<TOut>(Y.y * f);
+              d[k] = from_f32_at<TOut>(Y.x * f, j);
+              d[v.hs + k] = from_f32_at<TOut>(Y.y * f, j);
             }
           }
         } else {
@@ -397,8 +413,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int p = t + P * j;
             const float2 Y = x[Two<P>::outreg(j)];
             if (p >= 1) {
-              d[p - 1] = from_f32<TOut>(-Y.y * sc);
-              d[v.hs + p - 1] = from_f32<TOut>(Y.x * sc);
+              d[p - 1] = from_f32_at<TOut>(-Y.y * sc, j);
+              d[v.hs + p - 1] = from_f32_at<TOut>(Y.x * sc, j);
             }
           }
         }
@@ -553,14 +569,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         if constexpr (EV) {
           const int idx = q < 16 ? s : M - s;
-          float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
+          float2 v = make_float2(to_f32_at(s0[idx], q), to_f32_at(s1[idx], q));
           if (!lv) v = make_float2(0.f, 0.f);
           if (inv && (s == 0 || s == L)) v = cscale(v, 1.41421356237309515f);
           x[q] = v;
         } else {
           const bool ok = lv && (q < 16 ? s > 0 : s > L);
           const int idx = q < 16 ? (s > 0 ? s - 1 : 0) : (s > L ? M - s - 1 : 0);
-          float2 v = make_float2(to_f32(s0[idx]), to_f32(s1[idx]));
+          float2 v = make_float2(to_f32_at(s0[idx], q), to_f32_at(s1[idx], q));
           if (!ok) v = make_float2(0.f, 0.f);
           if (q >= 16) { v.x = -v.x; v.y = -v.y; }
           x[q] = v;
