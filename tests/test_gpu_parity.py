@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on seeded inputs.
 
-Tolerances (derived from the arithmetic, see DESIGN.md):
+Tolerances (derived from the arithmetic):
   FP64 transforms / operators : relative 2-norm error <= 1e-12 (rounding of O(log size) stages)
   FP32 preconditioner         : relative 2-norm error <= 2e-6  (FP32 unit roundoff 6e-8 times the
                                 ~30 transform stages and the pointwise solve)
