@@ -317,8 +317,8 @@ __global__ void __launch_bounds__(256, 2) k_dst_any(const Geom* __restrict__ G, 
 // other choice of Sec. 2).  Slot r of the DFT of x_t exp(-i zeta t/n) has frequency
 // psi_r = -(zeta + 2 pi r)/n; unlike zeta = pi, the transform of a real series has no conjugate
 // partner slot, so each half runs as its own complex line: forward DFT of v_h(t) exp(-i zeta t/n),
-// the per-slot solve on (V_1, V_2) at each r, inverse DFT, unscale, real part (reading A12:
-// the operator applied to real vectors is Re(P^-1)).
+// the per-slot solve on (V_1, V_2) at each r, inverse DFT, unscale, real part (the operator
+// applied to real vectors is Re(P^-1), symmetric positive definite for |P_S| and P_MS).
 // ------------------------------------------------------------------------------------------
 template <typename R, int Q>
 __device__ __forceinline__ void time_body_general(const Geom& g, int lb, int kind) {

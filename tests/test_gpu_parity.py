@@ -88,7 +88,7 @@ ZETA_SHAPES = [(15, 16, 1.0, 1e-2, 0.0), (31, 64, 0.5, 1e-3, 0.4), (63, 32, 1.0,
 @pytest.mark.parametrize("kind", ["abs_ps", "ps", "pms"])
 def test_precond_parity_general_zeta(P, shape, kind):
     # omega = exp(i zeta) other than -1 (zeta = 0: circulant): two complex time lines per point,
-    # the real part of the complex operator (reading A12)
+    # the real part of the complex operator
     N, n, theta, gamma, zeta = shape
     prob = ds.Problem(N, n, theta, gamma, zeta=zeta)
     v = synth.random_vector(2 * prob.m * n, seed=500 + N + n)
