@@ -153,9 +153,10 @@ typedef struct {
                           /* recorded on the problem's stream (fills the *_ms fields of info)   */
   double inner_floor;     /* mixed precision: an inner solve stops once its residual estimate is */
                           /* below max(tol*||b||/||r||, inner_floor); <= 0 => no floor          */
-  int no_graphs;          /* != 0: launch every MINRES iteration's kernels directly.  0: capture */
-                          /* one iteration's launches into a CUDA graph once per solve setting   */
-                          /* and replay it (not with profile != 0 or a variable a(x))           */
+  int no_graphs;          /* != 0: launch every iteration's kernels directly.  0: capture one    */
+                          /* MINRES iteration, or one FGMRES Arnoldi step per index, into CUDA   */
+                          /* graphs once per solve setting and replay them (not with            */
+                          /* profile != 0 or a variable a(x))                                   */
 } pcb_solve_opts;
 
 typedef struct {

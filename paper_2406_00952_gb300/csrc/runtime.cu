@@ -126,6 +126,11 @@ struct pcb_problem {
   cudaGraphExec_t git = nullptr;
   int git_kind = -1, git_prec = -1, git_sx = -1;
   long long git_launches = 0;
+  // CUDA graphs of the FGMRES Arnoldi steps, one per index j, for one (preconditioner, precision,
+  // restart) setting
+  cudaGraphExec_t garn[PCB_MAX_RESTART] = {};
+  long long garn_launches[PCB_MAX_RESTART] = {};
+  int garn_kind = -1, garn_prec = -1, garn_restart = -1;
   double* dtol = nullptr;         // device copy of the running tolerance read by the scalar steps
   // per-solve counters and optional event profiling
   long long launches = 0;
@@ -330,6 +335,7 @@ void pcb_destroy(pcb_problem* p) {
   cudaFreeHost(p->hSpin);
   cudaFree(p->host_io);
   if (p->git) cudaGraphExecDestroy(p->git);
+  for (cudaGraphExec_t e : p->garn) if (e) cudaGraphExecDestroy(e);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   cudaFree(p->dtol);
   for (cudaEvent_t e : p->ev_prec) cudaEventDestroy(e);
@@ -671,31 +677,43 @@ static int minres_iter_launches(pcb_problem* p, const Batch& B, const SolveCfg& 
 // Capture minres_iter_launches into p->git (on a private stream: the caller's may be the legacy
 // default stream, which cannot be captured).  Returns false when capture is not possible; the
 // caller then launches directly.  Counters are restored: the captured launches did not run.
-static bool capture_minres_iter(pcb_problem* p, const Batch& B, const SolveCfg& c, int s_x) {
-  if (p->git) { cudaGraphExecDestroy(p->git); p->git = nullptr; }
+// Capture the launches `issue(Bc)` makes on a private stream into an executable graph (null when
+// capture is not possible).  *launches gets the kernel count; the counters are restored, since
+// the captured launches did not run.
+template <typename F>
+static cudaGraphExec_t capture_launches(pcb_problem* p, const Batch& B, F&& issue, long long* launches) {
   if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError(); p->cap_stream = nullptr; return false;
+    cudaGetLastError(); p->cap_stream = nullptr; return nullptr;
   }
   Batch Bc = B;
   Bc.stream = p->cap_stream;
   const long long l0 = p->launches;
   const int a0 = p->prec_applies, m0 = p->matvecs;
   if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    cudaGetLastError(); return false;
+    cudaGetLastError(); return nullptr;
   }
-  const int rc = minres_iter_launches(p, Bc, c, s_x);
+  const int rc = issue(Bc);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
-  p->git_launches = p->launches - l0;
+  *launches = p->launches - l0;
   p->launches = l0; p->prec_applies = a0; p->matvecs = m0;
   if (rc != PCB_OK || e != cudaSuccess || !graph) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
-    return false;
+    return nullptr;
   }
-  const cudaError_t ei = cudaGraphInstantiate(&p->git, graph, 0);
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
-  if (ei != cudaSuccess) { p->git = nullptr; cudaGetLastError(); return false; }
+  if (ei != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return exec;
+}
+
+static bool capture_minres_iter(pcb_problem* p, const Batch& B, const SolveCfg& c, int s_x) {
+  if (p->git) { cudaGraphExecDestroy(p->git); p->git = nullptr; }
+  p->git = capture_launches(p, B, [&](const Batch& Bc) { return minres_iter_launches(p, Bc, c, s_x); },
+                            &p->git_launches);
+  if (!p->git) return false;
   p->git_kind = c.kind; p->git_prec = c.prec; p->git_sx = s_x;
   return true;
 }
@@ -771,6 +789,29 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   return PCB_OK;
 }
 
+// Arnoldi step j of FGMRES: z_j = P^-1 v_j, w = op z_j, two classical Gram-Schmidt passes,
+// ||w||, the Hessenberg column and its rotations (scalar step), v_{j+1} = w/||w||.  All operands
+// come from device memory (slots, scalars, the tolerance in B.tols), so a graph per j serves every
+// restart cycle and solve with the same setting.
+static int arnoldi_launches(pcb_problem* p, const Batch& B, const SolveCfg& c, int j) {
+  int rc;
+  const int op = PCB_OP_AHAT;
+  CK(LC(p) launch_setslot(B, SL_VJ, SL_VBASE, j));
+  CK(LC(p) launch_setslot(B, SL_ZJ, SL_ZBASE, j));
+  CK(LC(p) launch_setslot(B, SL_VJ1, SL_VBASE, j + 1));
+  if ((rc = P_precond(p, B, c.kind, c.prec, SL_VJ, SL_ZJ))) return rc;
+  CK(P_matvec(p, B, op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
+  for (int pass = 0; pass < 2; ++pass) {
+    CK(LC(p) launch_multidot(B, SL_VBASE, j, SL_VJ1));
+    CK(LC(p) launch_reduce_multi(B, j, pass));
+    CK(LC(p) launch_multiaxpy(B, SL_VBASE, j, SL_VJ1, pass));
+  }
+  CK(LC(p) launch_dot(B, SL_VJ1, SL_VJ1));
+  CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_GMRES_ARNOLDI, c.tol, j, c.restart));
+  CK(LC(p) launch_axpby(B, AX_SCALE_INV_HNORM, SL_VJ1, SL_VJ1, -1));
+  return PCB_OK;
+}
+
 static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Scal* hs, double* relres_out,
                          int* it_out, bool* conv_out) {
   const Batch& B = p->B;
@@ -788,6 +829,19 @@ static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   if (hs->bnorm == 0.0) { *conv_out = true; *relres_out = 0.0; return PCB_OK; }
   const int limit = c.fixed > 0 ? c.fixed : c.maxit;
   int total = 0;
+  // Arnoldi steps replay per-j graphs (the first j = 0 step of a solve runs directly)
+  if (!p->dtol && cudaMalloc(&p->dtol, sizeof(double)) != cudaSuccess) { cudaGetLastError(); p->dtol = nullptr; }
+  Batch Bt = B;
+  const bool graph = c.graphs && !p->prof && !va && p->dtol;
+  if (p->dtol) {
+    CK(cudaMemcpyAsync(p->dtol, &c.tol, sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    Bt.tols = p->dtol;
+  }
+  if (graph && !(p->garn_kind == c.kind && p->garn_prec == c.prec && p->garn_restart == c.restart)) {
+    for (cudaGraphExec_t& e : p->garn) if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    p->garn_kind = c.kind; p->garn_prec = c.prec; p->garn_restart = c.restart;
+  }
+  bool direct_first = true;
   while (total < limit) {
     CK(P_matvec(p, B, op, s_x, SL_R, s_b, EPI_RESID));
     CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_GMRES_START, c.tol, 0, 0));
@@ -800,19 +854,21 @@ static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
     const int mres = std::min(c.restart, limit - total);
     int k = 0;
     for (int j = 0; j < mres; ++j) {
-      CK(LC(p) launch_setslot(B, SL_VJ, SL_VBASE, j));
-      CK(LC(p) launch_setslot(B, SL_ZJ, SL_ZBASE, j));
-      CK(LC(p) launch_setslot(B, SL_VJ1, SL_VBASE, j + 1));
-      if ((rc = P_precond(p, B, c.kind, c.prec, SL_VJ, SL_ZJ))) return rc;
-      CK(P_matvec(p, B, op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
-      for (int pass = 0; pass < 2; ++pass) {
-        CK(LC(p) launch_multidot(B, SL_VBASE, j, SL_VJ1));
-        CK(LC(p) launch_reduce_multi(B, j, pass));
-        CK(LC(p) launch_multiaxpy(B, SL_VBASE, j, SL_VJ1, pass));
+      bool replayed = false;
+      if (graph && !(direct_first && j == 0)) {
+        if (!p->garn[j])
+          p->garn[j] = capture_launches(p, Bt, [&](const Batch& Bc) { return arnoldi_launches(p, Bc, c, j); },
+                                        &p->garn_launches[j]);
+        if (p->garn[j]) {
+          CK(cudaGraphLaunch(p->garn[j], p->stream));
+          p->launches += p->garn_launches[j];
+          p->prec_applies += 1;
+          p->matvecs += 1;
+          replayed = true;
+        }
       }
-      CK(LC(p) launch_dot(B, SL_VJ1, SL_VJ1));
-      CK(LC(p) launch_reduce(B, B.off_vec, 1, 0, SS_GMRES_ARNOLDI, c.tol, j, c.restart));
-      CK(LC(p) launch_axpby(B, AX_SCALE_INV_HNORM, SL_VJ1, SL_VJ1, -1));
+      if (!replayed && (rc = arnoldi_launches(p, Bt, c, j))) return rc;
+      direct_first = false;
       if ((rc = read_scal(B, hs, 1))) return rc;
       k = j + 1;
       total += 1;

@@ -377,3 +377,20 @@ def test_solve_host_buffers(P, pinned):
     assert np.array_equal(xh, xd.cpu().numpy())
     assert ih["iterations"] == idev["iterations"]
     assert ih["launches"] == idev["launches"] + (2 if pinned else 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gmres_graph_replay_matches_direct_launches(P, precision):
+    """FGMRES Arnoldi steps replayed from per-index CUDA graphs (restart cycles and repeated solves
+    reuse them) give the directly launched iterates bit for bit, with equal counts."""
+    inst = synth.config0()
+    prob = ds.Problem(inst.N, inst.n, 0.5, inst.gamma)
+    b = dev(ds.rhs_gmres(prob, inst.g, inst.f))
+    gp = P.Problem(inst.N, inst.n, 0.5, inst.gamma, precision=precision)
+    xd, idir = gp.solve(b, method="gmres", precond="ps", tol=1e-10, restart=4, graphs=False)
+    xg, igr = gp.solve(b, method="gmres", precond="ps", tol=1e-10, restart=4, graphs=True)
+    xg2, igr2 = gp.solve(b, method="gmres", precond="ps", tol=1e-10, restart=4, graphs=True)
+    assert igr["iterations"] == idir["iterations"] == igr2["iterations"] > 4
+    assert igr["launches"] == idir["launches"] == igr2["launches"]
+    assert torch.equal(xd, xg) and torch.equal(xd, xg2)
+    assert igr["relres"] <= 1e-10
