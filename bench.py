@@ -49,6 +49,7 @@ def args():
                     help="seconds of the serving trace replayed for the serving figures (0: skip)")
     ap.add_argument("--small", action="store_true", help="N=255, n=256 instead (quick checks only)")
     ap.add_argument("--no-neumann", action="store_true", help="skip the Example 3 (Neumann) figures")
+    ap.add_argument("--no-zeta-sweep", action="store_true", help="skip the omega = exp(i zeta) sweep")
     return ap.parse_args()
 
 
@@ -243,6 +244,31 @@ def neumann_figures(P, synth, np, torch, stream, steps):
     return out
 
 
+def zeta_sweep(P, synth, torch, stream):
+    """Mixed MINRES-|P_S| on the bench family at N = 255, n = 256 (gamma = 1e-2) for several
+    omega = exp(i zeta): the choice the paper settled on (zeta = pi) against the circulant
+    (zeta = 0) and intermediate values; iterations and solve time (CUDA events)."""
+    N, n, gam = 255, 256, 1e-2
+    g = torch.from_numpy(synth.random_target(N, n, seed=1).ravel()).cuda()
+    f = torch.from_numpy(synth.manufactured_source(N, n).ravel()).cuda()
+    rows = []
+    for zeta in (0.0, math.pi / 4, math.pi / 2, 3 * math.pi / 4, math.pi):
+        pr = P.Problem(N, n, 1.0, gam, zeta=zeta, precision="mixed", stream=stream)
+        b = pr.assemble_rhs(g, f)
+        x = pr._empty()
+        pr.solve(b, x, tol=1e-8)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, info = pr.solve(b, x, tol=1e-8)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rows.append({"zeta": round(zeta, 6), "iterations": info["iterations"], "ms_per_solve": e0.elapsed_time(e1),
+                     "relres": info["relres"]})
+        pr.close(); del b, x
+    return {"workload": f"heat-control N={N} n={n} backward-Euler a=1 gamma={gam:g}, mixed MINRES-|P_S|",
+            "rows": rows}
+
+
 def main():
     a = args()
     rank = int(os.environ.get("RANK", 0)); world = int(os.environ.get("WORLD_SIZE", 1))
@@ -383,6 +409,9 @@ def main():
     neumann = None
     if rank == 0 and not a.no_neumann:
         neumann = neumann_figures(P, synth, np, torch, stream, a.steps)
+    zsweep = None
+    if rank == 0 and not a.no_zeta_sweep:
+        zsweep = zeta_sweep(P, synth, torch, stream)
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
@@ -420,6 +449,7 @@ def main():
             "gpu_launches": sum(i["launches"] for i in infos),
             "serving": serving,
             "neumann": neumann,
+            "zeta_sweep": zsweep,
         }
         print(json.dumps(line))
     if world > 1:
