@@ -460,3 +460,36 @@ def test_multigrid_contraction_variable_a():
         rates.append((e3 / e1) ** 0.5)
     assert max(rates) < 0.2, rates
     assert rates[-1] < 1.5 * rates[0] + 0.02, rates
+
+
+# ---------------------------------------------------------------- omega sweep (real-part reading)
+def test_real_part_preconditioner_is_the_mean_of_omega_and_conjugate():
+    """For real v, Re(|P_S(omega)|^{-1}) v equals the mean of the applies at omega and conj(omega)
+    (zeta and 2 pi - zeta), each taken complex; and it is symmetric positive definite."""
+    N, n, theta, gamma, zeta = 3, 4, 1.0, 1e-2, 1.1
+    p1 = ds.Problem(N, n, theta, gamma, zeta=zeta)
+    p2 = ds.Problem(N, n, theta, gamma, zeta=2 * math.pi - zeta)
+    m = 2 * p1.m * n
+    E = np.eye(m)
+    R = np.stack([pc.apply_abs_ps_inv(p1, E[:, k]) for k in range(m)], axis=1)
+    C1 = np.linalg.inv(pc.dense_abs_P_S(p1))
+    C2 = np.linalg.inv(pc.dense_abs_P_S(p2))
+    assert np.abs(R - 0.5 * (C1 + C2)).max() < 1e-10 * np.abs(R).max()
+    assert np.abs(R - R.T).max() < 1e-10 * np.abs(R).max()
+    assert np.linalg.eigvalsh(0.5 * (R + R.T)).min() > 0
+
+
+def test_zeta_sweep_half_pi_beats_zero_and_pi():
+    """MINRES-|P_S| iterations on the bench family (N = 31, n = 32, gamma = 1e-2): under the
+    real-part reading, zeta = pi/2 needs fewer iterations than zeta = 0 and zeta = pi (a measured
+    property of that reading, kept as a regression check, not a statement of the paper)."""
+    N, n, gamma = 31, 32, 1e-2
+    g = synth.random_target(N, n, seed=1); f = synth.manufactured_source(N, n)
+    its = {}
+    for zeta in (0.0, math.pi / 2, math.pi):
+        prob = ds.Problem(N, n, 1.0, gamma, zeta=zeta)
+        b = ds.rhs_minres(prob, g, f)
+        _, info = kr.minres(lambda z: op.matvec_A(prob, z), b, lambda r: pc.apply_abs_ps_inv(prob, r), tol=1e-8)
+        assert info.converged
+        its[zeta] = info.iterations
+    assert its[math.pi / 2] < its[math.pi] and its[math.pi / 2] < its[0.0], its
