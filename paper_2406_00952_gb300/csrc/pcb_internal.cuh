@@ -150,16 +150,18 @@ struct Sel {
 };
 
 // family code <-> bit of Batch::fam_*_set: 0 -> 0, P -> log2 P, + 6 with flag 64 (time-major
-// hand-off), + 12 with flag 128 (DCT-I lines); at most kFamilies bits
-constexpr int kFamilies = 24;
+// hand-off), + 12 with flag 128 (DCT-I lines), + 24 with flag 256 (general-zeta time pass, never
+// with 64 or 128); at most kFamilies bits
+constexpr int kFamilies = 30;
 __host__ __device__ inline int fam_index(int code) {
   if (!code) return 0;
   int b = 0;
   while ((2 << b) <= (code & 63)) ++b;
-  return b + ((code & 64) ? 6 : 0) + ((code & 128) ? 12 : 0);
+  return b + ((code & 64) ? 6 : 0) + ((code & 128) ? 12 : 0) + ((code & 256) ? 24 : 0);
 }
 __host__ __device__ inline int fam_code(int index) {
   if (index == 0) return 0;
+  if (index >= 24) return (1 << (index - 24)) | 256;
   const int ev = index >= 12 ? 128 : 0;
   if (ev) index -= 12;
   const int tm = index >= 6 ? 64 : 0;

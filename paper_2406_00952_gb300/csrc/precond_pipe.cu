@@ -780,6 +780,121 @@ __global__ void __launch_bounds__(kThreads, 2)
   cp_wait<0>();
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Time pass for a general zeta (omega = exp(i zeta) other than -1) with the pipelined line FFT.
+// The two halves of a spatial column are separate complex lines v_h(t) exp(-i zeta t/n); they
+// sit in the adjacent lane groups 2l and 2l + 1 of a warp (P <= 16), which meet through one
+// shuffle per slot for the 2x2 solve of P_S (slot r of both lines has the same frequency
+// psi_r = -(zeta + 2 pi r)/n).  The result is the real part of each inverse line (Re(P^-1) on
+// real vectors).  Tiles of LPB / 2 columns of buffer 0, in place; two blocks per SM.
+// ------------------------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_time_gz(const Geom* __restrict__ G, const int* __restrict__ off, int count, Sel sel, int kind, int tot) {
+  static_assert(P <= 16, "the two halves of a column share one warp");
+  constexpr int n = 32 * P, LPB = kThreads / P, CPB = LPB / 2;
+  constexpr int PITCH = pitch_for<P>(n);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw2 = (float2*)smem_raw;
+  float2* tw3 = tw2 + n;
+  float2* pre = tw3 + n;
+  float2* rows = pre + n;                  // row 2 l + h: column c0 + l, half h (n floats, then exchange)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  const Geom& g0 = G[table_inst(off, count, sel)];
+  fill_twiddles<P>(tw2, tw3, g0.twt_f);
+  for (int k = tid; k < n; k += kThreads) pre[k] = __ldg(&g0.pre_f[k]);
+
+  // element e of a tile: column c0 + e % CPB, half / time (e / CPB) = h n + tt
+  auto issue = [&](int tile) {
+    if (tile >= tot) return;
+    const int inst = find_inst(off, count, tile);
+    if (sel.skip(inst)) return;
+    const Geom& g = G[inst];
+    const int c0 = (tile - off[inst]) * CPB;
+    const long long m = g.mp, mn = (long long)g.n * g.mp;
+    for (int e = tid; e < 2 * n * CPB; e += kThreads) {
+      const int cl = e % CPB, rest = e / CPB, h = rest / n, tt = rest - h * n;
+      const bool cv = c0 + cl < g.mp;
+      const float* y = (const float*)g.scratch + h * mn + tt * m + (cv ? c0 + cl : 0);
+      cp_async<4>((float*)(rows + (2 * cl + h) * PITCH) + tt, y, cv);
+    }
+  };
+
+  issue(blockIdx.x);
+  cp_commit();
+  const int t = lane % P;
+  const int lw = warp * (32 / P) + lane / P, cl = lw >> 1, h = lw & 1;
+  const float scale = 1.0f / (float)n;
+
+  for (int tile = blockIdx.x; tile < tot; tile += gridDim.x) {
+    cp_wait<0>();
+    __syncthreads();
+    const int inst = find_inst(off, count, tile);
+    const bool on = !sel.skip(inst);
+    const Geom& g = G[inst];
+    const int c0 = (tile - off[inst]) * CPB;
+    if (on) {
+      float2* ln = rows + lw * PITCH;
+      float* raw = (float*)ln;
+      float2 x[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) x[q] = cscale(pre[t + P * q], raw[t + P * q]);
+      __syncwarp();                          // the row is free: it serves as exchange space
+      fwd2<P>(x, t, ln, tw2);
+      const long long col = min((long long)(c0 + cl), g.mp - 1);      // padded columns compute junk
+      const int jj = (int)(col / g.lr), ii = min((int)(col - (long long)jj * g.lr), g.N - 1);
+      const float c = (float)(g.tau * (__ldg(&g.kap[ii]) + __ldg(&g.kap[jj])));
+      const float a2 = (float)(g.alpha * g.alpha), alpha = (float)g.alpha;
+      const float2* __restrict__ mu = g.mu_f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float2 v = x[Two<P>::outreg(j)];
+        const float2 mr = __ldg(&mu[t + P * j]);
+        if (kind == PK_PS) {
+          float2 o;                            // the other half's value at the same slot
+          o.x = __shfl_xor_sync(0xffffffffu, v.x, P);
+          o.y = __shfl_xor_sync(0xffffffffu, v.y, P);
+          const float2 V1 = h ? o : v, V2 = h ? v : o;
+          const float2 lam = make_float2(mr.x + c, mr.y);
+          const float inv = 1.0f / (lam.x * lam.x + lam.y * lam.y + a2);
+          const float2 U = h ? csub(cmul(lam, V2), cscale(V1, alpha)) : cadd(cmul(cconj(lam), V1), cscale(V2, alpha));
+          x[Two<P>::outreg(j)] = cscale(U, inv);
+        } else {
+          float w;
+          if (kind == PK_ABS_PS) {
+            const float lx = mr.x + c;
+            w = rsqrtf(lx * lx + mr.y * mr.y + a2);
+          } else {
+            w = 1.0f / (sqrtf(mr.x * mr.x + mr.y * mr.y + a2) + c);
+          }
+          x[Two<P>::outreg(j)] = cscale(v, w);
+        }
+      }
+      inv2<P>(x, t, ln, tw3);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float2 z = x[pos<32>(q)], pq = pre[t + P * q];
+        raw[t + P * q] = (z.x * pq.x + z.y * pq.y) * scale;      // Re(z conj(pre)) / n
+      }
+    }
+    __syncthreads();
+    if (on) {
+      const long long m = g.mp, mn = (long long)g.n * g.mp;
+      for (int e = tid; e < 2 * n * CPB; e += kThreads) {
+        const int el = e % CPB, rest = e / CPB, hh = rest / n, tt = rest - hh * n;
+        if (c0 + el < g.mp)
+          ((float*)g.scratch)[hh * mn + tt * m + c0 + el] = ((const float*)(rows + (2 * el + hh) * PITCH))[tt];
+      }
+    }
+    __syncthreads();
+    issue(tile + gridDim.x);
+    cp_commit();
+  }
+  cp_wait<0>();
+}
+
 // ------------------------------------------------------------------------------------------
 // Time pass for n = 512 with one line per warp: lane t holds x[t + 32 q] (16 values).
 //   forward: 16-point register DFT over q, twiddle W_512^{t k1}, exchange through the line's own
@@ -1085,6 +1200,13 @@ cudaError_t launch_time(const Batch& B, int kind, bool time_major = false) {
                            B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
 }
 
+template <int P>
+cudaError_t launch_time_gz(const Batch& B, int kind) {
+  static int resident = 0;
+  return launch_persistent(k_time_gz<P>, time_smem<P>(), B.tot_time[1], resident, B.stream, B.G, B.off_time[1],
+                           B.count, B.sel(), kind, B.tot_time[1]);
+}
+
 // pass `stage` (1, 2, 4, 5) of the FP32 apply; scratch buffers: -1 = buffer 0, -2 = buffer 1.
 // time_major: pass 2 writes time-major lines to buffer 1 and the time pass writes buffer 0 back
 // in the row layout, so pass 4 finds its input where it would otherwise be.  EV: the Neumann
@@ -1117,22 +1239,31 @@ int pipe_dst_p(const Geom& g) {
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
 int pipe_time_p(const Geom& g) {
-  if (g.var_a || !g.zeta_pi || g.n % 32) return 0;   // general zeta: per-instance kernels
+  if (g.var_a || g.n % 32) return 0;
   const int P = g.n / 32;
+  if (!g.zeta_pi && P > 16) return 0;        // general zeta: the two halves of a column share a warp
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
 // family codes: P, plus 64 when pass 2 writes time-major lines for the n = 512 time pass, plus
 // 128 for the DCT-I lines of the Neumann route
+// (the time-major hand-off serves the zeta = pi kernel of n = 512 only; general-zeta time passes,
+// flag 256, take tiles of columns in place)
 int pipe_dst_code(const Geom& g) {
   const int p = pipe_dst_p(g);
-  return p ? (p | (g.n == 512 ? 64 : 0) | (g.bc == PCB_BC_NEUMANN ? 128 : 0)) : 0;
+  return p ? (p | (g.n == 512 && g.zeta_pi ? 64 : 0) | (g.bc == PCB_BC_NEUMANN ? 128 : 0)) : 0;
 }
 int pipe_time_code(const Geom& g) {
   const int p = pipe_time_p(g);
-  return p ? (p | (pipe_dst_p(g) && g.n == 512 ? 64 : 0)) : 0;
+  if (!p) return 0;
+  if (!g.zeta_pi) return p | 256;
+  return p | (pipe_dst_p(g) && g.n == 512 ? 64 : 0);
 }
-// spatial columns per tile of the pipelined time pass (n = 512: one line per warp)
-int pipe_time_cols(int n) { return n == 512 ? kWarps : kThreads / (n / 32); }
+// spatial columns per tile of the pipelined time pass (n = 512: one line per warp; general zeta:
+// two lines, the halves, per column)
+int pipe_time_cols(int n, int zeta_pi) {
+  if (!zeta_pi) return kThreads / (n / 32) / 2;
+  return n == 512 ? kWarps : kThreads / (n / 32);
+}
 // lines per tile of the pipelined DST passes
 int pipe_dst_lines(int L) { return kThreads / (2 * L / 32); }
 
@@ -1161,6 +1292,15 @@ cudaError_t pipe_dst_pass(const Batch& B, int stage, int in_slot, int out_slot) 
 
 cudaError_t pipe_time_pass(const Batch& B, int kind) {
   const bool tm = B.pipe_pt & 64;
+  if (B.pipe_pt & 256) {
+    switch (B.pipe_pt & 63) {
+      case 2: return launch_time_gz<2>(B, kind);
+      case 4: return launch_time_gz<4>(B, kind);
+      case 8: return launch_time_gz<8>(B, kind);
+      case 16: return launch_time_gz<16>(B, kind);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (B.pipe_pt & 63) {
     case 2: return launch_time<2>(B, kind);
     case 4: return launch_time<4>(B, kind);

@@ -70,7 +70,7 @@ int pipe_dst_p(const Geom& g);
 int pipe_time_p(const Geom& g);
 int pipe_dst_code(const Geom& g);
 int pipe_time_code(const Geom& g);
-int pipe_time_cols(int n);
+int pipe_time_cols(int n, int zeta_pi);
 int pipe_dst_lines(int L);
 cudaError_t upload_constants();
 struct TableLayout { size_t kap, mud, muf, twdd, twdf, twtd, twtf, pred, pref, ax, ay, dg, bytes; };
@@ -198,7 +198,7 @@ void set_shapes(Geom& g) {
     g.dst_blocks_j[p] = g.n * ((g.N + lpbj - 1) / lpbj);
     int cpb = pow2_floor(std::min(256, std::max(1, budget[p] / lst)));
     cpb = std::max(lpwt, std::min(cpb, pow2_floor(std::max(1, g.m))));
-    if (p == 1 && pt) cpb = pipe_time_cols(g.n);
+    if (p == 1 && pt) cpb = pipe_time_cols(g.n, g.zeta_pi);
     g.time_cpb[p] = cpb;
     g.time_blocks[p] = (int)(((p == 1 && pt ? g.mp : (long long)g.m) + cpb - 1) / cpb);
     if (p == 1 && (pipe_time_code(g) & 64)) g.time_blocks[p] = g.N * ((g.N + cpb - 1) / cpb);   // rows of points

@@ -81,7 +81,9 @@ def test_precond_misaligned_input(P, shape):
 
 
 ZETA_SHAPES = [(15, 16, 1.0, 1e-2, 0.0), (31, 64, 0.5, 1e-3, 0.4), (63, 32, 1.0, 1e-4, 2.0),
-               (47, 512, 1.0, 1e-2, 1.0), (23, 1024, 0.5, 1e-2, 0.0)]
+               (47, 512, 1.0, 1e-2, 1.0), (23, 1024, 0.5, 1e-2, 0.0),
+               # pipelined FP32 passes with the general-zeta time pass (P = 4, 8, 16)
+               (63, 128, 1.0, 1e-4, 0.0), (255, 256, 1.0, 1e-2, math.pi / 2), (127, 512, 0.5, 1e-3, math.pi / 2)]
 
 
 @pytest.mark.parametrize("shape", ZETA_SHAPES, ids=lambda s: "N%d-n%d-th%g-g%g-z%g" % s)
@@ -394,3 +396,21 @@ def test_gmres_graph_replay_matches_direct_launches(P, precision):
     assert igr["launches"] == idir["launches"] == igr2["launches"]
     assert torch.equal(xd, xg) and torch.equal(xd, xg2)
     assert igr["relres"] <= 1e-10
+
+
+@pytest.mark.parametrize("gamma", [1e-2, 1e-6])
+def test_mixed_solve_half_pi(P, gamma):
+    """omega = i (zeta = pi/2) on the pipelined FP32 passes: the mixed MINRES-|P_S| solve meets
+    the FP64 residual checked by the oracle, within two iterations of the FP64 GPU solve."""
+    N, n = 127, 128
+    prob = ds.Problem(N, n, 1.0, gamma, zeta=math.pi / 2)
+    g = synth.random_target(N, n, seed=1); f = synth.manufactured_source(N, n)
+    b = ds.rhs_minres(prob, g, f)
+    its = {}
+    for precision in ("fp64", "mixed"):
+        gp = P.Problem(N, n, 1.0, gamma, zeta=math.pi / 2, precision=precision)
+        x, info = gp.solve(dev(b), tol=1e-8)
+        assert info["relres"] <= 1e-8
+        assert np.linalg.norm(b - op.matvec_A(prob, x.cpu().numpy())) / np.linalg.norm(b) <= 1.5e-8
+        its[precision] = info["iterations"]
+    assert its["mixed"] <= its["fp64"] + 2, its
