@@ -50,6 +50,7 @@ def args():
     ap.add_argument("--small", action="store_true", help="N=255, n=256 instead (quick checks only)")
     ap.add_argument("--no-neumann", action="store_true", help="skip the Example 3 (Neumann) figures")
     ap.add_argument("--no-zeta-sweep", action="store_true", help="skip the omega = exp(i zeta) sweep")
+    ap.add_argument("--no-omega-i", action="store_true", help="skip the omega = i run of the bench workload")
     return ap.parse_args()
 
 
@@ -269,6 +270,44 @@ def zeta_sweep(P, synth, torch, stream):
             "rows": rows}
 
 
+def omega_i_figures(P, torch, stream, W, g, f, steps):
+    """The bench workload with omega = i (zeta = pi/2) instead of the paper's -1: under the
+    real-part reading the preconditioner is the mean of the omega = i and omega = -i ones.  Mixed
+    step (both gamma) timed with CUDA events like the headline, and one FP64 solve per gamma."""
+    N, n = W["N"], W["n"]
+    probs, bs = [], []
+    for gam in W["gammas"]:
+        pr = P.Problem(N, n, W["theta"], gam, W["T"], zeta=math.pi / 2, precision="mixed", stream=stream)
+        probs.append(pr)
+        bs.append(pr.assemble_rhs(g, f))
+    xs = [pr._empty() for pr in probs]
+    for pr, b, x in zip(probs, bs, xs):
+        pr.solve(b, x, tol=1e-8, maxit=400)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its = []
+    for _ in range(steps):
+        for pr, b, x in zip(probs, bs, xs):
+            its.append(pr.solve(b, x, tol=1e-8, maxit=400)[1]["iterations"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    fp = []
+    for gam, b in zip(W["gammas"], bs):
+        pr = P.Problem(N, n, W["theta"], gam, W["T"], zeta=math.pi / 2, precision="fp64", stream=stream)
+        x = pr._empty()
+        torch.cuda.synchronize(); t0 = time.perf_counter()
+        _, inf = pr.solve(b, x, tol=1e-8, maxit=400)
+        torch.cuda.synchronize()
+        fp.append({"iterations": inf["iterations"], "s": time.perf_counter() - t0})
+        pr.close(); del x
+    for pr in probs:
+        pr.close()
+    return {"zeta": math.pi / 2, "workload": W["name"], "mixed": {"solves_per_s": len(W["gammas"]) / (ms / 1e3),
+            "ms_per_step": ms, "iterations": its[:len(W["gammas"])]},
+            "fp64_gpu": {"solves_per_s": len(fp) / sum(r["s"] for r in fp), "iterations": [r["iterations"] for r in fp]}}
+
+
 def main():
     a = args()
     rank = int(os.environ.get("RANK", 0)); world = int(os.environ.get("WORLD_SIZE", 1))
@@ -306,6 +345,7 @@ def main():
         pr = P.Problem(N, n, W["theta"], gam, W["T"], precision="mixed", stream=stream)
         probs.append(pr)
         bs.append(pr.assemble_rhs(g, f))
+    gf = (g, f)
     del g, f
     xs = [pr._empty() for pr in probs]
     unknowns = probs[0].size
@@ -412,6 +452,10 @@ def main():
     zsweep = None
     if rank == 0 and not a.no_zeta_sweep:
         zsweep = zeta_sweep(P, synth, torch, stream)
+    omega_i = None
+    if rank == 0 and not a.no_omega_i:
+        omega_i = omega_i_figures(P, torch, stream, W, gf[0], gf[1], a.steps)
+    del gf
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
@@ -450,6 +494,7 @@ def main():
             "serving": serving,
             "neumann": neumann,
             "zeta_sweep": zsweep,
+            "omega_i": omega_i,
         }
         print(json.dumps(line))
     if world > 1:
