@@ -93,9 +93,9 @@ typedef struct {
   double theta;           /* 1/2 <= theta <= 1                                                 */
   double T;               /* horizon, > 0                                                      */
   double gamma;           /* regularisation, > 0                                               */
-  double zeta;            /* omega = exp(i zeta), Sec. 2; pi (skew-circulant) runs the fastest */
-                          /* kernels, other values (0: circulant) run per-instance kernels;   */
-                          /* variable a(x) needs zeta = pi                                     */
+  double zeta;            /* omega = exp(i zeta), Sec. 2 (pi: the paper's skew-circulant).      */
+                          /* Any zeta runs the pipelined FP32 kernels for n <= 512 (pi also for */
+                          /* n = 1024); variable a(x) needs zeta = pi                           */
   const double* a_edges;  /* host; NULL => a(x) = 1; else 2*N*(N+1) values of a at cell-edge   */
                           /* midpoints: first ax[j][e] (N rows of N+1; x1-edge between nodes   */
                           /* e and e+1 of row j+1), then ay[e][i] (N+1 rows of N)              */
