@@ -414,3 +414,22 @@ def test_mixed_solve_half_pi(P, gamma):
         assert np.linalg.norm(b - op.matvec_A(prob, x.cpu().numpy())) / np.linalg.norm(b) <= 1.5e-8
         its[precision] = info["iterations"]
     assert its["mixed"] <= its["fp64"] + 2, its
+
+
+def test_batch_mixing_zeta_families(P):
+    """A batch of zeta = pi and zeta = pi/2 instances (separate FP32 time-pass families, shared
+    spatial launches where the families agree): each result equals the instance solved alone."""
+    specs = [(63, 128, math.pi), (63, 128, math.pi / 2), (31, 512, math.pi / 2), (31, 512, math.pi)]
+    probs, bs, gps = [], [], []
+    for k, (N, n, zeta) in enumerate(specs):
+        prob = ds.Problem(N, n, 1.0, 1e-3, zeta=zeta)
+        g = synth.random_target(N, n, seed=60 + k); f = synth.manufactured_source(N, n)
+        probs.append(prob); bs.append(ds.rhs_minres(prob, g, f))
+        gps.append(P.Problem(N, n, 1.0, 1e-3, zeta=zeta, precision="mixed"))
+    xs, infos = P.batch_solve(gps, [dev(b) for b in bs], tol=1e-8, restart=16)
+    for prob, b, gp, x, info in zip(probs, bs, gps, xs, infos):
+        xo = x.cpu().numpy()
+        assert info["relres"] <= 1e-8
+        assert np.linalg.norm(b - op.matvec_A(prob, xo)) / np.linalg.norm(b) <= 1.5e-8
+        x1, i1 = P.batch_solve([gp], [dev(b)], tol=1e-8, restart=16)
+        assert rel(xo, x1[0].cpu().numpy()) <= 1e-12 and i1[0]["iterations"] == info["iterations"]
