@@ -1,11 +1,11 @@
 """Profiling driver: runs a few preconditioner applies (or operator products) on one problem so a
 profiler can capture individual launches.
 
-    python -m paper_2406_00952_gb300.profile_apply N n [mixed|fp64] [abs_ps|ps|pms|matvec] [repeats] [neumann]
+    python -m paper_2406_00952_gb300.profile_apply N n [mixed|fp64] [abs_ps|ps|pms|matvec] [repeats] [neumann|zeta=Z]
 
 Each apply is five launches (x1-line DST, x2-line DST, time pass, x2-line DST, x1-line DST).
 With `neumann` the problem is Example 3's (N nodes per side with the boundary, a = 1e-3,
-Crank-Nicolson), whose applies run the DCT-I passes (kind ps).
+Crank-Nicolson), whose applies run the DCT-I passes (kind ps); `zeta=Z` sets omega = exp(i Z).
 """
 from __future__ import annotations
 
@@ -25,6 +25,8 @@ def main(argv):
     reps = int(argv[4]) if len(argv) > 4 else 3
     if len(argv) > 5 and argv[5] == "neumann":
         gp = P.Problem(N, n, 0.5, 1e-2, precision=prec, bc="neumann", a=1e-3)
+    elif len(argv) > 5 and argv[5].startswith("zeta="):
+        gp = P.Problem(N, n, 1.0, 1e-2, zeta=float(argv[5][5:]), precision=prec)
     else:
         gp = P.Problem(N, n, 1.0, 1e-2, precision=prec)
     g = torch.Generator(device="cuda").manual_seed(0)
