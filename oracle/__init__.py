@@ -26,10 +26,17 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   precond.apply_mg_ps_inv
                         pinned: Lemma 3.14 decomposition (scalar 2x2 check); with many V-cycles it
                         converges to apply_ps_inv on a = 1 (the paper's exact route).
-  multigrid.vcycle      partly pinned: converges to the exact shifted solve with a grid-independent
-                        contraction factor; the fixed-count V-cycle itself (smoother, transfer
-                        operators, coarse coefficients) is a reading of a method the paper does not
-                        specify -- parity unpinned beyond that.
+  multigrid.*           the paper names a multigrid V-cycle but does not specify it; the reading
+                        (damped Jacobi 4/5, full weighting, bilinear prolongation, averaged coarse
+                        edge coefficients, nu1 = nu2 = 2) is pinned part by part
+                        (tests/test_oracle_multigrid.py): Jacobi mode multipliers and the
+                        smoothing factor 3/5 of local Fourier analysis, exact transfer of bilinear
+                        functions, coarse coefficients of an affine a(x), the finest operator
+                        against the assembled K, and the two-grid operator (and the two-level
+                        V-cycle) against its 4 x 4 Fourier block analysis; the whole V-cycle also
+                        converges to the exact shifted solve with a grid-independent contraction.
+                        That this reading is the paper's own multigrid remains unpinned (the paper
+                        prints no multigrid numbers beyond the iteration counts of Tables 3 and 4).
   krylov.*              pinned: sparse direct solve; Table 1 iteration counts.
   Neumann route (Problem(bc="neumann"): discretisation.apply_K / K_sparse, spectra.kappa_neumann,
   spectra.dct1_*, precond.apply_ps_inv)

@@ -75,22 +75,25 @@ def prolong(E, Nf):
     return out
 
 
+def smooth(L, mu, Z, R, sweeps):
+    """`sweeps` damped Jacobi sweeps on (mu I + tau K) Z = R at level L."""
+    diag = mu + L.tau * L.diagK
+    for _ in range(sweeps):
+        Z = Z + JACOBI_WEIGHT * (R - (mu * Z + L.tau * L.K(Z))) / diag
+    return Z
+
+
 def vcycle(levels, mu, R, nu1=2, nu2=2, lev=0):
     """One V-cycle with zero initial guess for (mu I + tau K) Z = R; mu broadcasts against
     R[..., j, i] (shape (...,) -> use mu[..., None, None])."""
     L = levels[lev]
-    diag = mu + L.tau * L.diagK
     if L.N == 1:
-        return R / diag
-    Z = np.zeros_like(R)
-    for _ in range(nu1):
-        Z = Z + JACOBI_WEIGHT * (R - (mu * Z + L.tau * L.K(Z))) / diag
+        return R / (mu + L.tau * L.diagK)
+    Z = smooth(L, mu, np.zeros_like(R), R, nu1)
     res = R - (mu * Z + L.tau * L.K(Z))
     Ec = vcycle(levels, mu, restrict(res), nu1, nu2, lev + 1)
     Z = Z + prolong(Ec, L.N)
-    for _ in range(nu2):
-        Z = Z + JACOBI_WEIGHT * (R - (mu * Z + L.tau * L.K(Z))) / diag
-    return Z
+    return smooth(L, mu, Z, R, nu2)
 
 
 def solve(levels, mu, R, cycles=2, nu1=2, nu2=2):
