@@ -196,15 +196,18 @@ int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* opts, const double* b_h
  * live in one file-scope device array of PCB_NOALLOC_ARENA_BYTES that every GPU loading the
  * library holds until the process exits.
  *   desc       : as for pcb_create (a_edges must be NULL; desc->precision is ignored in favour of
- *                `precision`); work is queued on desc->stream, the call does not wait for it.
+ *                `precision`); the apply is queued on desc->stream.  The call first copies its
+ *                descriptor and spectral tables (at most 160 KB) from host memory into the
+ *                array with cudaMemcpyAsync, so the host may wait for earlier work on the
+ *                stream, and no call may be made while that stream is being captured.
  *   x_dev/y_dev: caller-owned device buffers of 2*m*n FP64 values; they may be the same buffer.
  * Errors: INVALID_ARG, UNSUPPORTED (as pcb_create, or variable a(x)), TOO_LARGE when the tables
  * plus 2*m*n scratch values (4 bytes each for PCB_MIXED, 8 for PCB_FP64) exceed the arena (about
  * 16.7 million unknowns mixed, 8.3 million FP64), CUDA.
  * Every call shares the one array: calls whose GPU work overlaps (different streams, or several
  * host threads) race on it; serialise them, e.g. on one stream.  The scratch needs no clearing
- * between calls (each apply overwrites all of it).  The first call on a device looks up the
- * array's device address; make that first call before any stream capture. */
+ * between calls (each apply overwrites all of it).  The first call on a device also looks up the
+ * array's device address and uploads the transforms' constant tables (synchronous copies). */
 #define PCB_NOALLOC_ARENA_BYTES (64ull * 1024ull * 1024ull)
 int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int precision, const double* x_dev,
                               double* y_dev);

@@ -504,12 +504,11 @@ static cudaError_t mg_apply(const Batch& B, const Geom& g, const MgHost& h, int 
   const int P = g.n / Q, lpw = 32 / P, cpw = 1;
   const int cols = 8 * lpw * cpw;
   const size_t smem = (size_t)cols * padded_len_mg(g.n) * sizeof(T);
-  static bool done = false;
-  if (!done) {
+  static DeviceOnce once;
+  once([] {
     cudaFuncSetAttribute(k_mg_time_fwd<R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_mg_time_inv<R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    done = true;
-  }
+    return cudaFuncSetAttribute(k_mg_time_inv<R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
   const unsigned tb = (unsigned)((g.m + cols - 1) / cols);
   k_mg_time_fwd<R, Q><<<tb, 256, smem, st>>>(B.G, B.S, in_slot, tab, kind, r0, cpw);
   g_mg_launches += 2;

@@ -9,7 +9,10 @@
 //
 // The array's name in host code is only a host-side stand-in for the symbol; its device address
 // comes from cudaGetSymbolAddress, once per device, with that device current.  The first call on
-// a device performs that look-up, so that first call should come before any stream capture.
+// a device performs that look-up and uploads the transforms' constant tables.  Every call copies
+// its small descriptor and spectral tables from host memory with cudaMemcpyAsync (pageable
+// source), so the host may wait for earlier work on the stream, and no call may be made while
+// the stream is being captured into a graph.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -38,7 +41,6 @@ namespace {
 // The arena: [Geom | Slots | block offsets | tables | transform scratch], 256-byte aligned parts.
 static __device__ __align__(256) unsigned char g_arena[PCB_NOALLOC_ARENA_BYTES];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;                                  // serialises the host side of calls
 unsigned char* g_arena_dev[kMaxDevices] = {};     // device address of g_arena, per device
 constexpr size_t kTableHostBytes = 160 * 1024;    // largest table set (N = 511, n = 1024) fits
@@ -50,8 +52,10 @@ int arena_for_current_device(unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PCB_ERR_CUDA;
   if (!g_arena_dev[dev]) {
+    // once per device: the arena's device address and the transforms' __constant__ tables
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_arena) != cudaSuccess || !ptr) { cudaGetLastError(); return PCB_ERR_CUDA; }
+    if (upload_constants() != cudaSuccess) { cudaGetLastError(); return PCB_ERR_CUDA; }
     g_arena_dev[dev] = (unsigned char*)ptr;
   }
   *out = g_arena_dev[dev];
@@ -87,7 +91,6 @@ extern "C" int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int pre
   std::lock_guard<std::mutex> lock(g_mu);
   unsigned char* base = nullptr;
   if ((rc = arena_for_current_device(&base)) != PCB_OK) return rc;
-  if (upload_constants() != cudaSuccess) return PCB_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)desc->stream;
 
   fill_tables(desc, g, lay, g_table_host);

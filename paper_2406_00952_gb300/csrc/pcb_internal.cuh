@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/pcb.h"
 
 #define PCB_MAX_STAGES 12
@@ -16,6 +18,55 @@
 #define PCB_MAX_RESTART 32
 
 namespace pcb {
+
+// ------------------------------------------------------------------------------------------
+// per-device host state.  Kernel attributes (the dynamic shared-memory limit), __constant__
+// tables and occupancy figures belong to a device, so each device the library runs on needs its
+// own setup: a process-wide "done" flag would leave a second device unconfigured.
+// ------------------------------------------------------------------------------------------
+constexpr int kMaxDevices = 64;
+
+// Runs f() the first time the current device reaches this flag (again after a failure).  Two
+// host threads may both run f() for the same device at first, so f() must be idempotent.
+struct DeviceOnce {
+  std::atomic<unsigned long long> mask{0};
+  template <typename F>
+  cudaError_t operator()(F&& f) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < kMaxDevices) ? 1ull << dev : 0ull;
+    if (bit && (mask.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = f();
+    if (e == cudaSuccess && bit) mask.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+  }
+};
+
+// A per-device integer computed once (0 = not yet known).
+struct DeviceInt {
+  std::atomic<int> v[kMaxDevices] = {};
+  template <typename F>
+  cudaError_t get(int* out, F&& compute) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return compute(out);
+    int x = v[dev].load(std::memory_order_acquire);
+    if (!x) {
+      if ((e = compute(&x)) != cudaSuccess) return e;
+      v[dev].store(x, std::memory_order_release);
+    }
+    *out = x;
+    return cudaSuccess;
+  }
+};
+
+// the dynamic shared-memory limit of kernel `k`, once per device
+template <typename K>
+cudaError_t set_smem_limit(DeviceOnce& once, K k, int bytes) {
+  return once([&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
+}
 
 // ------------------------------------------------------------------------------------------
 // complex helpers (float2 / double2)

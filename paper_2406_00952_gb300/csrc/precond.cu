@@ -617,13 +617,12 @@ cudaError_t upload_constants() {
 template <typename R, int Q>
 static void launch_dst_q(const Batch& B, int axis, int in_slot, int out_slot, int inv, size_t smem) {
   const int p = sizeof(R) == 4;
-  static bool done = false;
-  if (!done) {
+  static DeviceOnce once;
+  once([] {
     cudaFuncSetAttribute(k_dst<double, R, R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k_dst<R, R, R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_dst<R, double, R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    done = true;
-  }
+    return cudaFuncSetAttribute(k_dst<R, double, R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
   const int* off = axis == 0 ? B.off_dst_i[p] : B.off_dst_j[p];
   const int tot = axis == 0 ? B.tot_dst_i[p] : B.tot_dst_j[p];
   if (in_slot >= 0)
@@ -637,11 +636,8 @@ static void launch_dst_q(const Batch& B, int axis, int in_slot, int out_slot, in
 template <typename R, int Q>
 static void launch_time_q(const Batch& B, int kind, size_t smem) {
   const int p = sizeof(R) == 4;
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(k_time<R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    done = true;
-  }
+  static DeviceOnce once;
+  set_smem_limit(once, k_time<R, Q>, 227 * 1024);
   k_time<R, Q><<<B.tot_time[p], 256, smem, B.stream>>>(B.G, B.off_time[p], B.count, B.sel(), kind);
 }
 
@@ -650,13 +646,12 @@ static cudaError_t dispatch_dst(const Batch& B, int axis, int in_slot, int out_s
   const int p = sizeof(R) == 4;
   const size_t smem = B.dst_smem[p];
   if (B.dst_q == 0) {   // instances with different line lengths in one launch
-    static bool done = false;
-    if (!done) {
+    static DeviceOnce once;
+    once([] {
       cudaFuncSetAttribute(k_dst_any<double, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       cudaFuncSetAttribute(k_dst_any<R, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      cudaFuncSetAttribute(k_dst_any<R, double, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      done = true;
-    }
+      return cudaFuncSetAttribute(k_dst_any<R, double, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
     const int* off = axis == 0 ? B.off_dst_i[p] : B.off_dst_j[p];
     const int tot = axis == 0 ? B.tot_dst_i[p] : B.tot_dst_j[p];
     if (in_slot >= 0)
@@ -688,11 +683,8 @@ static cudaError_t dispatch_time(const Batch& B, int kind) {
   const int p = sizeof(R) == 4;
   const size_t smem = B.time_smem[p];
   if (B.time_q == 0) {
-    static bool done = false;
-    if (!done) {
-      cudaFuncSetAttribute(k_time_any<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      done = true;
-    }
+    static DeviceOnce once;
+    set_smem_limit(once, k_time_any<R>, 227 * 1024);
     k_time_any<R><<<B.tot_time[p], 256, smem, B.stream>>>(B.G, B.off_time[p], B.count, B.sel(), kind);
     return cudaGetLastError();
   }

@@ -1138,37 +1138,30 @@ size_t time_smem() {
 }
 size_t time512_smem() { return (size_t)(3 * 512 + 32 + kNsTime * kWarps * pitch_for<32>(512)) * sizeof(float2); }
 
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
-
-// Launch a persistent kernel: at most as many blocks as fit on the device at once (queried once
-// per kernel; `resident` caches the figure).
+// Launch a persistent kernel: at most as many blocks as fit on the device at once.  The figure
+// (and the shared-memory limit it needs) is set up once per kernel and device; `resident` keeps it.
 template <typename K, typename... Args>
-cudaError_t launch_persistent(K kern, size_t smem, int tot, int& resident, cudaStream_t st, Args... args) {
+cudaError_t launch_persistent(K kern, size_t smem, int tot, DeviceInt& resident, cudaStream_t st, Args... args) {
   if (tot <= 0) return cudaSuccess;
-  if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    resident = std::max(1, occ) * sm_count();
-  }
-  kern<<<std::min(tot, resident), kThreads, smem, st>>>(args...);
+  int res = 0;
+  cudaError_t e = resident.get(&res, [&](int* out) {
+    cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e2 != cudaSuccess) return e2;
+    int occ = 0, dev = 0, sms = 0;
+    if ((e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem)) != cudaSuccess) return e2;
+    if ((e2 = cudaGetDevice(&dev)) != cudaSuccess) return e2;
+    if ((e2 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e2;
+    *out = std::max(1, occ) * std::max(1, sms);
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
+  kern<<<std::min(tot, res), kThreads, smem, st>>>(args...);
   return cudaGetLastError();
 }
 
 template <typename TIn, typename TOut, int P, bool EV>
 cudaError_t launch_rows(const Batch& B, int in_sel, int out_sel, int inv) {
-  static int resident = 0;
+  static DeviceInt resident;
   return launch_persistent(k_dst_rows<TIn, TOut, P, EV>, dst_rows_smem<TIn, P, EV>(), B.tot_dst_i[1], resident,
                            B.stream, B.G, (const Slots*)B.S, B.off_dst_i[1], B.count, B.sel(), in_sel, out_sel,
                            B.tot_dst_i[1], inv);
@@ -1176,7 +1169,7 @@ cudaError_t launch_rows(const Batch& B, int in_sel, int out_sel, int inv) {
 
 template <typename TIn, int P, int MODE, bool EV>
 cudaError_t launch_rowsT(const Batch& B, int in_sel, int out_sel, int inv) {
-  static int resident = 0;
+  static DeviceInt resident;
   // MODE 0 tiles: (time step, LPB rows) -> dst_j offsets; MODE 1 tiles: (row, LPB time steps),
   // as many as the contiguous-line tiles -> dst_i offsets
   const int* off = MODE == 0 ? B.off_dst_j[1] : B.off_dst_i[1];
@@ -1187,9 +1180,9 @@ cudaError_t launch_rowsT(const Batch& B, int in_sel, int out_sel, int inv) {
 
 template <int P>
 cudaError_t launch_time(const Batch& B, int kind, bool time_major = false) {
-  static int resident = 0;
+  static DeviceInt resident;
   if (P == 16) {
-    static int resident512[2] = {0, 0};
+    static DeviceInt resident512[2];
     if (time_major)
       return launch_persistent(k_time512<kNsTime, 1>, time512_smem(), B.tot_time[1], resident512[1], B.stream, B.G,
                                B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
@@ -1202,7 +1195,7 @@ cudaError_t launch_time(const Batch& B, int kind, bool time_major = false) {
 
 template <int P>
 cudaError_t launch_time_gz(const Batch& B, int kind) {
-  static int resident = 0;
+  static DeviceInt resident;
   return launch_persistent(k_time_gz<P>, time_smem<P>(), B.tot_time[1], resident, B.stream, B.G, B.off_time[1],
                            B.count, B.sel(), kind, B.tot_time[1]);
 }
