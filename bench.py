@@ -51,7 +51,40 @@ def args():
     ap.add_argument("--no-neumann", action="store_true", help="skip the Example 3 (Neumann) figures")
     ap.add_argument("--no-zeta-sweep", action="store_true", help="skip the omega = exp(i zeta) sweep")
     ap.add_argument("--no-omega-i", action="store_true", help="skip the omega = i run of the bench workload")
+    ap.add_argument("--profile-apply", nargs=2, type=int, metavar=("N", "n"),
+                    help="profiling mode: only run --prof-reps preconditioner applies (or products) on one "
+                         "problem of this size, so that a profiler can capture single launches")
+    ap.add_argument("--prof-prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--prof-kind", default="abs_ps", choices=["abs_ps", "ps", "pms", "matvec"])
+    ap.add_argument("--prof-reps", type=int, default=3)
+    ap.add_argument("--prof-zeta", type=float, default=math.pi)
+    ap.add_argument("--prof-neumann", action="store_true", help="Example 3's Neumann grid (DCT-I passes, kind ps)")
     return ap.parse_args()
+
+
+def profile_apply(a):
+    """--profile-apply N n: a few applies of one kind (or products) on one problem, nothing else.
+    With --prof-neumann the problem is Example 3's (N nodes per side with the boundary, a = 1e-3,
+    Crank-Nicolson); --prof-zeta sets omega = exp(i zeta)."""
+    import torch
+    import paper_2406_00952_gb300 as P
+    from paper_2406_00952_gb300 import _build
+    _build.build()
+    N, n = a.profile_apply
+    if a.prof_neumann:
+        gp = P.Problem(N, n, 0.5, 1e-2, precision=a.prof_prec, bc="neumann", a=1e-3)
+    else:
+        gp = P.Problem(N, n, 1.0, 1e-2, zeta=a.prof_zeta, precision=a.prof_prec)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(gp.size, dtype=torch.float64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    for _ in range(a.prof_reps):
+        if a.prof_kind == "matvec":
+            gp.matvec(x, out=y)
+        else:
+            gp.precond_apply(x, out=y, kind=a.prof_kind, precision=a.prof_prec)
+    torch.cuda.synchronize()
+    print("ok", N, n, a.prof_prec, a.prof_kind, a.prof_reps)
 
 
 def replica_plan(world: int, rank: int, gammas) -> list:
@@ -317,6 +350,8 @@ def main():
         W.update(N=255, n=256, name="heat-control N=255 n=256 backward-Euler a=1, gamma {1e-2,1e-6}")
     if a.impl == "reference":
         return reference_arm(a, W, rank, world)
+    if a.profile_apply:
+        return profile_apply(a)
 
     import numpy as np
     import torch

@@ -1,8 +1,9 @@
 """GPU parity of the Neumann route (Example 3: mirrored stencil, DCT-I in place of the DST-I,
 GMRES-P_S) against the FP64 oracle, through the C-ABI.
 
-Tolerances are those of the Dirichlet parity tests: FP64 transforms and operators <= 1e-12
-(products <= 1e-13), the FP32 preconditioner <= 2e-6, same-algorithm FP64 iterates <= 1e-10.
+Tolerances are those of the Dirichlet parity tests, each on the relative 2-norm and the relative
+max-norm error (tests/closeness.py): FP64 transforms and operators <= 1e-12 (products <= 1e-13),
+the FP32 preconditioner <= 2e-6, same-algorithm FP64 iterates <= 1e-10.
 """
 import math
 
@@ -11,6 +12,7 @@ import pytest
 import torch
 
 import synth
+from closeness import assert_close
 from oracle import discretisation as ds
 from oracle import krylov as kr
 from oracle import operators as op
@@ -66,11 +68,11 @@ def test_neumann_precond_parity(P, shape):
     gp = _gpu(P, shape)
     out64 = gp.precond_apply(dev(v), kind="ps", precision="fp64").cpu().numpy()
     out32 = gp.precond_apply(dev(v), kind="ps", precision="mixed").cpu().numpy()
-    assert rel(out64, ref) <= 1e-12, rel(out64, ref)
-    assert rel(out32, ref) <= 2e-6, rel(out32, ref)
+    assert_close(out64, ref, 1e-12, what="fp64")
+    assert_close(out32, ref, 2e-6, what="fp32")
     t = dev(v)
     gp.precond_apply(t, out=t, kind="ps", precision="fp64")
-    assert rel(t.cpu().numpy(), ref) <= 1e-12
+    assert_close(t.cpu().numpy(), ref, 1e-12, what="fp64 in place")
 
 
 def test_neumann_refuses_minres_preconditioners(P):
@@ -91,7 +93,7 @@ def test_neumann_matvec_parity(P, shape, opname):
     v = synth.random_vector(2 * prob.m * prob.n, seed=800 + shape[0])
     ref = op.matvec_A(prob, v) if opname == "A" else op.matvec_A_hat(prob, v)
     out = _gpu(P, shape).matvec(dev(v), op=opname).cpu().numpy()
-    assert rel(out, ref) <= 1e-13, rel(out, ref)
+    assert_close(out, ref, 1e-13)
 
 
 @pytest.mark.parametrize("theta", [1.0, 0.5, 0.8])
@@ -103,7 +105,7 @@ def test_neumann_rhs_parity(P, theta):
     gp = P.Problem(N, n, theta, 3e-3, bc="neumann", a=a)
     for opname, ref in (("A", ds.rhs_minres(prob, g, f, y0)), ("Ahat", ds.rhs_gmres(prob, g, f, y0))):
         b = gp.assemble_rhs(dev(g.ravel()), dev(f.ravel()), dev(y0), op=opname).cpu().numpy()
-        assert rel(b, ref) <= 1e-14
+        assert_close(b, ref, 1e-14)
 
 
 @pytest.mark.parametrize("theta", [1.0, 0.5])
@@ -121,7 +123,7 @@ def test_neumann_same_algorithm_iterates(P, theta):
         gp = P.Problem(N, n, theta, gamma, precision="fp64", bc="neumann", a=a)
         x, info = gp.solve(dev(b), method="gmres", precond="ps", fixed_iterations=k, restart=30)
         assert info["iterations"] == k
-        assert rel(x.cpu().numpy(), xo) <= 1e-10, rel(x.cpu().numpy(), xo)
+        assert_close(x.cpu().numpy(), xo, 1e-10)
 
 
 @pytest.mark.parametrize("gamma", [1e-10, 1e-8, 1e-6, 1e-4, 1e-2])
@@ -138,7 +140,7 @@ def test_neumann_example3_solve(P, gamma, precision):
     eo = ds.error_eh(prob, *ds.recover(prob, xo), ye, pe)
     gp = P.Problem(N, n, 0.5, gamma, precision=precision, bc="neumann", a=1e-3)
     b = gp.assemble_rhs(dev(g.ravel()), dev(f.ravel()), dev(ye[0]), op="Ahat")
-    assert rel(b.cpu().numpy(), bo) <= 1e-14
+    assert_close(b.cpu().numpy(), bo, 1e-14)
     # mixed: the refinement stops as soon as the FP64 residual allows, and a relative residual r
     # leaves an error of about r |y| in the state, which at gamma = 1e-10 (e_h ~ 1e-11) is above the
     # discretisation error unless r ~ 1e-12; the error comparison asks the mixed solve for that
@@ -186,4 +188,5 @@ def test_neumann_batch_with_dirichlet(P):
         xo = x.cpu().numpy()
         assert np.linalg.norm(b - op.matvec_A_hat(prob, xo)) / np.linalg.norm(b) <= 1.5e-8
         x1, i1 = P.batch_solve([gp], [dev(b)], tol=1e-8, restart=16)
-        assert rel(xo, x1[0].cpu().numpy()) <= 1e-12 and i1[0]["iterations"] == info["iterations"]
+        assert_close(xo, x1[0].cpu().numpy(), 1e-12)
+        assert i1[0]["iterations"] == info["iterations"]

@@ -1,11 +1,14 @@
 """GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on seeded inputs.
 
-Tolerances (derived from the arithmetic):
-  FP64 transforms / operators : relative 2-norm error <= 1e-12 (rounding of O(log size) stages)
-  FP32 preconditioner         : relative 2-norm error <= 2e-6  (FP32 unit roundoff 6e-8 times the
-                                ~30 transform stages and the pointwise solve)
+Tolerances (derived from the arithmetic), each applied to the relative 2-norm error AND to the
+relative max-norm error max|out - ref| / max|ref| (tests/closeness.py):
+  FP64 transforms / operators : <= 1e-12 (rounding of O(log size) stages)
+  FP32 preconditioner         : <= 2e-6  (FP32 unit roundoff 6e-8 times the ~30 transform stages
+                                and the pointwise solve)
   FP64 solves                 : same-algorithm iterates agree to <= 1e-10 relative
-  mixed solves                : error against the FP64 oracle solution <= 1e-7 relative
+  mixed solves                : error against the FP64 oracle solution <= 1e-7 relative, iteration
+                                count within +2 of the FP64 solve (xfail where measured otherwise,
+                                with the measured cause)
 """
 import math
 
@@ -14,6 +17,7 @@ import pytest
 import torch
 
 import synth
+from closeness import assert_close, assert_close_by_parts, errors
 from oracle import discretisation as ds
 from oracle import krylov as kr
 from oracle import operators as op
@@ -56,12 +60,43 @@ def test_precond_parity(P, shape, kind):
     gp = P.Problem(N, n, theta, gamma, precision="fp64")
     out64 = gp.precond_apply(dev(v), kind=kind, precision="fp64").cpu().numpy()
     out32 = gp.precond_apply(dev(v), kind=kind, precision="mixed").cpu().numpy()
-    assert rel(out64, ref) <= 1e-12, rel(out64, ref)
-    assert rel(out32, ref) <= 2e-6, rel(out32, ref)
+    assert_close(out64, ref, 1e-12, what="fp64")
+    assert_close(out32, ref, 2e-6, what="fp32")
     # in place (x and y the same buffer)
     t = dev(v)
     gp.precond_apply(t, out=t, kind=kind, precision="fp64")
-    assert rel(t.cpu().numpy(), ref) <= 1e-12
+    assert_close(t.cpu().numpy(), ref, 1e-12, what="fp64 in place")
+
+
+@pytest.fixture(scope="module")
+def full_size_input():
+    """The bench workload's shape: N = 511 (m = 261,121), n = 512, 267,387,904 values."""
+    N, n = 511, 512
+    return N, n, synth.random_vector(2 * N * N * n, seed=2024)
+
+
+@pytest.mark.parametrize("kind,zeta", [("abs_ps", math.pi), ("ps", math.pi), ("abs_ps", math.pi / 2)],
+                         ids=["abs_ps-zeta_pi", "ps-zeta_pi", "abs_ps-zeta_pi_2"])
+def test_precond_parity_full_size(P, full_size_input, kind, zeta):
+    """Element by element at the bench workload's size (N = 511, n = 512, theta = 1): the only shape
+    that runs the P = 32 x2-line pass writing time-major lines and the n = 512 time pass over all
+    261,121 columns (zeta = pi), and the general-zeta time pass at n = 512 (zeta = pi/2).  Beside the
+    whole-vector figures, the worst (half, time) slice, the worst x2 row and the worst x1 column are
+    checked on their own.  The oracle apply takes about a minute and 13 GB of host memory here."""
+    N, n, v = full_size_input
+    prob = ds.Problem(N, n, 1.0, 1e-2, zeta=zeta)
+    ref = ORACLE[kind](prob, v)
+    gp = P.Problem(N, n, 1.0, 1e-2, zeta=zeta, precision="mixed")
+    x = dev(v)
+    shape, parts = (2, n, N, N), [(0, 1), (2,), (3,), (0,)]
+    out32 = gp.precond_apply(x, kind=kind, precision="mixed").cpu().numpy()
+    e32 = assert_close(out32, ref, 2e-6, what="fp32")
+    w32 = assert_close_by_parts(out32, ref, shape, 6e-6, parts, what="fp32 parts")
+    del out32
+    out64 = gp.precond_apply(x, kind=kind, precision="fp64").cpu().numpy()
+    e64 = assert_close(out64, ref, 1e-12, what="fp64")
+    w64 = assert_close_by_parts(out64, ref, shape, 3e-12, parts, what="fp64 parts")
+    print(f"full size {kind} zeta={zeta:.4f}: fp32 {e32} parts {w32}; fp64 {e64} parts {w64}")
 
 
 @pytest.mark.parametrize("shape", [(511, 4, 1.0, 1e-2), (63, 64, 0.5, 1e-2)], ids=lambda s: "N%d-n%d" % s[:2])
@@ -77,7 +112,7 @@ def test_precond_misaligned_input(P, shape):
     xin = buf[1:]
     assert xin.data_ptr() % 16 == 8
     out = gp.precond_apply(xin, kind="abs_ps", precision="mixed").cpu().numpy()
-    assert rel(out, ref) <= 2e-6, rel(out, ref)
+    assert_close(out, ref, 2e-6)
 
 
 ZETA_SHAPES = [(15, 16, 1.0, 1e-2, 0.0), (31, 64, 0.5, 1e-3, 0.4), (63, 32, 1.0, 1e-4, 2.0),
@@ -98,8 +133,8 @@ def test_precond_parity_general_zeta(P, shape, kind):
     gp = P.Problem(N, n, theta, gamma, zeta=zeta, precision="fp64")
     out64 = gp.precond_apply(dev(v), kind=kind, precision="fp64").cpu().numpy()
     out32 = gp.precond_apply(dev(v), kind=kind, precision="mixed").cpu().numpy()
-    assert rel(out64, ref) <= 1e-12, rel(out64, ref)
-    assert rel(out32, ref) <= 2e-6, rel(out32, ref)
+    assert_close(out64, ref, 1e-12, what="fp64")
+    assert_close(out32, ref, 2e-6, what="fp32")
 
 
 @pytest.mark.parametrize("zeta", [0.0, 0.4])
@@ -113,7 +148,7 @@ def test_same_algorithm_iterates_general_zeta(P, zeta):
         gp = P.Problem(inst.N, inst.n, 1.0, inst.gamma, zeta=zeta, precision="fp64")
         x, info = gp.solve(dev(b), method="minres", precond="abs_ps", fixed_iterations=k)
         assert info["iterations"] == k
-        assert rel(x.cpu().numpy(), xo) <= 1e-10, rel(x.cpu().numpy(), xo)
+        assert_close(x.cpu().numpy(), xo, 1e-10, what=f"iterate {k}")
     gm = P.Problem(inst.N, inst.n, 1.0, inst.gamma, zeta=zeta, precision="mixed")
     x, info = gm.solve(dev(b), tol=1e-8)
     assert info["relres"] <= 1e-8
@@ -135,7 +170,7 @@ def test_precond_special_values(P):
     gp = P.Problem(N, n, 1.0, 1e-2, precision="mixed")
     out = gp.precond_apply(dev(v), kind="abs_ps", precision="mixed").cpu().numpy()
     assert np.all(np.isfinite(out))
-    assert rel(out, pc.apply_abs_ps_inv(prob, v)) <= 2e-6
+    assert_close(out, pc.apply_abs_ps_inv(prob, v), 2e-6)
     z = gp.precond_apply(dev(np.zeros_like(v)), kind="abs_ps", precision="mixed").cpu().numpy()
     assert np.all(z == 0.0)
 
@@ -149,7 +184,7 @@ def test_matvec_parity(P, shape, opname):
     ref = op.matvec_A(prob, v) if opname == "A" else op.matvec_A_hat(prob, v)
     gp = P.Problem(N, n, theta, gamma)
     out = gp.matvec(dev(v), op=opname).cpu().numpy()
-    assert rel(out, ref) <= 1e-13, rel(out, ref)
+    assert_close(out, ref, 1e-13)
 
 
 @pytest.mark.parametrize("theta", [1.0, 0.5, 0.8])
@@ -161,13 +196,14 @@ def test_rhs_and_recover_parity(P, theta):
     gp = P.Problem(N, n, theta, 3e-3)
     for opname, ref in (("A", ds.rhs_minres(prob, g, f, y0)), ("Ahat", ds.rhs_gmres(prob, g, f, y0))):
         b = gp.assemble_rhs(dev(g.ravel()), dev(f.ravel()), dev(y0), op=opname).cpu().numpy()
-        assert rel(b, ref) <= 1e-14
+        assert_close(b, ref, 1e-14)
     b0 = gp.assemble_rhs(dev(g.ravel()), dev(f.ravel()), None).cpu().numpy()
-    assert rel(b0, ds.rhs_minres(prob, g, f)) <= 1e-14
+    assert_close(b0, ds.rhs_minres(prob, g, f), 1e-14)
     x = synth.random_vector(2 * prob.m * n, seed=13)
     y, p = gp.recover(dev(x))
     yr, pr = ds.recover(prob, x)
-    assert rel(y.cpu().numpy(), yr.ravel()) <= 1e-13 and rel(p.cpu().numpy(), pr.ravel()) <= 1e-13
+    assert_close(y.cpu().numpy(), yr.ravel(), 1e-13)
+    assert_close(p.cpu().numpy(), pr.ravel(), 1e-13)
 
 
 def _oracle_solve(prob, b, method, kind, tol, fixed=None):
@@ -190,7 +226,7 @@ def test_same_algorithm_iterates(P, case):
         gp = P.Problem(inst.N, inst.n, theta, inst.gamma, precision="fp64")
         x, info = gp.solve(dev(b), method=method, precond=kind, fixed_iterations=k, restart=30)
         assert info["iterations"] == k
-        assert rel(x.cpu().numpy(), xo) <= 1e-10, rel(x.cpu().numpy(), xo)
+        assert_close(x.cpu().numpy(), xo, 1e-10, what=f"iterate {k}")
 
 
 def test_config0_fp64_and_mixed(P):
@@ -215,11 +251,16 @@ def test_config0_fp64_and_mixed(P):
     xm, im = gm.solve(dev(b), tol=1e-8)
     x8, i8 = gp.solve(dev(b), tol=1e-8)
     assert im["relres"] <= 1e-8
-    assert rel(xm.cpu().numpy(), xs) <= 1e-7 * 100
+    assert rel(xm.cpu().numpy(), xs) <= 1e-7
     assert im["iterations"] <= i8["iterations"] + 2, (im, i8)
 
 
-@pytest.mark.parametrize("gamma", [1e-10, 1e-6, 1e-2])
+MIXED_GMRES_GAP = ("FP32 rounding of the P_S apply: P_S is nearly exact here (3 FP64 iterations), so the "
+                   "mixed solve is limited by the apply's rounding, amplified by ||A|| ||P_S^-1||, and needs a "
+                   "second refinement sweep: 6 iterations against 3 (measured)")
+
+
+@pytest.mark.parametrize("gamma", [1e-10, 1e-6, pytest.param(1e-2, marks=pytest.mark.xfail(reason=MIXED_GMRES_GAP))])
 def test_table1_on_gpu(P, gamma):
     """Example 1, h = 2^-5, Crank-Nicolson: iteration counts and e_h as printed in Table 1."""
     import os
@@ -244,10 +285,14 @@ def test_table1_on_gpu(P, gamma):
     x, info = gp.solve(b, method="minres", precond="abs_ps", tol=1e-8)
     assert info["iterations"] == mit
     # FP32 preconditioner: rounding noise in P^{-1} v is amplified by about ||A|| ||P^{-1}||, which
-    # costs extra iterations when that product is large (gamma = 1e-2: 6 instead of 3).
+    # costs extra iterations when that product is large (gamma = 1e-2: 6 instead of 3; xfail above).
     gm = P.Problem(N, n, 0.5, gamma, precision="mixed")
     x, info = gm.solve(bh, method="gmres", precond="ps", tol=1e-8)
-    assert info["relres"] <= 1e-8 and info["iterations"] <= 2 * git, info
+    assert info["relres"] <= 1e-8
+    xs, _ = kr.fgmres(lambda z: op.matvec_A_hat(prob, z), bh.cpu().numpy(), lambda r: pc.apply_ps_inv(prob, r),
+                      tol=1e-12)
+    assert rel(x.cpu().numpy(), xs) <= 1e-7
+    assert info["iterations"] <= git + 2, info
 
 
 def test_errors_are_reported_not_raised_in_kernels(P):
@@ -277,8 +322,57 @@ def test_mg_precond_parity(P, shape, kind):
     gp = P.Problem(N, n, theta, gamma, a_edges=a, mg_cycles=2)
     out64 = gp.precond_apply(dev(v), kind=kind, precision="fp64").cpu().numpy()
     out32 = gp.precond_apply(dev(v), kind=kind, precision="mixed").cpu().numpy()
-    assert rel(out64, ref) <= 1e-12, rel(out64, ref)
-    assert rel(out32, ref) <= 5e-6, rel(out32, ref)
+    assert_close(out64, ref, 1e-12, what="fp64")
+    assert_close(out32, ref, 5e-6, what="fp32")
+
+
+def _minres_pms_problem(N, n, gamma=1e-4, seed=5):
+    a = synth.variable_coefficient_edges(N)
+    prob = ds.Problem(N, n, 1.0, gamma, a_edges=a)
+    g = synth.random_target(N, n, seed=seed); f = synth.manufactured_source(N, n)
+    return a, prob, ds.rhs_minres(prob, g, f)
+
+
+@pytest.mark.parametrize("N,n", [(31, 32), (63, 64)])
+def test_minres_pms_variable_a_end_to_end(P, N, n):
+    """MINRES-P_MS with the multigrid shifted solves (variable a(x), backward Euler; Eq. matrix_P_MS,
+    Thm 3.11, the three P_MS^-1 steps of Sec. 3.5): FP64 iterates after 3 and 8 steps equal the
+    oracle's (two V-cycles per shifted solve); the FP64 and mixed solves reach relres 1e-8, their
+    solutions are within 1e-7 of the oracle's solution, and the mixed count is within +2."""
+    a, prob, b = _minres_pms_problem(N, n)
+    M = lambda r: pc.apply_pms_inv(prob, r, cycles=2)
+    A = lambda z: op.matvec_A(prob, z)
+    gp = P.Problem(N, n, 1.0, prob.gamma, a_edges=a, mg_cycles=2, precision="fp64")
+    for k in (3, 8):
+        xo, _ = kr.minres(A, b, M, fixed_iterations=k)
+        x, info = gp.solve(dev(b), method="minres", precond="pms", fixed_iterations=k)
+        assert info["iterations"] == k and info["method"] == 1 and info["precond"] == 3
+        assert_close(x.cpu().numpy(), xo, 1e-10, what=f"iterate {k}")
+    xs, io = kr.minres(A, b, M, tol=1e-12)
+    x, info = gp.solve(dev(b), tol=1e-8)                     # AUTO: MINRES with P_MS
+    assert info["method"] == 1 and info["precond"] == 3 and info["relres"] <= 1e-8
+    assert rel(x.cpu().numpy(), xs) <= 1e-7
+    gm = P.Problem(N, n, 1.0, prob.gamma, a_edges=a, mg_cycles=2, precision="mixed")
+    xm, im = gm.solve(dev(b), tol=1e-8)
+    assert im["relres"] <= 1e-8 and rel(xm.cpu().numpy(), xs) <= 1e-7
+    assert np.linalg.norm(b - A(xm.cpu().numpy())) / np.linalg.norm(b) <= 1.5e-8
+    assert im["iterations"] <= info["iterations"] + 2, (im, info)
+
+
+def test_minres_pms_variable_a_iteration_trend(P):
+    """Thm 3.11 / Remark 4: the P_MS-preconditioned spectrum lies in fixed intervals, so the MINRES
+    count stays essentially flat as the grid is refined (N = 63, 127, 255 with n = N + 1), as in
+    Table 3's MINRES-P_MS columns (which use another a(x), so the trend is compared, not the counts)."""
+    its = []
+    for N in (63, 127, 255):
+        a, prob, b = _minres_pms_problem(N, N + 1, gamma=1e-4)
+        gp = P.Problem(N, N + 1, 1.0, prob.gamma, a_edges=a, mg_cycles=2, precision="mixed")
+        _, info = gp.solve(dev(b), tol=1e-8)
+        assert info["relres"] <= 1e-8
+        its.append(info["iterations"])
+        gp.close()
+    print("MINRES-P_MS iterations, N = 63, 127, 255:", its)
+    assert max(its) - min(its) <= 6, its
 
 
 def test_variable_a_matvec_and_fgmres(P):
@@ -290,19 +384,20 @@ def test_variable_a_matvec_and_fgmres(P):
     g = synth.random_target(N, n, seed=2); f = synth.manufactured_source(N, n)
     v = synth.random_vector(2 * prob.m * n, seed=9)
     gp = P.Problem(N, n, 0.5, 1e-4, a_edges=a, precision="fp64")
-    assert rel(gp.matvec(dev(v), op="Ahat").cpu().numpy(), op.matvec_A_hat(prob, v)) <= 1e-13
-    assert rel(gp.matvec(dev(v), op="A").cpu().numpy(), op.matvec_A(prob, v)) <= 1e-13
+    assert_close(gp.matvec(dev(v), op="Ahat").cpu().numpy(), op.matvec_A_hat(prob, v), 1e-13)
+    assert_close(gp.matvec(dev(v), op="A").cpu().numpy(), op.matvec_A(prob, v), 1e-13)
     b = ds.rhs_gmres(prob, g, f)
     xo, _ = kr.fgmres(lambda z: op.matvec_A_hat(prob, z), b, lambda r: pc.apply_mg_ps_inv(prob, r), fixed_iterations=4)
     x, info = gp.solve(dev(b), method="fgmres", precond="ps", fixed_iterations=4)
-    assert rel(x.cpu().numpy(), xo) <= 1e-10
+    assert_close(x.cpu().numpy(), xo, 1e-10)
     x, info = gp.solve(dev(b), tol=1e-8)
     assert info["method"] == 3 and info["relres"] <= 1e-8
     xs, io = kr.fgmres(lambda z: op.matvec_A_hat(prob, z), b, lambda r: pc.apply_mg_ps_inv(prob, r), tol=1e-12)
-    assert rel(x.cpu().numpy(), xs) <= 1e-6
+    assert rel(x.cpu().numpy(), xs) <= 1e-7
     gm = P.Problem(N, n, 0.5, 1e-4, a_edges=a, precision="mixed")
     xm, im = gm.solve(dev(b), tol=1e-8)
-    assert im["relres"] <= 1e-8 and rel(xm.cpu().numpy(), xs) <= 1e-6
+    assert im["relres"] <= 1e-8 and rel(xm.cpu().numpy(), xs) <= 1e-7
+    assert im["iterations"] <= info["iterations"] + 2, (im, info)
 
 
 # ---------------------------------------------------------------- batches with shared launches
@@ -339,7 +434,8 @@ def test_batch_solve_uneven(P, precision, shapes):
         A = (lambda z: op.matvec_A(pr, z)) if pr.theta == 1.0 else (lambda z: op.matvec_A_hat(pr, z))
         assert np.linalg.norm(b - A(xo)) / np.linalg.norm(b) <= 1.5e-8    # oracle's FP64 residual
         x1, i1 = P.batch_solve([gp], [dev(b)], tol=1e-8, restart=16)      # the same instance alone
-        assert rel(xo, x1[0].cpu().numpy()) <= 1e-12 and i1[0]["iterations"] == info["iterations"]
+        assert_close(xo, x1[0].cpu().numpy(), 1e-12)
+        assert i1[0]["iterations"] == info["iterations"]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -432,4 +528,5 @@ def test_batch_mixing_zeta_families(P):
         assert info["relres"] <= 1e-8
         assert np.linalg.norm(b - op.matvec_A(prob, xo)) / np.linalg.norm(b) <= 1.5e-8
         x1, i1 = P.batch_solve([gp], [dev(b)], tol=1e-8, restart=16)
-        assert rel(xo, x1[0].cpu().numpy()) <= 1e-12 and i1[0]["iterations"] == info["iterations"]
+        assert_close(xo, x1[0].cpu().numpy(), 1e-12)
+        assert i1[0]["iterations"] == info["iterations"]
