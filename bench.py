@@ -45,7 +45,8 @@ def args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--serve-window", type=float, default=0.25,
+    ap.add_argument("--no-configs", action="store_true", help="skip the variable-a and uneven-batch figures")
+    ap.add_argument("--serve-window", type=float, default=0.5,
                     help="seconds of the serving trace replayed for the serving figures (0: skip)")
     ap.add_argument("--small", action="store_true", help="N=255, n=256 instead (quick checks only)")
     ap.add_argument("--no-neumann", action="store_true", help="skip the Example 3 (Neumann) figures")
@@ -174,72 +175,236 @@ def profile_traffic():
         return None
 
 
-SAMPLE = dict(N=255, n=256)
+SAMPLE_STEPS = 64     # time steps of the oracle's bounded sample (of the workload's 512)
 
 
-def cpu_baseline(W):
-    """The FP64 oracle as it stands, timed on the host cores on a bounded sample: the oracle's own
-    MINRES-|P_S| run for one iteration on the same problem family at N=255, n=256 (gamma = 1e-2),
-    divided by its number of preconditioner applies (one iteration = one apply and one product),
-    then scaled to the full workload by the ratio of unknowns (the oracle's cost is O(mn log mn),
-    so the linear scaling slightly favours the CPU)."""
-    import synth
-    from oracle import discretisation as ds
-    from oracle import krylov as kr
-    from oracle import operators as op
-    from oracle import precond as pc
-    N, n = SAMPLE["N"], SAMPLE["n"]
-    prob = ds.Problem(N, n, W["theta"], W["gammas"][0], W["T"])
-    b = ds.rhs_minres(prob, synth.random_target(N, n, seed=1), synth.manufactured_source(N, n))
-    cnt = {"M": 0}
-
-    def M(r):
-        cnt["M"] += 1
-        return pc.apply_abs_ps_inv(prob, r)
-
-    t0 = time.perf_counter()
-    kr.minres(lambda z: op.matvec_A(prob, z), b, M, fixed_iterations=1)
-    dt = time.perf_counter() - t0
-    scale = (W["N"] ** 2 * W["n"]) / (N * N * n)
-    return dt / cnt["M"] * scale, oracle_iterations(W)
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def oracle_iterations(W):
-    """Iteration count of the oracle's MINRES-|P_S| on this workload (gamma = 1e-2), written by
-    oracle/count_iterations.py; None if that file is absent."""
+    """FP64 oracle MINRES-|P_S| iteration counts on the full workload, per gamma, written by
+    oracle/count_iterations.py (a full-size oracle run); {} if that file is absent."""
     p = os.path.join(ROOT, "tests", "golden", f"oracle_iterations_N{W['N']}_n{W['n']}.txt")
+    out = {}
     try:
         for line in open(p):
             if line.strip() and not line.startswith("#"):
-                return int(line.split()[-1])
+                g, secs, its = line.split()
+                out[float(g)] = int(its)
     except Exception:
-        return None
-    return None
+        return {}
+    return out
+
+
+def oracle_sample(W, workers):
+    """The oracle as it stands, on a bounded sample of the workload: one MINRES-|P_S| iteration's
+    operator work (one |P_S|^-1 apply and one product A x, the dominant cost of an iteration) on the
+    workload's own grid (N = 511, gamma = 1e-2) with 64 of its 512 time steps, the library FFTs on
+    `workers` host threads (scipy.fft.set_workers; the oracle's code is unchanged).  Returns the
+    measured seconds of the sample and the seconds it scales to for one full-size iteration
+    (x 512/64: the oracle's work per unknown is nearly independent of n; the full-size figure in
+    tests/golden/oracle_iterations_N511_n512.txt, 84 s per iteration on one core, checks it)."""
+    import numpy as np
+    import scipy.fft
+    from oracle import discretisation as ds
+    from oracle import operators as op
+    from oracle import precond as pc
+    N, n = W["N"], SAMPLE_STEPS
+    prob = ds.Problem(N, n, W["theta"], W["gammas"][0], W["T"])
+    v = np.random.default_rng(0).standard_normal(2 * prob.m * n)
+    with scipy.fft.set_workers(workers):
+        t0 = time.perf_counter()
+        pc.apply_abs_ps_inv(prob, v)
+        op.matvec_A(prob, v)
+        dt = time.perf_counter() - t0
+    return dt, dt * W["n"] / n
+
+
+def cpu_solves_per_s(W, t_iter):
+    """Solves/s of the oracle on the workload (one solve per gamma) from the full-size time of one
+    iteration and the oracle's own full-size iteration count for each gamma."""
+    its = oracle_iterations(W)
+    n_its = [its.get(g) for g in W["gammas"]]
+    if not all(n_its):
+        return None, n_its
+    return len(W["gammas"]) / (t_iter * sum(n_its)), n_its
+
+
+def cpu_baseline(W):
+    workers = host_cores()
+    dt, t_iter = oracle_sample(W, workers)
+    val, n_its = cpu_solves_per_s(W, t_iter)
+    return {"value": val, "unit": "solves/s", "cores": workers, "kind": "oracle",
+            "sample": f"one oracle MINRES-|P_S| iteration's operator work (|P_S|^-1 apply + A x) at N=511 with "
+                      f"{SAMPLE_STEPS} of the 512 time steps, {dt:.1f} s measured on {workers} host threads; scaled "
+                      f"x{W['n'] // SAMPLE_STEPS} to {t_iter:.1f} s per full-size iteration, x the oracle's own "
+                      f"full-size iteration counts {n_its} (gamma {list(W['gammas'])})"}
 
 
 def reference_arm(a, W, rank, world):
-    """--impl reference: the FP64 oracle (CPU) timed on the host cores on the same workload; each
-    step is one bounded sample (one MINRES iteration's operator work at full size)."""
+    """--impl reference: the FP64 oracle (CPU) as it stands, on the host cores; each step is one
+    bounded sample (oracle_sample) of the workload, and the line's value is the solves/s it scales
+    to (cpu_solves_per_s).  Under torchrun only rank 0 runs."""
     if rank != 0:
         return
+    workers = host_cores()
     times = []
-    iters = oracle_iterations(W) or 0
     for s in range(a.warmup + a.steps):
-        dt, _ = cpu_baseline(W)
+        dt, t_iter = oracle_sample(W, workers)
         if s >= a.warmup:
-            times.append(dt)
-    t_iter = statistics.median(times)
-    val = 1.0 / (t_iter * iters) if iters else None
+            times.append((dt, t_iter))
+    dt = statistics.median(t for t, _ in times)
+    t_iter = statistics.median(t for _, t in times)
+    val, n_its = cpu_solves_per_s(W, t_iter)
+    sample = (f"per step: one oracle MINRES-|P_S| iteration's operator work (|P_S|^-1 apply + A x) at N=511 with "
+              f"{SAMPLE_STEPS} of the 512 time steps on {workers} host threads ({dt:.1f} s median); value = solves/s "
+              f"scaled x{W['n'] // SAMPLE_STEPS} to {t_iter:.1f} s per full-size iteration and x the oracle's own "
+              f"full-size iteration counts {n_its}")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": True,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W["name"], "sample": "one oracle MINRES iteration per step"},
-            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"oracle MINRES-|P_S| one-iteration run at N=255, n=256 per step, scaled by "
-                                       f"unknowns to {t_iter:.1f} s per full-size iteration, x {iters} "
-                                       f"oracle iterations"},
+            "config": {"workload": W["name"], "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": workers, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def solution_sample(tag):
+    """(size, positions, values) of an FP64 oracle solution sample stored in tests/golden (a data
+    file the oracle's reference_solutions script writes), or None."""
+    import numpy as np
+    p = os.path.join(GOLDEN, f"solution_sample_{tag}.txt")
+    if not os.path.exists(p):
+        return None
+    size, pos, val = None, [], []
+    for line in open(p):
+        if line.startswith("#") or not line.strip():
+            continue
+        a_, b_ = line.split()
+        if a_ == "size":
+            size = int(b_)
+        elif a_ != "norm2":
+            pos.append(int(a_)); val.append(float(b_))
+    return size, np.array(pos), np.array(val)
+
+
+def forward_error(tag, x):
+    """||x[S] - x*[S]|| / ||x*[S]|| on the stored positions S of the oracle solution x* (tag), read
+    from the device without copying the whole vector; None without a stored sample."""
+    import numpy as np
+    import torch
+    s = solution_sample(tag)
+    if s is None or x.numel() != s[0]:
+        return None
+    xs = x[torch.from_numpy(s[1]).to(x.device)].cpu().numpy()
+    return float(np.linalg.norm(xs - s[2]) / np.linalg.norm(s[2]))
+
+
+def timed(torch, stream, fn, reps=1):
+    """Mean milliseconds of fn() over reps calls, CUDA events on `stream` (after the caller's warm-up)."""
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = [fn() for _ in range(reps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def config2_figures(P, synth, torch, stream):
+    """The variable-coefficient Crank-Nicolson workload (N = 255, n = 256, gamma = 1e-4,
+    a = 1 + 0.5 sin sin): FGMRES(30) with two multigrid V-cycles per shifted solve, mixed (FP32
+    multigrid) and FP64, to relres 1e-8; solve time from CUDA events after one warm-up solve."""
+    inst = synth.config2()
+    out = {"workload": f"N={inst.N} n={inst.n} Crank-Nicolson gamma={inst.gamma:g} a=1+0.5 sin(pi x1) sin(pi x2), "
+                       "FGMRES(30) + 2 V-cycles", "unknowns": 2 * inst.N * inst.N * inst.n}
+    g = torch.from_numpy(inst.g.ravel()).cuda(); f = torch.from_numpy(inst.f.ravel()).cuda()
+    its = {}
+    for prec in ("mixed", "fp64"):
+        pr = P.Problem(inst.N, inst.n, inst.theta, inst.gamma, a_edges=inst.a_edges, mg_cycles=2, precision=prec,
+                       stream=stream)
+        b = pr.assemble_rhs(g, f, op="Ahat")
+        x = pr._empty()
+        pr.solve(b, x, tol=1e-8)
+        ms, infos = timed(torch, stream, lambda: pr.solve(b, x, tol=1e-8)[1])
+        its[prec] = infos[-1]["iterations"]
+        out[prec] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iterations": its[prec],
+                     "relres": infos[-1]["relres"], "forward_error_vs_oracle": forward_error("cfg2", x)}
+        pr.close(); del b, x
+    out["within_plus2"] = its["mixed"] <= its["fp64"] + 2
+    return out
+
+
+def config3_figures(P, synth, torch, stream):
+    """The uneven batch: 64 independent problems (N in {63..255}, n in {32..256}, theta in {1, 1/2},
+    gamma log-uniform in [1e-6, 1e-1]) solved in mixed precision to relres 1e-8 with shared launches
+    (pcb_batch_solve), against the same problems one at a time (mixed and FP64)."""
+    insts = synth.config3()
+    probs, bs = [], []
+    for inst in insts:
+        pr = P.Problem(inst.N, inst.n, inst.theta, inst.gamma, precision="mixed", stream=stream)
+        probs.append(pr)
+        bs.append(pr.assemble_rhs(torch.from_numpy(inst.g.ravel()).cuda(), torch.from_numpy(inst.f.ravel()).cuda(),
+                                  op="A" if inst.theta == 1.0 else "Ahat"))
+    unknowns = sum(p.size for p in probs)
+    xs = [p._empty() for p in probs]
+    P.batch_solve(probs, bs, xs, tol=1e-8, restart=16)
+    ms_b, res = timed(torch, stream, lambda: P.batch_solve(probs, bs, xs, tol=1e-8, restart=16)[1])
+    infos = res[-1]
+    errs = {k: forward_error(f"cfg3_{k}", xs[k]) for k in (0, 2, 3, 4)}
+    ms_1, _ = timed(torch, stream, lambda: [p.solve(b, x, tol=1e-8, restart=16) for p, b, x in zip(probs, bs, xs)])
+    fp = [P.Problem(i.N, i.n, i.theta, i.gamma, precision="fp64", stream=stream) for i in insts]
+    its64 = [p.solve(b, x, tol=1e-8, restart=16)[1]["iterations"] for p, b, x in zip(fp, bs, xs)]
+    ms_64, _ = timed(torch, stream, lambda: [p.solve(b, x, tol=1e-8, restart=16) for p, b, x in zip(fp, bs, xs)])
+    itsm = [i["iterations"] for i in infos]
+    for p in probs + fp:
+        p.close()
+    return {"workload": f"{len(insts)} uneven instances (synth.config3), {unknowns:.3g} unknowns in all, mixed",
+            "batched": {"solves_per_s": len(insts) / (ms_b / 1e3), "unknowns_per_s": unknowns / (ms_b / 1e3),
+                        "ms": ms_b, "max_relres": max(i["relres"] for i in infos)},
+            "one_at_a_time_mixed": {"solves_per_s": len(insts) / (ms_1 / 1e3), "ms": ms_1},
+            "one_at_a_time_fp64": {"solves_per_s": len(insts) / (ms_64 / 1e3), "ms": ms_64},
+            "iterations_mixed_minus_fp64_max": max(m - f for m, f in zip(itsm, its64)),
+            "within_plus2_count": sum(m <= f + 2 for m, f in zip(itsm, its64)),
+            "forward_error_vs_oracle_sample": errs}
+
+
+def serving_figures(synth, torch, window):
+    """A window of the serving trace (Poisson arrivals at 200/s; 95% of requests sized like the
+    uneven batch, 5% at N = 511, n = 512; random g and gamma), served by the continuous-batching
+    server in mixed precision under a 150 GB budget, against single FP64 solves in arrival order.
+    The offered 200/s exceeds what one GPU sustains, so the same requests are also replayed at
+    the sustained rate (arrivals slowed to 90% of the measured throughput) for steady-state
+    latencies."""
+    from paper_2406_00952_gb300 import serve
+    trace = synth.serving_trace(duration_s=window)
+    reqs = serve.build_requests(trace)
+    torch.cuda.synchronize()
+    srv = serve.run(reqs, budget_bytes=150 << 30, max_slots=32, precision="mixed")
+    rate = srv["solves_per_s"]
+    scale = 200.0 / (0.9 * rate)
+    for r in reqs:
+        r.x = None
+    for r, q in zip(reqs, trace):
+        r.arrival_s = q.arrival_s * scale
+    steady = serve.run(reqs, budget_bytes=150 << 30, max_slots=32, precision="mixed")
+    for r, q in zip(reqs, trace):
+        r.arrival_s = q.arrival_s
+    base = serve.one_at_a_time(reqs, precision="fp64")
+    keys = ("solves_per_s", "p50_latency_s", "p99_latency_s")
+    return {"trace": f"Poisson 200/s, first {window:g} s ({len(reqs)} requests, {sum(r.N == 511 for r in reqs)} at "
+                     f"N=511 n=512), HBM budget 150 GB", "offered_rate_hz": 200.0,
+            "solves_per_s": srv["solves_per_s"], "p50_latency_s": srv["p50_latency_s"],
+            "p99_latency_s": srv["p99_latency_s"], "max_relres": srv["max_relres"], "failed": srv["failed"],
+            "sustained": {"arrival_rate_hz": 200.0 / scale, **{k: steady[k] for k in keys},
+                          "failed": steady["failed"]},
+            "fp64_one_at_a_time": {k: base[k] for k in keys}}
 
 
 def neumann_figures(P, synth, np, torch, stream, steps):
@@ -426,11 +591,13 @@ def main():
     achieved = alg_bytes / (pms / applies / 1e3) / 1e9
     mv_ach = 16.0 * unknowns / (mvms / mvs / 1e3) / 1e9
     iters = [i["iterations"] for i in infos]
+    # forward error of the mixed solutions against the oracle's (sampled positions, relres 1e-12 truth)
+    fe_mixed = [forward_error(f"cfg1_g{gam:g}", x) for gam, x in zip(W["gammas"], xs)] if not a.small else None
 
     # plain FP64 GPU solver on the same inputs (one solve per gamma)
     fp64 = None
     if not a.no_fp64:
-        t_fp = 0.0; it_fp = []
+        t_fp = 0.0; it_fp = []; fe_fp = []
         for gam, b in zip(W["gammas"], bs):
             pr = P.Problem(N, n, W["theta"], gam, W["T"], precision="fp64", stream=stream)
             x = pr._empty()
@@ -441,8 +608,10 @@ def main():
             torch.cuda.synchronize()
             t_fp += time.perf_counter() - t0
             it_fp.append(inf["iterations"])
+            fe_fp.append(forward_error(f"cfg1_g{gam:g}", x))
             pr.close(); del x
-        fp64 = {"value": len(W["gammas"]) / t_fp, "unit": "solves/s", "iterations": it_fp}
+        fp64 = {"value": len(W["gammas"]) / t_fp, "unit": "solves/s", "iterations": it_fp,
+                "forward_error_vs_oracle": fe_fp}
 
     # end to end through the host-buffer C-ABI call: b from pinned host memory, x back to host
     e2e = None
@@ -462,22 +631,12 @@ def main():
         e2e = {"value": len(W["gammas"]) * a.e2e_steps * world / dt, "unit": "solves/s",
                "h2d_bytes_per_step": nb * len(W["gammas"]), "d2h_bytes_per_step": nb * len(W["gammas"])}
 
-    # serving: a window of the Poisson request trace (uneven grids, 5% at N=511 n=512), served by the
-    # continuous-batching server in mixed precision, against single FP64 solves in arrival order
+    # serving: a window of the Poisson request trace, served by the continuous-batching server
     serving = None
     if rank == 0 and a.serve_window > 0:
-        from paper_2406_00952_gb300 import serve
-        trace = synth.serving_trace(duration_s=a.serve_window)
-        reqs = serve.build_requests(trace)
-        torch.cuda.synchronize()
-        srv = serve.run(reqs, budget_bytes=150 << 30, max_slots=32, precision="mixed")
-        base = serve.one_at_a_time(reqs, precision="fp64")
-        serving = {"trace": f"Poisson 200/s, first {a.serve_window:g} s ({len(reqs)} requests, "
-                            f"{sum(r.N == 511 for r in reqs)} at N=511 n=512), HBM budget 150 GB",
-                   "solves_per_s": srv["solves_per_s"], "p50_latency_s": srv["p50_latency_s"],
-                   "p99_latency_s": srv["p99_latency_s"], "max_relres": srv["max_relres"], "failed": srv["failed"],
-                   "fp64_one_at_a_time": {k: base[k] for k in ("solves_per_s", "p50_latency_s", "p99_latency_s")}}
-        del reqs
+        serving = serving_figures(synth, torch, a.serve_window)
+    cfg2 = config2_figures(P, synth, torch, stream) if rank == 0 and not a.no_configs else None
+    cfg3 = config3_figures(P, synth, torch, stream) if rank == 0 and not a.no_configs else None
 
     # Example 3 (homogeneous Neumann, a = 1e-3, Crank-Nicolson, gamma = 1e-2) at the size of
     # Table 4's finest row: 257 nodes per side (h = 1/256), n = 256, GMRES-P_S with the DCT-I passes
@@ -494,12 +653,7 @@ def main():
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
-        dt, it_o = cpu_baseline(W)
-        it_use = it_o if it_o else (fp64["iterations"][0] if fp64 else statistics.median(iters))
-        cpu = {"value": 1.0 / (dt * it_use), "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle MINRES-|P_S| one-iteration run at N=255, n=256 (gamma=1e-2), scaled by "
-                         f"unknowns to {dt:.1f} s per full-size iteration, x {it_use} iterations"
-                         + ("" if it_o else " (FP64 GPU iteration count; oracle count file absent)")}
+        cpu = cpu_baseline(W)
 
     if rank == 0:
         line = {
@@ -522,6 +676,13 @@ def main():
                                             "peak": 625.0,
                                             "frac": 10.0 * unknowns / (mvms / mvs / 1e3) / 1e9 / 625.0}},
             "fp64_gpu": fp64,
+            "mixed_vs_fp64": [{"gamma": gam, "mixed_iterations": im, "fp64_iterations": i64,
+                               "within_plus2": im <= i64 + 2, "mixed_forward_error_vs_oracle": fe}
+                              for gam, im, i64, fe in zip(W["gammas"], iters[:len(W["gammas"])],
+                                                          fp64["iterations"] if fp64 else [None] * len(W["gammas"]),
+                                                          fe_mixed or [None] * len(W["gammas"]))] if fp64 else None,
+            "config2_variable_a": cfg2,
+            "config3_uneven_batch": cfg3,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -222,16 +222,23 @@ int pcb_batch_solve(pcb_problem* const* problems, int count, const pcb_solve_opt
 /* ---- continuous-batching server -------------------------------------------------------- */
 /* Requests (independent control solves of any supported size) are queued with pcb_server_submit
  * and advanced by pcb_server_step.  Each step retires finished requests (their solution is copied
- * to the caller's host buffer), admits queued requests while a slot is free and the device bytes
- * of the admitted requests stay within the budget, and advances every admitted request by one
+ * to the caller's host buffer), admits queued requests, and advances every admitted request by one
  * Krylov iteration (or one refinement transition) in launches shared by all admitted requests of
  * the same method.  Krylov state stays on the device from admission to retirement.  Each request
  * runs the same rounds as pcb_batch_solve, so its result does not depend on which other requests
- * share the launches (reductions are per request and in a fixed order). */
+ * share the launches (reductions are per request and in a fixed order).
+ * Memory: pcb_server_create reserves the budget once (at most the device's free memory less 2 GiB);
+ * an admitted request's workspace is one block of that reservation (its tables, preconditioner
+ * scratch, Krylov vectors and device copies of b and x), returned when it retires, so admission and
+ * retirement allocate and free no device memory.
+ * Admission: queued requests are considered in arrival order, and each one that finds a free slot of
+ * its method and a block of the reservation is admitted, so a large request that does not fit yet
+ * does not hold back the small ones behind it; once the oldest queued request has been passed over
+ * for 64 steps, nothing else is admitted until it is. */
 typedef struct pcb_server pcb_server;
 
 typedef struct {
-  long long budget_bytes; /* device bytes the admitted requests may hold in total (> 0)           */
+  long long budget_bytes; /* device bytes reserved for the admitted requests' workspaces (> 0)    */
   int max_slots;          /* concurrent requests per method (1..256)                              */
   int precision;          /* pcb_precision of every request                                       */
   double tol;             /* target true relative residual; <= 0 => 1e-8                          */
@@ -254,7 +261,8 @@ void pcb_server_destroy(pcb_server* s);
  * the server).  op_rhs_host: the 2*m*n right-hand side for the method pcb_create would pick (A for
  * theta = 1, A_hat otherwise), host memory read when the request is admitted; x_host: 2*m*n host
  * values written when it retires.  Both must stay valid until the request is reported done.
- * Errors: INVALID_ARG, UNSUPPORTED, TOO_LARGE (the request alone exceeds the budget). */
+ * Errors: INVALID_ARG, UNSUPPORTED, TOO_LARGE (the request's workspace alone exceeds the
+ * reservation). */
 int pcb_server_submit(pcb_server* s, const pcb_desc* desc, const double* rhs_host, double* x_host, long long tag);
 /* One scheduling step (blocks while it runs).  Up to max_done retired requests are written to done[];
  * *n_done, *n_active and *n_queued report the counts after the step. */

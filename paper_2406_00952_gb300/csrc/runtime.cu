@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <vector>
@@ -535,8 +536,8 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
   std::vector<Geom> gs(1, g);
   std::vector<int> staging;
   std::memset(&p->B, 0, sizeof(Batch));
-  if ((rc = fill_batch(p->B, gs, p->doff, 0, staging)) != PCB_OK) return fail(rc);
-  if (cudaDeviceSynchronize() != cudaSuccess) return fail(PCB_ERR_CUDA);
+  if ((rc = fill_batch(p->B, gs, p->doff, p->stream, staging)) != PCB_OK) return fail(rc);
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(PCB_ERR_CUDA);   // staging is read
   p->B.G = p->dG; p->B.S = p->dS; p->B.Sc = p->dSc; p->B.active = nullptr; p->B.partial = p->partial;
   p->B.stream = p->stream;
   *out = p;
@@ -1404,11 +1405,103 @@ struct SrvReq {
   long long tag;
 };
 
+// First-fit sub-allocator over one device reservation: the server reserves its budget once, at
+// creation, and carves each admitted request's workspace (one block) out of it, so admitting and
+// retiring requests calls neither cudaMalloc nor cudaFree (both of which can stall the device).
+// Blocks are 256-byte aligned; adjacent free blocks merge.  Blocks above an eighth of the
+// reservation are placed from the top down and the rest from the bottom up, so that the many small
+// workspaces do not fragment the room the few large ones need.
+class DevArena {
+ public:
+  ~DevArena() { if (base_) cudaFree(base_); }
+  cudaError_t reserve(size_t bytes) {
+    bytes &= ~(size_t)255;
+    const cudaError_t e = cudaMalloc(&base_, bytes);
+    if (e != cudaSuccess) { base_ = nullptr; return e; }
+    size_ = bytes;
+    free_.clear(); used_.clear();
+    free_[0] = bytes;
+    return cudaSuccess;
+  }
+  size_t size() const { return size_; }
+  void* alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (!base_ || !bytes) return nullptr;
+    if (bytes > size_ / 8) {
+      for (auto it = free_.rbegin(); it != free_.rend(); ++it) {
+        if (it->second < bytes) continue;
+        const size_t off = it->first + it->second - bytes;
+        if (it->second == bytes) free_.erase(it->first); else it->second -= bytes;
+        used_[off] = bytes;
+        return base_ + off;
+      }
+      return nullptr;
+    }
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      const size_t off = it->first, len = it->second;
+      free_.erase(it);
+      if (len > bytes) free_[off + bytes] = len - bytes;
+      used_[off] = bytes;
+      return base_ + off;
+    }
+    return nullptr;
+  }
+  void release(void* ptr) {
+    if (!ptr) return;
+    const size_t off = (size_t)((char*)ptr - base_);
+    auto u = used_.find(off);
+    if (u == used_.end()) return;
+    size_t o = off, len = u->second;
+    used_.erase(u);
+    auto next = free_.lower_bound(o);
+    if (next != free_.end() && next->first == o + len) { len += next->second; next = free_.erase(next); }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == o) { o = prev->first; len += prev->second; free_.erase(prev); }
+    }
+    free_[o] = len;
+  }
+
+ private:
+  char* base_ = nullptr;
+  size_t size_ = 0;
+  std::map<size_t, size_t> free_;   // offset -> length
+  std::map<size_t, size_t> used_;
+};
+
+// One request's workspace inside its arena block: tables, preconditioner scratch, the MINRES
+// vectors, the refinement pair, the GMRES bases (GMRES requests), and the right-hand side and
+// solution; every part 256-byte aligned.
+struct SrvLayout {
+  size_t tab, scr, minres, mixed, gmres, io, total;
+  TableLayout tl;
+};
+
+size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+void srv_layout(const Geom& g, int method, int restart, SrvLayout& L) {
+  const size_t vb = (size_t)2 * g.mn * sizeof(double);
+  size_t o = 0;
+  L.tab = o; o += up256(table_layout(g, L.tl));
+  L.scr = o; o += up256(std::max<size_t>(vb, (size_t)16 * g.n * g.N * (size_t)g.lr));
+  L.minres = o; o += 7 * vb;
+  L.mixed = o; o += 2 * vb;
+  L.gmres = o; o += method == PCB_MINRES ? 0 : (size_t)(2 * restart + 2) * vb;
+  L.io = o; o += 2 * vb;
+  L.total = up256(o);
+}
+
+int srv_method(const pcb_desc& d) { return d.theta == 1.0 && d.bc != PCB_BC_NEUMANN ? PCB_MINRES : PCB_GMRES; }
+
 struct SrvSlot {
   int phase = PH_FREE;
-  pcb_problem* p = nullptr;
   SrvReq req;
-  double* b = nullptr;   // device copies (the problem's host-io staging)
+  Geom g;                   // the request's geometry, device pointers into its block
+  void* block = nullptr;    // its workspace in the server's arena
+  unsigned char* stage = nullptr;   // page-locked staging of its tables (kept with the slot)
+  size_t stage_bytes = 0;
+  double* b = nullptr;      // device copies of the right-hand side and the solution
   double* x = nullptr;
   double bnorm = 0, rnorm = 0;
   int iters = 0, sweeps = 0, status = PCB_OK;
@@ -1434,21 +1527,23 @@ struct SrvGroup {
 struct pcb_server {
   pcb_server_opts o;
   cudaStream_t st;
-  long long used = 0;
-  std::vector<SrvReq> queue;   // FIFO
+  DevArena arena;
+  std::vector<SrvReq> queue;   // arrival order; admitted entries are marked taken
+  std::vector<char> taken;
   size_t qhead = 0;
+  int head_wait = 0;           // steps the oldest queued request has been passed over
   SrvGroup grp[2];             // 0: MINRES (theta = 1), 1: GMRES
   std::vector<pcb_server_done> done;
 };
 
 namespace {
 
-long long srv_estimate(const pcb_desc* d, int method, int restart) {
-  const long long mn = (long long)d->N * d->N * d->n;
-  const long long vec = 16 * mn;                         // one 2mn FP64 vector
-  long long nv = 1 + 7 + 2 + 2;                          // scratch + MINRES + refinement + staging
-  if (method != PCB_MINRES) nv += 2 * restart + 2;
-  return nv * vec + (4 << 20);
+long long srv_bytes(const pcb_desc* d, int restart) {
+  Geom g;
+  init_geom(d, g);
+  SrvLayout L;
+  srv_layout(g, srv_method(*d), restart, L);
+  return (long long)L.total;
 }
 
 int srv_upload(SrvGroup& G, cudaStream_t st) {
@@ -1492,9 +1587,14 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
   const double tol = S->o.tol;
   const int prec = S->o.precision, restart = S->o.restart;
   int rc;
-  pcb_problem* p0 = nullptr;
-  for (auto& s : G.slots) if (s.p) { p0 = s.p; break; }
-  if (!p0) return PCB_OK;
+  bool any = false;
+  for (auto& s : G.slots) any |= s.phase != PH_FREE;
+  if (!any) return PCB_OK;
+  // server requests have a constant coefficient: the transform route of the preconditioner
+  auto precond = [&](int in_slot, int out_slot) {
+    const cudaError_t e = launch_precond_fast(G.B, G.kind, prec, in_slot, out_slot);
+    return e == cudaSuccess ? PCB_OK : cuda_status(e);
+  };
   if ((rc = srv_upload(G, st))) return rc;
   // ---- round end: x += d, r = b - op x
   if ((rc = srv_mask(G, st, PH_END)) < 0) return rc;
@@ -1541,7 +1641,7 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
       CK(launch_axpby(G.B, AX_ZERO, -1, SL_W2, -1));
       CK(launch_axpby(G.B, AX_COPY, SL_BI, SL_R1, -1));
       CK(launch_axpby(G.B, AX_COPY, SL_BI, SL_R2, -1));
-      if ((rc = apply_precond(p0, G.B, G.kind, prec, SL_R2, SL_Y))) return rc;
+      if ((rc = precond(SL_R2, SL_Y))) return rc;
       CK(launch_dot(G.B, SL_R2, SL_Y));
       CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_MINRES_INIT, tol, 0, 0));
     } else {
@@ -1563,7 +1663,7 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
     }
     // device-side slot pointers may have been set by setslot: refresh the host mirror from the rule
     for (int k = 0; k < G.cap; ++k)
-      if (G.method != PCB_MINRES && G.slots[k].phase == PH_ITER && G.slots[k].p) G.hS[k].v[SL_VJ] = G.hS[k].v[SL_VBASE];
+      if (G.method != PCB_MINRES && G.slots[k].phase == PH_ITER) G.hS[k].v[SL_VJ] = G.hS[k].v[SL_VBASE];
     if ((rc = srv_upload(G, st))) return rc;
   }
   // ---- one iteration
@@ -1575,7 +1675,7 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
       CK(launch_matvec(G.B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
       CK(launch_reduce(G.B, G.B.off_mv, 1, 0, SS_MINRES_ALFA, tol, 0, 0));
       CK(launch_axpby(G.B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
-      if ((rc = apply_precond(p0, G.B, G.kind, prec, SL_R1, SL_YO))) return rc;
+      if ((rc = precond(SL_R1, SL_YO))) return rc;
       CK(launch_dot(G.B, SL_R1, SL_YO));
       CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_MINRES_GIVENS, tol, 0, 0));
       CK(launch_minres_wx(G.B, SL_Y, SL_W, SL_W2, SL_XI));
@@ -1604,7 +1704,7 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
         H.v[SL_VJ1] = H.v[SL_VBASE] + (size_t)(j + 1) * nv;
       }
       if ((rc = srv_upload(G, st))) return rc;
-      if ((rc = apply_precond(p0, G.B, G.kind, prec, SL_VJ, SL_ZJ))) return rc;
+      if ((rc = precond(SL_VJ, SL_ZJ))) return rc;
       CK(launch_matvec(G.B, G.op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
       for (int pass = 0; pass < 2; ++pass) {
         CK(launch_multidot(G.B, SL_VBASE, -1, SL_VJ1, jmax));
@@ -1655,6 +1755,17 @@ int pcb_server_create(const pcb_server_opts* o, pcb_server** out) {
   if (S->o.restart <= 0) S->o.restart = 16;
   S->o.restart = std::min(S->o.restart, PCB_MAX_RESTART);
   S->st = (cudaStream_t)o->stream;
+  if (upload_constants() != cudaSuccess) { delete S; return PCB_ERR_CUDA; }
+  // the budget is reserved here, once (at most what the device has free, less 2 GiB of headroom)
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); delete S; return PCB_ERR_CUDA; }
+  const size_t head = (size_t)2 << 30;
+  const size_t want = std::min<size_t>((size_t)o->budget_bytes, free_b > head ? free_b - head : 0);
+  if (want < ((size_t)1 << 20) || S->arena.reserve(want) != cudaSuccess) {
+    cudaGetLastError();
+    delete S;
+    return PCB_ERR_OUT_OF_MEMORY;
+  }
   for (int q = 0; q < 2; ++q) {
     SrvGroup& G = S->grp[q];
     G.method = q == 0 ? PCB_MINRES : PCB_GMRES;
@@ -1691,11 +1802,11 @@ void pcb_server_destroy(pcb_server* S) {
   cudaStreamSynchronize(S->st);
   for (int q = 0; q < 2; ++q) {
     SrvGroup& G = S->grp[q];
-    for (auto& s : G.slots) if (s.p) pcb_destroy(s.p);
+    for (auto& s : G.slots) if (s.stage) cudaFreeHost(s.stage);
     cudaFree(G.dG); cudaFree(G.dS); cudaFree(G.dSc); cudaFree(G.dAct); cudaFree(G.dOff); cudaFree(G.dPart);
     cudaFree(G.dTol); cudaFreeHost(G.hSc); cudaFreeHost(G.hAct); cudaFreeHost(G.hTol); cudaFreeHost(G.hSpin);
   }
-  delete S;
+  delete S;   // the arena's reservation is freed with it
 }
 
 int pcb_server_submit(pcb_server* S, const pcb_desc* d, const double* rhs, double* x, long long tag) {
@@ -1706,85 +1817,125 @@ int pcb_server_submit(pcb_server* S, const pcb_desc* d, const double* rhs, doubl
   dd.stream = (void*)S->st;
   const int rc = validate_desc(&dd);
   if (rc != PCB_OK) return rc;
-  const int method = dd.theta == 1.0 && dd.bc != PCB_BC_NEUMANN ? PCB_MINRES : PCB_GMRES;
-  if (srv_estimate(&dd, method, S->o.restart) > S->o.budget_bytes) return PCB_ERR_TOO_LARGE;
+  const long long need = srv_bytes(&dd, S->o.restart);
+  if (need > S->o.budget_bytes || need > (long long)S->arena.size()) return PCB_ERR_TOO_LARGE;
   S->queue.push_back(SrvReq{dd, rhs, x, tag});
+  S->taken.push_back(0);
   return PCB_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// Admit request r into free slot k of group G: carve its workspace from the arena (nullptr
+// returned when no block fits), stage and upload its tables, copy its right-hand side.
+int srv_admit(pcb_server* S, SrvGroup& G, int k, const SrvReq& r, bool* fitted) {
+  *fitted = false;
+  Geom g;
+  init_geom(&r.desc, g);
+  SrvLayout L;
+  srv_layout(g, G.method, S->o.restart, L);
+  unsigned char* blk = (unsigned char*)S->arena.alloc(L.total);
+  if (!blk) return PCB_OK;
+  *fitted = true;
+  SrvSlot& s = G.slots[k];
+  const size_t tab_bytes = L.tl.bytes;
+  if (s.stage_bytes < tab_bytes) {
+    if (s.stage) cudaFreeHost(s.stage);
+    s.stage = nullptr; s.stage_bytes = 0;
+    const size_t sz = std::max<size_t>(tab_bytes, 192 * 1024);
+    if (cudaMallocHost(&s.stage, sz) != cudaSuccess) { cudaGetLastError(); S->arena.release(blk); return PCB_ERR_OUT_OF_MEMORY; }
+    s.stage_bytes = sz;
+  }
+  fill_tables(&r.desc, g, L.tl, s.stage);
+  bind_tables(g, L.tl, blk + L.tab);
+  g.scratch = blk + L.scr;
+  const size_t nv = (size_t)2 * g.mn;
+  s.phase = PH_START; s.req = r; s.g = g; s.block = blk; s.first = true;
+  s.b = (double*)(blk + L.io); s.x = s.b + nv;
+  s.bnorm = s.rnorm = 0; s.iters = s.sweeps = 0; s.status = PCB_OK;
+  s.bytes = (long long)L.total;
+  CK(cudaMemcpyAsync(blk + L.tab, s.stage, tab_bytes, cudaMemcpyHostToDevice, S->st));
+  CK(copy_host(s.b, r.rhs, nv, true, S->st, nullptr));
+  CK(cudaMemsetAsync(s.x, 0, nv * sizeof(double), S->st));
+  double* v = (double*)(blk + L.minres);
+  double* mixed = (double*)(blk + L.mixed);
+  CK(cudaMemcpyAsync(mixed, s.b, nv * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
+  Slots& H = G.hS[k];
+  std::memset(&H, 0, sizeof(H));
+  H.v[SL_R1] = v; H.v[SL_R2] = v + nv; H.v[SL_Y] = v + 2 * nv; H.v[SL_YO] = v + 3 * nv; H.v[SL_Q] = v + 4 * nv;
+  H.v[SL_W] = v + 5 * nv; H.v[SL_W2] = v + 6 * nv; H.v[SL_R] = v;
+  H.v[SL_BI] = mixed; H.v[SL_XI] = mixed + nv;
+  if (G.method != PCB_MINRES) {
+    double* gm = (double*)(blk + L.gmres);
+    H.v[SL_VBASE] = gm; H.v[SL_ZBASE] = gm + (size_t)(S->o.restart + 1) * nv;
+  }
+  H.v[SL_X] = s.x; H.v[SL_B] = s.b;
+  G.hG[k] = g;
+  G.dirty = true;
+  return PCB_OK;
+}
+
+constexpr int kSrvScan = 256;        // queued requests a step looks at for admission
+constexpr int kSrvMaxPass = 64;      // steps the oldest request may be passed over
+
+}  // namespace
+
+extern "C" {
 
 int pcb_server_step(pcb_server* S, pcb_server_done* done, int max_done, int* n_done, int* n_active, int* n_queued) {
   if (!S) return PCB_ERR_INVALID_ARG;
   int rc = PCB_OK;
-  // retire
+  // retire: copy the solution to the caller's buffer, return the workspace to the arena
+  bool retired = false;
   for (int q = 0; q < 2; ++q) {
     SrvGroup& G = S->grp[q];
     for (int k = 0; k < G.cap; ++k) {
       SrvSlot& s = G.slots[k];
       if (s.phase != PH_DONE) continue;
-      const size_t vb = (size_t)2 * s.p->g.mn * sizeof(double);
-      if (copy_host(s.req.x, s.x, vb / sizeof(double), false, S->st, nullptr) != cudaSuccess ||
-          cudaStreamSynchronize(S->st) != cudaSuccess)
-        return PCB_ERR_CUDA;
+      if (copy_host(s.req.x, s.x, (size_t)2 * s.g.mn, false, S->st, nullptr) != cudaSuccess) return PCB_ERR_CUDA;
+      retired = true;
       pcb_server_done r;
       r.tag = s.req.tag; r.status = s.status; r.iterations = s.iters; r.refinements = s.sweeps;
       r.relres = s.bnorm > 0 ? s.rnorm / s.bnorm : 0.0;
       S->done.push_back(r);
-      S->used -= s.bytes;
-      pcb_destroy(s.p);
-      s = SrvSlot();
+      s.phase = PH_FREE;
       std::memset(&G.hG[k], 0, sizeof(Geom));
       std::memset(&G.hS[k], 0, sizeof(Slots));
       G.dirty = true;
     }
   }
-  // admit (FIFO; a request waits for a slot of its method and room in the budget)
-  while (S->qhead < S->queue.size()) {
-    SrvReq& r = S->queue[S->qhead];
-    const int q = r.desc.theta == 1.0 && r.desc.bc != PCB_BC_NEUMANN ? 0 : 1;
-    SrvGroup& G = S->grp[q];
+  // the copies above end before any retired block is handed out again or reported done
+  if (retired && cudaStreamSynchronize(S->st) != cudaSuccess) return PCB_ERR_CUDA;
+  for (int q = 0; q < 2; ++q)
+    for (auto& s : S->grp[q].slots)
+      if (s.phase == PH_FREE && s.block) { S->arena.release(s.block); s.block = nullptr; }
+  // admit: the queued requests in arrival order, each one that finds a free slot of its method and
+  // a block in the arena; once the oldest has been passed over kSrvMaxPass steps, only it may enter
+  const bool head_only = S->head_wait >= kSrvMaxPass;
+  bool head_admitted = false;
+  int scanned = 0;
+  for (size_t i = S->qhead; i < S->queue.size() && scanned < kSrvScan; ++i) {
+    if (S->taken[i]) continue;
+    ++scanned;
+    const SrvReq& r = S->queue[i];
+    SrvGroup& G = S->grp[srv_method(r.desc) == PCB_MINRES ? 0 : 1];
     int free_k = -1;
-    for (int k = 0; k < G.cap; ++k) if (G.slots[k].phase == PH_FREE) { free_k = k; break; }
-    const long long est = srv_estimate(&r.desc, G.method, S->o.restart);
-    if (free_k < 0 || S->used + est > S->o.budget_bytes) break;
-    pcb_problem* p = nullptr;
-    if ((rc = pcb_create(&r.desc, &p)) != PCB_OK) return rc;
-    SolveCfg c;
-    pcb_solve_opts so;
-    std::memset(&so, 0, sizeof(so));
-    so.restart = S->o.restart;
-    resolve_defaults(p, &so, c);
-    if ((rc = ensure_minres(p)) || (rc = ensure_mixed(p)) || (G.method != PCB_MINRES && (rc = ensure_gmres(p, S->o.restart)))) {
-      pcb_destroy(p);
-      return rc;
+    for (int k = 0; k < G.cap; ++k) if (G.slots[k].phase == PH_FREE && !G.slots[k].block) { free_k = k; break; }
+    bool fitted = false;
+    if (free_k >= 0 && (rc = srv_admit(S, G, free_k, r, &fitted)) != PCB_OK) return rc;
+    if (fitted) {
+      S->taken[i] = 1;
+      if (i == S->qhead) head_admitted = true;
     }
-    const size_t nv = (size_t)2 * p->g.mn;
-    if (!p->host_io) {
-      if (cudaMalloc(&p->host_io, 2 * nv * sizeof(double)) != cudaSuccess) { cudaGetLastError(); pcb_destroy(p); return PCB_ERR_OUT_OF_MEMORY; }
-      p->bytes += 2 * nv * sizeof(double);
-    }
-    SrvSlot& s = G.slots[free_k];
-    s = SrvSlot();
-    s.p = p; s.req = r; s.b = p->host_io; s.x = p->host_io + nv; s.phase = PH_START; s.first = true;
-    s.bytes = p->bytes;
-    S->used += s.bytes;
-    if (copy_host(s.b, r.rhs, nv, true, S->st, nullptr) != cudaSuccess ||
-        cudaMemsetAsync(s.x, 0, nv * sizeof(double), S->st) != cudaSuccess ||
-        cudaMemcpyAsync(p->vec_mixed, s.b, nv * sizeof(double), cudaMemcpyDeviceToDevice, S->st) != cudaSuccess)
-      return PCB_ERR_CUDA;
-    double* v = p->vec_minres;
-    Slots& H = G.hS[free_k];
-    std::memset(&H, 0, sizeof(H));
-    H.v[SL_R1] = v; H.v[SL_R2] = v + nv; H.v[SL_Y] = v + 2 * nv; H.v[SL_YO] = v + 3 * nv; H.v[SL_Q] = v + 4 * nv;
-    H.v[SL_W] = v + 5 * nv; H.v[SL_W2] = v + 6 * nv; H.v[SL_R] = v;
-    H.v[SL_BI] = p->vec_mixed; H.v[SL_XI] = p->vec_mixed + nv;
-    if (G.method != PCB_MINRES) { H.v[SL_VBASE] = p->vec_gmres; H.v[SL_ZBASE] = p->vec_gmres + (size_t)(S->o.restart + 1) * nv; }
-    H.v[SL_X] = s.x; H.v[SL_B] = s.b;
-    G.hG[free_k] = p->g;
-    G.dirty = true;
-    S->qhead += 1;
+    if (head_only) break;
   }
+  while (S->qhead < S->queue.size() && S->taken[S->qhead]) { ++S->qhead; head_admitted = true; }
+  S->head_wait = (S->qhead < S->queue.size() && !head_admitted) ? S->head_wait + 1 : 0;
   if (S->qhead > 4096 && S->qhead * 2 > S->queue.size()) {
     S->queue.erase(S->queue.begin(), S->queue.begin() + S->qhead);
+    S->taken.erase(S->taken.begin(), S->taken.begin() + S->qhead);
     S->qhead = 0;
   }
   // advance every admitted request
@@ -1797,9 +1948,11 @@ int pcb_server_step(pcb_server* S, pcb_server_done* done, int max_done, int* n_d
   }
   int act = 0;
   for (int q = 0; q < 2; ++q) for (auto& s : S->grp[q].slots) act += s.phase != PH_FREE;
+  int queued = 0;
+  for (size_t i = S->qhead; i < S->queue.size(); ++i) queued += !S->taken[i];
   if (n_done) *n_done = nd;
   if (n_active) *n_active = act;
-  if (n_queued) *n_queued = (int)(S->queue.size() - S->qhead);
+  if (n_queued) *n_queued = queued;
   return PCB_OK;
 }
 

@@ -57,7 +57,9 @@ def test_budget_admission_and_rejection(P):
     big = max(2 * r.N * r.N * r.n for r, _, _ in reqs) * 8 * 60 + (8 << 20)
     res = serve.run([r for r, _, _ in reqs], budget_bytes=big, max_slots=8, precision="mixed")
     assert res["failed"] == 0 and res["max_relres"] <= 1e-8
-    srv = serve.Server(budget_bytes=1 << 20, max_slots=2)
+    # the budget is reserved up front and each request takes exactly its workspace (about 0.7 MB
+    # here): 256 KB holds none
+    srv = serve.Server(budget_bytes=1 << 18, max_slots=2)
     t = torch.zeros(2 * 15 * 15 * 16, dtype=torch.float64).pin_memory()
     with pytest.raises(Exception) as e:
         srv.submit(15, 16, 1.0, 1e-2, t, t.clone(), 0)
