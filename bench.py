@@ -363,11 +363,22 @@ def config3_figures(P, synth, torch, stream):
     its64 = [p.solve(b, x, tol=1e-8, restart=16)[1]["iterations"] for p, b, x in zip(fp, bs, xs)]
     ms_64, _ = timed(torch, stream, lambda: [p.solve(b, x, tol=1e-8, restart=16) for p, b, x in zip(fp, bs, xs)])
     itsm = [i["iterations"] for i in infos]
-    for p in probs + fp:
+    for p in fp:
+        p.close()
+    # autotuned kernel shapes: each problem tunes its apply (shapes seen before reuse the choice)
+    tuned = [p.autotune(reps=2) for p in probs]
+    P.batch_solve(probs, bs, xs, tol=1e-8, restart=16)
+    ms_t, _ = timed(torch, stream, lambda: P.batch_solve(probs, bs, xs, tol=1e-8, restart=16)[1])
+    for p in probs:
         p.close()
     return {"workload": f"{len(insts)} uneven instances (synth.config3), {unknowns:.3g} unknowns in all, mixed",
             "batched": {"solves_per_s": len(insts) / (ms_b / 1e3), "unknowns_per_s": unknowns / (ms_b / 1e3),
                         "ms": ms_b, "max_relres": max(i["relres"] for i in infos)},
+            "batched_autotuned": {"solves_per_s": len(insts) / (ms_t / 1e3), "ms": ms_t,
+                                  "non_default_choices": sum(t["chosen"] != 0 for t in tuned),
+                                  "rejected": sum(t["rejected"] for t in tuned),
+                                  "apply_ms_default_sum": sum(t["default_ms"] for t in tuned),
+                                  "apply_ms_tuned_sum": sum(t["best_ms"] for t in tuned)},
             "one_at_a_time_mixed": {"solves_per_s": len(insts) / (ms_1 / 1e3), "ms": ms_1},
             "one_at_a_time_fp64": {"solves_per_s": len(insts) / (ms_64 / 1e3), "ms": ms_64},
             "iterations_mixed_minus_fp64_max": max(m - f for m, f in zip(itsm, its64)),

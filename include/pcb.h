@@ -105,6 +105,10 @@ typedef struct {
   int bc;                 /* pcb_bc; 0 = Dirichlet                                             */
   double a_const;         /* constant a(x) when a_edges is NULL; <= 0 => 1.  Neumann requires   */
                           /* a_edges = NULL                                                    */
+  int fem;                /* 0: finite differences (M = I, K = -L).  1: bilinear (Q1) finite     */
+                          /* elements on the same grid (Sec. 1: M the mass, K the stiffness      */
+                          /* matrix; the system carries M^{-1/2} K M^{-1/2}); Dirichlet, constant */
+                          /* a, single problems (not batches or the server), y0 = 0              */
 } pcb_desc;
 
 /* Validate the descriptor, compute the spectral tables (Sec. 3.5: lambda_k(S_n), the eigenvalues
@@ -123,7 +127,8 @@ long long pcb_workspace_bytes(const pcb_problem* p);
 
 /* Right-hand side (Sec. 1, vectors f~, g~, then Eq. main_system / main_system_nonsym):
  * g_dev, f_dev: (n+1)*m samples at t_k = k*tau; y0_dev: m values or NULL (= 0).
- * Writes b_dev (2*m*n) for operator `op`. */
+ * Writes b_dev (2*m*n) for operator `op`.  Finite elements (fem = 1): f~, g~ carry the mass matrix
+ * and b the factor M^{-1/2} of Eq. (main_system); y0_dev must be NULL (else UNSUPPORTED). */
 int pcb_assemble_rhs(pcb_problem* p, int op, const double* g_dev, const double* f_dev,
                      const double* y0_dev, double* b_dev);
 
@@ -136,8 +141,38 @@ int pcb_matvec(pcb_problem* p, int op, const double* x_dev, double* y_dev);
  * P_MS for Neumann problems (MINRES preconditioners; the Neumann A is not symmetric). */
 int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_dev, double* y_dev);
 
+/* ---- autotuning of the preconditioner's kernel shapes ------------------------------------ */
+/* The transforms of Sec. 3.5 (steps 1 and 3) can run in several kernel configurations: the
+ * pipelined FP32 kernels or the tile kernels for the spatial and the time passes (and, for n = 512,
+ * with or without handing the time pass contiguous time lines), and for the tile kernels several
+ * register-FFT radices (values per lane) and tile sizes.  pcb_autotune times `reps` applications
+ * of preconditioner `kind` (PCB_PREC_NONE: the problem's default) in the problem's precision under
+ * each configuration that fits the problem's shape, keeps the fastest for this problem, and records
+ * it for the device and shape (N, n, boundary condition, zeta = pi or not, precision): problems
+ * and server requests of that shape created afterwards start with it.  Every configuration computes
+ * the same operator: each candidate's result is compared with the default configuration's on the
+ * same input, and one that differs by more than the precision's rounding (relative max-norm 1e-5
+ * in FP32, 1e-12 in FP64) is rejected instead of timed.  Blocks while it runs; uses a temporary
+ * device buffer of three vectors.  Constant coefficient only (UNSUPPORTED with variable a(x)).
+ * Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA. */
+typedef struct {
+  int candidates;          /* configurations timed                                               */
+  int rejected;            /* configurations whose result did not match the default's            */
+  int chosen;              /* index of the winner among them (0: the default configuration)      */
+  double default_ms;       /* mean apply time of the default configuration                       */
+  double best_ms;          /* mean apply time of the winner                                      */
+  int pipelined_dst;       /* winner: pipelined spatial passes (1) or tile kernels (0)            */
+  int pipelined_time;      /* winner: pipelined time pass (1) or tile kernel (0)                  */
+  int time_major_handoff;  /* winner: the n = 512 spatial pass writes contiguous time lines       */
+  int dst_lanes;           /* lanes per spatial line of the tile kernels (values per lane = M/lanes)*/
+  int time_lanes;          /* lanes per time line of the tile kernels                            */
+  double tile_scale;       /* tile size of the tile kernels relative to the default (0.5, 1, 2)   */
+} pcb_tune_info;
+int pcb_autotune(pcb_problem* p, int kind, int reps, pcb_tune_info* info);
+
 /* Undo the symmetrising change of variables of Eq. (main_system):
- * y = (B2^{-1} (x) I) x_half0 / sqrt(gamma), p = (B2^{-T} (x) I) x_half1; each m*n. */
+ * y = (B2^{-1} (x) M^{-1/2}) x_half0 / sqrt(gamma), p = (B2^{-T} (x) M^{-1/2}) x_half1; each m*n
+ * (M = I for finite differences). */
 int pcb_recover(pcb_problem* p, const double* x_dev, double* y_dev, double* p_dev);
 
 /* ---- solve ----------------------------------------------------------------------------- */

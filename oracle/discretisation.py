@@ -6,6 +6,12 @@ Eq. (main_system), and the error measure of Eq. (error_measure).
 Two boundary conditions:
   dirichlet (Examples 1-2): N interior nodes per side, h = 1/(N+1), zero boundary values,
             conservative edge-weighted stencil (a(x) at cell-edge midpoints, or the constant a0).
+            With fem=True the space discretisation is bilinear (Q1) finite elements on the same
+            grid instead (Sec. 1: M_m the mass and K_m the stiffness matrix, both symmetric, M_m
+            positive definite): M = M1 (x) M1, K = a0 (K1 (x) M1 + M1 (x) K1) with the 1D linear-
+            element matrices M1 = (h/6) tridiag(1, 4, 1) and K1 = (1/h) tridiag(-1, 2, -1).  The
+            symmetrised system then carries K~ = M^{-1/2} K M^{-1/2} (Eq. matrix_A), and the
+            right-hand side and unknowns the M^{-1/2}, M^{1/2} factors of Eq. (main_system).
   neumann   (Example 3, homogeneous Neumann): N nodes per side *including* the boundary,
             x_i = i h, h = 1/(N-1), the constant coefficient a0, second differences with the
             ghost values mirrored across the boundary (u_{-1} = u_1, u_N = u_{N-2}).  This K is
@@ -31,7 +37,7 @@ class Problem:
     boundary condition bc ("dirichlet" or "neumann") and constant coefficient a0 (used when
     a_edges is None)."""
 
-    def __init__(self, N, n, theta, gamma, T=1.0, zeta=math.pi, a_edges=None, bc="dirichlet", a0=1.0):
+    def __init__(self, N, n, theta, gamma, T=1.0, zeta=math.pi, a_edges=None, bc="dirichlet", a0=1.0, fem=False):
         self.N, self.n = int(N), int(n)
         self.theta, self.gamma, self.T, self.zeta = float(theta), float(gamma), float(T), float(zeta)
         self.a_edges = None if a_edges is None else np.asarray(a_edges, dtype=np.float64)
@@ -39,12 +45,14 @@ class Problem:
             raise ValueError("bc must be 'dirichlet' or 'neumann'")
         if bc == "neumann" and (a_edges is not None or self.N < 3):
             raise ValueError("neumann takes a constant coefficient and N >= 3")
-        self.bc, self.a0 = bc, float(a0)
+        if fem and (bc != "dirichlet" or a_edges is not None):
+            raise ValueError("the finite-element discretisation is built for Dirichlet data and a constant a")
+        self.bc, self.a0, self.fem = bc, float(a0), bool(fem)
 
     @classmethod
     def from_instance(cls, inst):
         return cls(inst.N, inst.n, inst.theta, inst.gamma, inst.T, inst.zeta, inst.a_edges,
-                   getattr(inst, "bc", "dirichlet"), getattr(inst, "a0", 1.0))
+                   getattr(inst, "bc", "dirichlet"), getattr(inst, "a0", 1.0), getattr(inst, "fem", False))
 
     @property
     def m(self):
@@ -78,11 +86,70 @@ class Problem:
 # Spatial operator K = -L_m (Sec. 1: M = I, K = -L for finite differences)
 # ----------------------------------------------------------------------------------------
 
+# ----------------------------------------------------------------------------------------
+# Bilinear (Q1) finite elements on the Dirichlet grid (the M_m != I case of Sec. 1)
+# ----------------------------------------------------------------------------------------
+
+def mass_1d(N):
+    """1D linear-element mass matrix on N interior nodes, h = 1/(N+1): (h/6) tridiag(1, 4, 1)."""
+    h = 1.0 / (N + 1)
+    return sp.diags([np.full(N - 1, h / 6), np.full(N, 4 * h / 6), np.full(N - 1, h / 6)], [-1, 0, 1], format="csr")
+
+
+def stiffness_1d(N):
+    """1D linear-element stiffness matrix on N interior nodes: (1/h) tridiag(-1, 2, -1)."""
+    h = 1.0 / (N + 1)
+    return sp.diags([np.full(N - 1, -1 / h), np.full(N, 2 / h), np.full(N - 1, -1 / h)], [-1, 0, 1], format="csr")
+
+
+def _along(A1, U, axis):
+    """Apply the 1D matrix A1 along one grid axis of U[..., j, i] (axis -1: x1, -2: x2)."""
+    V = np.moveaxis(U, axis, -1)
+    sh = V.shape
+    W = (A1 @ V.reshape(-1, sh[-1]).T).T.reshape(sh)
+    return np.moveaxis(W, -1, axis)
+
+
+def apply_M(prob: Problem, u: np.ndarray) -> np.ndarray:
+    """M u: the identity for finite differences, M1 (x) M1 for finite elements."""
+    if not prob.fem:
+        return np.array(u, dtype=np.float64, copy=True)
+    N = prob.N
+    M1 = mass_1d(N)
+    U = u.reshape(u.shape[:-1] + (N, N))
+    return _along(M1, _along(M1, U, -1), -2).reshape(u.shape)
+
+
+def M_sparse(prob: Problem) -> sp.csr_matrix:
+    if not prob.fem:
+        return sp.identity(prob.m, format="csr")
+    M1 = mass_1d(prob.N)
+    return sp.kron(M1, M1, format="csr")
+
+
+def apply_M_power(prob: Problem, u: np.ndarray, power: float) -> np.ndarray:
+    """M^power u (power = 1/2 or -1/2 in Eq. main_system).  M is symmetric positive definite and
+    its square roots are taken through its eigendecomposition, for which the orthonormal DST-I
+    S_N (x) S_N serves (it diagonalises M1: the textbook eigenvectors of a symmetric tridiagonal
+    Toeplitz matrix)."""
+    if not prob.fem:
+        return np.array(u, dtype=np.float64, copy=True)
+    from . import spectra as spc
+    lam = spc.mass_eigenvalues_2d(prob.N).ravel()
+    return spc.dst2(lam ** power * spc.dst2(u, prob.N), prob.N)
+
+
 def apply_K(prob: Problem, u: np.ndarray) -> np.ndarray:
     """K u for u of shape (..., N*N).  Dirichlet: conservative 5-point stencil with zero boundary
     data, (K u)_ij = sum over the four edges of a_edge (u_ij - u_neighbour) / h^2.  Neumann:
-    a0 (4 u_ij - sum of the four neighbours) / h^2 with mirrored ghost values."""
+    a0 (4 u_ij - sum of the four neighbours) / h^2 with mirrored ghost values.  Finite elements:
+    a0 (K1 (x) M1 + M1 (x) K1) u."""
     N = prob.N
+    if prob.fem:
+        U = u.reshape(u.shape[:-1] + (N, N))
+        M1, K1 = mass_1d(N), stiffness_1d(N)
+        out = _along(M1, _along(K1, U, -1), -2) + _along(K1, _along(M1, U, -1), -2)
+        return (prob.a0 * out).reshape(u.shape)
     if prob.bc == "neumann":
         U = u.reshape(u.shape[:-1] + (N, N))
         # mirror: padded index 0 holds u_1, padded index N+1 holds u_{N-2}
@@ -102,9 +169,19 @@ def apply_K(prob: Problem, u: np.ndarray) -> np.ndarray:
     return out.reshape(u.shape)
 
 
+def apply_K_tilde(prob: Problem, u: np.ndarray) -> np.ndarray:
+    """K~ u = M^{-1/2} K M^{-1/2} u, the spatial operator of Eq. (matrix_A) (K itself when M = I)."""
+    if not prob.fem:
+        return apply_K(prob, u)
+    return apply_M_power(prob, apply_K(prob, apply_M_power(prob, u, -0.5)), -0.5)
+
+
 def K_sparse(prob: Problem) -> sp.csr_matrix:
     """K as a sparse m x m matrix, assembled entry by entry from the same stencil definition."""
     N = prob.N
+    if prob.fem:
+        M1, K1 = mass_1d(N), stiffness_1d(N)
+        return (prob.a0 * (sp.kron(M1, K1) + sp.kron(K1, M1))).tocsr()
     if prob.bc == "neumann":
         c = prob.a0 / prob.h ** 2
         rows, cols, vals = [], [], []
@@ -198,38 +275,41 @@ def apply_Bn(theta, x, transpose=False):
 # ----------------------------------------------------------------------------------------
 
 def tilde_rhs(prob: Problem, g, f, y0=None):
-    """(g_tilde, f_tilde), each (n, m), from samples g, f of shape (n+1, m) at t_k = k tau:
-      f_tilde^(r) = tau (theta f^(r) + (1-theta) f^(r-1)) [+ (I - (1-theta) tau K) y0 for r = 1]
-      g_tilde^(r) = tau (theta g^(r-1) + (1-theta) g^(r)) [- tau (1-theta) y0 for r = 1]."""
+    """(g_tilde, f_tilde), each (n, m), from samples g, f of shape (n+1, m) at t_k = k tau (Sec. 1):
+      f_tilde^(r) = M tau (theta f^(r) + (1-theta) f^(r-1)) [+ (M - (1-theta) tau K) y0 for r = 1]
+      g_tilde^(r) = tau M (theta g^(r-1) + (1-theta) g^(r)) [- tau (1-theta) M y0 for r = 1]."""
     th, tau = prob.theta, prob.tau
     g = np.asarray(g, dtype=np.float64); f = np.asarray(f, dtype=np.float64)
-    ft = tau * (th * f[1:] + (1.0 - th) * f[:-1])
-    gt = tau * (th * g[:-1] + (1.0 - th) * g[1:])
+    ft = apply_M(prob, tau * (th * f[1:] + (1.0 - th) * f[:-1]))
+    gt = apply_M(prob, tau * (th * g[:-1] + (1.0 - th) * g[1:]))
     if y0 is not None:
         y0 = np.asarray(y0, dtype=np.float64)
-        ft[0] += y0 - (1.0 - th) * tau * apply_K(prob, y0)
-        gt[0] -= tau * (1.0 - th) * y0
+        ft[0] += apply_M(prob, y0) - (1.0 - th) * tau * apply_K(prob, y0)
+        gt[0] -= tau * (1.0 - th) * apply_M(prob, y0)
     return gt, ft
 
 
 def rhs_minres(prob, g, f, y0=None):
-    """b = [g; sqrt(gamma) f] of Eq. (main_system) (M = I), flattened to 2mn."""
+    """b = [g; sqrt(gamma) f] of Eq. (main_system), g = (I (x) M^{-1/2}) g_tilde and
+    f = (I (x) M^{-1/2}) f_tilde, flattened to 2mn."""
     gt, ft = tilde_rhs(prob, g, f, y0)
-    return np.concatenate([gt.ravel(), math.sqrt(prob.gamma) * ft.ravel()])
+    gs, fs = apply_M_power(prob, gt, -0.5), apply_M_power(prob, ft, -0.5)
+    return np.concatenate([gs.ravel(), math.sqrt(prob.gamma) * fs.ravel()])
 
 
 def rhs_gmres(prob, g, f, y0=None):
     """b_hat = [sqrt(gamma) f; g] of Eq. (main_system_nonsym)."""
     gt, ft = tilde_rhs(prob, g, f, y0)
-    return np.concatenate([math.sqrt(prob.gamma) * ft.ravel(), gt.ravel()])
+    gs, fs = apply_M_power(prob, gt, -0.5), apply_M_power(prob, ft, -0.5)
+    return np.concatenate([math.sqrt(prob.gamma) * fs.ravel(), gs.ravel()])
 
 
 def A_tilde_sparse(prob: Problem) -> sp.csr_matrix:
-    """The unsymmetrised block matrix of Eq. (matrix_A_before) with M = I:
-      [[tau B2 (x) I,          B1^T (x) I + tau B2^T (x) K],
-       [B1 (x) I + tau B2 (x) K,  -(tau/gamma) B2^T (x) I ]]  acting on [y; p]."""
+    """The unsymmetrised block matrix of Eq. (matrix_A_before):
+      [[tau B2 (x) M,          B1^T (x) M + tau B2^T (x) K],
+       [B1 (x) M + tau B2 (x) K,  -(tau/gamma) B2^T (x) M ]]  acting on [y; p]."""
     n, th, tau, gam = prob.n, prob.theta, prob.tau, prob.gamma
-    I = sp.identity(prob.m, format="csr")
+    I = M_sparse(prob)
     K = K_sparse(prob)
     B1 = sp.csr_matrix(B1_dense(n)); B2 = sp.csr_matrix(B2_dense(n, th))
     top = sp.hstack([tau * sp.kron(B2, I), sp.kron(B1.T, I) + tau * sp.kron(B2.T, K)])
@@ -250,20 +330,21 @@ def solve_direct(prob, g, f, y0=None):
 # ----------------------------------------------------------------------------------------
 
 def to_symmetric_unknowns(prob, y, p):
-    """x = [sqrt(gamma) (B2 (x) I) y ; (B2^T (x) I) p]."""
+    """x = [sqrt(gamma) (B2 (x) M^{1/2}) y ; (B2^T (x) M^{1/2}) p]."""
     th = prob.theta
     yt = th * y.copy(); yt[1:] += (1.0 - th) * y[:-1]
     pt = th * p.copy(); pt[:-1] += (1.0 - th) * p[1:]
+    yt, pt = apply_M_power(prob, yt, 0.5), apply_M_power(prob, pt, 0.5)
     return np.concatenate([math.sqrt(prob.gamma) * yt.ravel(), pt.ravel()])
 
 
 def recover(prob, x):
-    """Inverse of the change of variables: y = (B2^{-1} (x) I) x1 / sqrt(gamma),
-    p = (B2^{-T} (x) I) x2; returns (y, p), each (n, m)."""
+    """Inverse of the change of variables: y = (B2^{-1} (x) M^{-1/2}) x1 / sqrt(gamma),
+    p = (B2^{-T} (x) M^{-1/2}) x2; returns (y, p), each (n, m)."""
     mn = prob.m * prob.n
     x1 = x[:mn].reshape(prob.n, prob.m); x2 = x[mn:].reshape(prob.n, prob.m)
-    y = _solve_B2(prob.theta, x1) / math.sqrt(prob.gamma)
-    p = _solve_B2(prob.theta, x2, transpose=True)
+    y = apply_M_power(prob, _solve_B2(prob.theta, x1), -0.5) / math.sqrt(prob.gamma)
+    p = apply_M_power(prob, _solve_B2(prob.theta, x2, transpose=True), -0.5)
     return y, p
 
 

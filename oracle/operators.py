@@ -1,19 +1,19 @@
 """All-at-once matrix-vector products (paper Sec. 1 and Sec. 3.5):
   A     = [[alpha I, T^T], [T, -alpha I]]      (Eq. matrix_A, MINRES)
   A_hat = [[T, -alpha I], [alpha I, T^T]]      (Eq. matrix_A_hat, GMRES)
-  T     = B_n (x) I_m + tau I_n (x) K          (Eq. matrix_T, M = I)
+  T     = B_n (x) I_m + tau I_n (x) M^{-1/2} K M^{-1/2}   (Eq. matrix_T; K itself when M = I)
 written from the definitions; B_n is applied as B^(1) followed by (B^(2))^{-1}.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .discretisation import apply_Bn, apply_K
+from .discretisation import apply_Bn, apply_K_tilde
 
 
 def apply_T(prob, x, transpose=False):
     """T x (or T^T x) for x of shape (n, m)."""
-    return apply_Bn(prob.theta, x, transpose) + prob.tau * apply_K(prob, x)
+    return apply_Bn(prob.theta, x, transpose) + prob.tau * apply_K_tilde(prob, x)
 
 
 def matvec_A(prob, x):

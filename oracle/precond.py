@@ -31,7 +31,7 @@ import numpy as np
 
 from . import spectra as spc
 from . import multigrid as mg
-from .discretisation import K_sparse, B1_dense, B2_dense
+from .discretisation import K_sparse, M_sparse, B1_dense, B2_dense
 
 
 def _halves(prob, v):
@@ -50,8 +50,9 @@ def _inverse(prob, w):
 
 
 def _kappa2d(prob):
-    """a0 (kappa_p + kappa_q): eigenvalues of K (constant coefficient)."""
-    return prob.a0 * spc.kappa2d(prob.N, prob.bc)
+    """a0 (kappa_p + kappa_q): eigenvalues of K (constant coefficient); with finite elements, of
+    K~ = M^{-1/2} K M^{-1/2}."""
+    return prob.a0 * spc.kappa2d(prob.N, prob.bc, getattr(prob, "fem", False))
 
 
 def _modes(prob):
@@ -160,7 +161,13 @@ def apply_mg_ps_inv(prob, v, cycles=2, nu1=2, nu2=2, real=True):
 # ---------------------------------------------------------------------------------------
 
 def dense_K(prob):
-    return K_sparse(prob).toarray()
+    """The spatial operator of Eq. (matrix_A): K, or M^{-1/2} K M^{-1/2} with finite elements
+    (the square root from a dense symmetric eigendecomposition of M)."""
+    K = K_sparse(prob).toarray()
+    if getattr(prob, "fem", False):
+        Mi = _sqrtm_herm(np.linalg.inv(M_sparse(prob).toarray()))
+        K = Mi @ K @ Mi
+    return K
 
 
 def dense_Sn(prob):

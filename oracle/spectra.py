@@ -87,9 +87,38 @@ def kappa_neumann(N):
     return (4.0 / h ** 2) * np.sin(k * math.pi / (2.0 * (N - 1))) ** 2
 
 
-def kappa2d(N, bc="dirichlet"):
-    """kappa_p + kappa_q laid out [q, p] (x1-mode p fastest), matching the spatial vector layout."""
-    k = kappa_neumann(N) if bc == "neumann" else kappa(N)
+def mass_eigenvalues(N):
+    """Eigenvalues of the 1D linear-element mass matrix (h/6) tridiag(1, 4, 1), p = 1..N (the
+    same sine eigenvectors as the second difference): (h/6)(4 + 2 cos(p pi h))."""
+    h = 1.0 / (N + 1)
+    p = np.arange(1, N + 1)
+    return (h / 6.0) * (4.0 + 2.0 * np.cos(p * math.pi * h))
+
+
+def stiffness_eigenvalues(N):
+    """Eigenvalues of the 1D linear-element stiffness matrix (1/h) tridiag(-1, 2, -1), p = 1..N."""
+    h = 1.0 / (N + 1)
+    p = np.arange(1, N + 1)
+    return (2.0 - 2.0 * np.cos(p * math.pi * h)) / h
+
+
+def mass_eigenvalues_2d(N):
+    """Eigenvalues of M1 (x) M1 laid out [q, p]."""
+    mu = mass_eigenvalues(N)
+    return mu[None, :] * mu[:, None]
+
+
+def kappa_fem(N):
+    """Eigenvalues of M1^{-1/2} K1 M1^{-1/2} (the 1D factor of K~ = M^{-1/2} K M^{-1/2}): since
+    M1 and K1 share their eigenvectors, kappa1_p / mu_p."""
+    return stiffness_eigenvalues(N) / mass_eigenvalues(N)
+
+
+def kappa2d(N, bc="dirichlet", fem=False):
+    """kappa_p + kappa_q laid out [q, p] (x1-mode p fastest), matching the spatial vector layout.
+    With fem: the eigenvalues of K~ = M^{-1/2} K M^{-1/2} / a0 (K = a0 (K1 (x) M1 + M1 (x) K1) gives
+    K~ = a0 (K1^ (x) I + I (x) K1^) with K1^ = M1^{-1/2} K1 M1^{-1/2})."""
+    k = kappa_neumann(N) if bc == "neumann" else (kappa_fem(N) if fem else kappa(N))
     return k[None, :] + k[:, None]
 
 

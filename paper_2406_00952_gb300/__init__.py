@@ -14,7 +14,7 @@ import math
 import torch
 
 from . import _lib
-from ._lib import PcbDesc, PcbSolveInfo, PcbSolveOpts, check
+from ._lib import PcbDesc, PcbSolveInfo, PcbSolveOpts, PcbTuneInfo, check
 
 OPS = {"A": 0, "Ahat": 1}
 PRECONDS = {None: 0, "none": 0, "abs_ps": 1, "ps": 2, "pms": 3}
@@ -43,10 +43,11 @@ def _opts(method="auto", precond=None, tol=1e-8, maxit=500, restart=30, max_refi
 class Problem:
     """One control problem on the current CUDA device and stream (C-ABI pcb_create).
     bc="neumann" selects Example 3's homogeneous Neumann grid (N nodes per side including the
-    boundary); a is the constant coefficient when a_edges is None."""
+    boundary); a is the constant coefficient when a_edges is None; fem=True selects bilinear finite
+    elements (mass matrix M != I) in place of finite differences."""
 
     def __init__(self, N, n, theta, gamma, T=1.0, zeta=math.pi, a_edges=None, precision="fp64", mg_cycles=2,
-                 stream: torch.cuda.Stream | None = None, bc="dirichlet", a=1.0):
+                 stream: torch.cuda.Stream | None = None, bc="dirichlet", a=1.0, fem=False):
         self.lib = _lib.load()
         self.N, self.n, self.theta, self.gamma, self.T = int(N), int(n), float(theta), float(gamma), float(T)
         self.m = self.N * self.N
@@ -59,7 +60,7 @@ class Problem:
             self._a = np.ascontiguousarray(a_edges, dtype=np.float64)
             ap = self._a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         d = PcbDesc(self.N, self.n, self.theta, self.T, self.gamma, float(zeta), ap, PRECISIONS[precision],
-                    int(mg_cycles), ctypes.c_void_p(self.stream.cuda_stream), BCS[bc], float(a))
+                    int(mg_cycles), ctypes.c_void_p(self.stream.cuda_stream), BCS[bc], float(a), int(bool(fem)))
         h = ctypes.c_void_p()
         check("pcb_create", self.lib.pcb_create(ctypes.byref(d), ctypes.byref(h)))
         self.h = h
@@ -94,6 +95,13 @@ class Problem:
         check("pcb_precond_apply", self.lib.pcb_precond_apply(self.h, PRECONDS[kind], prec, _ptr(x, self.size),
                                                              _ptr(out, self.size)))
         return out
+
+    def autotune(self, kind=None, reps=3) -> dict:
+        """Time the preconditioner apply under each kernel configuration that fits this problem and
+        keep the fastest (C-ABI pcb_autotune); later problems of the same shape start with it."""
+        info = PcbTuneInfo()
+        check("pcb_autotune", self.lib.pcb_autotune(self.h, PRECONDS[kind], int(reps), ctypes.byref(info)))
+        return info.as_dict()
 
     def assemble_rhs(self, g, f, y0=None, op="A", out=None):
         out = self._empty() if out is None else out

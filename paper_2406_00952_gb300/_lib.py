@@ -22,7 +22,8 @@ STATUS = {0: "ok", 1: "not converged", -1: "invalid argument", -2: "unsupported"
 class PcbDesc(ctypes.Structure):
     _fields_ = [("N", c_int), ("n", c_int), ("theta", c_double), ("T", c_double), ("gamma", c_double),
                 ("zeta", c_double), ("a_edges", POINTER(c_double)), ("precision", c_int),
-                ("mg_cycles", c_int), ("stream", c_void_p), ("bc", c_int), ("a_const", c_double)]
+                ("mg_cycles", c_int), ("stream", c_void_p), ("bc", c_int), ("a_const", c_double),
+                ("fem", c_int)]
 
 
 class PcbSolveOpts(ctypes.Structure):
@@ -36,6 +37,16 @@ class PcbSolveInfo(ctypes.Structure):
                 ("refinements", c_int), ("relres", c_double), ("seconds", c_double),
                 ("launches", c_longlong), ("precond_applies", c_int), ("precond_ms", c_double),
                 ("matvecs", c_int), ("matvec_ms", c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PcbTuneInfo(ctypes.Structure):
+    _fields_ = [("candidates", c_int), ("rejected", c_int), ("chosen", c_int), ("default_ms", c_double),
+                ("best_ms", c_double),
+                ("pipelined_dst", c_int), ("pipelined_time", c_int), ("time_major_handoff", c_int),
+                ("dst_lanes", c_int), ("time_lanes", c_int), ("tile_scale", c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -85,6 +96,7 @@ def load() -> ctypes.CDLL:
         "pcb_batch_solve": (c_int, [POINTER(c_void_p), c_int, POINTER(PcbSolveOpts), POINTER(c_void_p),
                                     POINTER(c_void_p), POINTER(PcbSolveInfo)]),
         "pcb_precond_apply_noalloc": (c_int, [POINTER(PcbDesc), c_int, c_int, P, P]),
+        "pcb_autotune": (c_int, [P, c_int, c_int, POINTER(PcbTuneInfo)]),
         "pcb_server_create": (c_int, [POINTER(PcbServerOpts), POINTER(c_void_p)]),
         "pcb_server_destroy": (None, [P]),
         "pcb_server_submit": (c_int, [P, POINTER(PcbDesc), P, P, c_longlong]),

@@ -236,7 +236,36 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
   }
 }
 
+// Epilogue of a finite-element product already written to out (see k_matvec's epilogues): one
+// instance, grid-stride blocks, one partial per block (the layout the scalar steps read).
+__global__ void __launch_bounds__(256) k_fem_epilogue(const Geom* __restrict__ G, const Slots* __restrict__ S,
+                                                      Scal* __restrict__ Sc, int x_slot, int out_slot, int aux_slot,
+                                                      int epi_kind, double* __restrict__ partial) {
+  const Geom& g = G[0];
+  const double* __restrict__ x = S[0].v[x_slot];
+  double* __restrict__ out = S[0].v[out_slot];
+  const double* __restrict__ aux = aux_slot >= 0 ? S[0].v[aux_slot] : nullptr;
+  const Epi e = make_epi(epi_kind, Sc);
+  const long long len = 2 * g.mn;
+  double part = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    out[i] = epi_apply(e, out[i], aux, x, i, part);
+  if (partial) {
+    if (epi_kind == EPI_MINRES) part *= e.s;
+    block_reduce_store(part, partial + blockIdx.x);
+  }
+}
+
+cudaError_t launch_fem_spatial(const Batch& B, int mode, int op, int in_slot, int out_slot);
+
 cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi) {
+  if (B.fem_m > 0) {
+    // finite elements: the product through the sine basis (FEM_PRODUCT = 2), then the epilogue
+    cudaError_t e = launch_fem_spatial(B, 2, op, x_slot, out_slot);
+    if (e != cudaSuccess || epi == EPI_PLAIN) return e;
+    k_fem_epilogue<<<B.tot_mv, 256, 0, B.stream>>>(B.G, B.S, B.Sc, x_slot, out_slot, aux_slot, epi, B.partial);
+    return cudaGetLastError();
+  }
   k_matvec<<<B.tot_mv, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_mv, B.count, B.active, op, x_slot, out_slot,
                                            aux_slot, epi, B.partial);
   return cudaGetLastError();

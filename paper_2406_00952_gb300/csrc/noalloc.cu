@@ -22,7 +22,7 @@
 #include "pcb_internal.cuh"
 
 namespace pcb {
-struct TableLayout { size_t kap, mud, muf, twdd, twdf, twtd, twtf, pred, pref, ax, ay, dg, bytes; };
+struct TableLayout { size_t kap, mud, muf, twdd, twdf, twtd, twtf, pred, pref, ax, ay, dg, ms, bytes; };
 int validate_desc(const pcb_desc* d);
 void init_geom(const pcb_desc* d, Geom& g);
 size_t table_layout(const Geom& g, TableLayout& t);
@@ -72,6 +72,7 @@ extern "C" int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int pre
   int rc = validate_desc(desc);
   if (rc != PCB_OK) return rc;
   if (desc->a_edges) return PCB_ERR_UNSUPPORTED;     // the multigrid route needs its own workspace
+  if (desc->fem) return PCB_ERR_UNSUPPORTED;         // finite elements: the allocating entry points only
   if (desc->bc == PCB_BC_NEUMANN && kind != PCB_PREC_PS) return PCB_ERR_UNSUPPORTED;   // GMRES route only
 
   Geom g;

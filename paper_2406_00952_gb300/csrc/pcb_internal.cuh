@@ -119,6 +119,8 @@ struct Geom {
   int zeta_pi;                    // 1 when zeta = pi: the two halves share one complex time line
   double c;                       // tau a / h^2 (a: the constant coefficient)
   int var_a;                      // 0: a = 1; 1: coefficient tables below
+  int fem;                        // 1: Q1 finite elements (spatial operator M^{-1/2} K M^{-1/2}, applied
+                                  //    through the DST-I; kap holds its 1D eigenvalues a kappa1_p / mu_p)
   // FP32 scratch layout of the pipelined passes: rows of lr values (lr = L + 16 when the pipelined
   // DST runs: 64-byte aligned rows, stride off a power of two; else N), slices of mp = N lr values;
   // buffer b, half h, time t, row r, index i at (float*)scratch + (2b + h) n mp + t mp + r lr + i
@@ -132,13 +134,15 @@ struct Geom {
   int dst_blocks_i[2], dst_blocks_j[2]; // blocks of the x1-line and x2-line DST passes
   int time_cpb[2];                // spatial columns per block of the time pass
   int time_blocks[2];
+  int tune;                       // kernel choices of the autotuner (TUNE_* bits; 0 = defaults)
   int mv_tchunk;                  // time steps per thread in the theta = 1 matvec
   int mv_blocks;                  // blocks of the matvec
   int vec_blocks;                 // blocks of the vector kernels over 2mn
   FftPlan pdst, ptime;
   // tables (device)
   const double* kap;              // N: eigenvalues a kappa_p of the 1D second difference (Dirichlet p = 1..N,
-                                  //    Neumann k = 0..N-1)
+                                  //    Neumann k = 0..N-1); finite elements: of M1^{-1/2} K1 M1^{-1/2}
+  const double* mass;             // fem: N eigenvalues mu_p of the 1D mass matrix (h/6) tridiag(1, 4, 1)
   const double2* mu_d;            // n: lambda(S_n) at F-slot r (FP64)
   const float2* mu_f;
   const double2* twd_d;           // M: exp(-2 pi i k / M)
@@ -153,6 +157,11 @@ struct Geom {
   void* scratch;                  // preconditioner workspace: 2mn values of the apply's Real type
   const void* mg;                 // multigrid workspace (variable a), else null
 };
+
+// Autotuner choices (Geom::tune): kernel families the FP32 apply may not use, and the tile-size
+// scale of the tile kernels (bits 4-5: 0 = default, 1 = half, 2 = double the per-tile element budget)
+enum { TUNE_NO_PIPE_DST = 1, TUNE_NO_PIPE_TIME = 2, TUNE_NO_HANDOFF = 4 };
+__host__ __device__ inline int tune_budget_shift(int tune) { return (tune >> 4) & 3; }
 
 // per-instance Krylov scalars (MINRES and GMRES share the struct)
 struct Scal {
@@ -248,6 +257,8 @@ struct Batch {
   const int* fam_dst;
   const int* fam_time;
   int fam_dst_set, fam_time_set;
+  int fem_m;              // > 0: a single finite-element instance with m = fem_m spatial points
+                          // (products through the DST-I)
   const int* filt;        // family filter of the launch being issued (null: none)
   int filt_want;
   Sel sel() const { Sel s; s.active = active; s.fam = filt; s.want = filt_want; return s; }

@@ -752,6 +752,82 @@ static cudaError_t precond_passes(const Batch& B, int kind, int in_slot, int out
 
 int precond_launch_count(bool var_a, int kind) { return var_a ? mg_launch_count(kind) : 5; }
 
+// ------------------------------------------------------------------------------------------
+// Finite elements (M != I, Sec. 1): the spatial operator K~ = M^{-1/2} K M^{-1/2} is diagonal in the
+// sine basis, so products with it, and with M^{1/2} and M^{-1/2}, run as FP64 2D DST-I, a per-mode
+// step, and the inverse DST-I (the DST-I is its own inverse).  The per-mode step works in place on
+// the problem's FP64 scratch, which the two DST passes leave in the vector layout with mode
+// (p, q) at the position of node (p, q).
+// ------------------------------------------------------------------------------------------
+enum { FEM_MASS_SQRT = 0, FEM_MASS_ISQRT = 1, FEM_PRODUCT = 2 };
+
+// One thread per mode col = (p, q), both halves, all time steps.
+//   FEM_MASS_SQRT / FEM_MASS_ISQRT: scale by (mu_p mu_q)^{+1/2} / ^{-1/2}.
+//   FEM_PRODUCT: the all-at-once product (Eq. matrix_A or matrix_A_hat) with K~ diagonal:
+//     T x1 = B_n x1 + tau kappa x1, B_n = B1 B2^{-1}: z_t = (x1_t - (1-theta) z_{t-1}) / theta, z_t - z_{t-1};
+//     T^T x2 = B1^T B2^{-T} x2 + tau kappa x2: u_t = (x2_t - (1-theta) u_{t+1}) / theta, u_t - u_{t+1}.
+//   The backward sweep parks u in the first half of `tmp` (a vector the caller overwrites later);
+//   the forward sweep then reads x1_t, x2_t and writes both outputs at t, after which nothing reads t.
+__global__ void __launch_bounds__(256) k_fem_modal(const Geom* __restrict__ G, const Slots* __restrict__ S, int mode,
+                                                   int op, int tmp_slot) {
+  const Geom& g = G[0];
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= g.m) return;
+  const int N = g.N, n = g.n, m = g.m;
+  const long long mn = g.mn;
+  const int q = col / N, p = col - q * N;
+  double* __restrict__ w = (double*)g.scratch;
+  if (mode != FEM_PRODUCT) {
+    const double mu = __ldg(&g.mass[p]) * __ldg(&g.mass[q]);
+    const double sc = mode == FEM_MASS_SQRT ? sqrt(mu) : 1.0 / sqrt(mu);
+    for (int t = 0; t < n; ++t) {
+      const long long a = (long long)t * m + col;
+      w[a] *= sc;
+      w[mn + a] *= sc;
+    }
+    return;
+  }
+  const double tk = g.tau * (__ldg(&g.kap[p]) + __ldg(&g.kap[q]));
+  const double th = g.theta, om = 1.0 - th, ith = 1.0 / th, alpha = g.alpha;
+  double* __restrict__ ubuf = S[0].v[tmp_slot];
+  const double* __restrict__ x1 = w;
+  const double* __restrict__ x2 = w + mn;
+  double unext = 0.0;
+  for (int t = n - 1; t >= 0; --t) {
+    const long long a = (long long)t * m + col;
+    const double u = fma(-om, unext, x2[a]) * ith;
+    ubuf[a] = u;
+    unext = u;
+  }
+  const long long offT = op == PCB_OP_A ? mn : 0, offTT = op == PCB_OP_A ? 0 : mn;
+  double zprev = 0.0;
+  for (int t = 0; t < n; ++t) {
+    const long long a = (long long)t * m + col;
+    const double x1c = x1[a], x2c = x2[a];
+    const double z = fma(-om, zprev, x1c) * ith;
+    const double un = t + 1 < n ? ubuf[a + m] : 0.0;
+    double oT = (z - zprev) + tk * x1c;
+    oT = fma(-alpha, x2c, oT);
+    double oTT = (ubuf[a] - un) + tk * x2c;
+    oTT = fma(alpha, x1c, oTT);
+    w[offT + a] = oT;
+    w[offTT + a] = oTT;
+    zprev = z;
+  }
+}
+
+// y = Op x through the sine basis; in_slot, out_slot: vector slots (they may coincide for the mass
+// factors; the product needs distinct ones, out_slot serving as the sweep's temporary).
+cudaError_t launch_fem_spatial(const Batch& B, int mode, int op, int in_slot, int out_slot) {
+  cudaError_t e;
+  if ((e = dst_pass<double>(B, 1, in_slot, -1)) != cudaSuccess) return e;
+  if ((e = dst_pass<double>(B, 2, -1, -1)) != cudaSuccess) return e;
+  k_fem_modal<<<(B.fem_m + 255) / 256, 256, 0, B.stream>>>(B.G, B.S, mode, op, out_slot);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = dst_pass<double>(B, 4, -1, -1)) != cudaSuccess) return e;
+  return dst_pass<double>(B, 5, -1, out_slot);
+}
+
 // B.dst_q / B.time_q = 0 selects the shared-launch kernels for instances of different sizes.
 cudaError_t launch_precond_fast(const Batch& B, int kind, int prec, int in_slot, int out_slot) {
   return prec == PCB_MIXED ? precond_passes<float>(B, kind, in_slot, out_slot)

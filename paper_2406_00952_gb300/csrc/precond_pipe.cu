@@ -1224,7 +1224,7 @@ cudaError_t dst_pass_p(const Batch& B, int stage, int in_slot, int out_slot, boo
 int pipe_time_p(const Geom& g);
 int pipe_dst_p(const Geom& g) {
   // the padded scratch layout needs the pipelined time pass
-  if (g.var_a || !pipe_time_p(g)) return 0;
+  if (g.var_a || (g.tune & TUNE_NO_PIPE_DST) || !pipe_time_p(g)) return 0;
   const int M = 2 * g.L;
   if (M % 32) return 0;
   const int P = M / 32;
@@ -1232,7 +1232,7 @@ int pipe_dst_p(const Geom& g) {
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
 int pipe_time_p(const Geom& g) {
-  if (g.var_a || g.n % 32) return 0;
+  if (g.var_a || (g.tune & TUNE_NO_PIPE_TIME) || g.n % 32) return 0;
   const int P = g.n / 32;
   if (!g.zeta_pi && P > 16) return 0;        // general zeta: the two halves of a column share a warp
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
@@ -1243,13 +1243,14 @@ int pipe_time_p(const Geom& g) {
 // flag 256, take tiles of columns in place)
 int pipe_dst_code(const Geom& g) {
   const int p = pipe_dst_p(g);
-  return p ? (p | (g.n == 512 && g.zeta_pi ? 64 : 0) | (g.bc == PCB_BC_NEUMANN ? 128 : 0)) : 0;
+  const bool tm = g.n == 512 && g.zeta_pi && !(g.tune & TUNE_NO_HANDOFF);
+  return p ? (p | (tm ? 64 : 0) | (g.bc == PCB_BC_NEUMANN ? 128 : 0)) : 0;
 }
 int pipe_time_code(const Geom& g) {
   const int p = pipe_time_p(g);
   if (!p) return 0;
   if (!g.zeta_pi) return p | 256;
-  return p | (pipe_dst_p(g) && g.n == 512 ? 64 : 0);
+  return p | (pipe_dst_p(g) && g.n == 512 && !(g.tune & TUNE_NO_HANDOFF) ? 64 : 0);
 }
 // spatial columns per tile of the pipelined time pass (n = 512: one line per warp; general zeta:
 // two lines, the halves, per column)

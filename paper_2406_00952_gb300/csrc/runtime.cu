@@ -10,7 +10,9 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "pcb_internal.cuh"
@@ -27,6 +29,7 @@ cudaError_t launch_rhs(const Geom& g, cudaStream_t st, int op, const double* gs,
                        double* b);
 cudaError_t launch_recover(const Geom& g, cudaStream_t st, const double* x, double* y, double* p);
 cudaError_t launch_copy_mapped(cudaStream_t st, const double* src, double* dst, long long n);
+cudaError_t launch_fem_spatial(const Batch& B, int mode, int op, int in_slot, int out_slot);
 
 // device address of page-locked host memory the device maps, or null (pageable memory)
 static const void* mapped_ptr(const void* host) {
@@ -74,7 +77,7 @@ int pipe_time_code(const Geom& g);
 int pipe_time_cols(int n, int zeta_pi);
 int pipe_dst_lines(int L);
 cudaError_t upload_constants();
-struct TableLayout { size_t kap, mud, muf, twdd, twdf, twtd, twtf, pred, pref, ax, ay, dg, bytes; };
+struct TableLayout { size_t kap, mud, muf, twdd, twdf, twtd, twtf, pred, pref, ax, ay, dg, ms, bytes; };
 cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host);
 
 // step ids of the scalar kernels (mirror krylov.cu)
@@ -175,7 +178,6 @@ int vec_blocks_for(long long len) {
   return (int)b;
 }
 
-int round_down(int v, int q) { return std::max(q, (v / q) * q); }
 int pow2_floor(int v) { int p = 1; while (p * 2 <= v) p *= 2; return p; }
 
 void set_shapes(Geom& g) {
@@ -185,7 +187,9 @@ void set_shapes(Geom& g) {
   const int lsd = padded_len_host(g.L), lst = padded_len_host(g.n);
   const int Pd = 2 * g.L / g.dst_q, Pt = g.n / g.time_q;
   const int lpwd = 32 / Pd, lpwt = 32 / Pt;
-  const int budget[2] = {4300, 8600};   // complex elements per tile: FP64, FP32 (~68 KB)
+  // complex elements per tile: FP64, FP32 (~68 KB); the autotuner may halve or double them
+  const int bs = tune_budget_shift(g.tune);
+  const int budget[2] = {bs == 1 ? 2150 : bs == 2 ? 8600 : 4300, bs == 1 ? 4300 : bs == 2 ? 17200 : 8600};
   for (int p = 0; p < 2; ++p) {
     // powers of two (the kernels split thread indices with shifts) that are multiples of lpw
     // Q = 32 lines use one warp each plus a per-warp transpose scratch: 8 lines per block
@@ -214,6 +218,39 @@ void set_shapes(Geom& g) {
     g.mv_blocks = 2 * ncb;
   }
   g.vec_blocks = vec_blocks_for(2 * g.mn);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Autotuner cache: the winning kernel choices (Geom::tune, dst_q, time_q) per device and problem
+// shape, shared by every problem of that shape the process creates afterwards.
+// ---------------------------------------------------------------------------------------------
+struct TuneKey {
+  int dev, N, n, bc, zeta_pi, prec;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, N, n, bc, zeta_pi, prec) < std::tie(o.dev, o.N, o.n, o.bc, o.zeta_pi, o.prec);
+  }
+};
+struct TuneChoice { int tune, dst_q, time_q; };
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+TuneKey tune_key(const Geom& g, int prec) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return TuneKey{dev, g.N, g.n, g.bc, g.zeta_pi, prec == PCB_MIXED ? 1 : 0};
+}
+
+void apply_choice(Geom& g, const TuneChoice& c) {
+  g.tune = c.tune; g.dst_q = c.dst_q; g.time_q = c.time_q;
+  set_shapes(g);
+}
+
+// constant-coefficient problems only: the multigrid route has its own shapes
+void apply_cached_tuning(Geom& g, int prec) {
+  if (g.var_a) return;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune_cache.find(tune_key(g, prec));
+  if (it != g_tune_cache.end()) apply_choice(g, it->second);
 }
 
 }  // namespace
@@ -266,6 +303,7 @@ int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStream_t st
   B.off_vec = doff + 7 * stride; B.tot_vec = tots[7];
   B.count = count;
   B.stream = st;
+  B.fem_m = count == 1 && gs[0].fem ? gs[0].m : 0;
   B.dst_q = gs[0].dst_q;
   B.time_q = gs[0].time_q;
   for (const Geom& g : gs) {   // mixed sizes: shared launches dispatch per instance
@@ -370,6 +408,8 @@ int validate_desc(const pcb_desc* d) {
   if (d->a_edges && !pow2(d->N + 1)) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges && !mg_available()) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges && d->n > 512) return PCB_ERR_UNSUPPORTED;
+  if (d->fem != 0 && d->fem != 1) return PCB_ERR_INVALID_ARG;
+  if (d->fem && (neu || d->a_edges)) return PCB_ERR_UNSUPPORTED;
   if (d->a_edges) {
     const long long ne = 2LL * d->N * (d->N + 1);
     for (long long k = 0; k < ne; ++k)
@@ -390,6 +430,7 @@ void init_geom(const pcb_desc* d, Geom& g) {
   const double a0 = d->a_const > 0.0 ? d->a_const : 1.0;
   g.c = a0 * g.tau / (g.h * g.h);
   g.var_a = d->a_edges ? 1 : 0;
+  g.fem = d->fem ? 1 : 0;
   g.zeta = d->zeta;
   g.zeta_pi = std::fabs(d->zeta - M_PI) <= 1e-12 ? 1 : 0;
   make_plan(g.M, g.pdst);
@@ -409,6 +450,7 @@ size_t table_layout(const Geom& g, TableLayout& t) {
   t.twdd = take((size_t)M * 16); t.twdf = take((size_t)M * 8); t.twtd = take((size_t)n * 16);
   t.twtf = take((size_t)n * 8); t.pred = take((size_t)n * 16); t.pref = take((size_t)n * 8);
   t.ax = take(ne * 8); t.ay = take(ne * 8); t.dg = take(g.var_a ? (size_t)g.m * 8 : 0);
+  t.ms = take(g.fem ? (size_t)N * 8 : 0);
   t.bytes = off_b;
   return off_b;
 }
@@ -424,6 +466,14 @@ void fill_tables(const pcb_desc* d, const Geom& g, const TableLayout& t, unsigne
     const int k = g.bc == PCB_BC_NEUMANN ? q : q + 1;
     const double s = std::sin(k * M_PI / (2.0 * g.L));
     kap[q] = a0 * 4.0 / (g.h * g.h) * s * s;
+    if (g.fem) {
+      // linear elements: K1 = (1/h) tridiag(-1, 2, -1) and M1 = (h/6) tridiag(1, 4, 1) share the sine
+      // modes; kappa1 = (4/h) sin^2(k pi h/2), mu = (h/6)(4 + 2 cos(k pi h)); M1^{-1/2} K1 M1^{-1/2}
+      // has the eigenvalues kappa1/mu
+      const double mu = g.h / 6.0 * (4.0 + 2.0 * std::cos(k * M_PI * g.h));
+      ((double*)(host + t.ms))[q] = mu;
+      kap[q] = a0 * (4.0 / g.h) * s * s / mu;
+    }
   }
   // lambda(S_n) at F-slot r: psi_r = -(zeta + 2 pi r)/n (zeta = pi: -pi (2r+1)/n), f1/f2 with
   // f1 = 1 - e^{i psi}, f2 = theta + (1-theta) e^{i psi}
@@ -480,6 +530,7 @@ void bind_tables(Geom& g, const TableLayout& t, unsigned char* tb) {
   if (g.var_a) {
     g.axs = (const double*)(tb + t.ax); g.ays = (const double*)(tb + t.ay); g.dgs = (const double*)(tb + t.dg);
   }
+  g.mass = g.fem ? (const double*)(tb + t.ms) : nullptr;
 }
 
 }  // namespace pcb
@@ -500,6 +551,7 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
   cudaGetDevice(&p->device);
   Geom& g = p->g;
   init_geom(d, g);
+  apply_cached_tuning(g, d->precision);
   if (upload_constants() != cudaSuccess) { delete p; return PCB_ERR_CUDA; }
   auto fail = [&](int code) { pcb_destroy(p); return code; };
   TableLayout lay;
@@ -512,7 +564,9 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
   bind_tables(g, lay, (unsigned char*)p->tables);
   // ---- preconditioner scratch: 2mn values, FP64-sized so both precisions fit ----
   // (the pipelined FP32 passes keep two buffers of padded rows in it: 16 n N lr bytes)
-  const size_t sbytes = std::max<size_t>((size_t)2 * g.mn * sizeof(double), (size_t)16 * g.n * g.N * (size_t)g.lr);
+  // (sized for the padded layout of the pipelined passes even when a tuned choice does not use it,
+  // so that pcb_autotune may try every kernel family on this problem)
+  const size_t sbytes = std::max<size_t>((size_t)2 * g.mn * sizeof(double), (size_t)16 * g.n * g.N * (size_t)(g.L + 16));
   if (cudaMalloc(&p->scratch, sbytes) != cudaSuccess) return fail(PCB_ERR_OUT_OF_MEMORY);
   p->bytes += sbytes;
   g.scratch = p->scratch;
@@ -1019,7 +1073,17 @@ extern "C" {
 int pcb_assemble_rhs(pcb_problem* p, int op, const double* g_dev, const double* f_dev, const double* y0_dev,
                      double* b_dev) {
   if (!p || !g_dev || !f_dev || !b_dev || (op != PCB_OP_A && op != PCB_OP_AHAT)) return PCB_ERR_INVALID_ARG;
+  if (p->g.fem && y0_dev) return PCB_ERR_UNSUPPORTED;
   CK(launch_rhs(p->g, p->stream, op, g_dev, f_dev, y0_dev, b_dev));
+  if (p->g.fem) {
+    // f~, g~ carry M (Sec. 1) and the system's right-hand side M^{-1/2}: with y0 = 0 both halves are
+    // M^{1/2} applied to the time combinations of the samples (FEM_MASS_SQRT = 0)
+    p->hS.v[SL_UIN] = b_dev;
+    p->hS.v[SL_UOUT] = b_dev;
+    int rc;
+    if ((rc = upload_slots(p))) return rc;
+    CK(launch_fem_spatial(p->B, 0, PCB_OP_A, SL_UIN, SL_UOUT));
+  }
   return PCB_OK;
 }
 
@@ -1047,8 +1111,219 @@ int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_d
   return apply_precond(p, p->B, kind, precision, SL_UIN, SL_UOUT);
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Autotuner (pcb_autotune): times the preconditioner apply of one problem under each candidate
+// kernel configuration and keeps the fastest.  Candidates (constant coefficient only):
+//   * the pipelined FP32 kernel families on or off for the spatial and the time passes, and the
+//     n = 512 time-major hand-off on or off;
+//   * for the tile kernels, the register-FFT radix (values per lane Q, i.e. P = M / Q lanes per
+//     line, with Q and 2Q where the kernels support them) and the tile size (lines or columns
+//     per block, from a per-tile element budget at 1/2, 1 and 2 times the default).
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void k_tune_fill(double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = sin(0.37 * (double)(i % 100003)) + 0.25;
+}
+
+// out[0] = max |a - b|, out[1] = max |b| (non-negative doubles order like their bit patterns, so
+// an integer atomic max serves; out must start at zero)
+__global__ void k_tune_diff(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                            unsigned long long* __restrict__ out) {
+  double d = 0.0, r = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    d = fmax(d, fabs(a[i] - bi));
+    r = fmax(r, fabs(bi));
+  }
+  if (!(d == d)) d = INFINITY;      // a NaN difference counts as infinite
+  for (int o = 16; o > 0; o >>= 1) {
+    d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, (unsigned long long)__double_as_longlong(d));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(r));
+  }
+}
+
+constexpr size_t kSmemMax = 227 * 1024;
+
+double __longlong_as_double_host(unsigned long long v) {
+  double d;
+  std::memcpy(&d, &v, sizeof(d));
+  return d;
+}
+
+bool tune_valid(const Geom& g0, TuneChoice c, int prec) {
+  Geom g = g0;
+  apply_choice(g, c);
+  const int pr = prec == PCB_MIXED ? 1 : 0;
+  const bool pipe_d = pr && pipe_dst_p(g), pipe_t = pr && pipe_time_p(g);
+  if (!pipe_d && dst_smem_bytes(g, pr) > kSmemMax) return false;
+  if (!pipe_t && time_smem_bytes(g, pr) > kSmemMax) return false;
+  return true;
+}
+
+std::vector<TuneChoice> tune_candidates(const Geom& g, int prec) {
+  const int q0d = dst_Q(g.M), q0t = time_Q(g.n);
+  std::vector<int> qd{q0d}, qt{q0t};
+  const int P0d = g.M / q0d;
+  if (2 * q0d <= 24 && q_supported(2 * q0d) && P0d >= 2 && g.M % (2 * q0d) == 0) qd.push_back(2 * q0d);
+  if (2 * q0t <= 16 && g.n / q0t >= 2) qt.push_back(2 * q0t);
+  std::vector<TuneChoice> out;
+  auto add = [&](int tune, int dq, int tq) {
+    const TuneChoice c{tune, dq, tq};
+    for (const auto& o : out) if (o.tune == c.tune && o.dst_q == dq && o.time_q == tq) return;
+    if (tune_valid(g, c, prec)) out.push_back(c);
+  };
+  add(0, q0d, q0t);                                   // the default shapes come first
+  Geom d = g;
+  apply_choice(d, out.empty() ? TuneChoice{0, q0d, q0t} : out[0]);
+  const bool mixed = prec == PCB_MIXED;
+  const bool can_pipe_t = mixed && pipe_time_p(d), can_pipe_d = mixed && pipe_dst_p(d);
+  if (can_pipe_d && g.n == 512 && g.zeta_pi) add(TUNE_NO_HANDOFF, q0d, q0t);
+  for (int b = 0; b < 3; ++b) {
+    const int bs = b << 4;
+    for (int dq : qd) {
+      if (can_pipe_t) add(TUNE_NO_PIPE_DST | bs, dq, q0t);          // tile spatial passes, pipelined time
+      for (int tq : qt) add(TUNE_NO_PIPE_DST | TUNE_NO_PIPE_TIME | bs, dq, tq);   // tile kernels only
+    }
+  }
+  return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pcb_autotune(pcb_problem* p, int kind, int reps, pcb_tune_info* info) {
+  if (!p) return PCB_ERR_INVALID_ARG;
+  if (kind == PCB_PREC_NONE) kind = p->g.bc == PCB_BC_NEUMANN ? PCB_PREC_PS : PCB_PREC_ABS_PS;
+  if (kind != PCB_PREC_ABS_PS && kind != PCB_PREC_PS && kind != PCB_PREC_PMS) return PCB_ERR_INVALID_ARG;
+  if (p->g.var_a) return PCB_ERR_UNSUPPORTED;        // the multigrid route is not tuned
+  if (kind != PCB_PREC_PS && p->g.bc == PCB_BC_NEUMANN) return PCB_ERR_UNSUPPORTED;
+  if (reps <= 0) reps = 3;
+  const int prec = p->desc.precision;
+  const size_t nv = (size_t)2 * p->g.mn;
+  double* buf = nullptr;
+  unsigned long long* dmax = nullptr;
+  unsigned long long hmax[2] = {0, 0};
+  if (cudaMalloc(&buf, 3 * nv * sizeof(double)) != cudaSuccess || cudaMalloc(&dmax, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError(); cudaFree(buf); return PCB_ERR_OUT_OF_MEMORY;
+  }
+  auto done = [&](int rc) { cudaStreamSynchronize(p->stream); cudaFree(buf); cudaFree(dmax); return rc; };
+  double* yref = buf + 2 * nv;
+  // a candidate whose result differs from the default configuration's by more than the rounding of
+  // the precision (relative max-norm) is rejected rather than timed
+  const double vtol = prec == PCB_MIXED ? 1e-5 : 1e-12;
+  int rejected = 0;
+  k_tune_fill<<<1024, 256, 0, p->stream>>>(buf, (long long)nv);
+  p->hS.v[SL_UIN] = buf;
+  p->hS.v[SL_UOUT] = buf + nv;
+  int rc;
+  if ((rc = upload_slots(p))) return done(rc);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return done(PCB_ERR_CUDA);
+  const Geom g0 = p->g;
+  Geom gd = g0;
+  gd.tune = 0; gd.dst_q = dst_Q(gd.M); gd.time_q = time_Q(gd.n);
+  set_shapes(gd);
+  const std::vector<TuneChoice> cands = tune_candidates(gd, prec);
+  std::vector<int> staging;
+  // make candidate c the problem's configuration (host mirror, device Geom, launch offsets)
+  auto install = [&](const TuneChoice& c) -> int {
+    Geom g = gd;
+    apply_choice(g, c);
+    g.scratch = g0.scratch;
+    p->g = g;
+    CK(cudaMemcpyAsync(p->dG, &p->g, sizeof(Geom), cudaMemcpyHostToDevice, p->stream));
+    int r = fill_batch(p->B, std::vector<Geom>(1, p->g), p->doff, p->stream, staging);
+    if (r) return r;
+    CK(cudaStreamSynchronize(p->stream));
+    return PCB_OK;
+  };
+  double best = 1e300, def_ms = 0.0;
+  int best_k = -1, timed = 0;
+  for (size_t k = 0; k < cands.size(); ++k) {
+    if ((rc = install(cands[k]))) break;
+    if (launch_precond_fast(p->B, kind, prec, SL_UIN, SL_UOUT) != cudaSuccess) { cudaGetLastError(); continue; }
+    if (k == 0) {
+      if (cudaMemcpyAsync(yref, buf + nv, nv * sizeof(double), cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess) {
+        cudaGetLastError(); break;
+      }
+    } else {
+      if (cudaMemsetAsync(dmax, 0, 2 * sizeof(unsigned long long), p->stream) != cudaSuccess) { cudaGetLastError(); break; }
+      k_tune_diff<<<1024, 256, 0, p->stream>>>(buf + nv, yref, (long long)nv, dmax);
+      if (cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+          cudaStreamSynchronize(p->stream) != cudaSuccess) { cudaGetLastError(); break; }
+      const double dm = __longlong_as_double_host(hmax[0]), rm = __longlong_as_double_host(hmax[1]);
+      if (!(dm <= vtol * rm)) { ++rejected; continue; }
+    }
+    cudaEventRecord(e0, p->stream);
+    bool ok = true;
+    for (int r = 0; r < reps && ok; ++r) ok = launch_precond_fast(p->B, kind, prec, SL_UIN, SL_UOUT) == cudaSuccess;
+    cudaEventRecord(e1, p->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || !ok) { cudaGetLastError(); continue; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double avg = ms / reps;
+    ++timed;
+    if (k == 0) def_ms = avg;
+    if (avg < best) { best = avg; best_k = (int)k; }
+  }
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  if (best_k < 0) {           // nothing could be timed: keep the configuration the problem had
+    p->g = g0;
+    cudaMemcpyAsync(p->dG, &p->g, sizeof(Geom), cudaMemcpyHostToDevice, p->stream);
+    fill_batch(p->B, std::vector<Geom>(1, p->g), p->doff, p->stream, staging);
+    return done(rc ? rc : PCB_ERR_CUDA);
+  }
+  if ((rc = install(cands[best_k]))) return done(rc);
+  // captured iterations launch the kernels of the old configuration
+  if (p->git) { cudaGraphExecDestroy(p->git); p->git = nullptr; }
+  for (cudaGraphExec_t& e : p->garn) if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+  p->git_kind = p->garn_kind = -1;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[tune_key(p->g, prec)] = cands[best_k];
+  }
+  if (info) {
+    info->candidates = timed;
+    info->rejected = rejected;
+    info->chosen = best_k;
+    info->default_ms = def_ms;
+    info->best_ms = best;
+    info->pipelined_dst = prec == PCB_MIXED && pipe_dst_p(p->g);
+    info->pipelined_time = prec == PCB_MIXED && pipe_time_p(p->g);
+    info->time_major_handoff = prec == PCB_MIXED && (pipe_dst_code(p->g) & 64) ? 1 : 0;
+    info->dst_lanes = p->g.M / p->g.dst_q;
+    info->time_lanes = p->g.n / p->g.time_q;
+    info->tile_scale = tune_budget_shift(p->g.tune) == 1 ? 0.5 : tune_budget_shift(p->g.tune) == 2 ? 2.0 : 1.0;
+  }
+  return done(PCB_OK);
+}
+
 int pcb_recover(pcb_problem* p, const double* x_dev, double* y_dev, double* p_dev) {
   if (!p || !x_dev || !y_dev || !p_dev) return PCB_ERR_INVALID_ARG;
+  if (p->g.fem) {
+    // (B2^{-1} (x) M^{-1/2}): the spatial factor first (FEM_MASS_ISQRT = 1) into a staging vector
+    const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
+    if (!p->host_io) {
+      if (cudaMalloc(&p->host_io, 2 * vb) != cudaSuccess) { cudaGetLastError(); p->host_io = nullptr; return PCB_ERR_OUT_OF_MEMORY; }
+      p->bytes += 2 * vb;
+    }
+    p->hS.v[SL_UIN] = (double*)x_dev;
+    p->hS.v[SL_UOUT] = p->host_io;
+    int rc;
+    if ((rc = upload_slots(p))) return rc;
+    CK(launch_fem_spatial(p->B, 1, PCB_OP_A, SL_UIN, SL_UOUT));
+    CK(launch_recover(p->g, p->stream, p->host_io, y_dev, p_dev));
+    return PCB_OK;
+  }
   CK(launch_recover(p->g, p->stream, x_dev, y_dev, p_dev));
   return PCB_OK;
 }
@@ -1335,6 +1610,7 @@ extern "C" int pcb_batch_solve(pcb_problem* const* problems, int count, const pc
     resolve_defaults(problems[k], opts, c);
     if (c.method == PCB_MINRES && c.kind == PCB_PREC_PS) return PCB_ERR_INVALID_ARG;
     if (problems[k]->g.var_a) return PCB_ERR_UNSUPPORTED;      // multigrid instances solve one at a time
+    if (problems[k]->g.fem) return PCB_ERR_UNSUPPORTED;        // finite elements: single problems
     if (problems[k]->g.bc == PCB_BC_NEUMANN && (c.method == PCB_MINRES || c.kind != PCB_PREC_PS))
       return PCB_ERR_UNSUPPORTED;
     BGroup* G = nullptr;
@@ -1541,6 +1817,7 @@ namespace {
 long long srv_bytes(const pcb_desc* d, int restart) {
   Geom g;
   init_geom(d, g);
+  apply_cached_tuning(g, d->precision);
   SrvLayout L;
   srv_layout(g, srv_method(*d), restart, L);
   return (long long)L.total;
@@ -1761,7 +2038,7 @@ int pcb_server_create(const pcb_server_opts* o, pcb_server** out) {
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); delete S; return PCB_ERR_CUDA; }
   const size_t head = (size_t)2 << 30;
   const size_t want = std::min<size_t>((size_t)o->budget_bytes, free_b > head ? free_b - head : 0);
-  if (want < ((size_t)1 << 20) || S->arena.reserve(want) != cudaSuccess) {
+  if (want < 256 || S->arena.reserve(want) != cudaSuccess) {
     cudaGetLastError();
     delete S;
     return PCB_ERR_OUT_OF_MEMORY;
@@ -1811,7 +2088,7 @@ void pcb_server_destroy(pcb_server* S) {
 
 int pcb_server_submit(pcb_server* S, const pcb_desc* d, const double* rhs, double* x, long long tag) {
   if (!S || !d || !rhs || !x) return PCB_ERR_INVALID_ARG;
-  if (d->a_edges) return PCB_ERR_UNSUPPORTED;
+  if (d->a_edges || d->fem) return PCB_ERR_UNSUPPORTED;
   pcb_desc dd = *d;
   dd.precision = S->o.precision;
   dd.stream = (void*)S->st;
@@ -1834,6 +2111,7 @@ int srv_admit(pcb_server* S, SrvGroup& G, int k, const SrvReq& r, bool* fitted) 
   *fitted = false;
   Geom g;
   init_geom(&r.desc, g);
+  apply_cached_tuning(g, S->o.precision);
   SrvLayout L;
   srv_layout(g, G.method, S->o.restart, L);
   unsigned char* blk = (unsigned char*)S->arena.alloc(L.total);

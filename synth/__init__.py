@@ -90,6 +90,45 @@ def example1_data(N: int, n: int, T: float = 1.0):
     return y.copy(), (2.0 * math.pi ** 2 - 1.0) * y, y, np.zeros_like(y)
 
 
+EXAMPLE2_EPS = 1e-5
+
+
+def example2_coefficient(x1, x2):
+    """a(x1, x2) = 1e-5 sin(pi x1 x2) of Example 2."""
+    return EXAMPLE2_EPS * np.sin(math.pi * x1 * x2)
+
+
+def example2_data(N: int, n: int, gamma: float, T: float = 1.0):
+    """Example 2 of the paper's numerical section (variable a = 1e-5 sin(pi x1 x2)), with the exact
+    solution y = e^{-t} x1(1-x1) x2(1-x2), p = gamma sin(pi t) sin(pi x1) sin(pi x2).  The printed
+    f and g are partly garbled; they are the data that make (y, p) solve the optimality system
+    y_t - div(a grad y) = f + p/gamma, -p_t - div(a grad p) = g - y, i.e.
+      f = y_t - div(a grad y) - p/gamma,   g = -p_t - div(a grad p) + y,
+    with div(a grad u) = a_x1 u_x1 + a u_x1x1 + a_x2 u_x2 + a u_x2x2 written out below (they agree
+    term by term with the legible parts of the printed formulas).  Returns (g, f, y_exact,
+    p_exact, a_edges), the first four (n+1, N*N) at t_k = k tau on the interior nodes."""
+    X, Y = grid(N)
+    X, Y = X.reshape(1, -1), Y.reshape(1, -1)
+    t = times(n, T)[:, None]
+    eps, pi = EXAMPLE2_EPS, math.pi
+    q = lambda s: s * (1.0 - s)
+    sxy, cxy = np.sin(pi * X * Y), np.cos(pi * X * Y)
+    a, ax, ay = eps * sxy, eps * pi * Y * cxy, eps * pi * X * cxy
+    Q = q(X) * q(Y)
+    # y = e^{-t} Q: y_x1 = e^{-t} (1 - 2 x1) q(x2), y_x1x1 = -2 e^{-t} q(x2) (and symmetrically)
+    div_a_grad_Q = ax * (1 - 2 * X) * q(Y) + a * (-2.0) * q(Y) + ay * q(X) * (1 - 2 * Y) + a * (-2.0) * q(X)
+    S = np.sin(pi * X) * np.sin(pi * Y)
+    # p = gamma sin(pi t) S: S_x1 = pi cos(pi x1) sin(pi x2), S_x1x1 = -pi^2 S (and symmetrically)
+    div_a_grad_S = (ax * pi * np.cos(pi * X) * np.sin(pi * Y) + ay * pi * np.sin(pi * X) * np.cos(pi * Y)
+                    - 2.0 * pi ** 2 * a * S)
+    et = np.exp(-t)
+    y = et * Q
+    p = gamma * np.sin(pi * t) * S
+    f = -et * Q - et * div_a_grad_Q - np.sin(pi * t) * S
+    g = -gamma * pi * np.cos(pi * t) * S - gamma * np.sin(pi * t) * div_a_grad_S + et * Q
+    return g, f, y, p, variable_coefficient_edges(N, example2_coefficient)
+
+
 def neumann_grid(N: int) -> tuple[np.ndarray, np.ndarray]:
     """Node coordinates x1[j, i], x2[j, i] (i fastest) of the Neumann grid: N nodes per side
     including the boundary, x = i h, h = 1/(N-1)."""
