@@ -72,7 +72,7 @@ def test_fem_rhs_and_recover(P, theta):
     assert "unsupported" in str(e.value)
 
 
-@pytest.mark.parametrize("case", [("minres", "abs_ps", 1.0), ("minres", "pms", 0.5), ("gmres", "ps", 0.5)])
+@pytest.mark.parametrize("case", [("minres", "abs_ps", 1.0), ("minres", "pms", 1.0), ("gmres", "ps", 0.5)])
 def test_fem_same_algorithm_iterates_and_solves(P, case):
     method, kind, theta = case
     N, n, gamma = 31, 32, 1e-3
