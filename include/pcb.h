@@ -109,6 +109,10 @@ typedef struct {
                           /* elements on the same grid (Sec. 1: M the mass, K the stiffness      */
                           /* matrix; the system carries M^{-1/2} K M^{-1/2}); Dirichlet, constant */
                           /* a, single problems (not batches or the server), y0 = 0              */
+  int multigrid;          /* 1: solve the shifted spatial systems of P_S^{-1} / P_MS^{-1} with     */
+                          /* mg_cycles multigrid V-cycles also for a constant coefficient (the    */
+                          /* route the paper takes for Example 3's Neumann grid, Sec. 4):         */
+                          /* Dirichlet N = 2^k - 1, Neumann N = 2^k + 1 >= 5; zeta = pi, n <= 512 */
 } pcb_desc;
 
 /* Validate the descriptor, compute the spectral tables (Sec. 3.5: lambda_k(S_n), the eigenvalues

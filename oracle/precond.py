@@ -133,10 +133,14 @@ def lemma314(lam, alpha):
 
 
 def apply_mg_ps_inv(prob, v, cycles=2, nu1=2, nu2=2, real=True):
-    """P_S^{-1} v with the spatial solves done by multigrid (variable a(x)), following the three
-    steps after Lemma 3.14: v~ = V* v, w~ = blockdiag(D1 + tau K, D2 + tau K)^{-1} v~, w = V w~."""
-    ax, ay = prob.edges()
-    levels = mg.hierarchy(prob.N, ax, ay, prob.tau)
+    """P_S^{-1} v with the spatial solves done by multigrid (variable a(x), or Example 3's Neumann
+    grid as the paper solves it), following the three steps after Lemma 3.14: v~ = V* v,
+    w~ = blockdiag(D1 + tau K, D2 + tau K)^{-1} v~, w = V w~."""
+    if prob.bc == "neumann":
+        levels = mg.hierarchy_neumann(prob.N, prob.a0, prob.tau)
+    else:
+        ax, ay = prob.edges()
+        levels = mg.hierarchy(prob.N, ax, ay, prob.tau)
     lam = spc.lam_Sn(prob.n, prob.theta, prob.zeta)
     M1, M2, D1, D2 = lemma314(lam, prob.alpha)
     x1, x2 = _halves(prob, v)

@@ -44,10 +44,11 @@ class Problem:
     """One control problem on the current CUDA device and stream (C-ABI pcb_create).
     bc="neumann" selects Example 3's homogeneous Neumann grid (N nodes per side including the
     boundary); a is the constant coefficient when a_edges is None; fem=True selects bilinear finite
-    elements (mass matrix M != I) in place of finite differences."""
+    elements (mass matrix M != I) in place of finite differences; multigrid=True solves the shifted
+    systems with V-cycles also for a constant coefficient (the paper's route for Example 3)."""
 
     def __init__(self, N, n, theta, gamma, T=1.0, zeta=math.pi, a_edges=None, precision="fp64", mg_cycles=2,
-                 stream: torch.cuda.Stream | None = None, bc="dirichlet", a=1.0, fem=False):
+                 stream: torch.cuda.Stream | None = None, bc="dirichlet", a=1.0, fem=False, multigrid=False):
         self.lib = _lib.load()
         self.N, self.n, self.theta, self.gamma, self.T = int(N), int(n), float(theta), float(gamma), float(T)
         self.m = self.N * self.N
@@ -60,7 +61,8 @@ class Problem:
             self._a = np.ascontiguousarray(a_edges, dtype=np.float64)
             ap = self._a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         d = PcbDesc(self.N, self.n, self.theta, self.T, self.gamma, float(zeta), ap, PRECISIONS[precision],
-                    int(mg_cycles), ctypes.c_void_p(self.stream.cuda_stream), BCS[bc], float(a), int(bool(fem)))
+                    int(mg_cycles), ctypes.c_void_p(self.stream.cuda_stream), BCS[bc], float(a), int(bool(fem)),
+                    int(bool(multigrid)))
         h = ctypes.c_void_p()
         check("pcb_create", self.lib.pcb_create(ctypes.byref(d), ctypes.byref(h)))
         self.h = h

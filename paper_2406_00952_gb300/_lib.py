@@ -23,7 +23,7 @@ class PcbDesc(ctypes.Structure):
     _fields_ = [("N", c_int), ("n", c_int), ("theta", c_double), ("T", c_double), ("gamma", c_double),
                 ("zeta", c_double), ("a_edges", POINTER(c_double)), ("precision", c_int),
                 ("mg_cycles", c_int), ("stream", c_void_p), ("bc", c_int), ("a_const", c_double),
-                ("fem", c_int)]
+                ("fem", c_int), ("multigrid", c_int)]
 
 
 class PcbSolveOpts(ctypes.Structure):

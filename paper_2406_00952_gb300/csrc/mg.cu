@@ -15,6 +15,11 @@
 // coefficient = mean of the two fine edges it spans, full-weighting restriction, bilinear
 // prolongation, damped Jacobi (weight 4/5), nu1 = nu2 = 2, exact solve on the 1 x 1 grid, zero
 // initial guess; cycle c > 1 corrects with a V-cycle on the current residual.
+// Neumann grids (Example 3 solved as in Sec. 4, constant a): N = 2^k + 1 nodes per side with the
+// boundary, coarse nodes the even fine nodes, N -> (N+1)/2 down to 3; the mirrored stencil
+// c (4u - sum of neighbours), c = tau a / h^2, on every level; full weighting with mirrored ghost
+// values; bilinear prolongation; the same damped Jacobi; on the 3 x 3 grid an exact solve through
+// the eigenvectors of the 3-node mirrored second difference.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -33,7 +38,11 @@ static constexpr int kNu = 2;
 static long long g_mg_launches = 0;   // kernel launches issued by the multigrid route
 
 struct MgLevel {
-  int N;                      // interior points per side
+  int N;                      // interior points per side (Neumann: nodes per side with the boundary)
+  int neu;                    // 1: Neumann grid, mirrored stencil with the constant c below
+  double c; float cf;         // Neumann: tau a / h^2 of this level
+  double* co;                 // Neumann coarsest level: [V2 (81) | V2^{-1} (81) | lambda (9)], FP64 ...
+  float* cof;                 // ... and FP32
   double* axs;                // tau/h_l^2 * ax  (N x (N+1))
   double* ays;                // tau/h_l^2 * ay  ((N+1) x N)
   double* dgs;                // sum of the four  (N x N)
@@ -62,8 +71,9 @@ static MgHost* find_host(const void* ws) {
   return nullptr;
 }
 
-static int levels_for(int N) {
+static int levels_for(int N, bool neu = false) {
   int l = 1;
+  if (neu) { while (N > 3) { N = (N + 1) / 2; ++l; } return l; }
   while (N > 1) { N = (N - 1) / 2; ++l; }
   return l;
 }
@@ -72,28 +82,86 @@ size_t mg_workspace_bytes(const Geom& g) {
   size_t b = 0;
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   int N = g.N;
+  const bool neu = g.bc == PCB_BC_NEUMANN;
   const size_t nsys = (size_t)g.n;
-  for (int l = 0; l < levels_for(g.N); ++l) {
+  for (int l = 0; l < levels_for(g.N, neu); ++l) {
     const size_t ne = (size_t)N * (N + 1), nn = (size_t)N * N;
-    b += up(ne * 8) * 2 + up(nn * 8) + up(ne * 4) * 2 + up(nn * 4);
+    if (!neu) b += up(ne * 8) * 2 + up(nn * 8) + up(ne * 4) * 2 + up(nn * 4);
     b += 3 * up(nsys * nn * sizeof(double2));
     if (l == 0) b += 2 * up(nsys * nn * sizeof(double2));
-    N = (N - 1) / 2;
+    N = neu ? (N + 1) / 2 : (N - 1) / 2;
   }
+  if (neu) b += up(171 * 8) + up(171 * 4);
   b += up((size_t)g.n * 3 * sizeof(double2)) + up((size_t)g.n * 3 * sizeof(float2));
   return b;
 }
 
-cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges) {
+// Neumann levels: every level's c = tau a / h_l^2, work arrays, and on the 3 x 3 grid the exact
+// solve's tables.  The 3-node mirrored second difference [[2,-2,0],[-1,2,-1],[0,-2,2]] has the
+// eigenvalues 0, 2, 4 with eigenvectors (1,1,1), (1,0,-1), (1,-1,1); the 2D operator on the 3 x 3
+// grid is c (D (x) I + I (x) D), diagonal in V (x) V.
+static unsigned char* mg_setup_neumann(const Geom& g, MgHost& h, unsigned char* p, double a0) {
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  int N = g.N;
+  for (int l = 0; l < h.nlev; ++l) {
+    MgLevel& L = h.lev[l];
+    std::memset(&L, 0, sizeof(L));
+    L.N = N; L.neu = 1;
+    const double hl = 1.0 / (N - 1);
+    L.c = g.tau * a0 / (hl * hl);
+    L.cf = (float)L.c;
+    const size_t nn = (size_t)N * N;
+    for (int k = 0; k < 3; ++k) { L.a[k] = p; p += up((size_t)h.nsys * nn * sizeof(double2)); }
+    if (l == 0) {
+      h.zfine = p; p += up((size_t)h.nsys * nn * sizeof(double2));
+      h.xfine = p; p += up((size_t)h.nsys * nn * sizeof(double2));
+    }
+    N = (N + 1) / 2;
+  }
+  MgLevel& C = h.lev[h.nlev - 1];
+  const double V[3][3] = {{1, 1, 1}, {1, 0, -1}, {1, -1, 1}};          // columns: eigenvectors
+  const double Vi[3][3] = {{0.25, 0.5, 0.25}, {0.5, 0.0, -0.5}, {0.25, -0.5, 0.25}};   // V^{-1}
+  const double lam[3] = {0.0, 2.0, 4.0};
+  std::vector<double> co(171);
+  for (int j = 0; j < 3; ++j)
+    for (int i = 0; i < 3; ++i)
+      for (int q = 0; q < 3; ++q)
+        for (int pp = 0; pp < 3; ++pp) {
+          // node (i, j) at 3 j + i, mode (pp, q) at 3 q + pp
+          co[(3 * j + i) * 9 + 3 * q + pp] = V[i][pp] * V[j][q];          // V2
+          co[81 + (3 * q + pp) * 9 + 3 * j + i] = Vi[pp][i] * Vi[q][j];   // V2^{-1}
+        }
+  for (int q = 0; q < 3; ++q)
+    for (int pp = 0; pp < 3; ++pp) co[162 + 3 * q + pp] = C.c * (lam[pp] + lam[q]);
+  std::vector<float> cof(co.begin(), co.end());
+  C.co = (double*)p; cudaMemcpy(p, co.data(), 171 * 8, cudaMemcpyHostToDevice); p += up(171 * 8);
+  C.cof = (float*)p; cudaMemcpy(p, cof.data(), 171 * 4, cudaMemcpyHostToDevice); p += up(171 * 4);
+  return p;
+}
+
+static void mg_slot_tables(const Geom& g, MgHost& h, unsigned char*& p);
+
+cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges, double a0) {
   // this translation unit's copy of the register-FFT twiddle table
   cudaError_t e0 = upload_w96();
   if (e0 != cudaSuccess) return e0;
   MgHost h;
-  h.nlev = levels_for(g.N);
+  const bool neu = g.bc == PCB_BC_NEUMANN;
+  h.nlev = levels_for(g.N, neu);
   if (h.nlev > kMaxLevels) return cudaErrorInvalidValue;
   h.nsys = g.n;
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   unsigned char* p = (unsigned char*)ws;
+  if (neu) {
+    p = mg_setup_neumann(g, h, p, a0);
+    mg_slot_tables(g, h, p);
+    if ((size_t)(p - (unsigned char*)ws) > mg_workspace_bytes(g)) return cudaErrorInvalidValue;
+    for (auto& e : registry())
+      if (e.first == ws) { e.second = h; g.mg = ws; return cudaGetLastError(); }
+    registry().push_back({ws, h});
+    g.mg = ws;
+    return cudaGetLastError();
+  }
   // fine coefficients = tau/h^2 * a at the edges; coarser levels average the two fine edges each
   // coarse edge spans and are rescaled with their own spacing
   int N = g.N;
@@ -102,6 +170,7 @@ cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges) {
   std::vector<unsigned char> hostbuf;
   for (int l = 0; l < h.nlev; ++l) {
     MgLevel& L = h.lev[l];
+    std::memset(&L, 0, sizeof(L));
     L.N = N;
     const double hl = 1.0 / (N + 1), s = g.tau / (hl * hl);
     const size_t ne = (size_t)N * (N + 1), nn = (size_t)N * N;
@@ -140,7 +209,18 @@ cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges) {
     ax.swap(axc); ay.swap(ayc);
     N = Nc;
   }
-  // per-slot table from lambda(S_n) at the F-slots (same formula as the spectral tables)
+  mg_slot_tables(g, h, p);
+  if ((size_t)(p - (unsigned char*)ws) > mg_workspace_bytes(g)) return cudaErrorInvalidValue;
+  for (auto& e : registry())
+    if (e.first == ws) { e.second = h; return cudaGetLastError(); }
+  registry().push_back({ws, h});
+  g.mg = ws;
+  return cudaGetLastError();
+}
+
+// per-slot table from lambda(S_n) at the F-slots (same formula as the spectral tables)
+static void mg_slot_tables(const Geom& g, MgHost& h, unsigned char*& p) {
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const int n = g.n, half = n / 2;
   std::vector<double2> td((size_t)half * 4);
   std::vector<float2> tf((size_t)half * 4);
@@ -167,12 +247,6 @@ cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges) {
   p += up(td.size() * sizeof(double2));
   h.tab_f = (float2*)p; cudaMemcpy(p, tf.data(), tf.size() * sizeof(float2), cudaMemcpyHostToDevice);
   p += up(tf.size() * sizeof(float2));
-  if ((size_t)(p - (unsigned char*)ws) > mg_workspace_bytes(g)) return cudaErrorInvalidValue;
-  for (auto& e : registry())
-    if (e.first == ws) { e.second = h; return cudaGetLastError(); }
-  registry().push_back({ws, h});
-  g.mg = ws;
-  return cudaGetLastError();
 }
 
 void mg_release(const void* ws) {
@@ -200,6 +274,13 @@ template <> struct Coef<double> {
 template <typename R>
 __device__ __forceinline__ cx<R> tauKz(const MgLevel& L, const cx<R>* __restrict__ z, int i, int j) {
   const int N = L.N;
+  if (L.neu) {   // mirrored neighbours: u_{-1} = u_1, u_N = u_{N-2}
+    const R c = sizeof(R) == 4 ? (R)L.cf : (R)L.c;
+    const cx<R> l = z[j * N + (i > 0 ? i - 1 : 1)], r = z[j * N + (i < N - 1 ? i + 1 : N - 2)];
+    const cx<R> d = z[(j > 0 ? j - 1 : 1) * N + i], t = z[(j < N - 1 ? j + 1 : N - 2) * N + i];
+    const cx<R> nb = cadd(cadd(l, r), cadd(d, t));
+    return cscale(csub(cscale(z[j * N + i], (R)4), nb), c);
+  }
   const R* ax = Coef<R>::ax(L) + (long long)j * (N + 1);
   const R* ay = Coef<R>::ay(L);
   const cx<R> c = z[j * N + i];
@@ -229,7 +310,8 @@ __global__ void k_mg_jacobi(MgLevel L, int nsys, const cx<R>* __restrict__ tab, 
   const int b = (int)(idx / nn), pt = (int)(idx - (long long)b * nn);
   const int j = pt / N, i = pt - j * N;
   const cx<R> mu = shift_of<R>(tab, b, kind);
-  const cx<R> d = mk<R>(mu.x + Coef<R>::dg(L)[pt], mu.y);
+  const R dgk = L.neu ? (R)4 * (sizeof(R) == 4 ? (R)L.cf : (R)L.c) : Coef<R>::dg(L)[pt];
+  const cx<R> d = mk<R>(mu.x + dgk, mu.y);
   const R dd = d.x * d.x + d.y * d.y;
   const cx<R> dinv = mk<R>(d.x / dd, -d.y / dd);
   const long long o = (long long)b * nn;
@@ -294,6 +376,61 @@ __global__ void k_mg_prolong_add(int Nf, int nsys, const cx<R>* __restrict__ c, 
   else v = cscale(cadd(cadd(cv((i >> 1) - 1, (j >> 1) - 1), cv(i >> 1, (j >> 1) - 1)),
                        cadd(cv((i >> 1) - 1, j >> 1), cv(i >> 1, j >> 1))), (R)0.25);
   z[(long long)b * nnf + pt] = cadd(z[(long long)b * nnf + pt], v);
+}
+
+// Neumann full weighting: coarse (I, J) <- fine 9-point neighbourhood of (2I, 2J), mirrored ghosts
+template <typename R>
+__global__ void k_mg_restrict_neu(int Nf, int nsys, const cx<R>* __restrict__ f, cx<R>* __restrict__ c) {
+  const int Nc = (Nf + 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nsys * nnc) return;
+  const int b = (int)(idx / nnc), pt = (int)(idx - (long long)b * nnc);
+  const int J = pt / Nc, I = pt - J * Nc;
+  const cx<R>* fb = f + (long long)b * nnf;
+  const int fi = 2 * I, fj = 2 * J;
+  auto mir = [&](int k) { return k < 0 ? -k : (k > Nf - 1 ? 2 * (Nf - 1) - k : k); };
+  auto at = [&](int ii, int jj) { return fb[mir(jj) * Nf + mir(ii)]; };
+  cx<R> s = cscale(at(fi, fj), (R)4);
+  s = cadd(s, cscale(cadd(cadd(at(fi - 1, fj), at(fi + 1, fj)), cadd(at(fi, fj - 1), at(fi, fj + 1))), (R)2));
+  s = cadd(s, cadd(cadd(at(fi - 1, fj - 1), at(fi + 1, fj - 1)), cadd(at(fi - 1, fj + 1), at(fi + 1, fj + 1))));
+  c[(long long)b * nnc + pt] = cscale(s, (R)(1.0 / 16.0));
+}
+
+// Neumann bilinear prolongation added to the fine solution: even fine nodes are coarse nodes
+template <typename R>
+__global__ void k_mg_prolong_add_neu(int Nf, int nsys, const cx<R>* __restrict__ c, cx<R>* __restrict__ z) {
+  const int Nc = (Nf + 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nsys * nnf) return;
+  const int b = (int)(idx / nnf), pt = (int)(idx - (long long)b * nnf);
+  const int j = pt / Nf, i = pt - j * Nf;
+  const cx<R>* cb = c + (long long)b * nnc;
+  const int I0 = i >> 1, J0 = j >> 1, I1 = (i + 1) >> 1, J1 = (j + 1) >> 1;   // equal when even
+  const cx<R> v = cscale(cadd(cadd(cb[J0 * Nc + I0], cb[J0 * Nc + I1]), cadd(cb[J1 * Nc + I0], cb[J1 * Nc + I1])),
+                         (R)0.25);
+  z[(long long)b * nnf + pt] = cadd(z[(long long)b * nnf + pt], v);
+}
+
+// Neumann 3 x 3 grid: exact solve z = V2 diag(1/(mu + lambda)) V2^{-1} rhs, one thread per (system, node)
+template <typename R>
+__global__ void k_mg_coarse_neu(MgLevel L, int nsys, const cx<R>* __restrict__ tab, int kind,
+                                const cx<R>* __restrict__ rhs, cx<R>* __restrict__ z) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nsys * 9) return;
+  const int b = (int)(idx / 9), node = (int)(idx - (long long)b * 9);
+  const R* co = sizeof(R) == 4 ? (const R*)L.cof : (const R*)L.co;
+  const cx<R> mu = shift_of<R>(tab, b, kind);
+  const cx<R>* rb = rhs + (long long)b * 9;
+  cx<R> acc = mk<R>(0, 0);
+  for (int md = 0; md < 9; ++md) {
+    cx<R> w = mk<R>(0, 0);
+    for (int k = 0; k < 9; ++k) w = cadd(w, cscale(rb[k], co[81 + md * 9 + k]));
+    const cx<R> den = mk<R>(mu.x + co[162 + md], mu.y);
+    const R dd = den.x * den.x + den.y * den.y;
+    w = cmul(w, mk<R>(den.x / dd, -den.y / dd));
+    acc = cadd(acc, cscale(w, co[node * 9 + md]));
+  }
+  z[(long long)b * 9 + node] = acc;
 }
 
 // a += b  or  a = b (copy)
@@ -461,8 +598,10 @@ static void vcycle(const MgHost& h, const cx<R>* tab, int kind, int l, const cx<
   const MgLevel& L = h.lev[l];
   const long long len = (long long)h.nsys * L.N * L.N;
   const R w = (R)kJacobiWeight;
-  if (L.N == 1) {   // exact solve on the single-unknown grid: z = rhs / diag
-    k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, nullptr, z, 1, (R)1);
+  if (l == h.nlev - 1) {
+    if (L.neu) k_mg_coarse_neu<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, z);
+    else        // exact solve on the single-unknown grid: z = rhs / diag
+      k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, nullptr, z, 1, (R)1);
     g_mg_launches += 1;
     return;
   }
@@ -479,9 +618,11 @@ static void vcycle(const MgHost& h, const cx<R>* tab, int kind, int l, const cx<
   const MgLevel& C = h.lev[l + 1];
   const long long lenc = (long long)h.nsys * C.N * C.N;
   cx<R>* crhs = (cx<R>*)C.a[0];
-  k_mg_restrict<R><<<blocks_for(lenc), 256, 0, st>>>(L.N, h.nsys, oth, crhs);
+  if (L.neu) k_mg_restrict_neu<R><<<blocks_for(lenc), 256, 0, st>>>(L.N, h.nsys, oth, crhs);
+  else k_mg_restrict<R><<<blocks_for(lenc), 256, 0, st>>>(L.N, h.nsys, oth, crhs);
   vcycle<R>(h, tab, kind, l + 1, crhs, (cx<R>*)C.a[1], (cx<R>*)C.a[2], st);
-  k_mg_prolong_add<R><<<blocks_for(len), 256, 0, st>>>(L.N, h.nsys, (const cx<R>*)C.a[1], cur);
+  if (L.neu) k_mg_prolong_add_neu<R><<<blocks_for(len), 256, 0, st>>>(L.N, h.nsys, (const cx<R>*)C.a[1], cur);
+  else k_mg_prolong_add<R><<<blocks_for(len), 256, 0, st>>>(L.N, h.nsys, (const cx<R>*)C.a[1], cur);
   for (int s = 0; s < kNu; ++s) {
     k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, cur, oth, 0, w);
     std::swap(cur, oth);

@@ -119,6 +119,8 @@ struct Geom {
   int zeta_pi;                    // 1 when zeta = pi: the two halves share one complex time line
   double c;                       // tau a / h^2 (a: the constant coefficient)
   int var_a;                      // 0: a = 1; 1: coefficient tables below
+  int mg_route;                   // 1: the shifted solves of the preconditioners run as multigrid V-cycles
+                                  //    (variable a, or on request with a constant one)
   int fem;                        // 1: Q1 finite elements (spatial operator M^{-1/2} K M^{-1/2}, applied
                                   //    through the DST-I; kap holds its 1D eigenvalues a kappa1_p / mu_p)
   // FP32 scratch layout of the pipelined passes: rows of lr values (lr = L + 16 when the pipelined

@@ -1224,7 +1224,7 @@ cudaError_t dst_pass_p(const Batch& B, int stage, int in_slot, int out_slot, boo
 int pipe_time_p(const Geom& g);
 int pipe_dst_p(const Geom& g) {
   // the padded scratch layout needs the pipelined time pass
-  if (g.var_a || (g.tune & TUNE_NO_PIPE_DST) || !pipe_time_p(g)) return 0;
+  if (g.mg_route || (g.tune & TUNE_NO_PIPE_DST) || !pipe_time_p(g)) return 0;
   const int M = 2 * g.L;
   if (M % 32) return 0;
   const int P = M / 32;
@@ -1232,7 +1232,7 @@ int pipe_dst_p(const Geom& g) {
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
 int pipe_time_p(const Geom& g) {
-  if (g.var_a || (g.tune & TUNE_NO_PIPE_TIME) || g.n % 32) return 0;
+  if (g.mg_route || (g.tune & TUNE_NO_PIPE_TIME) || g.n % 32) return 0;
   const int P = g.n / 32;
   if (!g.zeta_pi && P > 16) return 0;        // general zeta: the two halves of a column share a warp
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;

@@ -78,7 +78,7 @@ int pipe_time_cols(int n, int zeta_pi);
 int pipe_dst_lines(int L);
 cudaError_t upload_constants();
 struct TableLayout { size_t kap, mud, muf, twdd, twdf, twtd, twtf, pred, pref, ax, ay, dg, ms, bytes; };
-cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host);
+cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges_host, double a0);
 
 // step ids of the scalar kernels (mirror krylov.cu)
 enum { SS_NONE = 0, SS_MINRES_INIT, SS_MINRES_ALFA, SS_MINRES_GIVENS, SS_NORM, SS_GMRES_ARNOLDI, SS_GMRES_START,
@@ -247,7 +247,7 @@ void apply_choice(Geom& g, const TuneChoice& c) {
 
 // constant-coefficient problems only: the multigrid route has its own shapes
 void apply_cached_tuning(Geom& g, int prec) {
-  if (g.var_a) return;
+  if (g.mg_route) return;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune_cache.find(tune_key(g, prec));
   if (it != g_tune_cache.end()) apply_choice(g, it->second);
@@ -410,6 +410,12 @@ int validate_desc(const pcb_desc* d) {
   if (d->a_edges && d->n > 512) return PCB_ERR_UNSUPPORTED;
   if (d->fem != 0 && d->fem != 1) return PCB_ERR_INVALID_ARG;
   if (d->fem && (neu || d->a_edges)) return PCB_ERR_UNSUPPORTED;
+  if (d->multigrid != 0 && d->multigrid != 1) return PCB_ERR_INVALID_ARG;
+  if (d->multigrid && !d->a_edges) {
+    // the multigrid route with a constant coefficient: Dirichlet N = 2^k - 1, Neumann N = 2^k + 1
+    if (d->fem || std::fabs(d->zeta - M_PI) > 1e-12 || d->n > 512 || !mg_available()) return PCB_ERR_UNSUPPORTED;
+    if (neu ? (d->N < 5 || !pow2(d->N - 1)) : !pow2(d->N + 1)) return PCB_ERR_UNSUPPORTED;
+  }
   if (d->a_edges) {
     const long long ne = 2LL * d->N * (d->N + 1);
     for (long long k = 0; k < ne; ++k)
@@ -430,6 +436,7 @@ void init_geom(const pcb_desc* d, Geom& g) {
   const double a0 = d->a_const > 0.0 ? d->a_const : 1.0;
   g.c = a0 * g.tau / (g.h * g.h);
   g.var_a = d->a_edges ? 1 : 0;
+  g.mg_route = d->a_edges || d->multigrid ? 1 : 0;
   g.fem = d->fem ? 1 : 0;
   g.zeta = d->zeta;
   g.zeta_pi = std::fabs(d->zeta - M_PI) <= 1e-12 ? 1 : 0;
@@ -537,11 +544,20 @@ void bind_tables(Geom& g, const TableLayout& t, unsigned char* tb) {
 
 extern "C" {
 
-int pcb_create(const pcb_desc* d, pcb_problem** out) {
-  if (!d || !out) return PCB_ERR_INVALID_ARG;
+int pcb_create(const pcb_desc* d_in, pcb_problem** out) {
+  if (!d_in || !out) return PCB_ERR_INVALID_ARG;
   *out = nullptr;
-  int rc = validate_desc(d);
+  int rc = validate_desc(d_in);
   if (rc != PCB_OK) return rc;
+  // Dirichlet with multigrid requested for a constant coefficient: the variable-coefficient route
+  // with every edge value equal to a (the same operator)
+  pcb_desc dd = *d_in;
+  std::vector<double> const_edges;
+  if (dd.multigrid && !dd.a_edges && dd.bc != PCB_BC_NEUMANN) {
+    const_edges.assign((size_t)2 * dd.N * (dd.N + 1), dd.a_const > 0.0 ? dd.a_const : 1.0);
+    dd.a_edges = const_edges.data();
+  }
+  const pcb_desc* d = &dd;
   pcb_problem* p = new (std::nothrow) pcb_problem();
   if (!p) return PCB_ERR_OUT_OF_MEMORY;
   p->desc = *d;
@@ -570,11 +586,11 @@ int pcb_create(const pcb_desc* d, pcb_problem** out) {
   if (cudaMalloc(&p->scratch, sbytes) != cudaSuccess) return fail(PCB_ERR_OUT_OF_MEMORY);
   p->bytes += sbytes;
   g.scratch = p->scratch;
-  if (g.var_a) {
+  if (g.mg_route) {
     const size_t mb = mg_workspace_bytes(g);
     if (cudaMalloc(&p->mgws, mb) != cudaSuccess) return fail(PCB_ERR_OUT_OF_MEMORY);
     p->bytes += mb;
-    if (mg_setup(g, p->mgws, d->a_edges) != cudaSuccess) return fail(PCB_ERR_CUDA);
+    if (mg_setup(g, p->mgws, d->a_edges, d->a_const > 0.0 ? d->a_const : 1.0) != cudaSuccess) return fail(PCB_ERR_CUDA);
   }
   // ---- single-instance batch ----
   if (cudaMalloc(&p->dG, sizeof(Geom)) != cudaSuccess || cudaMalloc(&p->dS, sizeof(Slots)) != cudaSuccess ||
@@ -648,7 +664,7 @@ struct SolveCfg {
 static int apply_precond(const pcb_problem* p, const Batch& B, int kind, int prec, int in_slot, int out_slot) {
   cudaError_t e;
   if (kind == PCB_PREC_NONE) e = launch_axpby(B, AX_COPY, in_slot, out_slot, -1);
-  else if (p->g.var_a) e = launch_precond_mg(B, p->g, kind, prec, p->desc.mg_cycles, in_slot, out_slot);
+  else if (p->g.mg_route) e = launch_precond_mg(B, p->g, kind, prec, p->desc.mg_cycles, in_slot, out_slot);
   else e = launch_precond_fast(B, kind, prec, in_slot, out_slot);
   return e == cudaSuccess ? PCB_OK : cuda_status(e);
 }
@@ -670,7 +686,7 @@ static bool ev_pair(std::vector<cudaEvent_t>& pool, int& used, cudaEvent_t& a, c
 }
 
 static int P_precond(pcb_problem* p, const Batch& B, int kind, int prec, int in_slot, int out_slot) {
-  const bool va = p->g.var_a != 0;
+  const bool va = p->g.mg_route != 0;
   cudaEvent_t a = nullptr, b = nullptr;
   const bool ev = p->prof && ev_pair(p->ev_prec, p->ev_prec_used, a, b);
   if (ev) cudaEventRecord(a, B.stream);
@@ -777,7 +793,7 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
                          int* it_out, bool* conv_out) {
   const Batch& B = p->B;
   const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
-  const bool va = p->g.var_a != 0;
+  const bool va = p->g.mg_route != 0;      // multigrid applies launch directly (no graph)
   // x = 0, w = w2 = 0, r1 = r2 = b
   CK(cudaMemsetAsync(p->hS.v[s_x], 0, vb, p->stream));
   CK(cudaMemsetAsync(p->hS.v[SL_W], 0, vb, p->stream));
@@ -871,7 +887,7 @@ static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
                          int* it_out, bool* conv_out) {
   const Batch& B = p->B;
   const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
-  const bool va = p->g.var_a != 0;
+  const bool va = p->g.mg_route != 0;      // multigrid applies launch directly (no graph)
   const int op = PCB_OP_AHAT;
   CK(cudaMemsetAsync(p->hS.v[s_x], 0, vb, p->stream));
   CK(cudaMemsetAsync(p->dSc, 0, sizeof(Scal), p->stream));
@@ -962,7 +978,7 @@ static void resolve_defaults(const pcb_problem* p, const pcb_solve_opts* o, Solv
   c.prec = p->desc.precision;
   c.inner_floor = (o && o->inner_floor > 0) ? o->inner_floor : 0.0;
   c.graphs = !(o && o->no_graphs);
-  const bool va = p->g.var_a != 0;
+  const bool va = p->g.mg_route != 0;
   if (c.method == PCB_METHOD_AUTO) {
     if (p->g.theta == 1.0 && p->g.bc != PCB_BC_NEUMANN) c.method = PCB_MINRES;
     else c.method = va ? PCB_FGMRES : PCB_GMRES;
@@ -979,7 +995,7 @@ static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_d
   SolveCfg c;
   resolve_defaults(p, o, c);
   if (c.method == PCB_MINRES && (c.kind == PCB_PREC_PS)) return PCB_ERR_INVALID_ARG;   // P_S is not SPD
-  if (c.kind == PCB_PREC_ABS_PS && p->g.var_a) return PCB_ERR_UNSUPPORTED;
+  if (c.kind == PCB_PREC_ABS_PS && p->g.mg_route) return PCB_ERR_UNSUPPORTED;
   if (p->g.bc == PCB_BC_NEUMANN && (c.method == PCB_MINRES || c.kind != PCB_PREC_PS)) return PCB_ERR_UNSUPPORTED;
   int rc;
   if ((rc = ensure_minres(p))) return rc;
@@ -1102,7 +1118,7 @@ int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_d
   if (!p || !x_dev || !y_dev) return PCB_ERR_INVALID_ARG;
   if (kind != PCB_PREC_ABS_PS && kind != PCB_PREC_PS && kind != PCB_PREC_PMS) return PCB_ERR_INVALID_ARG;
   if (precision != PCB_FP64 && precision != PCB_MIXED) return PCB_ERR_INVALID_ARG;
-  if (kind == PCB_PREC_ABS_PS && p->g.var_a) return PCB_ERR_UNSUPPORTED;
+  if (kind == PCB_PREC_ABS_PS && p->g.mg_route) return PCB_ERR_UNSUPPORTED;
   if (kind != PCB_PREC_PS && p->g.bc == PCB_BC_NEUMANN) return PCB_ERR_UNSUPPORTED;
   p->hS.v[SL_UIN] = (double*)x_dev;
   p->hS.v[SL_UOUT] = y_dev;
@@ -1204,7 +1220,7 @@ int pcb_autotune(pcb_problem* p, int kind, int reps, pcb_tune_info* info) {
   if (!p) return PCB_ERR_INVALID_ARG;
   if (kind == PCB_PREC_NONE) kind = p->g.bc == PCB_BC_NEUMANN ? PCB_PREC_PS : PCB_PREC_ABS_PS;
   if (kind != PCB_PREC_ABS_PS && kind != PCB_PREC_PS && kind != PCB_PREC_PMS) return PCB_ERR_INVALID_ARG;
-  if (p->g.var_a) return PCB_ERR_UNSUPPORTED;        // the multigrid route is not tuned
+  if (p->g.mg_route) return PCB_ERR_UNSUPPORTED;     // the multigrid route is not tuned
   if (kind != PCB_PREC_PS && p->g.bc == PCB_BC_NEUMANN) return PCB_ERR_UNSUPPORTED;
   if (reps <= 0) reps = 3;
   const int prec = p->desc.precision;
@@ -1609,7 +1625,7 @@ extern "C" int pcb_batch_solve(pcb_problem* const* problems, int count, const pc
     SolveCfg c;
     resolve_defaults(problems[k], opts, c);
     if (c.method == PCB_MINRES && c.kind == PCB_PREC_PS) return PCB_ERR_INVALID_ARG;
-    if (problems[k]->g.var_a) return PCB_ERR_UNSUPPORTED;      // multigrid instances solve one at a time
+    if (problems[k]->g.mg_route) return PCB_ERR_UNSUPPORTED;   // multigrid instances solve one at a time
     if (problems[k]->g.fem) return PCB_ERR_UNSUPPORTED;        // finite elements: single problems
     if (problems[k]->g.bc == PCB_BC_NEUMANN && (c.method == PCB_MINRES || c.kind != PCB_PREC_PS))
       return PCB_ERR_UNSUPPORTED;
@@ -2088,7 +2104,7 @@ void pcb_server_destroy(pcb_server* S) {
 
 int pcb_server_submit(pcb_server* S, const pcb_desc* d, const double* rhs, double* x, long long tag) {
   if (!S || !d || !rhs || !x) return PCB_ERR_INVALID_ARG;
-  if (d->a_edges || d->fem) return PCB_ERR_UNSUPPORTED;
+  if (d->a_edges || d->fem || d->multigrid) return PCB_ERR_UNSUPPORTED;
   pcb_desc dd = *d;
   dd.precision = S->o.precision;
   dd.stream = (void*)S->st;

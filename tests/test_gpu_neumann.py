@@ -190,3 +190,61 @@ def test_neumann_batch_with_dirichlet(P):
         x1, i1 = P.batch_solve([gp], [dev(b)], tol=1e-8, restart=16)
         assert_close(xo, x1[0].cpu().numpy(), 1e-12)
         assert i1[0]["iterations"] == info["iterations"]
+
+
+# ---------------------------------------------------------------- multigrid route (Sec. 4, Example 3)
+MG_SHAPES = [(5, 4, 0.5, 1e-2, 1e-3), (17, 16, 1.0, 1e-4, 0.3), (33, 32, 0.5, 1e-2, 1e-3), (65, 64, 0.5, 1e-6, 1e-3),
+             (129, 8, 1.0, 1e-2, 1.0), (257, 32, 0.5, 1e-3, 1e-3)]
+
+
+@pytest.mark.parametrize("shape", MG_SHAPES, ids=lambda s: "N%d-n%d-th%g-g%g-a%g" % s)
+def test_neumann_multigrid_precond_parity(P, shape):
+    """P_S^{-1} with two V-cycles per shifted solve on the Neumann grid (N = 2^k + 1 nodes), against
+    the oracle's multigrid route element by element (FP64 <= 1e-12, FP32 <= 5e-6)."""
+    N, n, theta, gamma, a = shape
+    prob = ds.Problem(N, n, theta, gamma, bc="neumann", a0=a)
+    v = synth.random_vector(2 * prob.m * n, seed=950 + N + n)
+    ref = pc.apply_mg_ps_inv(prob, v, cycles=2)
+    gp = P.Problem(N, n, theta, gamma, bc="neumann", a=a, multigrid=True, mg_cycles=2)
+    assert_close(gp.precond_apply(dev(v), kind="ps", precision="fp64").cpu().numpy(), ref, 1e-12, what="fp64")
+    assert_close(gp.precond_apply(dev(v), kind="ps", precision="mixed").cpu().numpy(), ref, 5e-6, what="fp32")
+
+
+@pytest.mark.parametrize("gamma", [1e-10, 1e-6, 1e-2])
+def test_neumann_example3_multigrid_solve(P, gamma):
+    """Example 3 with the multigrid shifted solves on the GPU: FP64 GMRES-P_S iterates equal the
+    oracle's (8 iterations, same algorithm), the solve to 1e-8 takes the oracle's count and its e_h;
+    the mixed solve converges to the same tolerance."""
+    N, n = 33, 32
+    prob = ds.Problem(N, n, 0.5, gamma, bc="neumann", a0=1e-3)
+    g, f, ye, pe = synth.example3_data(N, n)
+    b = ds.rhs_gmres(prob, g, f, ye[0])
+    M = lambda r: pc.apply_mg_ps_inv(prob, r, cycles=2)
+    A = lambda z: op.matvec_A_hat(prob, z)
+    gp = P.Problem(N, n, 0.5, gamma, bc="neumann", a=1e-3, multigrid=True, mg_cycles=2, precision="fp64")
+    xo, _ = kr.fgmres(A, b, M, fixed_iterations=4)
+    x, info = gp.solve(dev(b), method="fgmres", precond="ps", fixed_iterations=4, restart=30)
+    assert_close(x.cpu().numpy(), xo, 1e-10)
+    xo, io = kr.fgmres(A, b, M, tol=1e-8)
+    x, info = gp.solve(dev(b), tol=1e-8)
+    assert info["method"] in (2, 3) and info["iterations"] == io.iterations and info["relres"] <= 1e-8
+    y, p = gp.recover(x)
+    e = ds.error_eh(prob, y.cpu().numpy().reshape(n, -1), p.cpu().numpy().reshape(n, -1), ye, pe)
+    assert abs(e - ds.error_eh(prob, *ds.recover(prob, xo), ye, pe)) <= 0.02 * e
+    gm = P.Problem(N, n, 0.5, gamma, bc="neumann", a=1e-3, multigrid=True, mg_cycles=2, precision="mixed")
+    xm, im = gm.solve(dev(b), tol=1e-8)
+    assert im["relres"] <= 1e-8
+    assert np.linalg.norm(b - A(xm.cpu().numpy())) / np.linalg.norm(b) <= 1.5e-8
+
+
+def test_dirichlet_constant_coefficient_multigrid_route(P):
+    """multigrid=True with a constant coefficient on a Dirichlet grid runs the variable-coefficient
+    route with every edge value equal to a: the same result as the oracle's multigrid route."""
+    N, n, a = 63, 32, 0.7
+    edges = np.full(2 * N * (N + 1), a)
+    prob = ds.Problem(N, n, 0.5, 1e-3, a_edges=edges)
+    v = synth.random_vector(2 * prob.m * n, seed=977)
+    ref = pc.apply_mg_ps_inv(prob, v, cycles=2)
+    gp = P.Problem(N, n, 0.5, 1e-3, a=a, multigrid=True, mg_cycles=2)
+    assert_close(gp.precond_apply(dev(v), kind="ps", precision="fp64").cpu().numpy(), ref, 1e-12)
+    assert_close(gp.matvec(dev(v), op="Ahat").cpu().numpy(), op.matvec_A_hat(prob, v), 1e-13)
