@@ -56,7 +56,9 @@ def args():
                     help="profiling mode: only run --prof-reps preconditioner applies (or products) on one "
                          "problem of this size, so that a profiler can capture single launches")
     ap.add_argument("--prof-prec", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--prof-kind", default="abs_ps", choices=["abs_ps", "ps", "pms", "matvec"])
+    ap.add_argument("--prof-kind", default="abs_ps", choices=["abs_ps", "ps", "pms", "matvec", "solve"])
+    ap.add_argument("--prof-var-a", action="store_true", help="variable a(x) (config 2's): the multigrid route")
+    ap.add_argument("--prof-fem", action="store_true", help="bilinear finite elements (M != I)")
     ap.add_argument("--prof-reps", type=int, default=3)
     ap.add_argument("--prof-zeta", type=float, default=math.pi)
     ap.add_argument("--prof-neumann", action="store_true", help="Example 3's Neumann grid (DCT-I passes, kind ps)")
@@ -74,12 +76,17 @@ def profile_apply(a):
     N, n = a.profile_apply
     if a.prof_neumann:
         gp = P.Problem(N, n, 0.5, 1e-2, precision=a.prof_prec, bc="neumann", a=1e-3)
+    elif a.prof_var_a:
+        import synth
+        gp = P.Problem(N, n, 1.0, 1e-2, a_edges=synth.variable_coefficient_edges(N), precision=a.prof_prec)
     else:
-        gp = P.Problem(N, n, 1.0, 1e-2, zeta=a.prof_zeta, precision=a.prof_prec)
+        gp = P.Problem(N, n, 1.0, 1e-2, zeta=a.prof_zeta, precision=a.prof_prec, fem=a.prof_fem)
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.randn(gp.size, dtype=torch.float64, device="cuda", generator=g)
     y = torch.empty_like(x)
-    for _ in range(a.prof_reps):
+    if a.prof_kind == "solve":     # MINRES iterations (the Krylov vector kernels with the rest)
+        gp.solve(x, y, fixed_iterations=a.prof_reps, graphs=False)
+    for _ in range(a.prof_reps if a.prof_kind != "solve" else 0):
         if a.prof_kind == "matvec":
             gp.matvec(x, out=y)
         else:
@@ -602,6 +609,8 @@ def main():
     achieved = alg_bytes / (pms / applies / 1e3) / 1e9
     mv_ach = 16.0 * unknowns / (mvms / mvs / 1e3) / 1e9
     iters = [i["iterations"] for i in infos]
+    fp64r = P.fp64_rates(stream)
+    fp64_peak = fp64r["fma_per_s"]
     # forward error of the mixed solutions against the oracle's (sampled positions, relres 1e-12 truth)
     fe_mixed = [forward_error(f"cfg1_g{gam:g}", x) for gam, x in zip(W["gammas"], xs)] if not a.small else None
 
@@ -680,12 +689,13 @@ def main():
             "kernels": {"precond_ms_share": pms / prof_ms, "matvec_ms_share": mvms / prof_ms, "matvec_avg_ms": mvms / mvs,
                         "matvec_alg_gbs": mv_ach,
                         # the product (with the MINRES epilogue) is bound by FP64 issue: 10 FP64
-                        # operations per unknown against the nominal FP64 rate of 1.25 TFLOP/s,
-                        # i.e. 625 G FMA-class instructions/s
-                        "matvec_roofline": {"bound": "alu", "unit": "G FP64 ops/s",
+                        # instructions per unknown against this device's FP64 FMA instruction rate,
+                        # measured here (pcb_measure_fp64_rates)
+                        "matvec_roofline": {"bound": "alu", "unit": "G FP64 instr/s",
                                             "achieved": 10.0 * unknowns / (mvms / mvs / 1e3) / 1e9,
-                                            "peak": 625.0,
-                                            "frac": 10.0 * unknowns / (mvms / mvs / 1e3) / 1e9 / 625.0}},
+                                            "peak": fp64_peak / 1e9, "peak_kind": "measured (FP64 FMA rate)",
+                                            "frac": 10.0 * unknowns / (mvms / mvs / 1e3) / fp64_peak,
+                                            "fp64_add_instr_per_s": fp64r["add_per_s"]}},
             "fp64_gpu": fp64,
             "mixed_vs_fp64": [{"gamma": gam, "mixed_iterations": im, "fp64_iterations": i64,
                                "within_plus2": im <= i64 + 2, "mixed_forward_error_vs_oracle": fe}

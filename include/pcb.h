@@ -251,6 +251,14 @@ int pcb_solve_host(pcb_problem* p, const pcb_solve_opts* opts, const double* b_h
 int pcb_precond_apply_noalloc(const pcb_desc* desc, int kind, int precision, const double* x_dev,
                               double* y_dev);
 
+/* ---- device figures -------------------------------------------------------------------- */
+/* The paper has no counterpart: a diagnostic for the rooflines of the FP64 steps (the product,
+ * the residual and the Krylov updates, which this GPU's narrow FP64 pipe bounds before its memory).
+ * Measures the device's FP64 fused multiply-add and add instruction rates (instructions per second;
+ * one FMA is two flops) with register-only kernels queued on `stream` (NULL = default); blocks until
+ * they finish (about a tenth of a second).  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+int pcb_measure_fp64_rates(void* stream, double* fma_per_s, double* add_per_s);
+
 /* ---- batches --------------------------------------------------------------------------- */
 /* Solve `count` independent problems (uneven N, n, theta, gamma allowed; all with the same
  * precision) with shared kernel launches: every launch of an iteration covers all unfinished

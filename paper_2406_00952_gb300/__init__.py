@@ -145,6 +145,17 @@ class Problem:
         return x_host, info.as_dict()
 
 
+def fp64_rates(stream: torch.cuda.Stream | None = None) -> dict:
+    """Measured FP64 fused multiply-add and add instruction rates of the current device
+    (C-ABI pcb_measure_fp64_rates), instructions per second."""
+    lib = _lib.load()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    f, a = ctypes.c_double(), ctypes.c_double()
+    check("pcb_measure_fp64_rates", lib.pcb_measure_fp64_rates(ctypes.c_void_p(st.cuda_stream), ctypes.byref(f),
+                                                               ctypes.byref(a)))
+    return {"fma_per_s": f.value, "add_per_s": a.value}
+
+
 def batch_solve(problems, bs, xs=None, allow_not_converged=False, **kw):
     """Solve independent problems with shared launches (C-ABI pcb_batch_solve)."""
     lib = _lib.load()

@@ -556,6 +556,7 @@ int pcb_create(const pcb_desc* d_in, pcb_problem** out) {
   if (dd.multigrid && !dd.a_edges && dd.bc != PCB_BC_NEUMANN) {
     const_edges.assign((size_t)2 * dd.N * (dd.N + 1), dd.a_const > 0.0 ? dd.a_const : 1.0);
     dd.a_edges = const_edges.data();
+    dd.a_const = 0.0;      // the edge values carry a (the stencil scale is then tau/h^2)
   }
   const pcb_desc* d = &dd;
   pcb_problem* p = new (std::nothrow) pcb_problem();
