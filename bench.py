@@ -59,6 +59,8 @@ def args():
     ap.add_argument("--prof-kind", default="abs_ps", choices=["abs_ps", "ps", "pms", "matvec", "solve"])
     ap.add_argument("--prof-var-a", action="store_true", help="variable a(x) (config 2's): the multigrid route")
     ap.add_argument("--prof-fem", action="store_true", help="bilinear finite elements (M != I)")
+    ap.add_argument("--prof-autotune", action="store_true", help="autotune the apply first (as the bench does)")
+    ap.add_argument("--no-autotune", action="store_true", help="bench: keep the default kernel configuration")
     ap.add_argument("--prof-reps", type=int, default=3)
     ap.add_argument("--prof-zeta", type=float, default=math.pi)
     ap.add_argument("--prof-neumann", action="store_true", help="Example 3's Neumann grid (DCT-I passes, kind ps)")
@@ -81,6 +83,8 @@ def profile_apply(a):
         gp = P.Problem(N, n, 1.0, 1e-2, a_edges=synth.variable_coefficient_edges(N), precision=a.prof_prec)
     else:
         gp = P.Problem(N, n, 1.0, 1e-2, zeta=a.prof_zeta, precision=a.prof_prec, fem=a.prof_fem)
+    if a.prof_autotune:
+        print("autotune", gp.autotune(kind=None if a.prof_kind in ("solve", "matvec") else a.prof_kind))
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.randn(gp.size, dtype=torch.float64, device="cuda", generator=g)
     y = torch.empty_like(x)
@@ -565,6 +569,12 @@ def main():
         bs.append(pr.assemble_rhs(g, f))
     gf = (g, f)
     del g, f
+    # autotuned kernel shapes (north star (2)): the first problem times the candidate configurations
+    # of its preconditioner apply and keeps the fastest; the second, of the same shape, inherits it
+    tune = None if a.no_autotune else probs[0].autotune(reps=3)
+    if tune is not None:
+        probs[1:] = [P.Problem(N, n, W["theta"], gam, W["T"], precision="mixed", stream=stream)
+                     for gam in W["gammas"][1:]]
     xs = [pr._empty() for pr in probs]
     unknowns = probs[0].size
     opts = dict(tol=1e-8, maxit=400)
@@ -702,6 +712,7 @@ def main():
                               for gam, im, i64, fe in zip(W["gammas"], iters[:len(W["gammas"])],
                                                           fp64["iterations"] if fp64 else [None] * len(W["gammas"]),
                                                           fe_mixed or [None] * len(W["gammas"]))] if fp64 else None,
+            "autotune": tune,
             "config2_variable_a": cfg2,
             "config3_uneven_batch": cfg3,
             "e2e": e2e,

@@ -148,8 +148,9 @@ int pcb_precond_apply(pcb_problem* p, int kind, int precision, const double* x_d
 /* ---- autotuning of the preconditioner's kernel shapes ------------------------------------ */
 /* The transforms of Sec. 3.5 (steps 1 and 3) can run in several kernel configurations: the
  * pipelined FP32 kernels or the tile kernels for the spatial and the time passes (and, for n = 512,
- * with or without handing the time pass contiguous time lines), and for the tile kernels several
- * register-FFT radices (values per lane) and tile sizes.  pcb_autotune times `reps` applications
+ * with or without handing the time pass contiguous time lines, and with 2, 3 or 4 resident blocks
+ * per SM for that time pass), and for the tile kernels several register-FFT radices (values per
+ * lane) and tile sizes.  pcb_autotune times `reps` applications
  * of preconditioner `kind` (PCB_PREC_NONE: the problem's default) in the problem's precision under
  * each configuration that fits the problem's shape, keeps the fastest for this problem, and records
  * it for the device and shape (N, n, boundary condition, zeta = pi or not, precision): problems
@@ -171,6 +172,7 @@ typedef struct {
   int dst_lanes;           /* lanes per spatial line of the tile kernels (values per lane = M/lanes)*/
   int time_lanes;          /* lanes per time line of the tile kernels                            */
   double tile_scale;       /* tile size of the tile kernels relative to the default (0.5, 1, 2)   */
+  int time512_blocks;      /* winner: resident blocks per SM of the n = 512 time pass (2, 3 or 4) */
 } pcb_tune_info;
 int pcb_autotune(pcb_problem* p, int kind, int reps, pcb_tune_info* info);
 

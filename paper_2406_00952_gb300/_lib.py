@@ -46,7 +46,7 @@ class PcbTuneInfo(ctypes.Structure):
     _fields_ = [("candidates", c_int), ("rejected", c_int), ("chosen", c_int), ("default_ms", c_double),
                 ("best_ms", c_double),
                 ("pipelined_dst", c_int), ("pipelined_time", c_int), ("time_major_handoff", c_int),
-                ("dst_lanes", c_int), ("time_lanes", c_int), ("tile_scale", c_double)]
+                ("dst_lanes", c_int), ("time_lanes", c_int), ("tile_scale", c_double), ("time512_blocks", c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -162,7 +162,8 @@ struct Geom {
 
 // Autotuner choices (Geom::tune): kernel families the FP32 apply may not use, and the tile-size
 // scale of the tile kernels (bits 4-5: 0 = default, 1 = half, 2 = double the per-tile element budget)
-enum { TUNE_NO_PIPE_DST = 1, TUNE_NO_PIPE_TIME = 2, TUNE_NO_HANDOFF = 4 };
+enum { TUNE_NO_PIPE_DST = 1, TUNE_NO_PIPE_TIME = 2, TUNE_NO_HANDOFF = 4, TUNE_TIME512_3BLK = 8,
+       TUNE_TIME512_4BLK = 64 };
 __host__ __device__ inline int tune_budget_shift(int tune) { return (tune >> 4) & 3; }
 
 // per-instance Krylov scalars (MINRES and GMRES share the struct)
@@ -259,6 +260,8 @@ struct Batch {
   const int* fam_dst;
   const int* fam_time;
   int fam_dst_set, fam_time_set;
+  int t512v;              // 1 / 2: the n = 512 time pass runs its three / four-blocks-per-SM variant
+                          // (every instance of the batch that takes that pass chose it)
   int fem_m;              // > 0: a single finite-element instance with m = fem_m spatial points
                           // (products through the DST-I)
   const int* filt;        // family filter of the launch being issued (null: none)

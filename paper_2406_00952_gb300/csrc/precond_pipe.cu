@@ -908,8 +908,11 @@ __global__ void __launch_bounds__(kThreads, 2)
 // MODE 1: tiles of 8 spatial points (r, p0 .. p0+7) of the time-major buffer 1 (contiguous time
 // lines, 16-byte copies), result written to buffer 0 in the row layout of pass 4 (value
 // (t, r, p) at t mp + r lr + p): row segments of 8 values.
-template <int NS, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+// MINB: resident blocks per SM the compiler budgets registers for (2: 128 registers a thread, with
+// NS = 2 tile stages; 3 or 4: at most 85 or 64 registers and one stage, the extra blocks hiding
+// the loads).
+template <int NS, int MODE, int MINB = 2>
+__global__ void __launch_bounds__(kThreads, MINB)
     k_time512(const Geom* __restrict__ G, const int* __restrict__ off, int count, Sel sel, int kind, int tot) {
   constexpr int n = 512, LPB = kWarps;
   constexpr int PITCH = pitch_for<32>(n);
@@ -1136,7 +1139,7 @@ size_t time_smem() {
   return (size_t)(3 * 32 * P) * sizeof(float2) +
          (size_t)kNsTimePipe * (kThreads / P) * pitch_for<P>(32 * P) * sizeof(float2);
 }
-size_t time512_smem() { return (size_t)(3 * 512 + 32 + kNsTime * kWarps * pitch_for<32>(512)) * sizeof(float2); }
+size_t time512_smem(int ns = kNsTime) { return (size_t)(3 * 512 + 32 + ns * kWarps * pitch_for<32>(512)) * sizeof(float2); }
 
 // Launch a persistent kernel: at most as many blocks as fit on the device at once.  The figure
 // (and the shared-memory limit it needs) is set up once per kernel and device; `resident` keeps it.
@@ -1182,7 +1185,21 @@ template <int P>
 cudaError_t launch_time(const Batch& B, int kind, bool time_major = false) {
   static DeviceInt resident;
   if (P == 16) {
-    static DeviceInt resident512[2];
+    static DeviceInt resident512[6];
+    if (B.t512v == 1) {     // the autotuner's variants: one tile stage, three or four blocks per SM
+      if (time_major)
+        return launch_persistent(k_time512<1, 1, 3>, time512_smem(1), B.tot_time[1], resident512[3], B.stream, B.G,
+                                 B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
+      return launch_persistent(k_time512<1, 0, 3>, time512_smem(1), B.tot_time[1], resident512[2], B.stream, B.G,
+                               B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
+    }
+    if (B.t512v == 2) {
+      if (time_major)
+        return launch_persistent(k_time512<1, 1, 4>, time512_smem(1), B.tot_time[1], resident512[5], B.stream, B.G,
+                                 B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
+      return launch_persistent(k_time512<1, 0, 4>, time512_smem(1), B.tot_time[1], resident512[4], B.stream, B.G,
+                               B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
+    }
     if (time_major)
       return launch_persistent(k_time512<kNsTime, 1>, time512_smem(), B.tot_time[1], resident512[1], B.stream, B.G,
                                B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);

@@ -304,6 +304,15 @@ int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStream_t st
   B.count = count;
   B.stream = st;
   B.fem_m = count == 1 && gs[0].fem ? gs[0].m : 0;
+  {
+    int want = -1;     // the n = 512 zeta = pi time pass variant, when all its instances agree
+    for (const Geom& g : gs) {
+      if (!g.time_blocks[1] || pipe_time_p(g) != 16 || !g.zeta_pi) continue;
+      const int v = (g.tune & TUNE_TIME512_3BLK) ? 1 : (g.tune & TUNE_TIME512_4BLK) ? 2 : 0;
+      want = want < 0 ? v : (want == v ? v : 0);
+    }
+    B.t512v = want > 0 ? 1 : 0;
+  }
   B.dst_q = gs[0].dst_q;
   B.time_q = gs[0].time_q;
   for (const Geom& g : gs) {   // mixed sizes: shared launches dispatch per instance
@@ -1203,6 +1212,12 @@ std::vector<TuneChoice> tune_candidates(const Geom& g, int prec) {
   const bool mixed = prec == PCB_MIXED;
   const bool can_pipe_t = mixed && pipe_time_p(d), can_pipe_d = mixed && pipe_dst_p(d);
   if (can_pipe_d && g.n == 512 && g.zeta_pi) add(TUNE_NO_HANDOFF, q0d, q0t);
+  if (can_pipe_t && g.n == 512 && g.zeta_pi) {
+    for (int v : {TUNE_TIME512_3BLK, TUNE_TIME512_4BLK}) {
+      add(v, q0d, q0t);
+      if (can_pipe_d) add(v | TUNE_NO_HANDOFF, q0d, q0t);
+    }
+  }
   for (int b = 0; b < 3; ++b) {
     const int bs = b << 4;
     for (int dq : qd) {
@@ -1320,6 +1335,7 @@ int pcb_autotune(pcb_problem* p, int kind, int reps, pcb_tune_info* info) {
     info->dst_lanes = p->g.M / p->g.dst_q;
     info->time_lanes = p->g.n / p->g.time_q;
     info->tile_scale = tune_budget_shift(p->g.tune) == 1 ? 0.5 : tune_budget_shift(p->g.tune) == 2 ? 2.0 : 1.0;
+    info->time512_blocks = (p->g.tune & TUNE_TIME512_3BLK) ? 3 : (p->g.tune & TUNE_TIME512_4BLK) ? 4 : 2;
   }
   return done(PCB_OK);
 }
