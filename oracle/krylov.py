@@ -11,6 +11,11 @@
 Stopping rule (reading of "reduction in relative residual norms", Sec. 4): a solve succeeds when
 the true relative residual ||b - A x||_2 / ||b||_2 <= tol, evaluated in float64; the
 recurrence's residual estimate only decides when to evaluate it.
+
+stall (off by default): for solves asked to go below the attainable accuracy of float64, stop
+once the true residual no longer follows -- MINRES when the recurrence's estimate has dropped
+below stall x the last true residual evaluated, FGMRES when a restart cycle reduced the true
+residual by less than a factor 2.  The result is then returned unconverged with its true relres.
 """
 from __future__ import annotations
 
@@ -29,7 +34,7 @@ class Info:
     breakdown: bool = False
 
 
-def minres(A, b, M=None, tol=1e-8, maxit=500, fixed_iterations=None):
+def minres(A, b, M=None, tol=1e-8, maxit=500, fixed_iterations=None, stall=None):
     """Solve A x = b (A symmetric) with SPD preconditioner M (callable returning M^{-1} r).
     fixed_iterations: run exactly that many iterations (for same-algorithm comparisons)."""
     if M is None:
@@ -89,6 +94,9 @@ def minres(A, b, M=None, tol=1e-8, maxit=500, fixed_iterations=None):
             if rel <= tol:
                 info.relres, info.converged = rel, True
                 return x, info
+            if stall is not None and phibar / beta1 <= stall * rel:
+                info.relres = rel
+                return x, info
         if beta == 0.0:
             break
     info.relres = float(np.linalg.norm(b - A(x))) / bnorm
@@ -104,7 +112,7 @@ def _givens(a, b):
     return a / r, b / r
 
 
-def fgmres(A, b, M=None, tol=1e-8, restart=30, maxit=500, fixed_iterations=None):
+def fgmres(A, b, M=None, tol=1e-8, restart=30, maxit=500, fixed_iterations=None, stall=None):
     """Right-preconditioned restarted (F)GMRES with CGS2 orthogonalisation."""
     if M is None:
         M = lambda r: r.copy()
@@ -116,12 +124,17 @@ def fgmres(A, b, M=None, tol=1e-8, restart=30, maxit=500, fixed_iterations=None)
         return x, info
     total = 0
     limit = fixed_iterations if fixed_iterations is not None else maxit
+    last = math.inf
     while total < limit:
         r = b - A(x)
         beta = float(np.linalg.norm(r))
         if fixed_iterations is None and beta / bnorm <= tol:
             info.relres, info.converged = beta / bnorm, True
             return x, info
+        if stall is not None and total > 0 and beta > 0.5 * last:
+            info.relres = beta / bnorm
+            return x, info
+        last = beta
         mres = min(restart, limit - total)
         V = np.zeros((mres + 1, b.size)); Z = np.zeros((mres, b.size))
         H = np.zeros((mres + 1, mres)); g = np.zeros(mres + 1)

@@ -2,7 +2,8 @@
 results can be given a forward error against the oracle at sizes the oracle cannot re-solve
 inside a test or a benchmark run.  Calls only the oracle (and the seeded input generators).
 
-For each case the oracle solves its system to true relative residual 1e-12 (the "truth" x*) with
+For each case the oracle solves its system to true relative residual 1e-12, or to the attainable
+accuracy of float64 where that lies above it (no worse than 1e-10; the "truth" x*), with
 the method the paper uses for it (Sec. 4): MINRES-|P_S| for backward Euler with a = 1,
 FGMRES(30) with the multigrid P_S (two V-cycles, Lemma 3.14 decoupling) for the variable-a
 Crank-Nicolson case, GMRES-P_S for Crank-Nicolson with a = 1.  The file keeps ||x*||_2, the count,
@@ -45,26 +46,26 @@ def path_for(tag: str) -> str:
     return os.path.join(GOLDEN, f"solution_sample_{tag}.txt")
 
 
-def solve(inst, tol=1e-12):
+def solve(inst, tol=1e-12, accept=1e-10):
     """The oracle's solve of one instance; returns (x*, method, iterations, seconds)."""
     prob = ds.Problem.from_instance(inst)
     t0 = time.time()
     if inst.theta == 1.0 and inst.a_edges is None:
         b = ds.rhs_minres(prob, inst.g, inst.f)
         x, info = kr.minres(lambda z: op.matvec_A(prob, z), b, lambda r: pc.apply_abs_ps_inv(prob, r),
-                            tol=tol, maxit=1000)
+                            tol=tol, maxit=1000, stall=1e-3)
         method = "MINRES-|P_S|"
     elif inst.a_edges is None:
         b = ds.rhs_gmres(prob, inst.g, inst.f)
         x, info = kr.fgmres(lambda z: op.matvec_A_hat(prob, z), b, lambda r: pc.apply_ps_inv(prob, r),
-                            tol=tol, maxit=1000, restart=30)
+                            tol=tol, maxit=1000, restart=30, stall=1e-3)
         method = "GMRES(30)-P_S"
     else:
         b = ds.rhs_gmres(prob, inst.g, inst.f)
         x, info = kr.fgmres(lambda z: op.matvec_A_hat(prob, z), b, lambda r: pc.apply_mg_ps_inv(prob, r, cycles=2),
-                            tol=tol, maxit=1000, restart=30)
+                            tol=tol, maxit=1000, restart=30, stall=1e-3)
         method = "FGMRES(30)-P_S, 2 V-cycles"
-    if not info.converged:
+    if not info.relres <= accept:
         raise RuntimeError(f"oracle did not converge on {inst.tag}: {info}")
     return x, method, info.iterations, time.time() - t0, info.relres
 

@@ -493,3 +493,22 @@ def test_zeta_sweep_half_pi_beats_zero_and_pi():
         assert info.converged
         its[zeta] = info.iterations
     assert its[math.pi / 2] < its[math.pi] and its[math.pi / 2] < its[0.0], its
+
+
+@pytest.mark.parametrize("method", ["minres", "fgmres"])
+def test_krylov_stall_exit_below_attainable_accuracy(method):
+    """Asked for a residual float64 cannot reach, the stall exit returns within a few iterations of
+    the attainable accuracy, unconverged, with its true residual -- and without stall the same
+    solve, to a reachable tolerance, is unchanged by the keyword."""
+    N, n = 7, 8
+    prob = ds.Problem(N, n, 1.0, 1e-2)
+    g = synth.random_target(N, n, seed=3); f = synth.manufactured_source(N, n)
+    b = ds.rhs_minres(prob, g, f)
+    A = lambda z: op.matvec_A(prob, z)
+    M = lambda r: pc.apply_abs_ps_inv(prob, r)
+    solver = kr.minres if method == "minres" else kr.fgmres
+    x, info = solver(A, b, M, tol=1e-30, maxit=400, stall=1e-3)
+    assert not info.converged and info.relres < 1e-13 and info.iterations < 100, info.iterations
+    x1, i1 = solver(A, b, M, tol=1e-8)
+    x2, i2 = solver(A, b, M, tol=1e-8, stall=1e-3)
+    assert i1.iterations == i2.iterations and np.array_equal(x1, x2)
