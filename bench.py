@@ -67,6 +67,27 @@ def args():
     return ap.parse_args()
 
 
+class Nvtx:
+    """An NVTX range around a region, so that an ncu launch list can select it (`--nvtx
+    --nvtx-include <name>/`); a no-op where torch was built without NVTX."""
+
+    def __init__(self, torch, name):
+        self.torch, self.name = torch, name
+
+    def __enter__(self):
+        try:
+            self.torch.cuda.nvtx.range_push(self.name)
+            self.on = True
+        except Exception:
+            self.on = False
+        return self
+
+    def __exit__(self, *exc):
+        if self.on:
+            self.torch.cuda.nvtx.range_pop()
+        return False
+
+
 def profile_apply(a):
     """--profile-apply N n: a few applies of one kind (or products) on one problem, nothing else.
     With --prof-neumann the problem is Example 3's (N nodes per side with the boundary, a = 1e-3,
@@ -88,14 +109,16 @@ def profile_apply(a):
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.randn(gp.size, dtype=torch.float64, device="cuda", generator=g)
     y = torch.empty_like(x)
-    if a.prof_kind == "solve":     # MINRES iterations (the Krylov vector kernels with the rest)
-        gp.solve(x, y, fixed_iterations=a.prof_reps, graphs=False)
-    for _ in range(a.prof_reps if a.prof_kind != "solve" else 0):
-        if a.prof_kind == "matvec":
-            gp.matvec(x, out=y)
-        else:
-            gp.precond_apply(x, out=y, kind=a.prof_kind, precision=a.prof_prec)
     torch.cuda.synchronize()
+    with Nvtx(torch, "measured"):  # the launches below, without set-up and tuning
+        if a.prof_kind == "solve":     # MINRES iterations (the Krylov vector kernels with the rest)
+            gp.solve(x, y, fixed_iterations=a.prof_reps, graphs=False)
+        for _ in range(a.prof_reps if a.prof_kind != "solve" else 0):
+            if a.prof_kind == "matvec":
+                gp.matvec(x, out=y)
+            else:
+                gp.precond_apply(x, out=y, kind=a.prof_kind, precision=a.prof_prec)
+        torch.cuda.synchronize()
     print("ok", N, n, a.prof_prec, a.prof_kind, a.prof_reps)
 
 
@@ -591,12 +614,13 @@ def main():
     barrier()
     clk = Clocks(local)
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    infos = []
-    for _ in range(a.steps):
-        infos += step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    with Nvtx(torch, "timed"):
+        e0.record(stream)
+        infos = []
+        for _ in range(a.steps):
+            infos += step()
+        e1.record(stream)
+        torch.cuda.synchronize()
     clocks = clk.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), world, device="cuda")
     barrier()

@@ -512,3 +512,20 @@ def test_krylov_stall_exit_below_attainable_accuracy(method):
     x1, i1 = solver(A, b, M, tol=1e-8)
     x2, i2 = solver(A, b, M, tol=1e-8, stall=1e-3)
     assert i1.iterations == i2.iterations and np.array_equal(x1, x2)
+
+
+def test_stored_oracle_solution_sample_reproduces():
+    """The stored oracle solution of the smallest sampled uneven-batch instance (N = 63, n = 32)
+    is what the oracle computes now: a fresh MINRES-|P_S| solve to 1e-10 lies within 1e-9 of it
+    on the stored positions, and the stored norm is that of the fresh solve."""
+    from oracle import reference_solutions as rs
+    s = rs.read("cfg3_3")
+    if s is None:
+        pytest.skip("no stored sample")
+    inst = synth.config3()[3]
+    prob = ds.Problem.from_instance(inst)
+    b = ds.rhs_minres(prob, inst.g, inst.f)
+    x, info = kr.minres(lambda z: op.matvec_A(prob, z), b, lambda r: pc.apply_abs_ps_inv(prob, r), tol=1e-10)
+    assert info.converged and x.size == s[0]
+    assert rs.sampled_forward_error("cfg3_3", x) <= 1e-9
+    assert abs(np.linalg.norm(x) - s[1]) <= 1e-9 * s[1]
