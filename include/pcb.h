@@ -176,6 +176,14 @@ typedef struct {
 } pcb_tune_info;
 int pcb_autotune(pcb_problem* p, int kind, int reps, pcb_tune_info* info);
 
+/* Run this problem (only; nothing is recorded for its shape) in configuration `candidate` of the
+ * list pcb_autotune times for its shape and precision, in that list's order (0: the default
+ * configuration), without timing it; candidate < 0 changes nothing.  `info` (may be NULL) receives
+ * the configuration the problem then runs, with `candidates` the length of the list, `chosen` =
+ * candidate and zero times.  Lets a caller pin a configuration, and a test compare every one with
+ * the oracle.  Errors: INVALID_ARG (candidate past the list), UNSUPPORTED (variable a(x)), CUDA. */
+int pcb_tune_select(pcb_problem* p, int candidate, pcb_tune_info* info);
+
 /* Undo the symmetrising change of variables of Eq. (main_system):
  * y = (B2^{-1} (x) M^{-1/2}) x_half0 / sqrt(gamma), p = (B2^{-T} (x) M^{-1/2}) x_half1; each m*n
  * (M = I for finite differences). */

@@ -105,6 +105,13 @@ class Problem:
         check("pcb_autotune", self.lib.pcb_autotune(self.h, PRECONDS[kind], int(reps), ctypes.byref(info)))
         return info.as_dict()
 
+    def tune_select(self, candidate) -> dict:
+        """Run this problem in configuration `candidate` of the autotuner's list (C-ABI
+        pcb_tune_select; candidate < 0: report the list's length and the current configuration)."""
+        info = PcbTuneInfo()
+        check("pcb_tune_select", self.lib.pcb_tune_select(self.h, int(candidate), ctypes.byref(info)))
+        return info.as_dict()
+
     def assemble_rhs(self, g, f, y0=None, op="A", out=None):
         out = self._empty() if out is None else out
         ns = (self.n + 1) * self.m

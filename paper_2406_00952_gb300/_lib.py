@@ -97,6 +97,7 @@ def load() -> ctypes.CDLL:
                                     POINTER(c_void_p), POINTER(PcbSolveInfo)]),
         "pcb_precond_apply_noalloc": (c_int, [POINTER(PcbDesc), c_int, c_int, P, P]),
         "pcb_autotune": (c_int, [P, c_int, c_int, POINTER(PcbTuneInfo)]),
+        "pcb_tune_select": (c_int, [P, c_int, POINTER(PcbTuneInfo)]),
         "pcb_measure_fp64_rates": (c_int, [P, POINTER(c_double), POINTER(c_double)]),
         "pcb_server_create": (c_int, [POINTER(PcbServerOpts), POINTER(c_void_p)]),
         "pcb_server_destroy": (None, [P]),

@@ -256,8 +256,16 @@ void mg_release(const void* ws) {
 }
 
 // ------------------------------------------------------------------------------------------
-// kernels (one instance; thread per (system, grid point))
+// kernels (one instance; thread per (system, grid point)).  Blocks of 32 x 8 threads cover tiles
+// of 32 x 8 points of one system's grid (grid x, y over the tiles, z over the systems), so that
+// consecutive threads touch consecutive points and no index needs a division.
 // ------------------------------------------------------------------------------------------
+struct GridPt { int b, i, j; };
+__device__ __forceinline__ GridPt grid_pt() {
+  return GridPt{(int)blockIdx.z, (int)(blockIdx.x * 32 + threadIdx.x), (int)(blockIdx.y * 8 + threadIdx.y)};
+}
+static dim3 grid_for(int N, int nsys) { return dim3((unsigned)((N + 31) / 32), (unsigned)((N + 7) / 8), (unsigned)nsys); }
+static const dim3 kMgBlock(32, 8);
 template <typename R> struct Coef;
 template <> struct Coef<float> {
   static __device__ const float* ax(const MgLevel& L) { return L.axf; }
@@ -299,116 +307,142 @@ __device__ __forceinline__ cx<R> shift_of(const cx<R>* __restrict__ tab, int b, 
   return kind == 2 ? tab[4 * r + 0] : mk<R>(tab[4 * r + 3].x, (R)0);
 }
 
+// The two systems of a frequency slot (2r and 2r + 1) share the shift and hence the diagonal:
+// a thread treats one grid point of both, so the coefficients and the diagonal are loaded and
+// inverted once (grid z runs over the slots).
+
 // out = z + w (rhs - A z)/diag  (first: z = 0, so out = w rhs / diag)
 template <typename R>
-__global__ void k_mg_jacobi(MgLevel L, int nsys, const cx<R>* __restrict__ tab, int kind,
-                            const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z, cx<R>* __restrict__ out,
-                            int first, R w) {
+__global__ void __launch_bounds__(256) k_mg_jacobi(MgLevel L, const cx<R>* __restrict__ tab, int kind,
+                                                   const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z,
+                                                   cx<R>* __restrict__ out, int first, R w) {
   const int N = L.N, nn = N * N;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nsys * nn) return;
-  const int b = (int)(idx / nn), pt = (int)(idx - (long long)b * nn);
-  const int j = pt / N, i = pt - j * N;
+  const GridPt q = grid_pt();
+  if (q.i >= N || q.j >= N) return;
+  const int b = 2 * q.b, i = q.i, j = q.j, pt = j * N + i;
   const cx<R> mu = shift_of<R>(tab, b, kind);
   const R dgk = L.neu ? (R)4 * (sizeof(R) == 4 ? (R)L.cf : (R)L.c) : Coef<R>::dg(L)[pt];
   const cx<R> d = mk<R>(mu.x + dgk, mu.y);
-  const R dd = d.x * d.x + d.y * d.y;
-  const cx<R> dinv = mk<R>(d.x / dd, -d.y / dd);
-  const long long o = (long long)b * nn;
+  const R rd = (R)1 / (d.x * d.x + d.y * d.y);
+  const cx<R> dinv = mk<R>(d.x * rd, -d.y * rd);
+  const long long o0 = (long long)b * nn, o1 = o0 + nn;
   if (first) {
-    out[o + pt] = cscale(cmul(rhs[o + pt], dinv), w);
+    const cx<R> r0 = rhs[o0 + pt], r1 = rhs[o1 + pt];
+    out[o0 + pt] = cscale(cmul(r0, dinv), w);
+    out[o1 + pt] = cscale(cmul(r1, dinv), w);
     return;
   }
-  const cx<R>* zb = z + o;
-  const cx<R> Az = cadd(cmul(mu, zb[pt]), tauKz<R>(L, zb, i, j));
-  out[o + pt] = cadd(zb[pt], cscale(cmul(csub(rhs[o + pt], Az), dinv), w));
+  const cx<R> Az0 = cadd(cmul(mu, z[o0 + pt]), tauKz<R>(L, z + o0, i, j));
+  const cx<R> Az1 = cadd(cmul(mu, z[o1 + pt]), tauKz<R>(L, z + o1, i, j));
+  const cx<R> n0 = cadd(z[o0 + pt], cscale(cmul(csub(rhs[o0 + pt], Az0), dinv), w));
+  const cx<R> n1 = cadd(z[o1 + pt], cscale(cmul(csub(rhs[o1 + pt], Az1), dinv), w));
+  out[o0 + pt] = n0;
+  out[o1 + pt] = n1;
 }
 
 // res = rhs - A z
 template <typename R>
-__global__ void k_mg_resid(MgLevel L, int nsys, const cx<R>* __restrict__ tab, int kind,
-                           const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z, cx<R>* __restrict__ res) {
+__global__ void __launch_bounds__(256) k_mg_resid(MgLevel L, const cx<R>* __restrict__ tab, int kind,
+                                                  const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z,
+                                                  cx<R>* __restrict__ res) {
   const int N = L.N, nn = N * N;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nsys * nn) return;
-  const int b = (int)(idx / nn), pt = (int)(idx - (long long)b * nn);
-  const int j = pt / N, i = pt - j * N;
+  const GridPt q = grid_pt();
+  if (q.i >= N || q.j >= N) return;
+  const int b = 2 * q.b, i = q.i, j = q.j, pt = j * N + i;
   const cx<R> mu = shift_of<R>(tab, b, kind);
-  const long long o = (long long)b * nn;
-  const cx<R>* zb = z + o;
-  const cx<R> Az = cadd(cmul(mu, zb[pt]), tauKz<R>(L, zb, i, j));
-  res[o + pt] = csub(rhs[o + pt], Az);
+  const long long o0 = (long long)b * nn, o1 = o0 + nn;
+  const cx<R> Az0 = cadd(cmul(mu, z[o0 + pt]), tauKz<R>(L, z + o0, i, j));
+  const cx<R> Az1 = cadd(cmul(mu, z[o1 + pt]), tauKz<R>(L, z + o1, i, j));
+  const cx<R> r0 = csub(rhs[o0 + pt], Az0), r1 = csub(rhs[o1 + pt], Az1);
+  res[o0 + pt] = r0;
+  res[o1 + pt] = r1;
 }
+
+// Transfers between levels, one coarse (restriction) or fine (prolongation) point of both
+// systems of a slot per thread, like the smoother.
 
 // full weighting: coarse (I, J) <- fine 9-point neighbourhood of (2I+1, 2J+1) (0-based)
 template <typename R>
-__global__ void k_mg_restrict(int Nf, int nsys, const cx<R>* __restrict__ f, cx<R>* __restrict__ c) {
+__global__ void __launch_bounds__(256) k_mg_restrict(int Nf, const cx<R>* __restrict__ f, cx<R>* __restrict__ c) {
   const int Nc = (Nf - 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nsys * nnc) return;
-  const int b = (int)(idx / nnc), pt = (int)(idx - (long long)b * nnc);
-  const int J = pt / Nc, I = pt - J * Nc;
-  const cx<R>* fb = f + (long long)b * nnf;
+  const GridPt q = grid_pt();
+  if (q.i >= Nc || q.j >= Nc) return;
+  const int I = q.i, J = q.j, pt = J * Nc + I;
   const int fi = 2 * I + 1, fj = 2 * J + 1;
-  auto at = [&](int ii, int jj) { return fb[jj * Nf + ii]; };
-  cx<R> s = cscale(at(fi, fj), (R)4);
-  s = cadd(s, cscale(cadd(cadd(at(fi - 1, fj), at(fi + 1, fj)), cadd(at(fi, fj - 1), at(fi, fj + 1))), (R)2));
-  s = cadd(s, cadd(cadd(at(fi - 1, fj - 1), at(fi + 1, fj - 1)), cadd(at(fi - 1, fj + 1), at(fi + 1, fj + 1))));
-  c[(long long)b * nnc + pt] = cscale(s, (R)(1.0 / 16.0));
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long b = 2LL * q.b + k;
+    const cx<R>* fb = f + b * nnf;
+    auto at = [&](int ii, int jj) { return fb[jj * Nf + ii]; };
+    cx<R> s = cscale(at(fi, fj), (R)4);
+    s = cadd(s, cscale(cadd(cadd(at(fi - 1, fj), at(fi + 1, fj)), cadd(at(fi, fj - 1), at(fi, fj + 1))), (R)2));
+    s = cadd(s, cadd(cadd(at(fi - 1, fj - 1), at(fi + 1, fj - 1)), cadd(at(fi - 1, fj + 1), at(fi + 1, fj + 1))));
+    c[b * nnc + pt] = cscale(s, (R)(1.0 / 16.0));
+  }
 }
 
-// bilinear prolongation added to the fine solution
+// bilinear prolongation added to the fine solution.  Fine 0-based index 2K+1 sits on coarse node
+// K; an even fine index lies between coarse nodes K-1 and K.  With Ka = (k-1) >> 1 and Kb = k >> 1
+// in each direction (equal for an odd k) the value is 1/4 of the sum over the four (Ka|Kb) pairs,
+// which equals the usual one-, two- or four-node average exactly (scalings by powers of two), so
+// no thread branches on the parity of its point.
 template <typename R>
-__global__ void k_mg_prolong_add(int Nf, int nsys, const cx<R>* __restrict__ c, cx<R>* __restrict__ z) {
+__global__ void __launch_bounds__(256) k_mg_prolong_add(int Nf, const cx<R>* __restrict__ c, cx<R>* __restrict__ z) {
   const int Nc = (Nf - 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nsys * nnf) return;
-  const int b = (int)(idx / nnf), pt = (int)(idx - (long long)b * nnf);
-  const int j = pt / Nf, i = pt - j * Nf;
-  const cx<R>* cb = c + (long long)b * nnc;
-  // fine 0-based index 2K+1 sits on coarse node K; even fine indices lie between coarse nodes
-  auto cv = [&](int I, int J) { return (I < 0 || J < 0 || I >= Nc || J >= Nc) ? mk<R>(0, 0) : cb[J * Nc + I]; };
-  cx<R> v;
-  const bool oi = i & 1, oj = j & 1;
-  if (oi && oj) v = cv(i >> 1, j >> 1);
-  else if (oi) v = cscale(cadd(cv(i >> 1, (j >> 1) - 1), cv(i >> 1, j >> 1)), (R)0.5);
-  else if (oj) v = cscale(cadd(cv((i >> 1) - 1, j >> 1), cv(i >> 1, j >> 1)), (R)0.5);
-  else v = cscale(cadd(cadd(cv((i >> 1) - 1, (j >> 1) - 1), cv(i >> 1, (j >> 1) - 1)),
-                       cadd(cv((i >> 1) - 1, j >> 1), cv(i >> 1, j >> 1))), (R)0.25);
-  z[(long long)b * nnf + pt] = cadd(z[(long long)b * nnf + pt], v);
+  const GridPt q = grid_pt();
+  if (q.i >= Nf || q.j >= Nf) return;
+  const int i = q.i, j = q.j, pt = j * Nf + i;
+  const int Ia = (i - 1) >> 1, Ib = i >> 1, Ja = (j - 1) >> 1, Jb = j >> 1;
+  const bool xa = Ia >= 0, xb = Ib < Nc, ya = Ja >= 0, yb = Jb < Nc;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long b = 2LL * q.b + k;
+    const cx<R>* cb = c + b * nnc;
+    const cx<R> zero = mk<R>(0, 0);
+    const cx<R> c11 = xa && ya ? cb[Ja * Nc + Ia] : zero, c21 = xb && ya ? cb[Ja * Nc + Ib] : zero;
+    const cx<R> c12 = xa && yb ? cb[Jb * Nc + Ia] : zero, c22 = xb && yb ? cb[Jb * Nc + Ib] : zero;
+    const cx<R> v = cscale(cadd(cadd(c11, c21), cadd(c12, c22)), (R)0.25);
+    z[b * nnf + pt] = cadd(z[b * nnf + pt], v);
+  }
 }
 
 // Neumann full weighting: coarse (I, J) <- fine 9-point neighbourhood of (2I, 2J), mirrored ghosts
 template <typename R>
-__global__ void k_mg_restrict_neu(int Nf, int nsys, const cx<R>* __restrict__ f, cx<R>* __restrict__ c) {
+__global__ void __launch_bounds__(256) k_mg_restrict_neu(int Nf, const cx<R>* __restrict__ f, cx<R>* __restrict__ c) {
   const int Nc = (Nf + 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nsys * nnc) return;
-  const int b = (int)(idx / nnc), pt = (int)(idx - (long long)b * nnc);
-  const int J = pt / Nc, I = pt - J * Nc;
-  const cx<R>* fb = f + (long long)b * nnf;
+  const GridPt q = grid_pt();
+  if (q.i >= Nc || q.j >= Nc) return;
+  const int I = q.i, J = q.j, pt = J * Nc + I;
   const int fi = 2 * I, fj = 2 * J;
   auto mir = [&](int k) { return k < 0 ? -k : (k > Nf - 1 ? 2 * (Nf - 1) - k : k); };
-  auto at = [&](int ii, int jj) { return fb[mir(jj) * Nf + mir(ii)]; };
-  cx<R> s = cscale(at(fi, fj), (R)4);
-  s = cadd(s, cscale(cadd(cadd(at(fi - 1, fj), at(fi + 1, fj)), cadd(at(fi, fj - 1), at(fi, fj + 1))), (R)2));
-  s = cadd(s, cadd(cadd(at(fi - 1, fj - 1), at(fi + 1, fj - 1)), cadd(at(fi - 1, fj + 1), at(fi + 1, fj + 1))));
-  c[(long long)b * nnc + pt] = cscale(s, (R)(1.0 / 16.0));
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long b = 2LL * q.b + k;
+    const cx<R>* fb = f + b * nnf;
+    auto at = [&](int ii, int jj) { return fb[mir(jj) * Nf + mir(ii)]; };
+    cx<R> s = cscale(at(fi, fj), (R)4);
+    s = cadd(s, cscale(cadd(cadd(at(fi - 1, fj), at(fi + 1, fj)), cadd(at(fi, fj - 1), at(fi, fj + 1))), (R)2));
+    s = cadd(s, cadd(cadd(at(fi - 1, fj - 1), at(fi + 1, fj - 1)), cadd(at(fi - 1, fj + 1), at(fi + 1, fj + 1))));
+    c[b * nnc + pt] = cscale(s, (R)(1.0 / 16.0));
+  }
 }
 
 // Neumann bilinear prolongation added to the fine solution: even fine nodes are coarse nodes
 template <typename R>
-__global__ void k_mg_prolong_add_neu(int Nf, int nsys, const cx<R>* __restrict__ c, cx<R>* __restrict__ z) {
+__global__ void __launch_bounds__(256) k_mg_prolong_add_neu(int Nf, const cx<R>* __restrict__ c, cx<R>* __restrict__ z) {
   const int Nc = (Nf + 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nsys * nnf) return;
-  const int b = (int)(idx / nnf), pt = (int)(idx - (long long)b * nnf);
-  const int j = pt / Nf, i = pt - j * Nf;
-  const cx<R>* cb = c + (long long)b * nnc;
+  const GridPt q = grid_pt();
+  if (q.i >= Nf || q.j >= Nf) return;
+  const int i = q.i, j = q.j, pt = j * Nf + i;
   const int I0 = i >> 1, J0 = j >> 1, I1 = (i + 1) >> 1, J1 = (j + 1) >> 1;   // equal when even
-  const cx<R> v = cscale(cadd(cadd(cb[J0 * Nc + I0], cb[J0 * Nc + I1]), cadd(cb[J1 * Nc + I0], cb[J1 * Nc + I1])),
-                         (R)0.25);
-  z[(long long)b * nnf + pt] = cadd(z[(long long)b * nnf + pt], v);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long b = 2LL * q.b + k;
+    const cx<R>* cb = c + b * nnc;
+    const cx<R> v = cscale(cadd(cadd(cb[J0 * Nc + I0], cb[J0 * Nc + I1]), cadd(cb[J1 * Nc + I0], cb[J1 * Nc + I1])),
+                           (R)0.25);
+    z[b * nnf + pt] = cadd(z[b * nnf + pt], v);
+  }
 }
 
 // Neumann 3 x 3 grid: exact solve z = V2 diag(1/(mu + lambda)) V2^{-1} rhs, one thread per (system, node)
@@ -596,39 +630,45 @@ template <typename R>
 static void vcycle(const MgHost& h, const cx<R>* tab, int kind, int l, const cx<R>* rhs, cx<R>* z, cx<R>* spare,
                    cudaStream_t st) {
   const MgLevel& L = h.lev[l];
-  const long long len = (long long)h.nsys * L.N * L.N;
+  const dim3 grids = grid_for(L.N, h.nsys / 2);     // one slot (two systems) per grid z
   const R w = (R)kJacobiWeight;
   if (l == h.nlev - 1) {
-    if (L.neu) k_mg_coarse_neu<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, z);
+    if (L.neu) k_mg_coarse_neu<R><<<blocks_for((long long)h.nsys * 9), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, z);
     else        // exact solve on the single-unknown grid: z = rhs / diag
-      k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, nullptr, z, 1, (R)1);
+      k_mg_jacobi<R><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, nullptr, z, 1, (R)1);
     g_mg_launches += 1;
     return;
   }
-  // pre-smoothing from zero: z1 = w D^{-1} rhs, then nu1-1 sweeps ping-ponging with `spare`
-  cx<R>* cur = z;
-  cx<R>* oth = spare;
-  k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, nullptr, cur, 1, w);
+  // pre-smoothing from zero: the first sweep z1 = w D^{-1} rhs, then nu1 - 1 sweeps ping-ponging
+  // between `spare` and z.  The nu1 + nu2 = 2 nu sweeps alternate between the two buffers, so
+  // starting in `spare` leaves the last post-smoothing sweep in z.
+  cx<R>* cur = spare;
+  cx<R>* oth = z;
+  k_mg_jacobi<R><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, nullptr, cur, 1, w);
   for (int s = 1; s < kNu; ++s) {
-    k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, cur, oth, 0, w);
+    k_mg_jacobi<R><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, cur, oth, 0, w);
     std::swap(cur, oth);
   }
   // residual -> restrict to the coarse right-hand side
-  k_mg_resid<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, cur, oth);
+  k_mg_resid<R><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, cur, oth);
   const MgLevel& C = h.lev[l + 1];
-  const long long lenc = (long long)h.nsys * C.N * C.N;
+  const dim3 gridc = grid_for(C.N, h.nsys / 2);
   cx<R>* crhs = (cx<R>*)C.a[0];
-  if (L.neu) k_mg_restrict_neu<R><<<blocks_for(lenc), 256, 0, st>>>(L.N, h.nsys, oth, crhs);
-  else k_mg_restrict<R><<<blocks_for(lenc), 256, 0, st>>>(L.N, h.nsys, oth, crhs);
+  if (L.neu) k_mg_restrict_neu<R><<<gridc, kMgBlock, 0, st>>>(L.N, oth, crhs);
+  else k_mg_restrict<R><<<gridc, kMgBlock, 0, st>>>(L.N, oth, crhs);
   vcycle<R>(h, tab, kind, l + 1, crhs, (cx<R>*)C.a[1], (cx<R>*)C.a[2], st);
-  if (L.neu) k_mg_prolong_add_neu<R><<<blocks_for(len), 256, 0, st>>>(L.N, h.nsys, (const cx<R>*)C.a[1], cur);
-  else k_mg_prolong_add<R><<<blocks_for(len), 256, 0, st>>>(L.N, h.nsys, (const cx<R>*)C.a[1], cur);
+  if (L.neu) k_mg_prolong_add_neu<R><<<grids, kMgBlock, 0, st>>>(L.N, (const cx<R>*)C.a[1], cur);
+  else k_mg_prolong_add<R><<<grids, kMgBlock, 0, st>>>(L.N, (const cx<R>*)C.a[1], cur);
   for (int s = 0; s < kNu; ++s) {
-    k_mg_jacobi<R><<<blocks_for(len), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, cur, oth, 0, w);
+    k_mg_jacobi<R><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, cur, oth, 0, w);
     std::swap(cur, oth);
   }
   g_mg_launches += 2 * kNu + 3;
-  if (cur != z) { k_mg_axpy<R><<<blocks_for(len), 256, 0, st>>>(len, cur, z, 1); g_mg_launches += 1; }
+  if (cur != z) {
+    const long long len = (long long)h.nsys * L.N * L.N;
+    k_mg_axpy<R><<<blocks_for(len), 256, 0, st>>>(len, cur, z, 1);
+    g_mg_launches += 1;
+  }
 }
 
 template <typename R, int Q>
@@ -657,7 +697,7 @@ static cudaError_t mg_apply(const Batch& B, const Geom& g, const MgHost& h, int 
     if (c == 0) {
       vcycle<R>(h, tab, kind, 0, r0, z0, (T*)F.a[1], st);
     } else {
-      k_mg_resid<R><<<blocks_for(len), 256, 0, st>>>(F, h.nsys, tab, kind, r0, z0, x0);
+      k_mg_resid<R><<<grid_for(F.N, h.nsys / 2), kMgBlock, 0, st>>>(F, tab, kind, r0, z0, x0);
       vcycle<R>(h, tab, kind, 0, x0, (T*)F.a[2], (T*)F.a[1], st);
       k_mg_axpy<R><<<blocks_for(len), 256, 0, st>>>(len, (const T*)F.a[2], z0, 0);
       g_mg_launches += 2;

@@ -311,7 +311,7 @@ int fill_batch(Batch& B, const std::vector<Geom>& gs, int* doff, cudaStream_t st
       const int v = (g.tune & TUNE_TIME512_3BLK) ? 1 : (g.tune & TUNE_TIME512_4BLK) ? 2 : 0;
       want = want < 0 ? v : (want == v ? v : 0);
     }
-    B.t512v = want > 0 ? 1 : 0;
+    B.t512v = want > 0 ? want : 0;
   }
   B.dst_q = gs[0].dst_q;
   B.time_q = gs[0].time_q;
@@ -803,7 +803,6 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
                          int* it_out, bool* conv_out) {
   const Batch& B = p->B;
   const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
-  const bool va = p->g.mg_route != 0;      // multigrid applies launch directly (no graph)
   // x = 0, w = w2 = 0, r1 = r2 = b
   CK(cudaMemsetAsync(p->hS.v[s_x], 0, vb, p->stream));
   CK(cudaMemsetAsync(p->hS.v[SL_W], 0, vb, p->stream));
@@ -826,7 +825,7 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   // the iterations read the tolerance from the device, so a captured graph serves every sweep
   if (!p->dtol && cudaMalloc(&p->dtol, sizeof(double)) != cudaSuccess) { cudaGetLastError(); p->dtol = nullptr; }
   Batch Bt = B;
-  bool graph = c.graphs && !p->prof && !va && p->dtol;
+  bool graph = c.graphs && !p->prof && p->dtol;
   if (p->dtol) {
     CK(cudaMemcpyAsync(p->dtol, &c.tol, sizeof(double), cudaMemcpyHostToDevice, p->stream));
     Bt.tols = p->dtol;
@@ -897,7 +896,6 @@ static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
                          int* it_out, bool* conv_out) {
   const Batch& B = p->B;
   const size_t vb = (size_t)2 * p->g.mn * sizeof(double);
-  const bool va = p->g.mg_route != 0;      // multigrid applies launch directly (no graph)
   const int op = PCB_OP_AHAT;
   CK(cudaMemsetAsync(p->hS.v[s_x], 0, vb, p->stream));
   CK(cudaMemsetAsync(p->dSc, 0, sizeof(Scal), p->stream));
@@ -913,7 +911,7 @@ static int fgmres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
   // Arnoldi steps replay per-j graphs (the first j = 0 step of a solve runs directly)
   if (!p->dtol && cudaMalloc(&p->dtol, sizeof(double)) != cudaSuccess) { cudaGetLastError(); p->dtol = nullptr; }
   Batch Bt = B;
-  const bool graph = c.graphs && !p->prof && !va && p->dtol;
+  const bool graph = c.graphs && !p->prof && p->dtol;
   if (p->dtol) {
     CK(cudaMemcpyAsync(p->dtol, &c.tol, sizeof(double), cudaMemcpyHostToDevice, p->stream));
     Bt.tols = p->dtol;
@@ -1228,6 +1226,17 @@ std::vector<TuneChoice> tune_candidates(const Geom& g, int prec) {
   return out;
 }
 
+// the configuration a problem runs, in the terms of pcb_tune_info
+void describe_choice(const Geom& g, int prec, pcb_tune_info* info) {
+  info->pipelined_dst = prec == PCB_MIXED && pipe_dst_p(g);
+  info->pipelined_time = prec == PCB_MIXED && pipe_time_p(g);
+  info->time_major_handoff = prec == PCB_MIXED && (pipe_dst_code(g) & 64) ? 1 : 0;
+  info->dst_lanes = g.M / g.dst_q;
+  info->time_lanes = g.n / g.time_q;
+  info->tile_scale = tune_budget_shift(g.tune) == 1 ? 0.5 : tune_budget_shift(g.tune) == 2 ? 2.0 : 1.0;
+  info->time512_blocks = (g.tune & TUNE_TIME512_3BLK) ? 3 : (g.tune & TUNE_TIME512_4BLK) ? 4 : 2;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1324,20 +1333,48 @@ int pcb_autotune(pcb_problem* p, int kind, int reps, pcb_tune_info* info) {
     g_tune_cache[tune_key(p->g, prec)] = cands[best_k];
   }
   if (info) {
+    describe_choice(p->g, prec, info);
     info->candidates = timed;
     info->rejected = rejected;
     info->chosen = best_k;
     info->default_ms = def_ms;
     info->best_ms = best;
-    info->pipelined_dst = prec == PCB_MIXED && pipe_dst_p(p->g);
-    info->pipelined_time = prec == PCB_MIXED && pipe_time_p(p->g);
-    info->time_major_handoff = prec == PCB_MIXED && (pipe_dst_code(p->g) & 64) ? 1 : 0;
-    info->dst_lanes = p->g.M / p->g.dst_q;
-    info->time_lanes = p->g.n / p->g.time_q;
-    info->tile_scale = tune_budget_shift(p->g.tune) == 1 ? 0.5 : tune_budget_shift(p->g.tune) == 2 ? 2.0 : 1.0;
-    info->time512_blocks = (p->g.tune & TUNE_TIME512_3BLK) ? 3 : (p->g.tune & TUNE_TIME512_4BLK) ? 4 : 2;
   }
   return done(PCB_OK);
+}
+
+int pcb_tune_select(pcb_problem* p, int candidate, pcb_tune_info* info) {
+  if (!p) return PCB_ERR_INVALID_ARG;
+  if (p->g.mg_route) return PCB_ERR_UNSUPPORTED;
+  const int prec = p->desc.precision;
+  Geom gd = p->g;
+  gd.tune = 0; gd.dst_q = dst_Q(gd.M); gd.time_q = time_Q(gd.n);
+  set_shapes(gd);
+  const std::vector<TuneChoice> cands = tune_candidates(gd, prec);
+  if (candidate >= (int)cands.size()) return PCB_ERR_INVALID_ARG;
+  if (candidate >= 0) {
+    CK(cudaStreamSynchronize(p->stream));
+    Geom g = gd;
+    apply_choice(g, cands[candidate]);
+    g.scratch = p->g.scratch;
+    p->g = g;
+    CK(cudaMemcpyAsync(p->dG, &p->g, sizeof(Geom), cudaMemcpyHostToDevice, p->stream));
+    std::vector<int> staging;
+    int rc = fill_batch(p->B, std::vector<Geom>(1, p->g), p->doff, p->stream, staging);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(p->stream));
+    if (p->git) { cudaGraphExecDestroy(p->git); p->git = nullptr; }
+    for (cudaGraphExec_t& e : p->garn) if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    p->git_kind = p->garn_kind = -1;
+  }
+  if (info) {
+    describe_choice(p->g, prec, info);
+    info->candidates = (int)cands.size();
+    info->rejected = 0;
+    info->chosen = candidate;
+    info->default_ms = info->best_ms = 0.0;
+  }
+  return PCB_OK;
 }
 
 int pcb_recover(pcb_problem* p, const double* x_dev, double* y_dev, double* p_dev) {

@@ -84,3 +84,35 @@ def test_autotuned_batch_equals_alone(P):
         x1, i1 = P.batch_solve([gp], [dev(b)], tol=1e-8, restart=16)
         assert_close(xo, x1[0].cpu().numpy(), 1e-12)
         assert i1[0]["iterations"] == info["iterations"]
+
+
+# every configuration of the autotuner's list, installed directly, against the oracle: shapes with
+# the n = 512 time pass (its three resident-block variants, with and without the time-major
+# hand-off), the pipelined and tile kernels with their radices and tile sizes, FP64 and Neumann
+SELECT_CASES = [(255, 512, 1.0, 1e-2, "abs_ps", "mixed", math.pi, "dirichlet"),
+                (63, 512, 0.5, 1e-3, "ps", "mixed", math.pi, "dirichlet"),
+                (127, 64, 1.0, 1e-4, "pms", "mixed", math.pi, "dirichlet"),
+                (63, 32, 0.5, 1e-2, "ps", "fp64", math.pi, "dirichlet"),
+                (129, 128, 0.5, 1e-2, "ps", "mixed", math.pi, "neumann")]
+
+
+@pytest.mark.parametrize("case", SELECT_CASES, ids=lambda c: "N%d-n%d-%s-%s-%s" % (c[0], c[1], c[4], c[5], c[7]))
+def test_every_configuration_matches_oracle(P, case):
+    N, n, theta, gamma, kind, prec, zeta, bc = case
+    a = 1e-3 if bc == "neumann" else 1.0
+    prob = ds.Problem(N, n, theta, gamma, zeta=zeta, bc=bc, a0=a)
+    v = synth.random_vector(2 * prob.m * n, seed=700 + N + n)
+    ref = ORACLE[kind](prob, v)
+    gp = P.Problem(N, n, theta, gamma, zeta=zeta, precision=prec, bc=bc, a=a)
+    count = gp.tune_select(-1)["candidates"]
+    assert count >= 1
+    seen = set()
+    for k in range(count):
+        info = gp.tune_select(k)
+        seen.add((info["pipelined_dst"], info["pipelined_time"], info["time_major_handoff"], info["time512_blocks"]))
+        out = gp.precond_apply(dev(v), kind=kind, precision=prec).cpu().numpy()
+        assert_close(out, ref, TOL[prec], what=info)
+    if n == 512 and prec == "mixed":
+        assert {b for *_, b in seen} == {2, 3, 4}, seen
+    with pytest.raises(Exception):
+        gp.tune_select(count)

@@ -539,6 +539,28 @@ def test_gmres_graph_replay_matches_direct_launches(P, precision):
     assert igr["relres"] <= 1e-10
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", [("fgmres", "ps", 0.5), ("minres", "pms", 1.0)])
+def test_multigrid_graph_replay_matches_direct_launches(P, precision, case):
+    """The multigrid route (variable a(x)) replays its iterations, V-cycles included, from CUDA
+    graphs: the iterates equal the directly launched ones bit for bit, with equal counts and
+    launch totals, over restart cycles and a repeated solve."""
+    method, kind, theta = case
+    N, n, gamma = 31, 32, 1e-3
+    edges = synth.variable_coefficient_edges(N)
+    prob = ds.Problem(N, n, theta, gamma, a_edges=edges)
+    g = synth.random_target(N, n, seed=12); f = synth.manufactured_source(N, n)
+    b = dev(ds.rhs_gmres(prob, g, f) if method == "fgmres" else ds.rhs_minres(prob, g, f))
+    gp = P.Problem(N, n, theta, gamma, a_edges=edges, mg_cycles=2, precision=precision)
+    kw = dict(method=method, precond=kind, tol=1e-10, restart=4)
+    xd, idir = gp.solve(b, graphs=False, **kw)
+    xg, igr = gp.solve(b, graphs=True, **kw)
+    xg2, igr2 = gp.solve(b, graphs=True, **kw)
+    assert igr["iterations"] == idir["iterations"] == igr2["iterations"] > 4
+    assert igr["launches"] == idir["launches"] == igr2["launches"]
+    assert torch.equal(xd, xg) and torch.equal(xd, xg2)
+
+
 @pytest.mark.parametrize("gamma", [1e-2, 1e-6])
 def test_mixed_solve_half_pi(P, gamma):
     """omega = i (zeta = pi/2) on the pipelined FP32 passes: the mixed MINRES-|P_S| solve meets
