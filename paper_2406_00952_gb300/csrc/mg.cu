@@ -53,6 +53,7 @@ struct MgLevel {
 struct MgHost {
   int nlev = 0;
   int nsys = 0;               // systems = n (n/2 frequency slots x 2 right-hand sides)
+  int tail_l0 = -1;           // first level of the fused coarse-level launch (-1: none)
   MgLevel lev[kMaxLevels];
   void* zfine = nullptr;      // outer solution (level 0)
   void* xfine = nullptr;      // outer residual (level 0)
@@ -140,6 +141,7 @@ static unsigned char* mg_setup_neumann(const Geom& g, MgHost& h, unsigned char* 
 }
 
 static void mg_slot_tables(const Geom& g, MgHost& h, unsigned char*& p);
+static int tail_level(const MgHost& h);
 
 cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges, double a0) {
   // this translation unit's copy of the register-FFT twiddle table
@@ -155,6 +157,7 @@ cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges, double a0) {
   if (neu) {
     p = mg_setup_neumann(g, h, p, a0);
     mg_slot_tables(g, h, p);
+    h.tail_l0 = tail_level(h);
     if ((size_t)(p - (unsigned char*)ws) > mg_workspace_bytes(g)) return cudaErrorInvalidValue;
     for (auto& e : registry())
       if (e.first == ws) { e.second = h; g.mg = ws; return cudaGetLastError(); }
@@ -210,6 +213,7 @@ cudaError_t mg_setup(Geom& g, void* ws, const double* a_edges, double a0) {
     N = Nc;
   }
   mg_slot_tables(g, h, p);
+  h.tail_l0 = tail_level(h);
   if ((size_t)(p - (unsigned char*)ws) > mg_workspace_bytes(g)) return cudaErrorInvalidValue;
   for (auto& e : registry())
     if (e.first == ws) { e.second = h; return cudaGetLastError(); }
@@ -307,154 +311,75 @@ __device__ __forceinline__ cx<R> shift_of(const cx<R>* __restrict__ tab, int b, 
   return kind == 2 ? tab[4 * r + 0] : mk<R>(tab[4 * r + 3].x, (R)0);
 }
 
-// The two systems of a frequency slot (2r and 2r + 1) share the shift and hence the diagonal:
-// a thread treats one grid point of both, so the coefficients and the diagonal are loaded and
-// inverted once (grid z runs over the slots).
+// Per-point operations, shared by the one-launch-per-step kernels of the fine levels and the
+// fused kernel of the coarse levels (identical arithmetic on either path).  Arrays hold one
+// system's grid, row j of N points at j N.
 
-// out = z + w (rhs - A z)/diag  (first: z = 0, so out = w rhs / diag)
+// Jacobi diagonal inverse of system shift mu at point pt
 template <typename R>
-__global__ void __launch_bounds__(256) k_mg_jacobi(MgLevel L, const cx<R>* __restrict__ tab, int kind,
-                                                   const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z,
-                                                   cx<R>* __restrict__ out, int first, R w) {
-  const int N = L.N, nn = N * N;
-  const GridPt q = grid_pt();
-  if (q.i >= N || q.j >= N) return;
-  const int b = 2 * q.b, i = q.i, j = q.j, pt = j * N + i;
-  const cx<R> mu = shift_of<R>(tab, b, kind);
+__device__ __forceinline__ cx<R> jacobi_dinv(const MgLevel& L, cx<R> mu, int pt) {
   const R dgk = L.neu ? (R)4 * (sizeof(R) == 4 ? (R)L.cf : (R)L.c) : Coef<R>::dg(L)[pt];
   const cx<R> d = mk<R>(mu.x + dgk, mu.y);
   const R rd = (R)1 / (d.x * d.x + d.y * d.y);
-  const cx<R> dinv = mk<R>(d.x * rd, -d.y * rd);
-  const long long o0 = (long long)b * nn, o1 = o0 + nn;
-  if (first) {
-    const cx<R> r0 = rhs[o0 + pt], r1 = rhs[o1 + pt];
-    out[o0 + pt] = cscale(cmul(r0, dinv), w);
-    out[o1 + pt] = cscale(cmul(r1, dinv), w);
-    return;
+  return mk<R>(d.x * rd, -d.y * rd);
+}
+
+// one damped Jacobi update at (i, j): out = z + w (rhs - A z) / diag (first: z = 0)
+template <typename R>
+__device__ __forceinline__ cx<R> jacobi_pt(const MgLevel& L, cx<R> mu, cx<R> dinv, const cx<R>* __restrict__ rhs,
+                                           const cx<R>* __restrict__ z, int i, int j, bool first, R w) {
+  const int pt = j * L.N + i;
+  if (first) return cscale(cmul(rhs[pt], dinv), w);
+  const cx<R> Az = cadd(cmul(mu, z[pt]), tauKz<R>(L, z, i, j));
+  return cadd(z[pt], cscale(cmul(csub(rhs[pt], Az), dinv), w));
+}
+
+// residual rhs - A z at (i, j)
+template <typename R>
+__device__ __forceinline__ cx<R> resid_pt(const MgLevel& L, cx<R> mu, const cx<R>* __restrict__ rhs,
+                                          const cx<R>* __restrict__ z, int i, int j) {
+  const int pt = j * L.N + i;
+  const cx<R> Az = cadd(cmul(mu, z[pt]), tauKz<R>(L, z, i, j));
+  return csub(rhs[pt], Az);
+}
+
+// full weighting: coarse (I, J) <- fine 9-point neighbourhood of (2I+1, 2J+1) (0-based); Neumann:
+// of (2I, 2J) with mirrored ghost values
+template <typename R>
+__device__ __forceinline__ cx<R> restrict_pt(int Nf, bool neu, const cx<R>* fb, int I, int J) {
+  const int fi = neu ? 2 * I : 2 * I + 1, fj = neu ? 2 * J : 2 * J + 1;
+  auto mir = [&](int k) { return k < 0 ? -k : (k > Nf - 1 ? 2 * (Nf - 1) - k : k); };
+  auto at = [&](int ii, int jj) { return neu ? fb[mir(jj) * Nf + mir(ii)] : fb[jj * Nf + ii]; };
+  cx<R> s = cscale(at(fi, fj), (R)4);
+  s = cadd(s, cscale(cadd(cadd(at(fi - 1, fj), at(fi + 1, fj)), cadd(at(fi, fj - 1), at(fi, fj + 1))), (R)2));
+  s = cadd(s, cadd(cadd(at(fi - 1, fj - 1), at(fi + 1, fj - 1)), cadd(at(fi - 1, fj + 1), at(fi + 1, fj + 1))));
+  return cscale(s, (R)(1.0 / 16.0));
+}
+
+// bilinear prolongation of the coarse grid cb (Nc points per side) at fine (i, j).  Dirichlet:
+// fine 0-based index 2K+1 sits on coarse node K, an even fine index between nodes K-1 and K; with
+// Ka = (k-1) >> 1 and Kb = k >> 1 in each direction (equal for an odd k) the value is 1/4 of the
+// sum over the four (Ka|Kb) pairs, which equals the one-, two- or four-node average exactly
+// (scalings by powers of two), so no thread branches on the parity of its point.  Neumann: even
+// fine nodes are coarse nodes.
+template <typename R>
+__device__ __forceinline__ cx<R> prolong_pt(int Nc, bool neu, const cx<R>* cb, int i, int j) {
+  if (neu) {
+    const int I0 = i >> 1, J0 = j >> 1, I1 = (i + 1) >> 1, J1 = (j + 1) >> 1;   // equal when even
+    return cscale(cadd(cadd(cb[J0 * Nc + I0], cb[J0 * Nc + I1]), cadd(cb[J1 * Nc + I0], cb[J1 * Nc + I1])), (R)0.25);
   }
-  const cx<R> Az0 = cadd(cmul(mu, z[o0 + pt]), tauKz<R>(L, z + o0, i, j));
-  const cx<R> Az1 = cadd(cmul(mu, z[o1 + pt]), tauKz<R>(L, z + o1, i, j));
-  const cx<R> n0 = cadd(z[o0 + pt], cscale(cmul(csub(rhs[o0 + pt], Az0), dinv), w));
-  const cx<R> n1 = cadd(z[o1 + pt], cscale(cmul(csub(rhs[o1 + pt], Az1), dinv), w));
-  out[o0 + pt] = n0;
-  out[o1 + pt] = n1;
-}
-
-// res = rhs - A z
-template <typename R>
-__global__ void __launch_bounds__(256) k_mg_resid(MgLevel L, const cx<R>* __restrict__ tab, int kind,
-                                                  const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z,
-                                                  cx<R>* __restrict__ res) {
-  const int N = L.N, nn = N * N;
-  const GridPt q = grid_pt();
-  if (q.i >= N || q.j >= N) return;
-  const int b = 2 * q.b, i = q.i, j = q.j, pt = j * N + i;
-  const cx<R> mu = shift_of<R>(tab, b, kind);
-  const long long o0 = (long long)b * nn, o1 = o0 + nn;
-  const cx<R> Az0 = cadd(cmul(mu, z[o0 + pt]), tauKz<R>(L, z + o0, i, j));
-  const cx<R> Az1 = cadd(cmul(mu, z[o1 + pt]), tauKz<R>(L, z + o1, i, j));
-  const cx<R> r0 = csub(rhs[o0 + pt], Az0), r1 = csub(rhs[o1 + pt], Az1);
-  res[o0 + pt] = r0;
-  res[o1 + pt] = r1;
-}
-
-// Transfers between levels, one coarse (restriction) or fine (prolongation) point of both
-// systems of a slot per thread, like the smoother.
-
-// full weighting: coarse (I, J) <- fine 9-point neighbourhood of (2I+1, 2J+1) (0-based)
-template <typename R>
-__global__ void __launch_bounds__(256) k_mg_restrict(int Nf, const cx<R>* __restrict__ f, cx<R>* __restrict__ c) {
-  const int Nc = (Nf - 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
-  const GridPt q = grid_pt();
-  if (q.i >= Nc || q.j >= Nc) return;
-  const int I = q.i, J = q.j, pt = J * Nc + I;
-  const int fi = 2 * I + 1, fj = 2 * J + 1;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const long long b = 2LL * q.b + k;
-    const cx<R>* fb = f + b * nnf;
-    auto at = [&](int ii, int jj) { return fb[jj * Nf + ii]; };
-    cx<R> s = cscale(at(fi, fj), (R)4);
-    s = cadd(s, cscale(cadd(cadd(at(fi - 1, fj), at(fi + 1, fj)), cadd(at(fi, fj - 1), at(fi, fj + 1))), (R)2));
-    s = cadd(s, cadd(cadd(at(fi - 1, fj - 1), at(fi + 1, fj - 1)), cadd(at(fi - 1, fj + 1), at(fi + 1, fj + 1))));
-    c[b * nnc + pt] = cscale(s, (R)(1.0 / 16.0));
-  }
-}
-
-// bilinear prolongation added to the fine solution.  Fine 0-based index 2K+1 sits on coarse node
-// K; an even fine index lies between coarse nodes K-1 and K.  With Ka = (k-1) >> 1 and Kb = k >> 1
-// in each direction (equal for an odd k) the value is 1/4 of the sum over the four (Ka|Kb) pairs,
-// which equals the usual one-, two- or four-node average exactly (scalings by powers of two), so
-// no thread branches on the parity of its point.
-template <typename R>
-__global__ void __launch_bounds__(256) k_mg_prolong_add(int Nf, const cx<R>* __restrict__ c, cx<R>* __restrict__ z) {
-  const int Nc = (Nf - 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
-  const GridPt q = grid_pt();
-  if (q.i >= Nf || q.j >= Nf) return;
-  const int i = q.i, j = q.j, pt = j * Nf + i;
   const int Ia = (i - 1) >> 1, Ib = i >> 1, Ja = (j - 1) >> 1, Jb = j >> 1;
   const bool xa = Ia >= 0, xb = Ib < Nc, ya = Ja >= 0, yb = Jb < Nc;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const long long b = 2LL * q.b + k;
-    const cx<R>* cb = c + b * nnc;
-    const cx<R> zero = mk<R>(0, 0);
-    const cx<R> c11 = xa && ya ? cb[Ja * Nc + Ia] : zero, c21 = xb && ya ? cb[Ja * Nc + Ib] : zero;
-    const cx<R> c12 = xa && yb ? cb[Jb * Nc + Ia] : zero, c22 = xb && yb ? cb[Jb * Nc + Ib] : zero;
-    const cx<R> v = cscale(cadd(cadd(c11, c21), cadd(c12, c22)), (R)0.25);
-    z[b * nnf + pt] = cadd(z[b * nnf + pt], v);
-  }
+  const cx<R> zero = mk<R>(0, 0);
+  const cx<R> c11 = xa && ya ? cb[Ja * Nc + Ia] : zero, c21 = xb && ya ? cb[Ja * Nc + Ib] : zero;
+  const cx<R> c12 = xa && yb ? cb[Jb * Nc + Ia] : zero, c22 = xb && yb ? cb[Jb * Nc + Ib] : zero;
+  return cscale(cadd(cadd(c11, c21), cadd(c12, c22)), (R)0.25);
 }
 
-// Neumann full weighting: coarse (I, J) <- fine 9-point neighbourhood of (2I, 2J), mirrored ghosts
+// Neumann 3 x 3 grid: exact solve z = V2 diag(1/(mu + lambda)) V2^{-1} rhs at `node`
 template <typename R>
-__global__ void __launch_bounds__(256) k_mg_restrict_neu(int Nf, const cx<R>* __restrict__ f, cx<R>* __restrict__ c) {
-  const int Nc = (Nf + 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
-  const GridPt q = grid_pt();
-  if (q.i >= Nc || q.j >= Nc) return;
-  const int I = q.i, J = q.j, pt = J * Nc + I;
-  const int fi = 2 * I, fj = 2 * J;
-  auto mir = [&](int k) { return k < 0 ? -k : (k > Nf - 1 ? 2 * (Nf - 1) - k : k); };
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const long long b = 2LL * q.b + k;
-    const cx<R>* fb = f + b * nnf;
-    auto at = [&](int ii, int jj) { return fb[mir(jj) * Nf + mir(ii)]; };
-    cx<R> s = cscale(at(fi, fj), (R)4);
-    s = cadd(s, cscale(cadd(cadd(at(fi - 1, fj), at(fi + 1, fj)), cadd(at(fi, fj - 1), at(fi, fj + 1))), (R)2));
-    s = cadd(s, cadd(cadd(at(fi - 1, fj - 1), at(fi + 1, fj - 1)), cadd(at(fi - 1, fj + 1), at(fi + 1, fj + 1))));
-    c[b * nnc + pt] = cscale(s, (R)(1.0 / 16.0));
-  }
-}
-
-// Neumann bilinear prolongation added to the fine solution: even fine nodes are coarse nodes
-template <typename R>
-__global__ void __launch_bounds__(256) k_mg_prolong_add_neu(int Nf, const cx<R>* __restrict__ c, cx<R>* __restrict__ z) {
-  const int Nc = (Nf + 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
-  const GridPt q = grid_pt();
-  if (q.i >= Nf || q.j >= Nf) return;
-  const int i = q.i, j = q.j, pt = j * Nf + i;
-  const int I0 = i >> 1, J0 = j >> 1, I1 = (i + 1) >> 1, J1 = (j + 1) >> 1;   // equal when even
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const long long b = 2LL * q.b + k;
-    const cx<R>* cb = c + b * nnc;
-    const cx<R> v = cscale(cadd(cadd(cb[J0 * Nc + I0], cb[J0 * Nc + I1]), cadd(cb[J1 * Nc + I0], cb[J1 * Nc + I1])),
-                           (R)0.25);
-    z[b * nnf + pt] = cadd(z[b * nnf + pt], v);
-  }
-}
-
-// Neumann 3 x 3 grid: exact solve z = V2 diag(1/(mu + lambda)) V2^{-1} rhs, one thread per (system, node)
-template <typename R>
-__global__ void k_mg_coarse_neu(MgLevel L, int nsys, const cx<R>* __restrict__ tab, int kind,
-                                const cx<R>* __restrict__ rhs, cx<R>* __restrict__ z) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nsys * 9) return;
-  const int b = (int)(idx / 9), node = (int)(idx - (long long)b * 9);
+__device__ __forceinline__ cx<R> coarse_neu_pt(const MgLevel& L, cx<R> mu, const cx<R>* rb, int node) {
   const R* co = sizeof(R) == 4 ? (const R*)L.cof : (const R*)L.co;
-  const cx<R> mu = shift_of<R>(tab, b, kind);
-  const cx<R>* rb = rhs + (long long)b * 9;
   cx<R> acc = mk<R>(0, 0);
   for (int md = 0; md < 9; ++md) {
     cx<R> w = mk<R>(0, 0);
@@ -464,7 +389,211 @@ __global__ void k_mg_coarse_neu(MgLevel L, int nsys, const cx<R>* __restrict__ t
     w = cmul(w, mk<R>(den.x / dd, -den.y / dd));
     acc = cadd(acc, cscale(w, co[node * 9 + md]));
   }
-  z[(long long)b * 9 + node] = acc;
+  return acc;
+}
+
+// The two systems of a frequency slot (2r and 2r + 1) share the shift and hence the diagonal:
+// a thread treats one grid point of both (grid z runs over the slots).
+
+template <typename R, bool FIRST>
+__global__ void __launch_bounds__(256) k_mg_jacobi(MgLevel L, const cx<R>* __restrict__ tab, int kind,
+                                                   const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z,
+                                                   cx<R>* __restrict__ out, R w) {
+  const int N = L.N, nn = N * N;
+  const GridPt q = grid_pt();
+  if (q.i >= N || q.j >= N) return;
+  const int b = 2 * q.b, pt = q.j * N + q.i;
+  const cx<R> mu = shift_of<R>(tab, b, kind);
+  const cx<R> dinv = jacobi_dinv<R>(L, mu, pt);
+  const long long o0 = (long long)b * nn, o1 = o0 + nn;
+  if (FIRST) {
+    const cx<R> r0 = rhs[o0 + pt], r1 = rhs[o1 + pt];
+    out[o0 + pt] = cscale(cmul(r0, dinv), w);
+    out[o1 + pt] = cscale(cmul(r1, dinv), w);
+    return;
+  }
+  // jacobi_pt's arithmetic, with both systems' products formed before either update so that all
+  // loads are in flight together
+  const cx<R> Az0 = cadd(cmul(mu, z[o0 + pt]), tauKz<R>(L, z + o0, q.i, q.j));
+  const cx<R> Az1 = cadd(cmul(mu, z[o1 + pt]), tauKz<R>(L, z + o1, q.i, q.j));
+  const cx<R> n0 = cadd(z[o0 + pt], cscale(cmul(csub(rhs[o0 + pt], Az0), dinv), w));
+  const cx<R> n1 = cadd(z[o1 + pt], cscale(cmul(csub(rhs[o1 + pt], Az1), dinv), w));
+  out[o0 + pt] = n0;
+  out[o1 + pt] = n1;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_mg_resid(MgLevel L, const cx<R>* __restrict__ tab, int kind,
+                                                  const cx<R>* __restrict__ rhs, const cx<R>* __restrict__ z,
+                                                  cx<R>* __restrict__ res) {
+  const int N = L.N, nn = N * N;
+  const GridPt q = grid_pt();
+  if (q.i >= N || q.j >= N) return;
+  const int b = 2 * q.b, pt = q.j * N + q.i;
+  const cx<R> mu = shift_of<R>(tab, b, kind);
+  const long long o0 = (long long)b * nn, o1 = o0 + nn;
+  const cx<R> r0 = resid_pt<R>(L, mu, rhs + o0, z + o0, q.i, q.j);
+  const cx<R> r1 = resid_pt<R>(L, mu, rhs + o1, z + o1, q.i, q.j);
+  res[o0 + pt] = r0;
+  res[o1 + pt] = r1;
+}
+
+template <typename R, bool NEU>
+__global__ void __launch_bounds__(256) k_mg_restrict(int Nf, const cx<R>* __restrict__ f, cx<R>* __restrict__ c) {
+  const int Nc = NEU ? (Nf + 1) / 2 : (Nf - 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
+  const GridPt q = grid_pt();
+  if (q.i >= Nc || q.j >= Nc) return;
+  const cx<R> v0 = restrict_pt<R>(Nf, NEU, f + 2LL * q.b * nnf, q.i, q.j);
+  const cx<R> v1 = restrict_pt<R>(Nf, NEU, f + (2LL * q.b + 1) * nnf, q.i, q.j);
+  c[2LL * q.b * nnc + q.j * Nc + q.i] = v0;
+  c[(2LL * q.b + 1) * nnc + q.j * Nc + q.i] = v1;
+}
+
+// the prolonged coarse correction added to the fine solution
+template <typename R, bool NEU>
+__global__ void __launch_bounds__(256) k_mg_prolong_add(int Nf, const cx<R>* __restrict__ c, cx<R>* __restrict__ z) {
+  const int Nc = NEU ? (Nf + 1) / 2 : (Nf - 1) / 2, nnc = Nc * Nc, nnf = Nf * Nf;
+  const GridPt q = grid_pt();
+  if (q.i >= Nf || q.j >= Nf) return;
+  const long long o0 = 2LL * q.b * nnf + q.j * Nf + q.i, o1 = o0 + nnf;
+  const cx<R> v0 = prolong_pt<R>(Nc, NEU, c + 2LL * q.b * nnc, q.i, q.j);
+  const cx<R> v1 = prolong_pt<R>(Nc, NEU, c + (2LL * q.b + 1) * nnc, q.i, q.j);
+  const cx<R> z0 = z[o0], z1 = z[o1];
+  z[o0] = cadd(z0, v0);
+  z[o1] = cadd(z1, v1);
+}
+
+// Neumann 3 x 3 grid, one thread per (system, node)
+template <typename R>
+__global__ void k_mg_coarse_neu(MgLevel L, int nsys, const cx<R>* __restrict__ tab, int kind,
+                                const cx<R>* __restrict__ rhs, cx<R>* __restrict__ z) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nsys * 9) return;
+  const int b = (int)(idx / 9), node = (int)(idx - (long long)b * 9);
+  z[(long long)b * 9 + node] = coarse_neu_pt<R>(L, shift_of<R>(tab, b, kind), rhs + (long long)b * 9, node);
+}
+
+// ------------------------------------------------------------------------------------------
+// The coarse levels in one launch.  Below about 33 points per side a level's steps are too small
+// to fill the GPU, and each one-per-step launch costs several microseconds whatever its size.
+// One block takes both systems of a slot through the V-cycle from level l0 down to the coarsest
+// grid and back, with every level's right-hand side, solution and spare grid in shared memory,
+// the same per-point arithmetic as the fine levels, and a block barrier between steps.
+// ------------------------------------------------------------------------------------------
+struct MgTail {
+  MgLevel lev[kMaxLevels];
+  int l0, nlev;
+};
+
+template <typename R>
+size_t tail_smem(const MgTail& t) {
+  size_t e = 0;
+  for (int l = t.l0; l < t.nlev; ++l) e += 3 * 2 * (size_t)t.lev[l].N * t.lev[l].N;
+  return e * sizeof(cx<R>);
+}
+
+static constexpr size_t kTailSmemMax = 200 * 1024;
+static_assert(kNu % 2 == 0, "the fused coarse levels expect the pre-smoothing to end in z");
+
+// first level of the fused launch: the first below the finest with at most 33 points per side whose
+// levels fit the shared-memory budget in FP64; -1 if none
+static int tail_level(const MgHost& h) {
+  for (int l = 1; l < h.nlev; ++l) {
+    if (h.lev[l].N > 33) continue;
+    MgTail T;
+    for (int k = 0; k < h.nlev; ++k) T.lev[k] = h.lev[k];
+    T.l0 = l; T.nlev = h.nlev;
+    return tail_smem<double>(T) <= kTailSmemMax ? l : -1;
+  }
+  return -1;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_mg_vcycle_tail(MgTail T, const cx<R>* __restrict__ tab, int kind,
+                                                        const cx<R>* __restrict__ grhs, cx<R>* __restrict__ gz) {
+  using C = cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* base[kMaxLevels][3];                         // [level][rhs, z, spare], each 2 systems x N^2
+  {
+    C* p = (C*)smem_raw;
+    for (int l = T.l0; l < T.nlev; ++l) {
+      const int nn2 = 2 * T.lev[l].N * T.lev[l].N;
+      for (int a = 0; a < 3; ++a) { base[l][a] = p; p += nn2; }
+    }
+  }
+  const int slot = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const cx<R> mu = shift_of<R>(tab, 2 * slot, kind);
+  const R w = (R)kJacobiWeight;
+  {   // right-hand sides of level l0
+    const int nn = T.lev[T.l0].N * T.lev[T.l0].N;
+    const C* src = grhs + (long long)2 * slot * nn;
+    for (int e = tid; e < 2 * nn; e += nt) base[T.l0][0][e] = src[e];
+  }
+  __syncthreads();
+  // sweep over every (system, point) of level l
+  auto each = [&](int l, auto&& f) {
+    const int N = T.lev[l].N, nn = N * N;
+    for (int e = tid; e < 2 * nn; e += nt) {
+      const int k = e >= nn ? 1 : 0, pt = e - k * nn, j = pt / N, i = pt - j * N;
+      f(k, pt, i, j, nn);
+    }
+    __syncthreads();
+  };
+  // descent: nu1 sweeps (the first from zero, into `spare`, so that the last post-smoothing
+  // sweep lands in z), residual, restriction
+  for (int l = T.l0; l < T.nlev - 1; ++l) {
+    const MgLevel& L = T.lev[l];
+    C* rhs = base[l][0];
+    C* cur = base[l][2];
+    C* oth = base[l][1];
+    each(l, [&](int k, int pt, int i, int j, int nn) {
+      cur[k * nn + pt] = jacobi_pt<R>(L, mu, jacobi_dinv<R>(L, mu, pt), rhs + k * nn, nullptr, i, j, true, w);
+    });
+    for (int s = 1; s < kNu; ++s) {
+      each(l, [&](int k, int pt, int i, int j, int nn) {
+        oth[k * nn + pt] = jacobi_pt<R>(L, mu, jacobi_dinv<R>(L, mu, pt), rhs + k * nn, cur + k * nn, i, j, false, w);
+      });
+      C* t = cur; cur = oth; oth = t;
+    }
+    each(l, [&](int k, int pt, int i, int j, int nn) {
+      oth[k * nn + pt] = resid_pt<R>(L, mu, rhs + k * nn, cur + k * nn, i, j);
+    });
+    each(l + 1, [&](int k, int pt, int i, int j, int nn) {
+      base[l + 1][0][k * nn + pt] = restrict_pt<R>(L.N, L.neu != 0, oth + k * L.N * L.N, i, j);
+    });
+  }
+  {   // coarsest grid: exact solve
+    const int l = T.nlev - 1;
+    const MgLevel& L = T.lev[l];
+    C* rhs = base[l][0];
+    C* z = base[l][1];
+    each(l, [&](int k, int pt, int i, int j, int nn) {
+      z[k * nn + pt] = L.neu ? coarse_neu_pt<R>(L, mu, rhs + k * nn, pt)
+                             : jacobi_pt<R>(L, mu, jacobi_dinv<R>(L, mu, pt), rhs + k * nn, nullptr, i, j, true, (R)1);
+    });
+  }
+  // ascent: prolongation added into z, nu2 sweeps ending in z
+  for (int l = T.nlev - 2; l >= T.l0; --l) {
+    const MgLevel& L = T.lev[l];
+    const int Nc = T.lev[l + 1].N;
+    C* rhs = base[l][0];
+    C* cur = base[l][1];
+    C* oth = base[l][2];
+    each(l, [&](int k, int pt, int i, int j, int nn) {
+      cur[k * nn + pt] = cadd(cur[k * nn + pt], prolong_pt<R>(Nc, L.neu != 0, base[l + 1][1] + k * Nc * Nc, i, j));
+    });
+    for (int s = 0; s < kNu; ++s) {
+      each(l, [&](int k, int pt, int i, int j, int nn) {
+        oth[k * nn + pt] = jacobi_pt<R>(L, mu, jacobi_dinv<R>(L, mu, pt), rhs + k * nn, cur + k * nn, i, j, false, w);
+      });
+      C* t = cur; cur = oth; oth = t;
+    }
+  }
+  {   // solution of level l0
+    const int nn = T.lev[T.l0].N * T.lev[T.l0].N;
+    C* dst = gz + (long long)2 * slot * nn;
+    for (int e = tid; e < 2 * nn; e += nt) dst[e] = base[T.l0][1][e];
+  }
 }
 
 // a += b  or  a = b (copy)
@@ -630,12 +759,22 @@ template <typename R>
 static void vcycle(const MgHost& h, const cx<R>* tab, int kind, int l, const cx<R>* rhs, cx<R>* z, cx<R>* spare,
                    cudaStream_t st) {
   const MgLevel& L = h.lev[l];
+  if (l > 0 && l == h.tail_l0) {      // the coarse levels in one launch, one block per slot
+    MgTail T;
+    for (int k = 0; k < h.nlev; ++k) T.lev[k] = h.lev[k];
+    T.l0 = l; T.nlev = h.nlev;
+    static DeviceOnce once;
+    set_smem_limit(once, k_mg_vcycle_tail<R>, (int)kTailSmemMax);
+    k_mg_vcycle_tail<R><<<h.nsys / 2, 256, tail_smem<R>(T), st>>>(T, tab, kind, rhs, z);
+    g_mg_launches += 1;
+    return;
+  }
   const dim3 grids = grid_for(L.N, h.nsys / 2);     // one slot (two systems) per grid z
   const R w = (R)kJacobiWeight;
   if (l == h.nlev - 1) {
     if (L.neu) k_mg_coarse_neu<R><<<blocks_for((long long)h.nsys * 9), 256, 0, st>>>(L, h.nsys, tab, kind, rhs, z);
     else        // exact solve on the single-unknown grid: z = rhs / diag
-      k_mg_jacobi<R><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, nullptr, z, 1, (R)1);
+      k_mg_jacobi<R, true><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, nullptr, z, (R)1);
     g_mg_launches += 1;
     return;
   }
@@ -644,9 +783,9 @@ static void vcycle(const MgHost& h, const cx<R>* tab, int kind, int l, const cx<
   // starting in `spare` leaves the last post-smoothing sweep in z.
   cx<R>* cur = spare;
   cx<R>* oth = z;
-  k_mg_jacobi<R><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, nullptr, cur, 1, w);
+  k_mg_jacobi<R, true><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, nullptr, cur, w);
   for (int s = 1; s < kNu; ++s) {
-    k_mg_jacobi<R><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, cur, oth, 0, w);
+    k_mg_jacobi<R, false><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, cur, oth, w);
     std::swap(cur, oth);
   }
   // residual -> restrict to the coarse right-hand side
@@ -654,13 +793,13 @@ static void vcycle(const MgHost& h, const cx<R>* tab, int kind, int l, const cx<
   const MgLevel& C = h.lev[l + 1];
   const dim3 gridc = grid_for(C.N, h.nsys / 2);
   cx<R>* crhs = (cx<R>*)C.a[0];
-  if (L.neu) k_mg_restrict_neu<R><<<gridc, kMgBlock, 0, st>>>(L.N, oth, crhs);
-  else k_mg_restrict<R><<<gridc, kMgBlock, 0, st>>>(L.N, oth, crhs);
+  if (L.neu) k_mg_restrict<R, true><<<gridc, kMgBlock, 0, st>>>(L.N, oth, crhs);
+  else k_mg_restrict<R, false><<<gridc, kMgBlock, 0, st>>>(L.N, oth, crhs);
   vcycle<R>(h, tab, kind, l + 1, crhs, (cx<R>*)C.a[1], (cx<R>*)C.a[2], st);
-  if (L.neu) k_mg_prolong_add_neu<R><<<grids, kMgBlock, 0, st>>>(L.N, (const cx<R>*)C.a[1], cur);
-  else k_mg_prolong_add<R><<<grids, kMgBlock, 0, st>>>(L.N, (const cx<R>*)C.a[1], cur);
+  if (L.neu) k_mg_prolong_add<R, true><<<grids, kMgBlock, 0, st>>>(L.N, (const cx<R>*)C.a[1], cur);
+  else k_mg_prolong_add<R, false><<<grids, kMgBlock, 0, st>>>(L.N, (const cx<R>*)C.a[1], cur);
   for (int s = 0; s < kNu; ++s) {
-    k_mg_jacobi<R><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, cur, oth, 0, w);
+    k_mg_jacobi<R, false><<<grids, kMgBlock, 0, st>>>(L, tab, kind, rhs, cur, oth, w);
     std::swap(cur, oth);
   }
   g_mg_launches += 2 * kNu + 3;
