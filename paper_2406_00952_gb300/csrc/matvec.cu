@@ -118,13 +118,14 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
   if (g.theta == 1.0 && !g.var_a && epi_kind != EPI_PLAIN) {
     // Same product with the epilogue's scale folded into the operator's coefficients (the kernel
     // is bound by FP64 instruction issue): out = sg*o + kp*aux with
-    //   sg*(T x1 - alpha x2) = (sg x1_t - sg x1_{t-1}) + (sg c)(4 u - sum of neighbours) - (sg alpha) x2
-    //   sg*(alpha x1 + T^T x2) = (sg x2_t - sg x2_{t+1}) + (sg c)(4 u - sum of neighbours) + (sg alpha) x1
-    // (MINRES: sg = 1/beta, kp = -beta/oldb; residual: sg = -1, kp = 1).  Ten FP64 operations per
-    // output value instead of eleven.
+    //   sg*(T x1 - alpha x2)     = (sg + 4 sg c) x1_t - sg x1_{t-1} - (sg alpha) x2 - (sg c) (sum of neighbours of x1)
+    //   sg*(alpha x1 + T^T x2)   = (sg + 4 sg c) x2_t - sg x2_{t+1} + (sg alpha) x1 - (sg c) (sum of neighbours of x2)
+    // (MINRES: sg = 1/beta, kp = -beta/oldb; residual: sg = -1, kp = 1).  Nine FP64 operations per
+    // output value (one product, three neighbour additions, five FMAs with the epilogue and its
+    // inner product) instead of eleven.
     const double sg = epi_kind == EPI_MINRES ? e.s : -1.0;
     const double kp = epi_kind == EPI_MINRES ? e.c : 1.0;
-    const double sgc = sg * g.c, sga = sg * alpha;
+    const double sgc = sg * g.c, sga = sg * alpha, kd = fma(4.0, sgc, sg);
     const int cb = lb % ncb, tc = lb / ncb;
     const int col = cb * 256 + threadIdx.x;
     if (col < m) {
@@ -137,23 +138,24 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
       const bool zL = oL == 0, zR = oR == 0, zD = oD == 0, zU = oU == 0;
       const int t0 = tc * g.mv_tchunk;
       const int t1 = min(n, t0 + g.mv_tchunk);
-      double s1prev = t0 > 0 ? sg * x1[(long long)(t0 - 1) * m + col] : 0.0;
-      double s2c = sg * x2[(long long)t0 * m + col];
+      double x1p = t0 > 0 ? x1[(long long)(t0 - 1) * m + col] : 0.0;
+      double x2c = x2[(long long)t0 * m + col];
       for (int t = t0; t < t1; ++t) {
         const long long a = (long long)t * m + col;
         const double* u1 = x1 + (long long)t * m;
         const double* u2 = x2 + (long long)t * m;
-        const double x1c = u1[col], x2c = u2[col];
+        const double x1c = u1[col];
         const double x2n = t + 1 < n ? x2[a + m] : 0.0;
         const double nb1 = ((zL ? 0.0 : u1[col + oL]) + (zR ? 0.0 : u1[col + oR])) +
                            ((zD ? 0.0 : u1[col + oD]) + (zU ? 0.0 : u1[col + oU]));
         const double nb2 = ((zL ? 0.0 : u2[col + oL]) + (zR ? 0.0 : u2[col + oR])) +
                            ((zD ? 0.0 : u2[col + oD]) + (zU ? 0.0 : u2[col + oU]));
-        const double s1 = sg * x1c, s2n = sg * x2n;
-        double vT = fma(-sga, x2c, s1 - s1prev);
-        vT = fma(sgc, fma(4.0, x1c, -nb1), vT);
-        double vTT = fma(sga, x1c, s2c - s2n);
-        vTT = fma(sgc, fma(4.0, x2c, -nb2), vTT);
+        double vT = fma(-sg, x1p, kd * x1c);
+        vT = fma(-sga, x2c, vT);
+        vT = fma(-sgc, nb1, vT);
+        double vTT = fma(-sg, x2n, kd * x2c);
+        vTT = fma(sga, x1c, vTT);
+        vTT = fma(-sgc, nb2, vTT);
         if (kp != 0.0) {
           vT = fma(kp, aux[offT + a], vT);
           vTT = fma(kp, aux[offTT + a], vTT);
@@ -167,8 +169,8 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
         }
         out[offT + a] = vT;
         out[offTT + a] = vTT;
-        s1prev = s1;
-        s2c = s2n;
+        x1p = x1c;
+        x2c = x2n;
       }
     }
   } else if (g.theta == 1.0) {
