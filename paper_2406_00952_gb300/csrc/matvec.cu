@@ -14,6 +14,9 @@
 namespace pcb {
 
 enum { EPI_PLAIN = 0, EPI_RESID = 1, EPI_MINRES = 2 };
+// flag on the epilogue kind: the inner product of a mixed-precision MINRES iteration may use the
+// nine-operation arithmetic of the theta = 1 product (see k_matvec)
+constexpr int EPI_FAST = 8;
 
 // tau*K u at spatial point (i, j) of the time block `u`
 __device__ __forceinline__ double tauK(const Geom& g, const double* __restrict__ u, int i, int j, int col) {
@@ -96,6 +99,8 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
                                                 Scal* __restrict__ Sc, const int* __restrict__ off, int count,
                                                 const int* __restrict__ active, int op, int x_slot, int out_slot,
                                                 int aux_slot, int epi_kind, double* __restrict__ partial) {
+  const bool fast = (epi_kind & EPI_FAST) != 0;
+  epi_kind &= EPI_FAST - 1;
   const int inst = find_inst(off, count, blockIdx.x);
   if (active && !active[inst]) return;
   const Geom& g = G[inst];
@@ -118,11 +123,15 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
   if (g.theta == 1.0 && !g.var_a && epi_kind != EPI_PLAIN) {
     // Same product with the epilogue's scale folded into the operator's coefficients (the kernel
     // is bound by FP64 instruction issue): out = sg*o + kp*aux with
-    //   sg*(T x1 - alpha x2)     = (sg + 4 sg c) x1_t - sg x1_{t-1} - (sg alpha) x2 - (sg c) (sum of neighbours of x1)
-    //   sg*(alpha x1 + T^T x2)   = (sg + 4 sg c) x2_t - sg x2_{t+1} + (sg alpha) x1 - (sg c) (sum of neighbours of x2)
-    // (MINRES: sg = 1/beta, kp = -beta/oldb; residual: sg = -1, kp = 1).  Nine FP64 operations per
-    // output value (one product, three neighbour additions, five FMAs with the epilogue and its
-    // inner product) instead of eleven.
+    //   sg*(T x1 - alpha x2)   = (sg x1_t - sg x1_{t-1}) + (sg c)(4 u - sum of neighbours) - (sg alpha) x2
+    //   sg*(alpha x1 + T^T x2) = (sg x2_t - sg x2_{t+1}) + (sg c)(4 u - sum of neighbours) + (sg alpha) x1
+    // (MINRES: sg = 1/beta, kp = -beta/oldb; residual: sg = -1, kp = 1): ten FP64 operations per
+    // output value instead of eleven.  With EPI_FAST (the inner product of a mixed-precision
+    // MINRES iteration) the time-difference and Laplacian diagonal terms share one coefficient,
+    //   (sg + 4 sg c) u_t - sg u_{t-+1} -+ (sg alpha) x_other - (sg c)(sum of neighbours),
+    // nine operations; on smooth vectors its rounding is about three times that of the ten-operation
+    // form (the large diagonal term cancels against the neighbours last), which delays FP64 MINRES
+    // at the bench size by two iterations but is far below the FP32 preconditioner's perturbation.
     const double sg = epi_kind == EPI_MINRES ? e.s : -1.0;
     const double kp = epi_kind == EPI_MINRES ? e.c : 1.0;
     const double sgc = sg * g.c, sga = sg * alpha, kd = fma(4.0, sgc, sg);
@@ -140,6 +149,7 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
       const int t1 = min(n, t0 + g.mv_tchunk);
       double x1p = t0 > 0 ? x1[(long long)(t0 - 1) * m + col] : 0.0;
       double x2c = x2[(long long)t0 * m + col];
+      double s1p = sg * x1p, s2c = sg * x2c;     // scaled values carried by the ten-operation form
       for (int t = t0; t < t1; ++t) {
         const long long a = (long long)t * m + col;
         const double* u1 = x1 + (long long)t * m;
@@ -150,12 +160,23 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
                            ((zD ? 0.0 : u1[col + oD]) + (zU ? 0.0 : u1[col + oU]));
         const double nb2 = ((zL ? 0.0 : u2[col + oL]) + (zR ? 0.0 : u2[col + oR])) +
                            ((zD ? 0.0 : u2[col + oD]) + (zU ? 0.0 : u2[col + oU]));
-        double vT = fma(-sg, x1p, kd * x1c);
-        vT = fma(-sga, x2c, vT);
-        vT = fma(-sgc, nb1, vT);
-        double vTT = fma(-sg, x2n, kd * x2c);
-        vTT = fma(sga, x1c, vTT);
-        vTT = fma(-sgc, nb2, vTT);
+        double vT, vTT;
+        if (fast) {
+          vT = fma(-sg, x1p, kd * x1c);
+          vT = fma(-sga, x2c, vT);
+          vT = fma(-sgc, nb1, vT);
+          vTT = fma(-sg, x2n, kd * x2c);
+          vTT = fma(sga, x1c, vTT);
+          vTT = fma(-sgc, nb2, vTT);
+        } else {
+          const double s1 = sg * x1c, s2n = sg * x2n;
+          vT = fma(-sga, x2c, s1 - s1p);
+          vT = fma(sgc, fma(4.0, x1c, -nb1), vT);
+          vTT = fma(sga, x1c, s2c - s2n);
+          vTT = fma(sgc, fma(4.0, x2c, -nb2), vTT);
+          s1p = s1;
+          s2c = s2n;
+        }
         if (kp != 0.0) {
           vT = fma(kp, aux[offT + a], vT);
           vTT = fma(kp, aux[offTT + a], vTT);
@@ -264,8 +285,9 @@ cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int 
   if (B.fem_m > 0) {
     // finite elements: the product through the sine basis (FEM_PRODUCT = 2), then the epilogue
     cudaError_t e = launch_fem_spatial(B, 2, op, x_slot, out_slot);
-    if (e != cudaSuccess || epi == EPI_PLAIN) return e;
-    k_fem_epilogue<<<B.tot_mv, 256, 0, B.stream>>>(B.G, B.S, B.Sc, x_slot, out_slot, aux_slot, epi, B.partial);
+    if (e != cudaSuccess || (epi & (EPI_FAST - 1)) == EPI_PLAIN) return e;
+    k_fem_epilogue<<<B.tot_mv, 256, 0, B.stream>>>(B.G, B.S, B.Sc, x_slot, out_slot, aux_slot, epi & (EPI_FAST - 1),
+                                                   B.partial);
     return cudaGetLastError();
   }
   k_matvec<<<B.tot_mv, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_mv, B.count, B.active, op, x_slot, out_slot,

@@ -85,6 +85,7 @@ enum { SS_NONE = 0, SS_MINRES_INIT, SS_MINRES_ALFA, SS_MINRES_GIVENS, SS_NORM, S
        SS_BNORM };
 enum { AX_COPY = 0, AX_MINRES_R = 1, AX_SCALE_INV_BETA = 2, AX_SCALE_INV_HNORM = 3, AX_ADD = 4, AX_ZERO = 5 };
 enum { EPI_PLAIN = 0, EPI_RESID = 1, EPI_MINRES = 2 };
+constexpr int EPI_FAST = 8;     // the inner MINRES product of a mixed-precision solve (matvec.cu)
 enum { PK_ABS_PS = 1, PK_PS = 2, PK_PMS = 3 };
 
 // vector slots
@@ -744,7 +745,7 @@ static int read_scal(const Batch& B, Scal* host, int count) {
 // B.tols), so one launch sequence serves every iteration and can be replayed from a graph.
 static int minres_iter_launches(pcb_problem* p, const Batch& B, const SolveCfg& c, int s_x) {
   int rc;
-  CK(P_matvec(p, B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
+  CK(P_matvec(p, B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES | (c.prec == PCB_MIXED ? EPI_FAST : 0)));
   CK(LC(p) launch_reduce(B, B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
   CK(LC(p) launch_axpby(B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
   if ((rc = P_precond(p, B, c.kind, c.prec, SL_R1, SL_YO))) return rc;
@@ -1579,7 +1580,7 @@ int round_step(BGroup& G, const SolveCfg& c) {
   std::vector<int> ending(n, 0);
   bool any_end = false;
   if (G.method == PCB_MINRES) {
-    CK(launch_matvec(G.B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
+    CK(launch_matvec(G.B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES | (G.prec == PCB_MIXED ? EPI_FAST : 0)));
     CK(launch_reduce(G.B, G.B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
     CK(launch_axpby(G.B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
     if ((rc = apply_precond(p0, G.B, G.kind, G.prec, SL_R1, SL_YO))) return rc;
@@ -2019,7 +2020,7 @@ int srv_group_step(pcb_server* S, SrvGroup& G) {
     std::vector<int> ending(G.cap, 0);
     bool any_end = false;
     if (G.method == PCB_MINRES) {
-      CK(launch_matvec(G.B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES));
+      CK(launch_matvec(G.B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES | (prec == PCB_MIXED ? EPI_FAST : 0)));
       CK(launch_reduce(G.B, G.B.off_mv, 1, 0, SS_MINRES_ALFA, tol, 0, 0));
       CK(launch_axpby(G.B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
       if ((rc = precond(SL_R1, SL_YO))) return rc;
