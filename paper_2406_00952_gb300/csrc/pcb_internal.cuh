@@ -216,14 +216,18 @@ struct Sel {
 // hand-off), + 12 with flag 128 (DCT-I lines), + 24 with flag 256 (general-zeta time pass, never
 // with 64 or 128); at most kFamilies bits
 constexpr int kFamilies = 30;
+// (general zeta, flag 256, has P <= 16: indices 24 + log2 P, and 29 for P = 16 with the
+// time-major hand-off, the only P it serves)
 __host__ __device__ inline int fam_index(int code) {
   if (!code) return 0;
   int b = 0;
   while ((2 << b) <= (code & 63)) ++b;
-  return b + ((code & 64) ? 6 : 0) + ((code & 128) ? 12 : 0) + ((code & 256) ? 24 : 0);
+  if (code & 256) return (code & 64) ? 29 : 24 + b;
+  return b + ((code & 64) ? 6 : 0) + ((code & 128) ? 12 : 0);
 }
 __host__ __device__ inline int fam_code(int index) {
   if (index == 0) return 0;
+  if (index == 29) return 16 | 64 | 256;
   if (index >= 24) return (1 << (index - 24)) | 256;
   const int ev = index >= 12 ? 128 : 0;
   if (ev) index -= 12;

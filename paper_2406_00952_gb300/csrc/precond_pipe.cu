@@ -789,10 +789,15 @@ __global__ void __launch_bounds__(kThreads, 2)
 // psi_r = -(zeta + 2 pi r)/n).  The result is the real part of each inverse line (Re(P^-1) on
 // real vectors).  Tiles of LPB / 2 columns of buffer 0, in place; two blocks per SM.
 // ------------------------------------------------------------------------------------------
-template <int P>
+// MODE 1 (n = 512, after the time-major hand-off of pass 2): tiles of CPB spatial points
+// (r, p0 .. p0+CPB-1); each line (point, half) is contiguous in buffer 1 and comes in with 16-byte
+// copies; the result goes to buffer 0 in the row layout of pass 4 (value (t, r, p) at
+// t mp + r lr + p), as the zeta = pi kernel does.
+template <int P, int MODE = 0>
 __global__ void __launch_bounds__(kThreads, 2)
     k_time_gz(const Geom* __restrict__ G, const int* __restrict__ off, int count, Sel sel, int kind, int tot) {
   static_assert(P <= 16, "the two halves of a column share one warp");
+  static_assert(MODE == 0 || P == 16, "the time-major hand-off serves n = 512");
   constexpr int n = 32 * P, LPB = kThreads / P, CPB = LPB / 2;
   constexpr int PITCH = pitch_for<P>(n);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -806,12 +811,32 @@ __global__ void __launch_bounds__(kThreads, 2)
   fill_twiddles<P>(tw2, tw3, g0.twt_f);
   for (int k = tid; k < n; k += kThreads) pre[k] = __ldg(&g0.pre_f[k]);
 
-  // element e of a tile: column c0 + e % CPB, half / time (e / CPB) = h n + tt
+  // MODE 1: the tile's row r and first point p0
+  auto rowpt = [&](const Geom& g, int lt, int& r, int& p0) {
+    const int nbs = (g.N + CPB - 1) / CPB;
+    r = lt / nbs;
+    p0 = (lt - r * nbs) * CPB;
+  };
+  // MODE 0: element e of a tile: column c0 + e % CPB, half / time (e / CPB) = h n + tt
   auto issue = [&](int tile) {
     if (tile >= tot) return;
     const int inst = find_inst(off, count, tile);
     if (sel.skip(inst)) return;
     const Geom& g = G[inst];
+    if (MODE == 1) {
+      int r, p0;
+      rowpt(g, tile - off[inst], r, p0);
+      const long long hs = (long long)g.n * g.m;
+      constexpr int CH = n / 4;                // 16-byte pieces of a line
+      for (int e = tid; e < 2 * CPB * CH; e += kThreads) {
+        const int line = e / CH, c = e - line * CH, cl = line >> 1, h = line & 1;
+        if (p0 + cl >= g.N) continue;          // points past the row compute junk that is not stored
+        const float* y = (const float*)g.scratch + 2LL * g.n * g.mp + h * hs + ((long long)r * g.N + p0 + cl) * n;
+        const unsigned sa = (unsigned)__cvta_generic_to_shared((float*)(rows + line * PITCH) + 4 * c);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(y + 4 * c) : "memory");
+      }
+      return;
+    }
     const int c0 = (tile - off[inst]) * CPB;
     const long long m = g.mp, mn = (long long)g.n * g.mp;
     for (int e = tid; e < 2 * n * CPB; e += kThreads) {
@@ -843,8 +868,17 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int q = 0; q < 32; ++q) x[q] = cscale(pre[t + P * q], raw[t + P * q]);
       __syncwarp();                          // the row is free: it serves as exchange space
       fwd2<P>(x, t, ln, tw2);
-      const long long col = min((long long)(c0 + cl), g.mp - 1);      // padded columns compute junk
-      const int jj = (int)(col / g.lr), ii = min((int)(col - (long long)jj * g.lr), g.N - 1);
+      int jj, ii;
+      if (MODE == 1) {
+        int r, p0;
+        rowpt(g, tile - off[inst], r, p0);
+        jj = r;
+        ii = min(p0 + cl, g.N - 1);                                   // points past N compute junk
+      } else {
+        const long long col = min((long long)(c0 + cl), g.mp - 1);    // padded columns compute junk
+        jj = (int)(col / g.lr);
+        ii = min((int)(col - (long long)jj * g.lr), g.N - 1);
+      }
       const float c = (float)(g.tau * (__ldg(&g.kap[ii]) + __ldg(&g.kap[jj])));
       const float a2 = (float)(g.alpha * g.alpha), alpha = (float)g.alpha;
       const float2* __restrict__ mu = g.mu_f;
@@ -882,10 +916,17 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     if (on) {
       const long long m = g.mp, mn = (long long)g.n * g.mp;
+      int base = c0, lim = (int)min((long long)CPB, g.mp - c0);      // MODE 0: columns c0 ..
+      if (MODE == 1) {
+        int r, p0;
+        rowpt(g, tile - off[inst], r, p0);
+        base = r * g.lr + p0;                                         // MODE 1: row r, points p0 ..
+        lim = min(CPB, g.N - p0);
+      }
       for (int e = tid; e < 2 * n * CPB; e += kThreads) {
         const int el = e % CPB, rest = e / CPB, hh = rest / n, tt = rest - hh * n;
-        if (c0 + el < g.mp)
-          ((float*)g.scratch)[hh * mn + tt * m + c0 + el] = ((const float*)(rows + (2 * el + hh) * PITCH))[tt];
+        if (el < lim)
+          ((float*)g.scratch)[hh * mn + tt * m + base + el] = ((const float*)(rows + (2 * el + hh) * PITCH))[tt];
       }
     }
     __syncthreads();
@@ -1211,9 +1252,14 @@ cudaError_t launch_time(const Batch& B, int kind, bool time_major = false) {
 }
 
 template <int P>
-cudaError_t launch_time_gz(const Batch& B, int kind) {
-  static DeviceInt resident;
-  return launch_persistent(k_time_gz<P>, time_smem<P>(), B.tot_time[1], resident, B.stream, B.G, B.off_time[1],
+cudaError_t launch_time_gz(const Batch& B, int kind, bool time_major = false) {
+  static DeviceInt resident[2];
+  if constexpr (P == 16) {
+    if (time_major)
+      return launch_persistent(k_time_gz<16, 1>, time_smem<16>(), B.tot_time[1], resident[1], B.stream, B.G,
+                               B.off_time[1], B.count, B.sel(), kind, B.tot_time[1]);
+  }
+  return launch_persistent(k_time_gz<P>, time_smem<P>(), B.tot_time[1], resident[0], B.stream, B.G, B.off_time[1],
                            B.count, B.sel(), kind, B.tot_time[1]);
 }
 
@@ -1255,19 +1301,19 @@ int pipe_time_p(const Geom& g) {
   return (P >= 2 && P <= 32 && (P & (P - 1)) == 0) ? P : 0;
 }
 // family codes: P, plus 64 when pass 2 writes time-major lines for the n = 512 time pass, plus
-// 128 for the DCT-I lines of the Neumann route
-// (the time-major hand-off serves the zeta = pi kernel of n = 512 only; general-zeta time passes,
-// flag 256, take tiles of columns in place)
+// 128 for the DCT-I lines of the Neumann route, plus 256 for the general-zeta time pass.  The
+// time-major hand-off needs pipelined spatial and time passes at n = 512 (P = 16 in time).
+static bool time_major_handoff(const Geom& g) {
+  return g.n == 512 && !(g.tune & TUNE_NO_HANDOFF) && pipe_dst_p(g) && pipe_time_p(g) == 16;
+}
 int pipe_dst_code(const Geom& g) {
   const int p = pipe_dst_p(g);
-  const bool tm = g.n == 512 && g.zeta_pi && !(g.tune & TUNE_NO_HANDOFF);
-  return p ? (p | (tm ? 64 : 0) | (g.bc == PCB_BC_NEUMANN ? 128 : 0)) : 0;
+  return p ? (p | (time_major_handoff(g) ? 64 : 0) | (g.bc == PCB_BC_NEUMANN ? 128 : 0)) : 0;
 }
 int pipe_time_code(const Geom& g) {
   const int p = pipe_time_p(g);
   if (!p) return 0;
-  if (!g.zeta_pi) return p | 256;
-  return p | (pipe_dst_p(g) && g.n == 512 && !(g.tune & TUNE_NO_HANDOFF) ? 64 : 0);
+  return p | (g.zeta_pi ? 0 : 256) | (time_major_handoff(g) ? 64 : 0);
 }
 // spatial columns per tile of the pipelined time pass (n = 512: one line per warp; general zeta:
 // two lines, the halves, per column)
@@ -1308,7 +1354,7 @@ cudaError_t pipe_time_pass(const Batch& B, int kind) {
       case 2: return launch_time_gz<2>(B, kind);
       case 4: return launch_time_gz<4>(B, kind);
       case 8: return launch_time_gz<8>(B, kind);
-      case 16: return launch_time_gz<16>(B, kind);
+      case 16: return launch_time_gz<16>(B, kind, tm);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -1210,7 +1210,7 @@ std::vector<TuneChoice> tune_candidates(const Geom& g, int prec) {
   apply_choice(d, out.empty() ? TuneChoice{0, q0d, q0t} : out[0]);
   const bool mixed = prec == PCB_MIXED;
   const bool can_pipe_t = mixed && pipe_time_p(d), can_pipe_d = mixed && pipe_dst_p(d);
-  if (can_pipe_d && g.n == 512 && g.zeta_pi) add(TUNE_NO_HANDOFF, q0d, q0t);
+  if (can_pipe_d && can_pipe_t && g.n == 512) add(TUNE_NO_HANDOFF, q0d, q0t);
   if (can_pipe_t && g.n == 512 && g.zeta_pi) {
     for (int v : {TUNE_TIME512_3BLK, TUNE_TIME512_4BLK}) {
       add(v, q0d, q0t);

@@ -93,10 +93,11 @@ SELECT_CASES = [(255, 512, 1.0, 1e-2, "abs_ps", "mixed", math.pi, "dirichlet"),
                 (63, 512, 0.5, 1e-3, "ps", "mixed", math.pi, "dirichlet"),
                 (127, 64, 1.0, 1e-4, "pms", "mixed", math.pi, "dirichlet"),
                 (63, 32, 0.5, 1e-2, "ps", "fp64", math.pi, "dirichlet"),
+                (127, 512, 1.0, 1e-3, "ps", "mixed", math.pi / 2, "dirichlet"),
                 (129, 128, 0.5, 1e-2, "ps", "mixed", math.pi, "neumann")]
 
 
-@pytest.mark.parametrize("case", SELECT_CASES, ids=lambda c: "N%d-n%d-%s-%s-%s" % (c[0], c[1], c[4], c[5], c[7]))
+@pytest.mark.parametrize("case", SELECT_CASES, ids=lambda c: "N%d-n%d-%s-%s-z%.2f-%s" % (c[0], c[1], c[4], c[5], c[6], c[7]))
 def test_every_configuration_matches_oracle(P, case):
     N, n, theta, gamma, kind, prec, zeta, bc = case
     a = 1e-3 if bc == "neumann" else 1.0
@@ -112,7 +113,9 @@ def test_every_configuration_matches_oracle(P, case):
         seen.add((info["pipelined_dst"], info["pipelined_time"], info["time_major_handoff"], info["time512_blocks"]))
         out = gp.precond_apply(dev(v), kind=kind, precision=prec).cpu().numpy()
         assert_close(out, ref, TOL[prec], what=info)
-    if n == 512 and prec == "mixed":
+    if n == 512 and prec == "mixed" and zeta == math.pi:
         assert {b for *_, b in seen} == {2, 3, 4}, seen
+    if n == 512 and prec == "mixed":       # with and without the time-major hand-off
+        assert {h for _, _, h, _ in seen} == {0, 1}, seen
     with pytest.raises(Exception):
         gp.tune_select(count)
