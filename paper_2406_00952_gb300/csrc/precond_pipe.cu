@@ -680,12 +680,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   float2* tw2 = (float2*)smem_raw;
   float2* tw3 = tw2 + n;
   float2* pre = tw3 + n;
-  float2* stages = pre + n;
+  float2* mus = pre + n;                   // lambda(S_n) of the current instance
+  float2* stages = mus + n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   const Geom& g0 = G[table_inst(off, count, sel)];
   fill_twiddles<P>(tw2, tw3, g0.twt_f);
   for (int k = tid; k < n; k += kThreads) pre[k] = __ldg(&g0.pre_f[k]);
+  int mu_inst = -1;
 
   auto issue = [&](int tile, int st) {
     if (tile >= tot) return;
@@ -723,6 +725,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     const Geom& g = G[inst];
     const int c0 = (tile - off[inst]) * LPB;
     float2* buf = stages + (size_t)st * LPB * PITCH;
+    if (on && inst != mu_inst) {       // block-uniform
+      for (int k = tid; k < n; k += kThreads) mus[k] = __ldg(&g.mu_f[k]);
+      mu_inst = inst;
+      __syncthreads();
+    }
     if (on) {
       float2* ln = buf + lw * PITCH;
       float2 x[32];
@@ -735,7 +742,6 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int jj = (int)(col / g.lr), ii = min((int)(col - (long long)jj * g.lr), g.N - 1);
       const float c = (float)(g.tau * (__ldg(&g.kap[ii]) + __ldg(&g.kap[jj])));
       const float a2 = (float)(g.alpha * g.alpha), alpha = (float)g.alpha;
-      const float2* __restrict__ mu = g.mu_f;
       if (kind == PK_PS) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -746,14 +752,14 @@ __global__ void __launch_bounds__(kThreads, 2)
           ra.y = __shfl_xor_sync(0xffffffffu, vb.y, P - 1);
           rb.x = __shfl_xor_sync(0xffffffffu, va.x, P - 1);
           rb.y = __shfl_xor_sync(0xffffffffu, va.y, P - 1);
-          x[Two<P>::outreg(j)] = pointwise(PK_PS, va, cconj(ra), __ldg(&mu[t + P * j]), c, a2, alpha);
-          x[Two<P>::outreg(jb)] = pointwise(PK_PS, vb, cconj(rb), __ldg(&mu[t + P * jb]), c, a2, alpha);
+          x[Two<P>::outreg(j)] = pointwise(PK_PS, va, cconj(ra), mus[t + P * j], c, a2, alpha);
+          x[Two<P>::outreg(jb)] = pointwise(PK_PS, vb, cconj(rb), mus[t + P * jb], c, a2, alpha);
         }
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          x[Two<P>::outreg(j)] = pointwise(kind, x[Two<P>::outreg(j)], x[Two<P>::outreg(j)], __ldg(&mu[t + P * j]), c,
-                                           a2, alpha);
+          x[Two<P>::outreg(j)] = pointwise(kind, x[Two<P>::outreg(j)], x[Two<P>::outreg(j)], mus[t + P * j], c, a2,
+                                           alpha);
       }
       inv2<P>(x, t, ln, tw3);
 #pragma unroll
@@ -804,12 +810,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   float2* tw2 = (float2*)smem_raw;
   float2* tw3 = tw2 + n;
   float2* pre = tw3 + n;
-  float2* rows = pre + n;                  // row 2 l + h: column c0 + l, half h (n floats, then exchange)
+  float2* mus = pre + n;                   // lambda(S_n) of the current instance
+  float2* rows = mus + n;                  // row 2 l + h: column c0 + l, half h (n floats, then exchange)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   const Geom& g0 = G[table_inst(off, count, sel)];
   fill_twiddles<P>(tw2, tw3, g0.twt_f);
   for (int k = tid; k < n; k += kThreads) pre[k] = __ldg(&g0.pre_f[k]);
+  int mu_inst = -1;
 
   // MODE 1: the tile's row r and first point p0
   auto rowpt = [&](const Geom& g, int lt, int& r, int& p0) {
@@ -860,6 +868,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     const bool on = !sel.skip(inst);
     const Geom& g = G[inst];
     const int c0 = (tile - off[inst]) * CPB;
+    if (on && inst != mu_inst) {       // block-uniform
+      for (int k = tid; k < n; k += kThreads) mus[k] = __ldg(&g.mu_f[k]);
+      mu_inst = inst;
+      __syncthreads();
+    }
     if (on) {
       float2* ln = rows + lw * PITCH;
       float* raw = (float*)ln;
@@ -881,11 +894,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       const float c = (float)(g.tau * (__ldg(&g.kap[ii]) + __ldg(&g.kap[jj])));
       const float a2 = (float)(g.alpha * g.alpha), alpha = (float)g.alpha;
-      const float2* __restrict__ mu = g.mu_f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const float2 v = x[Two<P>::outreg(j)];
-        const float2 mr = __ldg(&mu[t + P * j]);
+        const float2 mr = mus[t + P * j];
         if (kind == PK_PS) {
           float2 o;                            // the other half's value at the same slot
           o.x = __shfl_xor_sync(0xffffffffu, v.x, P);
@@ -1176,8 +1188,8 @@ size_t dst_rowsT_smem() {
          (size_t)kThreads / P * 2 * row_slot_elems<TIn>(line_values<P, EV>()) * sizeof(TIn);
 }
 template <int P>
-size_t time_smem() {
-  return (size_t)(3 * 32 * P) * sizeof(float2) +
+size_t time_smem() {     // twiddles, D_omega weights, lambda(S_n), tile stages
+  return (size_t)(4 * 32 * P) * sizeof(float2) +
          (size_t)kNsTimePipe * (kThreads / P) * pitch_for<P>(32 * P) * sizeof(float2);
 }
 size_t time512_smem(int ns = kNsTime) { return (size_t)(3 * 512 + 32 + ns * kWarps * pitch_for<32>(512)) * sizeof(float2); }
