@@ -35,9 +35,22 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
                         against the assembled K, and the two-grid operator (and the two-level
                         V-cycle) against its 4 x 4 Fourier block analysis; the whole V-cycle also
                         converges to the exact shifted solve with a grid-independent contraction.
-                        That this reading is the paper's own multigrid remains unpinned (the paper
-                        prints no multigrid numbers beyond the iteration counts of Tables 3 and 4).
-  krylov.*              pinned: sparse direct solve; Table 1 iteration counts.
+                        Against the paper's own multigrid numbers: Table 3 (Example 2, variable
+                        a) is reproduced in iteration counts at h = 2^-5 for every gamma and for
+                        MINRES-P_MS at 2^-6 and 2^-7 (tests/test_oracle_example2.py); where counts
+                        differ the paper's one-sided Gauss-Seidel cycle and this symmetric
+                        Jacobi cycle are different operators (the paper leaves it unspecified).
+  krylov.*              pinned: sparse direct solve; Table 1 iteration counts.  The optional stall
+                        exit (solves asked below float64's attainable accuracy) is checked to
+                        leave reachable solves unchanged.
+  finite elements (Problem(fem=True): discretisation.mass_1d, stiffness_1d, apply_M*, the M^{+-1/2}
+  change of variables; spectra.mass_eigenvalues, kappa_fem)
+                        pinned: element-by-element assembly of the linear and bilinear element
+                        matrices, the sine eigenbasis with textbook eigenvalues, a sparse direct
+                        solve of the unsymmetrised element system, dense preconditioners, and
+                        Table 1's counts with elements (tests/test_oracle_fem.py).
+  reference_solutions.* writes the stored FP64 solution samples (tests/golden/solution_sample_*);
+                        a fresh solve of the smallest sampled instance reproduces its sample.
   Neumann route (Problem(bc="neumann"): discretisation.apply_K / K_sparse, spectra.kappa_neumann,
   spectra.dct1_*, precond.apply_ps_inv)
                         pinned: the 1D stencil written out by hand, its cosine eigenbasis,
