@@ -359,9 +359,17 @@ __global__ void k_copy_mapped(const double* __restrict__ src, double* __restrict
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long st = (long long)gridDim.x * blockDim.x;
   if (vec2) {
+    // four 16-byte loads in flight per thread before their stores: reads of page-locked host
+    // memory cross the CPU-GPU link with a long latency
     const double2* s2 = (const double2*)src;
     double2* d2 = (double2*)dst;
-    for (long long i = i0; i < n / 2; i += st) d2[i] = s2[i];
+    const long long n2 = n / 2;
+    long long i = i0;
+    for (; i + 3 * st < n2; i += 4 * st) {
+      const double2 a = s2[i], b = s2[i + st], c = s2[i + 2 * st], d = s2[i + 3 * st];
+      d2[i] = a; d2[i + st] = b; d2[i + 2 * st] = c; d2[i + 3 * st] = d;
+    }
+    for (; i < n2; i += st) d2[i] = s2[i];
     if (i0 == 0 && (n & 1)) dst[n - 1] = src[n - 1];
   } else {
     for (long long i = i0; i < n; i += st) dst[i] = src[i];

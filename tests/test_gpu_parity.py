@@ -501,11 +501,13 @@ def test_minres_graph_replay_matches_direct_launches(P, precision):
     assert igr["relres"] <= 1e-10
 
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_solve_host_buffers(P, pinned):
+@pytest.mark.parametrize("pinned,N,n", [(True, 31, 32), (False, 31, 32), (True, 255, 64)],
+                         ids=["pinned", "pageable", "pinned-large"])
+def test_solve_host_buffers(P, pinned, N, n):
     """Host-buffer solve: page-locked buffers move with the copy kernel, pageable ones with the
-    runtime copy; both give the device solve's result bit for bit."""
-    N, n, theta, gamma = 31, 32, 1.0, 1e-3
+    runtime copy; both give the device solve's result bit for bit (the large case, 8.3 M values,
+    runs the copy kernel's four-loads-per-thread loop as well as its tail)."""
+    theta, gamma = 1.0, 1e-3
     prob = ds.Problem(N, n, theta, gamma)
     g = synth.random_target(N, n, seed=31); f = synth.manufactured_source(N, n)
     b = ds.rhs_minres(prob, g, f)
