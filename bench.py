@@ -273,14 +273,20 @@ def cpu_solves_per_s(W, t_iter):
 
 
 def cpu_baseline(W):
+    """The oracle on all host cores, and beside it on one core (the same sample)."""
     workers = host_cores()
     dt, t_iter = oracle_sample(W, workers)
     val, n_its = cpu_solves_per_s(W, t_iter)
+    dt1, t_iter1 = oracle_sample(W, 1)
+    val1, _ = cpu_solves_per_s(W, t_iter1)
     return {"value": val, "unit": "solves/s", "cores": workers, "kind": "oracle",
             "sample": f"one oracle MINRES-|P_S| iteration's operator work (|P_S|^-1 apply + A x) at N=511 with "
                       f"{SAMPLE_STEPS} of the 512 time steps, {dt:.1f} s measured on {workers} host threads; scaled "
                       f"x{W['n'] // SAMPLE_STEPS} to {t_iter:.1f} s per full-size iteration, x the oracle's own "
-                      f"full-size iteration counts {n_its} (gamma {list(W['gammas'])})"}
+                      f"full-size iteration counts {n_its} (gamma {list(W['gammas'])})",
+            "single_core": {"value": val1, "unit": "solves/s", "cores": 1,
+                            "sample": f"the same sample on one thread: {dt1:.1f} s, {t_iter1:.1f} s per full-size "
+                                      f"iteration"}}
 
 
 def reference_arm(a, W, rank, world):
