@@ -602,7 +602,7 @@ def main():
         bs.append(pr.assemble_rhs(g, f))
     gf = (g, f)
     del g, f
-    # autotuned kernel shapes (north star (2)): the first problem times the candidate configurations
+    # autotuned kernel shapes: the first problem times the candidate configurations
     # of its preconditioner apply and keeps the fastest; the second, of the same shape, inherits it
     tune = None if a.no_autotune else probs[0].autotune(reps=3)
     if tune is not None:
