@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // sit in the adjacent lane groups 2l and 2l + 1 of a warp (P <= 16), which meet through one
 // shuffle per slot for the 2x2 solve of P_S (slot r of both lines has the same frequency
 // psi_r = -(zeta + 2 pi r)/n).  The result is the real part of each inverse line (Re(P^-1) on
-// real vectors).  Tiles of LPB / 2 columns of buffer 0, in place; two blocks per SM.
+// real vectors).  MODE 0: tiles of LPB / 2 columns of buffer 0, in place; two blocks per SM.
 // ------------------------------------------------------------------------------------------
 // MODE 1 (n = 512, after the time-major hand-off of pass 2): tiles of CPB spatial points
 // (r, p0 .. p0+CPB-1); each line (point, half) is contiguous in buffer 1 and comes in with 16-byte
