@@ -1452,11 +1452,46 @@ struct BGroup {
   int j = 0;                          // Arnoldi index (lockstep)
   int it_round = 0;
   bool round_open = false;
+  // Lockstep iterations replayed from CUDA graphs: the group's launches take their instances,
+  // slot pointers, masks and tolerances from device memory, so one capture serves every round
+  // (MINRES) or every round at one Arnoldi index (FGMRES).  The first iteration runs directly.
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t git = nullptr;
+  std::vector<cudaGraphExec_t> garn;
+  int direct = 0;                     // iterations launched directly so far
   ~BGroup() {
+    if (git) cudaGraphExecDestroy(git);
+    for (cudaGraphExec_t e : garn) if (e) cudaGraphExecDestroy(e);
+    if (cap) cudaStreamDestroy(cap);
     cudaFree(dG); cudaFree(dS); cudaFree(dSc); cudaFree(dAct); cudaFree(dOff); cudaFree(dPart); cudaFree(dTol);
     cudaFreeHost(hSc); cudaFreeHost(hAct); cudaFreeHost(hTol);
   }
 };
+
+// capture the launches issue(Bc) makes into an executable graph, on the group's private stream
+// (the group's own may be the legacy default stream); null when capture is not possible
+template <typename F>
+static cudaGraphExec_t capture_group(BGroup& G, F&& issue) {
+  if (!G.cap && cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError(); G.cap = nullptr; return nullptr;
+  }
+  Batch Bc = G.B;
+  Bc.stream = G.cap;
+  if (cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  const int rc = issue(Bc);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(G.cap, &graph);
+  if (rc != PCB_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return exec;
+}
 
 int set_active(BGroup& G, const std::vector<int>& mask) {
   const int n = (int)G.probs.size();
@@ -1580,14 +1615,25 @@ int round_step(BGroup& G, const SolveCfg& c) {
   std::vector<int> ending(n, 0);
   bool any_end = false;
   if (G.method == PCB_MINRES) {
-    CK(launch_matvec(G.B, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES | (G.prec == PCB_MIXED ? EPI_FAST : 0)));
-    CK(launch_reduce(G.B, G.B.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
-    CK(launch_axpby(G.B, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
-    if ((rc = apply_precond(p0, G.B, G.kind, G.prec, SL_R1, SL_YO))) return rc;
-    CK(launch_dot(G.B, SL_R1, SL_YO));
-    CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_MINRES_GIVENS, c.tol, 0, 0));
-    CK(launch_minres_wx(G.B, SL_Y, SL_W, SL_W2, SL_XI));
-    CK(launch_swap(G.B, SL_R1, SL_R2, SL_Y, SL_YO, SL_W, SL_W2));
+    auto iter = [&](const Batch& Bx) -> int {
+      CK(launch_matvec(Bx, PCB_OP_A, SL_Y, SL_Q, SL_R1, EPI_MINRES | (G.prec == PCB_MIXED ? EPI_FAST : 0)));
+      CK(launch_reduce(Bx, Bx.off_mv, 1, 0, SS_MINRES_ALFA, c.tol, 0, 0));
+      CK(launch_axpby(Bx, AX_MINRES_R, SL_Q, SL_R2, SL_R1));
+      int r;
+      if ((r = apply_precond(p0, Bx, G.kind, G.prec, SL_R1, SL_YO))) return r;
+      CK(launch_dot(Bx, SL_R1, SL_YO));
+      CK(launch_reduce(Bx, Bx.off_vec, 1, 0, SS_MINRES_GIVENS, c.tol, 0, 0));
+      CK(launch_minres_wx(Bx, SL_Y, SL_W, SL_W2, SL_XI));
+      CK(launch_swap(Bx, SL_R1, SL_R2, SL_Y, SL_YO, SL_W, SL_W2));
+      return PCB_OK;
+    };
+    if (c.graphs && G.direct > 0 && !G.git) G.git = capture_group(G, iter);
+    if (c.graphs && G.git) {
+      CK(cudaGraphLaunch(G.git, G.B.stream));
+    } else {
+      if ((rc = iter(G.B))) return rc;
+      ++G.direct;
+    }
     if ((rc = read_all(G))) return rc;
     G.it_round += 1;
     for (int k = 0; k < n; ++k) {
@@ -1601,19 +1647,31 @@ int round_step(BGroup& G, const SolveCfg& c) {
     }
   } else {
     const int j = G.j;
-    CK(launch_setslot(G.B, SL_VJ, SL_VBASE, j));
-    CK(launch_setslot(G.B, SL_ZJ, SL_ZBASE, j));
-    CK(launch_setslot(G.B, SL_VJ1, SL_VBASE, j + 1));
-    if ((rc = apply_precond(p0, G.B, G.kind, G.prec, SL_VJ, SL_ZJ))) return rc;
-    CK(launch_matvec(G.B, G.op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
-    for (int pass = 0; pass < 2; ++pass) {
-      CK(launch_multidot(G.B, SL_VBASE, j, SL_VJ1));
-      CK(launch_reduce_multi(G.B, j, pass));
-      CK(launch_multiaxpy(G.B, SL_VBASE, j, SL_VJ1, pass));
+    auto step = [&](const Batch& Bx) -> int {
+      CK(launch_setslot(Bx, SL_VJ, SL_VBASE, j));
+      CK(launch_setslot(Bx, SL_ZJ, SL_ZBASE, j));
+      CK(launch_setslot(Bx, SL_VJ1, SL_VBASE, j + 1));
+      int r;
+      if ((r = apply_precond(p0, Bx, G.kind, G.prec, SL_VJ, SL_ZJ))) return r;
+      CK(launch_matvec(Bx, G.op, SL_ZJ, SL_VJ1, -1, EPI_PLAIN));
+      for (int pass = 0; pass < 2; ++pass) {
+        CK(launch_multidot(Bx, SL_VBASE, j, SL_VJ1));
+        CK(launch_reduce_multi(Bx, j, pass));
+        CK(launch_multiaxpy(Bx, SL_VBASE, j, SL_VJ1, pass));
+      }
+      CK(launch_dot(Bx, SL_VJ1, SL_VJ1));
+      CK(launch_reduce(Bx, Bx.off_vec, 1, 0, SS_GMRES_ARNOLDI, c.tol, j, c.restart));
+      CK(launch_axpby(Bx, AX_SCALE_INV_HNORM, SL_VJ1, SL_VJ1, -1));
+      return PCB_OK;
+    };
+    if ((int)G.garn.size() < c.restart) G.garn.resize(c.restart, nullptr);
+    if (c.graphs && G.direct > 0 && !G.garn[j]) G.garn[j] = capture_group(G, step);
+    if (c.graphs && G.garn[j]) {
+      CK(cudaGraphLaunch(G.garn[j], G.B.stream));
+    } else {
+      if ((rc = step(G.B))) return rc;
+      ++G.direct;
     }
-    CK(launch_dot(G.B, SL_VJ1, SL_VJ1));
-    CK(launch_reduce(G.B, G.B.off_vec, 1, 0, SS_GMRES_ARNOLDI, c.tol, j, c.restart));
-    CK(launch_axpby(G.B, AX_SCALE_INV_HNORM, SL_VJ1, SL_VJ1, -1));
     if ((rc = read_all(G))) return rc;
     G.it_round += 1;
     for (int k = 0; k < n; ++k) {

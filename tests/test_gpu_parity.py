@@ -484,6 +484,23 @@ def test_batch_solve_uneven(P, precision, shapes):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_graph_replay_matches_direct_launches(P, precision):
+    """Batched lockstep iterations replayed from CUDA graphs (one per MINRES group, one per
+    Arnoldi index for GMRES groups) give the directly launched results bit for bit, with the same
+    iteration counts, over several refinement rounds and instances that finish at different
+    rounds."""
+    insts = _batch_instances()
+    probs = [P.Problem(pr.N, pr.n, pr.theta, pr.gamma, precision=precision) for pr, _ in insts]
+    bs = [dev(b) for _, b in insts]
+    xd, idir = P.batch_solve(probs, bs, tol=1e-10, restart=8, graphs=False)
+    xg, igr = P.batch_solve(probs, bs, tol=1e-10, restart=8, graphs=True)
+    for a, b, ia, ib in zip(xd, xg, idir, igr):
+        assert ia["iterations"] == ib["iterations"] and ia["refinements"] == ib["refinements"]
+        assert torch.equal(a, b)
+    assert len({i["iterations"] for i in igr}) > 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_minres_graph_replay_matches_direct_launches(P, precision):
     """MINRES iterations replayed from the captured CUDA graph give the same iterates, bit for
     bit, as launching each kernel directly, with the same iteration and launch counts; the
