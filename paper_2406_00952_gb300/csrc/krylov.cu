@@ -339,22 +339,27 @@ cudaError_t launch_minres_wx(const Batch& B, int sy, int sw, int sw2, int sx) {
   k_minres_wx<<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, sy, sw, sw2, sx);
   return cudaGetLastError();
 }
-// basis-loop bound for Arnoldi index j (j < 0: per-instance indices, at most jmax when jmax >= 0)
+// basis-loop bound for Arnoldi index j (j < 0: per-instance indices, at most jmax when jmax >= 0).
+// The loops are unrolled to the bound and predicated beyond j + 1; the kernels are bound by FP64
+// issue, so a predicated-off step still costs its slot: the bound is exact up to 12 basis vectors
+// and a multiple of 4 above (the first restart cycles of a solve stay in the exact range).
 static int basis_bound(int j, int jmax) {
   if (j < 0) j = jmax;
   const int need = j < 0 ? PCB_MAX_RESTART + 1 : j + 1;
-  return need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : PCB_MAX_RESTART + 1;
+  if (need <= 12) return need < 1 ? 1 : need;
+  return need <= 16 ? 16 : need <= 20 ? 20 : need <= 24 ? 24 : need <= 28 ? 28 : PCB_MAX_RESTART + 1;
 }
+#define PCB_BASIS_BOUNDS(X) \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(16) X(20) X(24) X(28)
 cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw, int jmax) {
 #define PCB_MULTIDOT(JB) \
   k_multidot<JB><<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, B.partial)
+#define PCB_MULTIDOT_CASE(JB) case JB: PCB_MULTIDOT(JB); break;
   switch (basis_bound(j, jmax)) {
-    case 2: PCB_MULTIDOT(2); break;
-    case 4: PCB_MULTIDOT(4); break;
-    case 8: PCB_MULTIDOT(8); break;
-    case 16: PCB_MULTIDOT(16); break;
+    PCB_BASIS_BOUNDS(PCB_MULTIDOT_CASE)
     default: PCB_MULTIDOT(PCB_MAX_RESTART + 1); break;
   }
+#undef PCB_MULTIDOT_CASE
 #undef PCB_MULTIDOT
   return cudaGetLastError();
 }
@@ -365,13 +370,12 @@ cudaError_t launch_reduce_multi(const Batch& B, int j, int pass) {
 cudaError_t launch_multiaxpy(const Batch& B, int svbase, int j, int sw, int pass, int jmax) {
 #define PCB_MULTIAXPY(JB) \
   k_multiaxpy<JB><<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, pass)
+#define PCB_MULTIAXPY_CASE(JB) case JB: PCB_MULTIAXPY(JB); break;
   switch (basis_bound(j, jmax)) {
-    case 2: PCB_MULTIAXPY(2); break;
-    case 4: PCB_MULTIAXPY(4); break;
-    case 8: PCB_MULTIAXPY(8); break;
-    case 16: PCB_MULTIAXPY(16); break;
+    PCB_BASIS_BOUNDS(PCB_MULTIAXPY_CASE)
     default: PCB_MULTIAXPY(PCB_MAX_RESTART + 1); break;
   }
+#undef PCB_MULTIAXPY_CASE
 #undef PCB_MULTIAXPY
   return cudaGetLastError();
 }
