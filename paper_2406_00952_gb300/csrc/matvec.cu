@@ -93,9 +93,29 @@ __device__ __forceinline__ Epi make_epi(int kind, const Scal* sc) {
   return e;
 }
 
-// grid: instance blocks; theta == 1: blocks = ceil(m/256) * ceil(n/tchunk) (fused),
-// else blocks = 2 * ceil(m/256) (forward-marching T role, backward-marching T^T role).
-__global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, const Slots* __restrict__ S,
+// Blocks of kMvThreads threads, one spatial column per thread.  theta == 1: blocks =
+// ceil(m/kMvThreads) * ceil(n/tchunk) (fused); else blocks = 2 * ceil(m/kMvThreads) (forward-marching
+// T role, backward-marching T^T role), each thread marching over all n time steps.  The marching
+// form has only 2m threads, so the block is small enough that they all fit on the device at once:
+// with 256-thread blocks a problem of m = 66,049 columns needed a second wave of 62 blocks, which
+// took as long as the first.
+constexpr int kMvThreads = 128;
+
+void matvec_shape(Geom& g) {
+  const int ncb = (g.m + kMvThreads - 1) / kMvThreads;
+  if (g.theta == 1.0) {
+    // time chunks: enough blocks of 256 threads' worth of columns to fill the device 16 times over
+    const long long ncb256 = (g.m + 255) / 256;
+    const int tch = (int)std::min<long long>(32, std::max<long long>(1, (ncb256 * g.n) / 2432));
+    g.mv_tchunk = tch;
+    g.mv_blocks = ncb * ((g.n + tch - 1) / tch);
+  } else {
+    g.mv_tchunk = g.n;
+    g.mv_blocks = 2 * ncb;
+  }
+}
+
+__global__ void __launch_bounds__(kMvThreads) k_matvec(const Geom* __restrict__ G, const Slots* __restrict__ S,
                                                 Scal* __restrict__ Sc, const int* __restrict__ off, int count,
                                                 const int* __restrict__ active, int op, int x_slot, int out_slot,
                                                 int aux_slot, int epi_kind, double* __restrict__ partial) {
@@ -116,7 +136,7 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
   // output half of the T x1 - alpha x2 rows and of the alpha x1 + T^T x2 rows
   const long long offT = (op == PCB_OP_A) ? mn : 0;
   const long long offTT = (op == PCB_OP_A) ? 0 : mn;
-  const int ncb = (m + 255) / 256;
+  const int ncb = (m + kMvThreads - 1) / kMvThreads;
   const double alpha = g.alpha;
   double part = 0.0;
 
@@ -136,7 +156,7 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
     const double kp = epi_kind == EPI_MINRES ? e.c : 1.0;
     const double sgc = sg * g.c, sga = sg * alpha, kd = fma(4.0, sgc, sg);
     const int cb = lb % ncb, tc = lb / ncb;
-    const int col = cb * 256 + threadIdx.x;
+    const int col = cb * kMvThreads + threadIdx.x;
     if (col < m) {
       const int j = col / N, i = col - j * N;
       // neighbour offsets; at a Neumann boundary the missing one is the mirrored neighbour, at a
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
     }
   } else if (g.theta == 1.0) {
     const int cb = lb % ncb, tc = lb / ncb;
-    const int col = cb * 256 + threadIdx.x;
+    const int col = cb * kMvThreads + threadIdx.x;
     if (col < m) {
       const int j = col / N, i = col - j * N;
       const int t0 = tc * g.mv_tchunk;
@@ -222,13 +242,14 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
     }
   } else {
     const int role = lb / ncb, cb = lb - role * ncb;
-    const int col = cb * 256 + threadIdx.x;
+    const int col = cb * kMvThreads + threadIdx.x;
     if (col < m) {
       const int j = col / N, i = col - j * N;
       const double th = g.theta, om = 1.0 - th, ith = 1.0 / th;
       if (role == 0) {
         // forward: z_t = (x1_t - (1-theta) z_{t-1})/theta, (B_n x1)_t = z_t - z_{t-1}
         double zprev = 0.0;
+#pragma unroll 2
         for (int t = 0; t < n; ++t) {
           const long long a = (long long)t * m + col;
           const double* u1 = x1 + (long long)t * m;
@@ -241,6 +262,7 @@ __global__ void __launch_bounds__(256) k_matvec(const Geom* __restrict__ G, cons
       } else {
         // backward: u_t = (x2_t - (1-theta) u_{t+1})/theta, (B_n^T x2)_t = u_t - u_{t+1}
         double unext = 0.0;
+#pragma unroll 2
         for (int t = n - 1; t >= 0; --t) {
           const long long a = (long long)t * m + col;
           const double* u2 = x2 + (long long)t * m;
@@ -290,7 +312,7 @@ cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int 
                                                    B.partial);
     return cudaGetLastError();
   }
-  k_matvec<<<B.tot_mv, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_mv, B.count, B.active, op, x_slot, out_slot,
+  k_matvec<<<B.tot_mv, kMvThreads, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_mv, B.count, B.active, op, x_slot, out_slot,
                                            aux_slot, epi, B.partial);
   return cudaGetLastError();
 }

@@ -63,6 +63,7 @@ cudaError_t launch_multiaxpy(const Batch& B, int svbase, int j, int sw, int pass
 cudaError_t launch_swap(const Batch& B, int a0, int b0, int a1, int b1, int a2, int b2);
 cudaError_t launch_setslot(const Batch& B, int dst, int base, int k, int per_j = 0);
 size_t mg_workspace_bytes(const Geom& g);
+void matvec_shape(Geom& g);
 bool mg_available();
 int dst_Q(int N);
 int time_Q(int n);
@@ -209,15 +210,7 @@ void set_shapes(Geom& g) {
     g.time_blocks[p] = (int)(((p == 1 && pt ? g.mp : (long long)g.m) + cpb - 1) / cpb);
     if (p == 1 && (pipe_time_code(g) & 64)) g.time_blocks[p] = g.N * ((g.N + cpb - 1) / cpb);   // rows of points
   }
-  const int ncb = (g.m + 255) / 256;
-  if (g.theta == 1.0) {
-    int tch = (int)std::min<long long>(32, std::max<long long>(1, ((long long)ncb * g.n) / 2432));
-    g.mv_tchunk = tch;
-    g.mv_blocks = ncb * ((g.n + tch - 1) / tch);
-  } else {
-    g.mv_tchunk = g.n;
-    g.mv_blocks = 2 * ncb;
-  }
+  matvec_shape(g);
   g.vec_blocks = vec_blocks_for(2 * g.mn);
 }
 
