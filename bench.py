@@ -66,6 +66,7 @@ def args():
     ap.add_argument("--prof-autotune", action="store_true", help="autotune the apply first (as the bench does)")
     ap.add_argument("--no-autotune", action="store_true", help="bench: keep the default kernel configuration")
     ap.add_argument("--prof-reps", type=int, default=3)
+    ap.add_argument("--prof-theta", type=float, default=1.0, help="theta of the profiled problem (not --prof-neumann)")
     ap.add_argument("--prof-zeta", type=float, default=math.pi)
     ap.add_argument("--prof-neumann", action="store_true", help="Example 3's Neumann grid (DCT-I passes, kind ps)")
     return ap.parse_args()
@@ -105,9 +106,9 @@ def profile_apply(a):
         gp = P.Problem(N, n, 0.5, 1e-2, precision=a.prof_prec, bc="neumann", a=1e-3)
     elif a.prof_var_a:
         import synth
-        gp = P.Problem(N, n, 1.0, 1e-2, a_edges=synth.variable_coefficient_edges(N), precision=a.prof_prec)
+        gp = P.Problem(N, n, a.prof_theta, 1e-2, a_edges=synth.variable_coefficient_edges(N), precision=a.prof_prec)
     else:
-        gp = P.Problem(N, n, 1.0, 1e-2, zeta=a.prof_zeta, precision=a.prof_prec, fem=a.prof_fem)
+        gp = P.Problem(N, n, a.prof_theta, 1e-2, zeta=a.prof_zeta, precision=a.prof_prec, fem=a.prof_fem)
     if a.prof_autotune:
         print("autotune", gp.autotune(kind=None if a.prof_kind in ("solve", "matvec") else a.prof_kind))
     g = torch.Generator(device="cuda").manual_seed(0)
@@ -115,7 +116,7 @@ def profile_apply(a):
     y = torch.empty_like(x)
     torch.cuda.synchronize()
     with Nvtx(torch, "measured"):  # the launches below, without set-up and tuning
-        if a.prof_kind == "solve":     # MINRES iterations (the Krylov vector kernels with the rest)
+        if a.prof_kind == "solve":     # Krylov iterations (MINRES for theta = 1, else (F)GMRES), no graphs
             gp.solve(x, y, fixed_iterations=a.prof_reps, graphs=False)
         for _ in range(a.prof_reps if a.prof_kind != "solve" else 0):
             if a.prof_kind == "matvec":

@@ -341,16 +341,17 @@ cudaError_t launch_minres_wx(const Batch& B, int sy, int sw, int sw2, int sx) {
 }
 // basis-loop bound for Arnoldi index j (j < 0: per-instance indices, at most jmax when jmax >= 0).
 // The loops are unrolled to the bound and predicated beyond j + 1; the kernels are bound by FP64
-// issue, so a predicated-off step still costs its slot: the bound is exact up to 12 basis vectors
-// and a multiple of 4 above (the first restart cycles of a solve stay in the exact range).
+// issue, so a predicated-off step still costs its slot: the bound is exact up to 20 basis vectors
+// and a multiple of 4 above (most solves stay in the exact range).
 static int basis_bound(int j, int jmax) {
   if (j < 0) j = jmax;
   const int need = j < 0 ? PCB_MAX_RESTART + 1 : j + 1;
-  if (need <= 12) return need < 1 ? 1 : need;
-  return need <= 16 ? 16 : need <= 20 ? 20 : need <= 24 ? 24 : need <= 28 ? 28 : PCB_MAX_RESTART + 1;
+  if (need <= 20) return need < 1 ? 1 : need;
+  return need <= 24 ? 24 : need <= 28 ? 28 : PCB_MAX_RESTART + 1;
 }
-#define PCB_BASIS_BOUNDS(X) \
-  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(16) X(20) X(24) X(28)
+#define PCB_BASIS_BOUNDS(X)                                                                           \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) \
+  X(19) X(20) X(24) X(28)
 cudaError_t launch_multidot(const Batch& B, int svbase, int j, int sw, int jmax) {
 #define PCB_MULTIDOT(JB) \
   k_multidot<JB><<<B.tot_vec, 256, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_vec, B.count, B.active, svbase, j, sw, B.partial)
