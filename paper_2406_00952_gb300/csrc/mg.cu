@@ -821,7 +821,7 @@ static cudaError_t mg_apply(const Batch& B, const Geom& g, const MgHost& h, int 
   T* r0 = (T*)F.a[0];
   T* z0 = (T*)h.zfine;
   T* x0 = (T*)h.xfine;
-  const int P = g.n / Q, lpw = 32 / P, cpw = 1;
+  const int P = g.n / Q, lpw = 32 / P, cpw = 2;   // two lines per warp: 16-column tiles, 128-byte runs of FP64
   const int cols = 8 * lpw * cpw;
   const size_t smem = (size_t)cols * padded_len_mg(g.n) * sizeof(T);
   static DeviceOnce once;
