@@ -139,6 +139,27 @@ int pcb_assemble_rhs(pcb_problem* p, int op, const double* g_dev, const double* 
 /* y = A x or y = A_hat x (op = pcb_operator); x_dev and y_dev must not overlap. */
 int pcb_matvec(pcb_problem* p, int op, const double* x_dev, double* y_dev);
 
+/* One Lanczos step of preconditioned MINRES (Paige and Saunders; the Krylov solver of Sec. 3/4
+ * for the symmetric system of Eq. matrix_A): with A the all-at-once operator,
+ *     out  = A y / beta - (beta / oldb) r1      (the r1 term is left out when oldb == 0)
+ *     *dot = y . out / beta                      (host, FP64)
+ * which is the product a MINRES iteration of pcb_solve computes before its scalar step.
+ * precision PCB_FP64: FP64 arithmetic (the form of FP64 solves and of true residuals);
+ * PCB_MIXED: the two-word FP32 arithmetic of the inner iterations of a mixed-precision solve
+ * (inputs split into two FP32 words, 48 of their 53 significand bits; each value accurate to
+ * about 2^-47 of the magnitudes of its terms), used for theta = 1 and a constant coefficient;
+ * other instances compute in FP64 either way.  y_dev, r1_dev, out_dev: device, 2*m*n each,
+ * out_dev distinct from both inputs; r1_dev may be NULL when oldb == 0.  beta > 0 and oldb >= 0,
+ * both finite, else INVALID_ARG.  The two-word path splits y relative to the binade of beta and r1
+ * relative to that of oldb, so the scale of the right-hand side does not matter; the output and
+ * its terms must lie in the FP32 range (as they do in a MINRES iteration, where they do not
+ * depend on that scale); a value beyond it comes out non-finite, which the solver reports.
+ * Overwrites the problem's MINRES scalars (a later pcb_solve resets them); blocks until *dot is
+ * read.  Finite-element problems compute in FP64 whatever
+ * the precision. */
+int pcb_lanczos_product(pcb_problem* p, int precision, const double* y_dev, const double* r1_dev, double beta,
+                        double oldb, double* out_dev, double* dot);
+
 /* y = P^{-1} x for kind = pcb_precond, computed in `precision` (pcb_precision).
  * x_dev and y_dev may be the same buffer.  Uses the problem's scratch workspace, so calls on
  * one problem are serialised by its stream.  UNSUPPORTED: |P_S| with variable a(x); |P_S| and

@@ -91,6 +91,17 @@ class Problem:
         check("pcb_matvec", self.lib.pcb_matvec(self.h, OPS[op], _ptr(x, self.size), _ptr(out, self.size)))
         return out
 
+    def lanczos_product(self, y, beta, r1=None, oldb=0.0, out=None, precision=None):
+        """One Lanczos step of MINRES (C-ABI pcb_lanczos_product): out = A y/beta - (beta/oldb) r1 and
+        y . out / beta, in FP64 or in the two-word FP32 arithmetic of mixed-precision inner iterations."""
+        out = self._empty() if out is None else out
+        dot = ctypes.c_double()
+        r1p = _ptr(r1, self.size) if r1 is not None else None
+        check("pcb_lanczos_product", self.lib.pcb_lanczos_product(
+            self.h, PRECISIONS[precision or self.precision], _ptr(y, self.size), r1p, float(beta), float(oldb),
+            _ptr(out, self.size), ctypes.byref(dot)))
+        return out, dot.value
+
     def precond_apply(self, x, out=None, kind="abs_ps", precision=None):
         out = self._empty() if out is None else out
         prec = PRECISIONS[precision or self.precision]

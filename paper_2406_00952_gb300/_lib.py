@@ -90,6 +90,7 @@ def load() -> ctypes.CDLL:
         "pcb_assemble_rhs": (c_int, [P, c_int, P, P, P, P]),
         "pcb_matvec": (c_int, [P, c_int, P, P]),
         "pcb_precond_apply": (c_int, [P, c_int, c_int, P, P]),
+        "pcb_lanczos_product": (c_int, [P, c_int, P, P, c_double, c_double, P, POINTER(c_double)]),
         "pcb_recover": (c_int, [P, P, P, P]),
         "pcb_solve": (c_int, [P, POINTER(PcbSolveOpts), P, P, POINTER(PcbSolveInfo)]),
         "pcb_solve_host": (c_int, [P, POINTER(PcbSolveOpts), P, P, POINTER(PcbSolveInfo)]),

@@ -14,8 +14,8 @@
 namespace pcb {
 
 enum { EPI_PLAIN = 0, EPI_RESID = 1, EPI_MINRES = 2 };
-// flag on the epilogue kind: the inner product of a mixed-precision MINRES iteration may use the
-// nine-operation arithmetic of the theta = 1 product (see k_matvec)
+// flag on the epilogue kind: the product of an inner MINRES iteration of a mixed-precision solve,
+// in two-word FP32 arithmetic where the instance allows it (k_matvec_tw)
 constexpr int EPI_FAST = 8;
 
 // tau*K u at spatial point (i, j) of the time block `u`
@@ -100,6 +100,8 @@ __device__ __forceinline__ Epi make_epi(int kind, const Scal* sc) {
 // with 256-thread blocks a problem of m = 66,049 columns needed a second wave of 62 blocks, which
 // took as long as the first.
 constexpr int kMvThreads = 128;
+__host__ __device__ int tw_patches(int N);
+static_assert(32 * 4 == kMvThreads, "two-word product: one thread per point of a 32 x 4 patch");
 
 void matvec_shape(Geom& g) {
   const int ncb = (g.m + kMvThreads - 1) / kMvThreads;
@@ -108,27 +110,20 @@ void matvec_shape(Geom& g) {
     const long long ncb256 = (g.m + 255) / 256;
     const int tch = (int)std::min<long long>(32, std::max<long long>(1, (ncb256 * g.n) / 2432));
     g.mv_tchunk = tch;
-    g.mv_blocks = ncb * ((g.n + tch - 1) / tch);
+    // the two-word product (constant coefficient) tiles the grid in patches of its own
+    const int units = g.var_a ? ncb : std::max(ncb, tw_patches(g.N));
+    g.mv_blocks = units * ((g.n + tch - 1) / tch);
   } else {
     g.mv_tchunk = g.n;
     g.mv_blocks = 2 * ncb;
   }
 }
 
-__global__ void __launch_bounds__(kMvThreads) k_matvec(const Geom* __restrict__ G, const Slots* __restrict__ S,
-                                                Scal* __restrict__ Sc, const int* __restrict__ off, int count,
-                                                const int* __restrict__ active, int op, int x_slot, int out_slot,
-                                                int aux_slot, int epi_kind, double* __restrict__ partial) {
-  const bool fast = (epi_kind & EPI_FAST) != 0;
-  epi_kind &= EPI_FAST - 1;
-  const int inst = find_inst(off, count, blockIdx.x);
-  if (active && !active[inst]) return;
-  const Geom& g = G[inst];
-  const int lb = blockIdx.x - off[inst];
-  const double* __restrict__ x = S[inst].v[x_slot];
-  double* __restrict__ out = S[inst].v[out_slot];
-  const double* __restrict__ aux = aux_slot >= 0 ? S[inst].v[aux_slot] : nullptr;
-  const Epi e = make_epi(epi_kind, Sc + inst);
+// The FP64 product of block lb of one instance with its epilogue; returns the block's epilogue
+// partial (for MINRES already scaled by 1/beta, as the scalar step expects).
+__device__ __forceinline__ double matvec_block(const Geom& g, int lb, int op, const double* __restrict__ x,
+                                               double* __restrict__ out, const double* __restrict__ aux,
+                                               const Epi& e, int epi_kind) {
   const int N = g.N, m = g.m, n = g.n;
   const long long mn = g.mn;
   const double* __restrict__ x1 = x;
@@ -146,18 +141,15 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const Geom* __restrict__ 
     //   sg*(T x1 - alpha x2)   = (sg x1_t - sg x1_{t-1}) + (sg c)(4 u - sum of neighbours) - (sg alpha) x2
     //   sg*(alpha x1 + T^T x2) = (sg x2_t - sg x2_{t+1}) + (sg c)(4 u - sum of neighbours) + (sg alpha) x1
     // (MINRES: sg = 1/beta, kp = -beta/oldb; residual: sg = -1, kp = 1): ten FP64 operations per
-    // output value instead of eleven.  With EPI_FAST (the inner product of a mixed-precision
-    // MINRES iteration) the time-difference and Laplacian diagonal terms share one coefficient,
-    //   (sg + 4 sg c) u_t - sg u_{t-+1} -+ (sg alpha) x_other - (sg c)(sum of neighbours),
-    // nine operations; on smooth vectors its rounding is about three times that of the ten-operation
-    // form (the large diagonal term cancels against the neighbours last), which delays FP64 MINRES
-    // at the bench size by two iterations but is far below the FP32 preconditioner's perturbation.
+    // output value instead of eleven.  The inner iterations of a mixed-precision solve use the
+    // two-word FP32 form of this product instead (k_matvec_tw).
     const double sg = epi_kind == EPI_MINRES ? e.s : -1.0;
     const double kp = epi_kind == EPI_MINRES ? e.c : 1.0;
-    const double sgc = sg * g.c, sga = sg * alpha, kd = fma(4.0, sgc, sg);
+    const double sgc = sg * g.c, sga = sg * alpha;
     const int cb = lb % ncb, tc = lb / ncb;
     const int col = cb * kMvThreads + threadIdx.x;
-    if (col < m) {
+    // an instance may have more blocks than this layout uses (the two-word layout's count)
+    if (col < m && tc * g.mv_tchunk < n) {
       const int j = col / N, i = col - j * N;
       // neighbour offsets; at a Neumann boundary the missing one is the mirrored neighbour, at a
       // Dirichlet boundary it is masked to zero below
@@ -180,23 +172,13 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const Geom* __restrict__ 
                            ((zD ? 0.0 : u1[col + oD]) + (zU ? 0.0 : u1[col + oU]));
         const double nb2 = ((zL ? 0.0 : u2[col + oL]) + (zR ? 0.0 : u2[col + oR])) +
                            ((zD ? 0.0 : u2[col + oD]) + (zU ? 0.0 : u2[col + oU]));
-        double vT, vTT;
-        if (fast) {
-          vT = fma(-sg, x1p, kd * x1c);
-          vT = fma(-sga, x2c, vT);
-          vT = fma(-sgc, nb1, vT);
-          vTT = fma(-sg, x2n, kd * x2c);
-          vTT = fma(sga, x1c, vTT);
-          vTT = fma(-sgc, nb2, vTT);
-        } else {
-          const double s1 = sg * x1c, s2n = sg * x2n;
-          vT = fma(-sga, x2c, s1 - s1p);
-          vT = fma(sgc, fma(4.0, x1c, -nb1), vT);
-          vTT = fma(sga, x1c, s2c - s2n);
-          vTT = fma(sgc, fma(4.0, x2c, -nb2), vTT);
-          s1p = s1;
-          s2c = s2n;
-        }
+        const double s1 = sg * x1c, s2n = sg * x2n;
+        double vT = fma(-sga, x2c, s1 - s1p);
+        vT = fma(sgc, fma(4.0, x1c, -nb1), vT);
+        double vTT = fma(sga, x1c, s2c - s2n);
+        vTT = fma(sgc, fma(4.0, x2c, -nb2), vTT);
+        s1p = s1;
+        s2c = s2n;
         if (kp != 0.0) {
           vT = fma(kp, aux[offT + a], vT);
           vTT = fma(kp, aux[offTT + a], vTT);
@@ -217,7 +199,7 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const Geom* __restrict__ 
   } else if (g.theta == 1.0) {
     const int cb = lb % ncb, tc = lb / ncb;
     const int col = cb * kMvThreads + threadIdx.x;
-    if (col < m) {
+    if (col < m && tc * g.mv_tchunk < n) {
       const int j = col / N, i = col - j * N;
       const int t0 = tc * g.mv_tchunk;
       const int t1 = min(n, t0 + g.mv_tchunk);
@@ -275,10 +257,326 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const Geom* __restrict__ 
       }
     }
   }
-  if (partial && epi_kind != EPI_PLAIN) {
-    if (epi_kind == EPI_MINRES) part *= e.s;
-    block_reduce_store(part, partial + blockIdx.x);
+  if (epi_kind == EPI_MINRES) part *= e.s;
+  return part;
+}
+
+__global__ void __launch_bounds__(kMvThreads) k_matvec(const Geom* __restrict__ G, const Slots* __restrict__ S,
+                                                Scal* __restrict__ Sc, const int* __restrict__ off, int count,
+                                                const int* __restrict__ active, int op, int x_slot, int out_slot,
+                                                int aux_slot, int epi_kind, double* __restrict__ partial) {
+  const int inst = find_inst(off, count, blockIdx.x);
+  if (active && !active[inst]) return;
+  const Geom& g = G[inst];
+  const double* __restrict__ aux = aux_slot >= 0 ? S[inst].v[aux_slot] : nullptr;
+  const double part = matvec_block(g, blockIdx.x - off[inst], op, S[inst].v[x_slot], S[inst].v[out_slot], aux,
+                                   make_epi(epi_kind, Sc + inst), epi_kind);
+  if (partial && epi_kind != EPI_PLAIN) block_reduce_store(part, partial + blockIdx.x);
+}
+
+// ------------------------------------------------------------------------------------------
+// Two-word FP32 product for the inner iterations of a mixed-precision MINRES solve (theta = 1,
+// constant coefficient, Lanczos epilogue):
+//     out = A y / beta - (beta/oldb) r1,   partial = y . out / beta   (A: Eq. matrix_A)
+// On this GPU FP64 instructions issue at 1/64 of the FP32 rate, and the FP64 form above is
+// bound by them (ten per output value).  Here every FP64 input is split, with integer
+// operations, into two FP32 words that hold the leading 24 and the next 24 bits of its
+// significand (48 of its 53 bits), and the product is evaluated in two-word arithmetic built
+// from error-free transformations: Knuth's two-sum, Dekker's fast two-sum and the FMA-based
+// exact product (Dekker 1971; Knuth, TAOCP vol. 2, 4.2.2), on packed pairs of FP32 lanes that
+// carry the two output rows of a point (T x1 - alpha x2 and alpha x1 + T^T x2) side by side.
+// Each result is accurate to about 2^-47 of the magnitudes of its terms (the FP64 form: 2^-53),
+// which the iteration does not notice next to the FP32 preconditioner's rounding.  Results are
+// widened to FP64 with integer operations and one FP64 add per value.
+//
+// Scaling: y is split as y 2^-ky and r1 as r1 2^-ka, with 2^ky and 2^ka the binades of beta and
+// oldb, so the words stay far inside the FP32 range whatever the scale of the right-hand side
+// (the coefficients absorb 2^ky and 2^ka exactly).  A scaled value below 2^-103 becomes 0 (an
+// absolute error far below the rest); one beyond the FP32 range becomes NaN, which the
+// iteration's non-finite check reports.
+//
+// Layout: a block of 128 threads owns a patch of 32 x 4 spatial points (x1 fastest) and a chunk
+// of time levels.  For each level t the split words of x1(t) and x2(t) on the patch and its
+// one-point halo (Dirichlet: zero outside the grid; Neumann: the mirrored neighbour) sit in a
+// shared-memory tile of (x1 hi, x2 hi, x1 lo, x2 lo); three tiles rotate (t, t+1 being read,
+// t+2 being filled from loads issued one step ahead).
+// ------------------------------------------------------------------------------------------
+namespace tw {
+
+constexpr int kI = 32, kJ = 4;                  // patch: x1 by x2 points (kI * kJ = kMvThreads)
+constexpr int kW = kI + 2, kH = kJ + 2;         // with the halo
+constexpr int kSlots = kW * kH;
+constexpr int kHalo = 2 * kI + 2 * kJ;          // halo points (corners unused)
+
+using f2 = float2;
+__device__ __forceinline__ f2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 sub(f2 a, f2 b) { return __ffma2_rn(make_float2(-1.f, -1.f), b, a); }
+__device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 swp(f2 a) { return make_float2(a.y, a.x); }
+
+// s + e = a + b exactly (two-sum)
+__device__ __forceinline__ void two_sum(f2 a, f2 b, f2& s, f2& e) {
+  s = add(a, b);
+  const f2 bb = sub(s, a);
+  e = add(sub(a, sub(s, bb)), sub(b, bb));
+}
+// s + e = a - b exactly
+__device__ __forceinline__ void two_diff(f2 a, f2 b, f2& s, f2& e) {
+  s = sub(a, b);
+  const f2 bb = sub(s, a);
+  e = sub(sub(a, sub(s, bb)), add(b, bb));
+}
+// s + e = a + b exactly when |a| >= |b| (fast two-sum); renormalises a word pair
+__device__ __forceinline__ void renorm(f2& a, f2& b) {
+  const f2 s = add(a, b);
+  b = sub(b, sub(s, a));
+  a = s;
+}
+// (ph, pl) ~ k * (xh + xl) for a two-word coefficient (kh, kl) with nkh = -kh: the leading
+// product is exact in ph - nerr (nerr = ph - kh*xh exactly, by one FMA), the cross terms are
+// rounded once each.
+__device__ __forceinline__ void prod(f2 kh, f2 kl, f2 nkh, f2 xh, f2 xl, f2& ph, f2& pl) {
+  ph = mul(kh, xh);
+  const f2 nerr = fma2(nkh, xh, ph);
+  pl = sub(fma2(kh, xl, mul(kl, xh)), nerr);
+}
+// (h, l) += (ph, pl), unnormalised
+__device__ __forceinline__ void acc(f2& h, f2& l, f2 ph, f2 pl) {
+  f2 s, e;
+  two_sum(h, ph, s, e);
+  h = s;
+  l = add(l, add(e, pl));
+}
+
+// x 2^-k split into two FP32 words (b20 = (896 + k) << 20, the FP64 exponent bias of the scaled
+// value): hi = the leading 24 bits of the significand, lo = the next 24 (both truncated), so
+// |x 2^-k - hi - lo| < 2^-47 |x 2^-k|.  The second word is the difference of two FP32 numbers of
+// the same binade (exact).  Scaled values below 2^-103 and FP64 subnormals become 0.
+__device__ __forceinline__ void split(double x, int b20, float& hi, float& lo) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned sgn = hw & 0x80000000u;
+  const int u = (int)(hw & 0x7fffffffu) - b20;             // FP32 exponent field at bit 20
+  const unsigned hb = (__funnelshift_l(lw, (unsigned)u, 3) & 0x7fffffffu) | sgn;
+  const unsigned s3 = ((unsigned)u << 3) - (23u << 23);     // unit of the second word
+  const unsigned one = (s3 & 0x7f800000u) | sgn;
+  const float l = __fsub_rn(__uint_as_float(one | ((lw >> 6) & 0x007fffffu)), __uint_as_float(one));
+  // a normal FP64 value whose scaled exponent lies in [-103, 127] (zeros and FP64 subnormals give 0)
+  const bool ok = (hw & 0x7ff00000u) != 0u && (unsigned)(u - (24 << 20)) < (231u << 20);
+  hi = ok ? __uint_as_float(hb) : (u >= (255 << 20) ? __uint_as_float(0x7fc00000u) : 0.f);
+  lo = ok ? l : 0.f;
+}
+// exact FP64 value of an FP32 word (subnormal words give 0; infinities and NaN are kept)
+__device__ __forceinline__ double widen(float f) {
+  const unsigned b = __float_as_uint(f), a = b & 0x7fffffffu;
+  unsigned hw = (b & 0x80000000u) | ((a >> 3) + (896u << 20));
+  if (a >= 0x7f800000u) hw |= 0x7ff00000u;
+  const bool z = a < 0x00800000u;
+  return __hiloint2double((int)(z ? (b & 0x80000000u) : hw), (int)(z ? 0u : (b << 29)));
+}
+// a second word (never infinite or NaN when its leading word is finite)
+__device__ __forceinline__ double widen_lo(float f) {
+  const unsigned b = __float_as_uint(f), a = b & 0x7fffffffu;
+  const bool z = a < 0x00800000u;
+  const unsigned hw = (b & 0x80000000u) | ((a >> 3) + (896u << 20));
+  return __hiloint2double((int)(z ? 0u : hw), (int)(z ? 0u : (b << 29)));
+}
+// binade exponent of a positive normal double (0 otherwise)
+__device__ __forceinline__ int binade(double v) {
+  const int e = (int)(((unsigned)__double2hiint(v) >> 20) & 0x7ffu);
+  return (v > 0.0 && e > 0 && e < 2047) ? e - 1023 : 0;
+}
+__device__ __forceinline__ double pow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
+__device__ __forceinline__ void split_rn(double v, float& h, float& l) {
+  h = __double2float_rn(v);
+  l = __double2float_rn(v - (double)h);
+}
+
+// grid column of tile point (gi, gj) in [-1, N] x [-1, N], or -1 for a zero
+__device__ __forceinline__ int tile_src(int gi, int gj, int N, bool neu) {
+  if (neu) {
+    const bool oi = gi < 0 || gi >= N, oj = gj < 0 || gj >= N;
+    if (oi && oj) return -1;
+    if (gi == -1) gi = 1; else if (gi == N) gi = N - 2;
+    if (gj == -1) gj = 1; else if (gj == N) gj = N - 2;
   }
+  if (gi < 0 || gi >= N || gj < 0 || gj >= N) return -1;
+  return gj * N + gi;
+}
+
+}  // namespace tw
+
+__host__ __device__ int tw_patches(int N) { return ((N + tw::kI - 1) / tw::kI) * ((N + tw::kJ - 1) / tw::kJ); }
+
+// Block lb of one instance (theta = 1, constant coefficient) of the two-word product with the
+// MINRES epilogue e; returns the block's partial of y . out / beta.
+__device__ __forceinline__ double matvec_tw_block(const Geom& g, int lb, int op, const double* __restrict__ x,
+                                                  double* __restrict__ out, const double* __restrict__ aux,
+                                                  const Epi& e, const Scal& sc, float4 (*tile)[tw::kSlots]) {
+  using namespace tw;
+  const int N = g.N, m = g.m, n = g.n;
+  const long long mn = g.mn;
+  const int npi = (N + kI - 1) / kI, npatch = tw_patches(N);
+  const int p = lb % npatch, tc = lb / npatch;
+  const int t0 = tc * g.mv_tchunk;
+  if (t0 >= n) return 0.0;          // the FP64 layout of this instance may use more blocks
+  const int t1 = min(n, t0 + g.mv_tchunk);
+  const int i0 = (p % npi) * kI, j0 = (p / npi) * kJ;
+  const int ti = threadIdx.x % kI, tj = threadIdx.x / kI;
+  const int i = i0 + ti, j = j0 + tj;
+  const bool own = i < N && j < N;
+  const bool neu = g.bc == PCB_BC_NEUMANN;
+  const int os = (tj + 1) * kW + ti + 1;           // this thread's point in the tile
+  const int osrc = tile_src(i, j, N, neu);
+  const int col = own ? osrc : 0;
+  int hs = -1, hsrc = -1;                          // one halo point per thread below kHalo
+  if (threadIdx.x < kHalo) {
+    const int h = threadIdx.x;
+    int r, q;
+    if (h < kI) { r = 0; q = h + 1; }
+    else if (h < 2 * kI) { r = kJ + 1; q = h - kI + 1; }
+    else if (h < 2 * kI + kJ) { r = h - 2 * kI + 1; q = 0; }
+    else { r = h - 2 * kI - kJ + 1; q = kI + 1; }
+    hs = r * kW + q;
+    hsrc = tile_src(i0 + q - 1, j0 + r - 1, N, neu);
+  }
+  // scalings (powers of two) and two-word coefficients
+  const int ky = binade(sc.beta);
+  const bool use_aux = e.c != 0.0;
+  const int ka = use_aux ? binade(sc.oldb) : 0;
+  const double sgd = e.s * pow2(ky), kpd = e.c * pow2(ka);
+  const int by = (896 + ky) * (1 << 20), ba = (896 + ka) * (1 << 20);
+  float w0, w1;
+  split_rn(sgd, w0, w1);
+  const f2 SGh = pk(w0, w0), SGl = pk(w1, w1), nSG = pk(-w0, -w0);
+  split_rn(g.c, w0, w1);
+  const f2 Ch = pk(w0, w0), Cl = pk(w1, w1), nC = pk(-w0, -w0);
+  split_rn(g.alpha, w0, w1);
+  const f2 ALh = pk(-w0, w0), ALl = pk(-w1, w1), nAL = pk(w0, -w0);   // -alpha x2 | +alpha x1
+  split_rn(kpd, w0, w1);
+  const f2 KPh = pk(w0, w0), KPl = pk(w1, w1), nKP = pk(-w0, -w0);
+  const long long offT = (op == PCB_OP_A) ? mn : 0;
+  const long long offTT = (op == PCB_OP_A) ? 0 : mn;
+
+  // raw loads of tile tt (own point and halo point, both halves) and their split into the tile
+  auto fetch = [&](int tt, double& a1, double& a2, double& h1, double& h2) {
+    const long long base = (long long)tt * m;
+    const bool in = tt < n;
+    a1 = (in && osrc >= 0) ? x[base + osrc] : 0.0;
+    a2 = (in && osrc >= 0) ? x[mn + base + osrc] : 0.0;
+    h1 = (in && hsrc >= 0) ? x[base + hsrc] : 0.0;
+    h2 = (in && hsrc >= 0) ? x[mn + base + hsrc] : 0.0;
+  };
+  auto store = [&](int b, double a1, double a2, double h1, double h2) {
+    float4 v;
+    split(a1, by, v.x, v.z);
+    split(a2, by, v.y, v.w);
+    tile[b][os] = v;
+    if (hs >= 0) {
+      split(h1, by, v.x, v.z);
+      split(h2, by, v.y, v.w);
+      tile[b][hs] = v;
+    }
+  };
+  {
+    double a1, a2, h1, h2;
+    fetch(t0, a1, a2, h1, h2);
+    store(0, a1, a2, h1, h2);
+    fetch(t0 + 1, a1, a2, h1, h2);
+    store(1, a1, a2, h1, h2);
+  }
+  float x1ph = 0.f, x1pl = 0.f;                    // x1(t-1) at this point
+  if (own && t0 > 0) split(x[(long long)(t0 - 1) * m + col], by, x1ph, x1pl);
+  double ra = 0.0, rb = 0.0;                       // r1 at (t, point), both halves
+  if (own && use_aux) { ra = aux[offT + (long long)t0 * m + col]; rb = aux[offTT + (long long)t0 * m + col]; }
+  f2 dh = pk(0.f, 0.f), dl = pk(0.f, 0.f);         // y . out (scaled), two words per lane
+  __syncthreads();
+  int b0 = 0, b1 = 1, b2 = 2;                      // tiles of levels t, t+1, t+2
+  for (int t = t0; t < t1; ++t) {
+    const bool pre = t + 2 <= t1;                  // level t+2 is read by step t+1
+    double n1 = 0.0, n2 = 0.0, nh1 = 0.0, nh2 = 0.0, nra = 0.0, nrb = 0.0;
+    if (pre) fetch(t + 2, n1, n2, nh1, nh2);
+    if (own && use_aux && t + 1 < t1) {
+      nra = aux[offT + (long long)(t + 1) * m + col];
+      nrb = aux[offTT + (long long)(t + 1) * m + col];
+    }
+    if (own) {
+      const float4 c = tile[b0][os];
+      const float4 qL = tile[b0][os - 1], qR = tile[b0][os + 1], qD = tile[b0][os - kW], qU = tile[b0][os + kW];
+      const float4 q1 = tile[b1][os];
+      const f2 ch = pk(c.x, c.y), cl = pk(c.z, c.w);
+      // (x1(t) - x1(t-1) | x2(t) - x2(t+1))
+      f2 H, L, ex;
+      two_diff(ch, pk(x1ph, q1.y), H, ex);
+      L = add(sub(cl, pk(x1pl, q1.w)), ex);
+      // 4 u - (sum of the four neighbours), renormalised before it is scaled
+      f2 lh, ll;
+      {
+        f2 s1, e1, s2, e2, s, e3;
+        two_sum(pk(qL.x, qL.y), pk(qR.x, qR.y), s1, e1);
+        two_sum(pk(qD.x, qD.y), pk(qU.x, qU.y), s2, e2);
+        two_sum(s1, s2, s, e3);
+        const f2 sl = add(add(add(pk(qL.z, qL.w), pk(qR.z, qR.w)), add(pk(qD.z, qD.w), pk(qU.z, qU.w))),
+                          add(add(e1, e2), e3));
+        const f2 four = pk(4.f, 4.f);
+        two_diff(mul(four, ch), s, lh, ex);
+        ll = sub(fma2(four, cl, ex), sl);
+        renorm(lh, ll);
+      }
+      f2 ph, pl;
+      prod(Ch, Cl, nC, lh, ll, ph, pl);              // + c (4 u - sum)
+      acc(H, L, ph, pl);
+      prod(ALh, ALl, nAL, swp(ch), swp(cl), ph, pl); // - alpha x2 | + alpha x1
+      acc(H, L, ph, pl);
+      renorm(H, L);
+      f2 oh, ol;
+      prod(SGh, SGl, nSG, H, L, oh, ol);             // 2^ky / beta
+      if (use_aux) {
+        float rah, ral, rbh, rbl;
+        split(ra, ba, rah, ral);
+        split(rb, ba, rbh, rbl);
+        prod(KPh, KPl, nKP, pk(rah, rbh), pk(ral, rbl), ph, pl);   // - (beta/oldb) r1
+        acc(oh, ol, ph, pl);
+      }
+      renorm(oh, ol);
+      const long long a = (long long)t * m + col;
+      out[offT + a] = widen(oh.x) + widen_lo(ol.x);
+      out[offTT + a] = widen(oh.y) + widen_lo(ol.y);
+      // epilogue: y at each output's own index times the output
+      const f2 yh = (op == PCB_OP_A) ? swp(ch) : ch, yl = (op == PCB_OP_A) ? swp(cl) : cl;
+      prod(yh, yl, mul(yh, pk(-1.f, -1.f)), oh, ol, ph, pl);
+      acc(dh, dl, ph, pl);
+      x1ph = c.x;
+      x1pl = c.z;
+    }
+    if (pre) store(b2, n1, n2, nh1, nh2);
+    ra = nra;
+    rb = nrb;
+    __syncthreads();
+    const int bt = b0;
+    b0 = b1; b1 = b2; b2 = bt;
+  }
+  if (!own) return 0.0;
+  // y . out / beta = (2^ky / beta) * sum of (y 2^-ky) . out
+  return ((widen(dh.x) + widen(dh.y)) + (widen(dl.x) + widen(dl.y))) * sgd;
+}
+
+__global__ void __launch_bounds__(kMvThreads) k_matvec_tw(const Geom* __restrict__ G, const Slots* __restrict__ S,
+                                                   Scal* __restrict__ Sc, const int* __restrict__ off, int count,
+                                                   const int* __restrict__ active, int op, int x_slot, int out_slot,
+                                                   int aux_slot, double* __restrict__ partial) {
+  __shared__ float4 tile[3][tw::kSlots];
+  const int inst = find_inst(off, count, blockIdx.x);
+  if (active && !active[inst]) return;
+  const Geom& g = G[inst];
+  const double* __restrict__ aux = aux_slot >= 0 ? S[inst].v[aux_slot] : nullptr;
+  const Epi e = make_epi(EPI_MINRES, Sc + inst);
+  const int lb = blockIdx.x - off[inst];
+  const double part = (g.theta == 1.0 && !g.var_a)
+                          ? matvec_tw_block(g, lb, op, S[inst].v[x_slot], S[inst].v[out_slot], aux, e, Sc[inst], tile)
+                          : matvec_block(g, lb, op, S[inst].v[x_slot], S[inst].v[out_slot], aux, e, EPI_MINRES);
+  if (partial) block_reduce_store(part, partial + blockIdx.x);
 }
 
 // Epilogue of a finite-element product already written to out (see k_matvec's epilogues): one
@@ -312,8 +610,13 @@ cudaError_t launch_matvec(const Batch& B, int op, int x_slot, int out_slot, int 
                                                    B.partial);
     return cudaGetLastError();
   }
+  if ((epi & EPI_FAST) && (epi & (EPI_FAST - 1)) == EPI_MINRES) {
+    k_matvec_tw<<<B.tot_mv, kMvThreads, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_mv, B.count, B.active, op, x_slot,
+                                                       out_slot, aux_slot, B.partial);
+    return cudaGetLastError();
+  }
   k_matvec<<<B.tot_mv, kMvThreads, 0, B.stream>>>(B.G, B.S, B.Sc, B.off_mv, B.count, B.active, op, x_slot, out_slot,
-                                           aux_slot, epi, B.partial);
+                                           aux_slot, epi & (EPI_FAST - 1), B.partial);
   return cudaGetLastError();
 }
 

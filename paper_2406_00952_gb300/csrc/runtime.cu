@@ -95,7 +95,8 @@ enum {
   SL_X = 2, SL_B = 3,                // solve: solution and right-hand side (outer)
   SL_XI = 4, SL_BI = 5,              // inner solve solution / right-hand side
   SL_R1 = 6, SL_R2 = 7, SL_Y = 8, SL_YO = 9, SL_Q = 10, SL_W = 11, SL_W2 = 12,
-  SL_R = 13, SL_VBASE = 14, SL_ZBASE = 15, SL_VJ = 16, SL_ZJ = 17, SL_VJ1 = 18
+  SL_R = 13, SL_VBASE = 14, SL_ZBASE = 15, SL_VJ = 16, SL_ZJ = 17, SL_VJ1 = 18,
+  SL_UAUX = 19                       // third user buffer of standalone calls
 };
 
 }  // namespace pcb
@@ -1113,6 +1114,33 @@ int pcb_matvec(pcb_problem* p, int op, const double* x_dev, double* y_dev) {
   int rc;
   if ((rc = upload_slots(p))) return rc;
   CK(launch_matvec(p->B, op, SL_UIN, SL_UOUT, -1, EPI_PLAIN));
+  return PCB_OK;
+}
+
+int pcb_lanczos_product(pcb_problem* p, int precision, const double* y_dev, const double* r1_dev, double beta,
+                        double oldb, double* out_dev, double* dot) {
+  if (!p || !y_dev || !out_dev || !dot) return PCB_ERR_INVALID_ARG;
+  if (precision != PCB_FP64 && precision != PCB_MIXED) return PCB_ERR_INVALID_ARG;
+  if (!(beta > 0.0) || !std::isfinite(beta) || !(oldb >= 0.0) || !std::isfinite(oldb)) return PCB_ERR_INVALID_ARG;
+  if ((oldb > 0.0 && !r1_dev) || out_dev == y_dev || (r1_dev && out_dev == r1_dev)) return PCB_ERR_INVALID_ARG;
+  Scal* hs = p->hSc;
+  CK(cudaStreamSynchronize(p->stream));   // the pinned scalar buffer may still be in flight
+  std::memset(hs, 0, sizeof(Scal));
+  hs->beta = beta;
+  hs->oldb = oldb;
+  hs->itn = oldb > 0.0 ? 1 : 0;
+  hs->active = 1;
+  CK(cudaMemcpyAsync(p->dSc, hs, sizeof(Scal), cudaMemcpyHostToDevice, p->stream));
+  p->hS.v[SL_UIN] = (double*)y_dev;
+  p->hS.v[SL_UOUT] = out_dev;
+  p->hS.v[SL_UAUX] = (double*)r1_dev;
+  int rc;
+  if ((rc = upload_slots(p))) return rc;
+  const int epi = EPI_MINRES | (precision == PCB_MIXED ? EPI_FAST : 0);
+  CK(launch_matvec(p->B, PCB_OP_A, SL_UIN, SL_UOUT, oldb > 0.0 ? SL_UAUX : -1, epi));
+  CK(launch_reduce(p->B, p->B.off_mv, 1, 0, SS_NORM, 0.0, 0, 0));
+  if ((rc = read_scal(p->B, hs, 1))) return rc;
+  *dot = hs->dot1;
   return PCB_OK;
 }
 
