@@ -34,10 +34,11 @@ WORKLOAD = dict(name="heat-control N=511 n=512 backward-Euler a=1 (2.67e8 unknow
                 N=511, n=512, theta=1.0, T=1.0, gammas=(1e-2, 1e-6))
 METRIC = "solves/s to relres 1e-8 (mixed-precision MINRES-|P_S|)"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "precond_apply_N511_n512.md")
-# FP64 instructions per output value of the theta = 1 product with its MINRES epilogue: one
-# product, three neighbour additions and five FMAs (with the epilogue's scale folded into the
-# operator's coefficients)
-MV_FP64_OPS = 9.0
+# FP64 instructions per output value of the theta = 1 FP64 product with an epilogue (true
+# residuals): the epilogue's scale folded into the operator's coefficients, ten operations
+MV_FP64_OPS = 10.0
+# bytes per unknown of the product with the MINRES epilogue: y and r1 read, the output written
+MV_ALG_BYTES = 24.0
 
 
 def args():
@@ -650,9 +651,12 @@ def main():
     pms = sum(i["precond_ms"] for i in pinfos)
     mvs = sum(i["matvecs"] for i in pinfos)
     mvms = sum(i["matvec_ms"] for i in pinfos)
+    # the inner iterations' products (two-word FP32 arithmetic) and the FP64 true-residual products
+    mvi = sum(i["matvecs_inner"] for i in pinfos)
+    mvims = sum(i["matvec_inner_ms"] for i in pinfos)
+    mvr, mvrms = mvs - mvi, mvms - mvims
     alg_bytes = 16.0 * unknowns            # precond apply: read 2mn + write 2mn FP64 values
     achieved = alg_bytes / (pms / applies / 1e3) / 1e9
-    mv_ach = 16.0 * unknowns / (mvms / mvs / 1e3) / 1e9
     iters = [i["iterations"] for i in infos]
     fp64r = P.fp64_rates(stream)
     fp64_peak = fp64r["fma_per_s"]
@@ -731,17 +735,25 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": profile_traffic(), "kernel": "precond apply |P_S|^-1 (FP32)",
                          "alg_bytes_per_launch": alg_bytes, "avg_ms": pms / applies, "peak_kind": peak_kind},
-            "kernels": {"precond_ms_share": pms / prof_ms, "matvec_ms_share": mvms / prof_ms, "matvec_avg_ms": mvms / mvs,
-                        "matvec_alg_gbs": mv_ach,
-                        # the product (with the MINRES epilogue) is bound by FP64 issue: MV_FP64_OPS
+            "kernels": {"precond_ms_share": pms / prof_ms, "matvec_ms_share": mvms / prof_ms,
+                        # the inner iterations' product (k_matvec_tw, two-word FP32 arithmetic with the
+                        # MINRES epilogue): MV_ALG_BYTES per unknown against the copy bandwidth
+                        "matvec_roofline": {"bound": "hbm", "kernel": "MINRES product, two-word FP32 (inner iterations)",
+                                            "launches": mvi, "avg_ms": mvims / mvi if mvi else None,
+                                            "alg_bytes_per_unknown": MV_ALG_BYTES,
+                                            "achieved": MV_ALG_BYTES * unknowns / (mvims / mvi / 1e3) / 1e9 if mvi else None,
+                                            "peak": hbm, "unit": "GB/s", "peak_kind": peak_kind,
+                                            "frac": MV_ALG_BYTES * unknowns / (mvims / mvi / 1e3) / 1e9 / hbm if mvi else None},
+                        # the true-residual products stay FP64 and are bound by FP64 issue: MV_FP64_OPS
                         # FP64 instructions per unknown against this device's FP64 FMA instruction
                         # rate, measured here (pcb_measure_fp64_rates)
-                        "matvec_roofline": {"bound": "alu", "unit": "G FP64 instr/s",
-                                            "fp64_instr_per_unknown": MV_FP64_OPS,
-                                            "achieved": MV_FP64_OPS * unknowns / (mvms / mvs / 1e3) / 1e9,
-                                            "peak": fp64_peak / 1e9, "peak_kind": "measured (FP64 FMA rate)",
-                                            "frac": MV_FP64_OPS * unknowns / (mvms / mvs / 1e3) / fp64_peak,
-                                            "fp64_add_instr_per_s": fp64r["add_per_s"]}},
+                        "residual_product_roofline": {"bound": "alu", "unit": "G FP64 instr/s", "launches": mvr,
+                                                      "avg_ms": mvrms / mvr if mvr else None,
+                                                      "fp64_instr_per_unknown": MV_FP64_OPS,
+                                                      "achieved": MV_FP64_OPS * unknowns / (mvrms / mvr / 1e3) / 1e9 if mvr else None,
+                                                      "peak": fp64_peak / 1e9, "peak_kind": "measured (FP64 FMA rate)",
+                                                      "frac": MV_FP64_OPS * unknowns / (mvrms / mvr / 1e3) / fp64_peak if mvr else None,
+                                                      "fp64_add_instr_per_s": fp64r["add_per_s"]}},
             "fp64_gpu": fp64,
             "mixed_vs_fp64": [{"gamma": gam, "mixed_iterations": im, "fp64_iterations": i64,
                                "within_plus2": im <= i64 + 2, "mixed_forward_error_vs_oracle": fe}

@@ -242,6 +242,9 @@ typedef struct {
   double precond_ms;      /* profile != 0: summed device time of the applications              */
   int matvecs;            /* operator products (Krylov and true-residual)                      */
   double matvec_ms;       /* profile != 0: summed device time of the products                  */
+  int matvecs_inner;      /* products of the inner MINRES iterations of a mixed-precision solve */
+                          /* (two-word FP32 arithmetic where the problem allows it)            */
+  double matvec_inner_ms; /* profile != 0: their summed device time (included in matvec_ms)    */
 } pcb_solve_info;
 
 /* Solve op x = b from a zero initial guess, op = A for MINRES and A_hat for (F)GMRES.

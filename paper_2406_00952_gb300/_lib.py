@@ -36,7 +36,8 @@ class PcbSolveInfo(ctypes.Structure):
     _fields_ = [("status", c_int), ("method", c_int), ("precond", c_int), ("iterations", c_int),
                 ("refinements", c_int), ("relres", c_double), ("seconds", c_double),
                 ("launches", c_longlong), ("precond_applies", c_int), ("precond_ms", c_double),
-                ("matvecs", c_int), ("matvec_ms", c_double)]
+                ("matvecs", c_int), ("matvec_ms", c_double), ("matvecs_inner", c_int),
+                ("matvec_inner_ms", c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

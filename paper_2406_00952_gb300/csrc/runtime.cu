@@ -141,10 +141,10 @@ struct pcb_problem {
   double* dtol = nullptr;         // device copy of the running tolerance read by the scalar steps
   // per-solve counters and optional event profiling
   long long launches = 0;
-  int prec_applies = 0, matvecs = 0;
+  int prec_applies = 0, matvecs = 0, matvecs_inner = 0;
   bool prof = false;
-  std::vector<cudaEvent_t> ev_prec, ev_mv;   // pairs (start, stop)
-  int ev_prec_used = 0, ev_mv_used = 0;
+  std::vector<cudaEvent_t> ev_prec, ev_mv, ev_mvi;   // pairs (start, stop); ev_mvi: two-word products
+  int ev_prec_used = 0, ev_mv_used = 0, ev_mvi_used = 0;
 };
 
 namespace {
@@ -383,6 +383,7 @@ void pcb_destroy(pcb_problem* p) {
   cudaFree(p->dtol);
   for (cudaEvent_t e : p->ev_prec) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev_mv) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_mvi) cudaEventDestroy(e);
   delete p;
 }
 
@@ -705,12 +706,14 @@ static int P_precond(pcb_problem* p, const Batch& B, int kind, int prec, int in_
 
 static cudaError_t P_matvec(pcb_problem* p, const Batch& B, int op, int x_slot, int out_slot, int aux_slot, int epi) {
   cudaEvent_t a = nullptr, b = nullptr;
-  const bool ev = p->prof && ev_pair(p->ev_mv, p->ev_mv_used, a, b);
+  const bool inner = (epi & EPI_FAST) != 0;
+  const bool ev = p->prof && (inner ? ev_pair(p->ev_mvi, p->ev_mvi_used, a, b) : ev_pair(p->ev_mv, p->ev_mv_used, a, b));
   if (ev) cudaEventRecord(a, B.stream);
   const cudaError_t e = launch_matvec(B, op, x_slot, out_slot, aux_slot, epi);
   if (ev) cudaEventRecord(b, B.stream);
   p->launches += 1;
   p->matvecs += 1;
+  p->matvecs_inner += inner ? 1 : 0;
   return e;
 }
 
@@ -764,7 +767,7 @@ static cudaGraphExec_t capture_launches(pcb_problem* p, const Batch& B, F&& issu
   Batch Bc = B;
   Bc.stream = p->cap_stream;
   const long long l0 = p->launches;
-  const int a0 = p->prec_applies, m0 = p->matvecs;
+  const int a0 = p->prec_applies, m0 = p->matvecs, mi0 = p->matvecs_inner;
   if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError(); return nullptr;
   }
@@ -772,7 +775,7 @@ static cudaGraphExec_t capture_launches(pcb_problem* p, const Batch& B, F&& issu
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
   *launches = p->launches - l0;
-  p->launches = l0; p->prec_applies = a0; p->matvecs = m0;
+  p->launches = l0; p->prec_applies = a0; p->matvecs = m0; p->matvecs_inner = mi0;
   if (rc != PCB_OK || e != cudaSuccess || !graph) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
@@ -834,6 +837,7 @@ static int minres_single(pcb_problem* p, const SolveCfg& c, int s_b, int s_x, Sc
       p->launches += p->git_launches;
       p->prec_applies += 1;
       p->matvecs += 1;
+      p->matvecs_inner += c.prec == PCB_MIXED ? 1 : 0;
     } else if ((rc = minres_iter_launches(p, Bt, c, s_x))) {
       return rc;
     }
@@ -1022,9 +1026,9 @@ static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_d
   }
   if ((rc = upload_slots(p))) return rc;
   Scal* hs = p->hSc;
-  p->launches = 0; p->prec_applies = 0; p->matvecs = 0;
+  p->launches = 0; p->prec_applies = 0; p->matvecs = 0; p->matvecs_inner = 0;
   p->prof = o && o->profile;
-  p->ev_prec_used = 0; p->ev_mv_used = 0;
+  p->ev_prec_used = 0; p->ev_mv_used = 0; p->ev_mvi_used = 0;
   auto t0 = std::chrono::steady_clock::now();
   int iters = 0, sweeps = 0;
   double relres = 1.0;
@@ -1082,7 +1086,9 @@ static int solve_impl(pcb_problem* p, const pcb_solve_opts* o, const double* b_d
     info->refinements = sweeps; info->relres = relres; info->seconds = secs;
     info->launches = p->launches; info->precond_applies = p->prec_applies; info->matvecs = p->matvecs;
     info->precond_ms = p->prof ? ev_sum(p->ev_prec, p->ev_prec_used) : 0.0;
-    info->matvec_ms = p->prof ? ev_sum(p->ev_mv, p->ev_mv_used) : 0.0;
+    info->matvec_ms = p->prof ? ev_sum(p->ev_mv, p->ev_mv_used) + ev_sum(p->ev_mvi, p->ev_mvi_used) : 0.0;
+    info->matvecs_inner = p->matvecs_inner;
+    info->matvec_inner_ms = p->prof ? ev_sum(p->ev_mvi, p->ev_mvi_used) : 0.0;
   }
   return rc;
 }
