@@ -5,12 +5,16 @@ in FP32 (library single-precision transforms) except the stages named on the com
 the same FP64 iterative refinement the library runs (inner MINRES to tol ||b||/||r||, FP64 true
 residual, x += d), on the bench family's problem (backward Euler, a = 1, seed-1 target).
 
-    python tests/fp32_rounding_study.py N gamma 'exact;;t,ti;x1,x2,x2i,x1i'
+    python tests/fp32_rounding_study.py N gamma 'exact;;t,ti;x1,x2,x2i,x1i;@split48;@split48+noise=4e-15'
 
 Each ';'-separated variant lists the stages kept in FP64: x1, x2 (forward DSTs), t (forward time
 DFT), w (weights), ti (inverse time DFT), x2i, x1i (inverse DSTs); 'exact' is the FP64 oracle;
 'noise=E' is the FP64 oracle with a relative perturbation of size E (random sign, seeded) on every
-output value, which measures how much inexactness the solve tolerates.
+output value, which measures how much inexactness the solve tolerates.  A suffix '@split48' makes
+the inner iterations' product act on its input truncated to 48 significand bits (the two FP32
+words of the mixed solve's two-word product: the leading 24 bits and the next 24, both
+truncated), '@split48+noise=E' adds a perturbation of E |A| |z| with random signs to it; the
+refinement's true residuals keep the FP64 product.
 Prints one JSON line per variant: total inner iterations and the iterations of each sweep.
 """
 from __future__ import annotations
@@ -91,10 +95,22 @@ def minres_inner(A, b, M, tol, maxit):
     return x, maxit
 
 
-def refine(A, b, M, tol=1e-8, maxit=400):
+def trunc24(x):
+    """x with all but the leading 24 significand bits cleared (truncation toward zero)."""
+    return (x.view(np.uint64) & np.uint64(0xFFFFFFFFE0000000)).view(np.float64)
+
+
+def split48(x):
+    """The value the two FP32 words hold: leading 24 bits plus the next 24, both truncated."""
+    hi = trunc24(x)
+    return hi + trunc24(x - hi)
+
+
+def refine(A, b, M, tol=1e-8, maxit=400, A_inner=None):
+    A_inner = A_inner or A
     x = np.zeros_like(b); bn = np.linalg.norm(b); r = b.copy(); rn = bn; its = 0; sweeps = []
     while rn / bn > tol and its < maxit:
-        d, k = minres_inner(A, r, M, min(0.5, tol * bn / rn), maxit - its)
+        d, k = minres_inner(A_inner, r, M, min(0.5, tol * bn / rn), maxit - its)
         its += k; sweeps.append(k)
         x = x + d; r = b - A(x); rn = np.linalg.norm(r)
     return x, its, sweeps, rn / bn
@@ -106,6 +122,17 @@ def main(N, gamma, variants):
     b = ds.rhs_minres(prob, synth.random_target(N, n, seed=1), synth.manufactured_source(N, n))
     A = lambda z: op.matvec_A(prob, z)
     for var in variants:
+        var, _, inner = var.partition("@")
+        A_inner = None
+        if inner.startswith("split48"):
+            eps = float(inner.split("noise=")[1]) if "noise=" in inner else 0.0
+            rng_i = np.random.default_rng(3)
+
+            def A_inner(z, eps=eps, rng_i=rng_i):
+                y = A(split48(z))
+                if eps:   # the size of the terms taken as |A |z||
+                    y = y + eps * np.abs(A(np.abs(z))) * rng_i.choice([-1.0, 1.0], z.size)
+                return y
         if var == "exact":
             M = lambda r: pc.apply_abs_ps_inv(prob, r)
         elif var.startswith("noise="):
@@ -115,8 +142,9 @@ def main(N, gamma, variants):
         else:
             M = make_apply(prob, tuple(v for v in var.split(",") if v))
         t0 = time.time()
-        _, its, sw, rr = refine(A, b, M)
-        print(json.dumps({"N": N, "gamma": gamma, "fp64_stages": var, "iterations": its, "sweeps": sw,
+        _, its, sw, rr = refine(A, b, M, A_inner=A_inner)
+        print(json.dumps({"N": N, "gamma": gamma, "fp64_stages": var, "inner_product": inner or "fp64",
+                          "iterations": its, "sweeps": sw,
                           "relres": rr, "seconds": round(time.time() - t0, 1)}), flush=True)
 
 
