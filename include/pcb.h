@@ -146,8 +146,8 @@ int pcb_matvec(pcb_problem* p, int op, const double* x_dev, double* y_dev);
  * which is the product a MINRES iteration of pcb_solve computes before its scalar step.
  * precision PCB_FP64: FP64 arithmetic (the form of FP64 solves and of true residuals);
  * PCB_MIXED: the two-word FP32 arithmetic of the inner iterations of a mixed-precision solve
- * (inputs split into two FP32 words, 48 of their 53 significand bits; each value accurate to
- * about 2^-47 of the magnitudes of its terms), used for theta = 1 and a constant coefficient;
+ * (inputs split into two FP32 words, 47 of their 53 significand bits; each value accurate to
+ * about 2^-46 of the magnitudes of its terms), used for theta = 1 and a constant coefficient;
  * other instances compute in FP64 either way.  y_dev, r1_dev, out_dev: device, 2*m*n each,
  * out_dev distinct from both inputs; r1_dev may be NULL when oldb == 0.  beta > 0 and oldb >= 0,
  * both finite, else INVALID_ARG.  The two-word path splits y relative to the binade of beta and r1

@@ -280,12 +280,12 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const Geom* __restrict__ 
 //     out = A y / beta - (beta/oldb) r1,   partial = y . out / beta   (A: Eq. matrix_A)
 // On this GPU FP64 instructions issue at 1/64 of the FP32 rate, and the FP64 form above is
 // bound by them (ten per output value).  Here every FP64 input is split, with integer
-// operations, into two FP32 words that hold the leading 24 and the next 24 bits of its
-// significand (48 of its 53 bits), and the product is evaluated in two-word arithmetic built
+// operations, into two FP32 words that hold the leading 24 and the next 23 bits of its
+// significand (47 of its 53 bits), and the product is evaluated in two-word arithmetic built
 // from error-free transformations: Knuth's two-sum, Dekker's fast two-sum and the FMA-based
 // exact product (Dekker 1971; Knuth, TAOCP vol. 2, 4.2.2), on packed pairs of FP32 lanes that
 // carry the two output rows of a point (T x1 - alpha x2 and alpha x1 + T^T x2) side by side.
-// Each result is accurate to about 2^-47 of the magnitudes of its terms (the FP64 form: 2^-53),
+// Each result is accurate to about 2^-46 of the magnitudes of its terms (the FP64 form: 2^-53),
 // which the iteration does not notice next to the FP32 preconditioner's rounding.  Results are
 // widened to FP64 with integer operations and one FP64 add per value.
 //
@@ -351,8 +351,8 @@ __device__ __forceinline__ void acc(f2& h, f2& l, f2 ph, f2 pl) {
 }
 
 // x 2^-k split into two FP32 words (b20 = (896 + k) << 20, the FP64 exponent bias of the scaled
-// value): hi = the leading 24 bits of the significand, lo = the next 24 (both truncated), so
-// |x 2^-k - hi - lo| < 2^-47 |x 2^-k|.  The second word is the difference of two FP32 numbers of
+// value): hi = the leading 24 bits of the significand, lo = the next 23 (both truncated), so
+// |x 2^-k - hi - lo| < 2^-46 |x 2^-k|.  The second word is the difference of two FP32 numbers of
 // the same binade (exact).  Scaled values below 2^-103 and FP64 subnormals become 0.
 __device__ __forceinline__ void split(double x, int b20, float& hi, float& lo) {
   const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);

@@ -5,15 +5,15 @@ in FP32 (library single-precision transforms) except the stages named on the com
 the same FP64 iterative refinement the library runs (inner MINRES to tol ||b||/||r||, FP64 true
 residual, x += d), on the bench family's problem (backward Euler, a = 1, seed-1 target).
 
-    python tests/fp32_rounding_study.py N gamma 'exact;;t,ti;x1,x2,x2i,x1i;@split48;@split48+noise=4e-15'
+    python tests/fp32_rounding_study.py N gamma 'exact;;t,ti;x1,x2,x2i,x1i;@split47;@split47+noise=4e-15'
 
 Each ';'-separated variant lists the stages kept in FP64: x1, x2 (forward DSTs), t (forward time
 DFT), w (weights), ti (inverse time DFT), x2i, x1i (inverse DSTs); 'exact' is the FP64 oracle;
 'noise=E' is the FP64 oracle with a relative perturbation of size E (random sign, seeded) on every
-output value, which measures how much inexactness the solve tolerates.  A suffix '@split48' makes
-the inner iterations' product act on its input truncated to 48 significand bits (the two FP32
-words of the mixed solve's two-word product: the leading 24 bits and the next 24, both
-truncated), '@split48+noise=E' adds a perturbation of E |A| |z| with random signs to it; the
+output value, which measures how much inexactness the solve tolerates.  A suffix '@split47' makes
+the inner iterations' product act on its input truncated to 47 significand bits (the two FP32
+words of the mixed solve's two-word product: the leading 24 bits and the next 23, both
+truncated), '@split47+noise=E' adds a perturbation of E |A| |z| with random signs to it; the
 refinement's true residuals keep the FP64 product.
 Prints one JSON line per variant: total inner iterations and the iterations of each sweep.
 """
@@ -95,15 +95,10 @@ def minres_inner(A, b, M, tol, maxit):
     return x, maxit
 
 
-def trunc24(x):
-    """x with all but the leading 24 significand bits cleared (truncation toward zero)."""
-    return (x.view(np.uint64) & np.uint64(0xFFFFFFFFE0000000)).view(np.float64)
-
-
-def split48(x):
-    """The value the two FP32 words hold: leading 24 bits plus the next 24, both truncated."""
-    hi = trunc24(x)
-    return hi + trunc24(x - hi)
+def split47(x):
+    """The value the two FP32 words hold: the leading 24 significand bits and the next 23, i.e. x
+    with the last 6 of its 52 stored mantissa bits cleared (normal values)."""
+    return (x.view(np.uint64) & np.uint64(0xFFFFFFFFFFFFFFC0)).view(np.float64)
 
 
 def refine(A, b, M, tol=1e-8, maxit=400, A_inner=None):
@@ -124,12 +119,12 @@ def main(N, gamma, variants):
     for var in variants:
         var, _, inner = var.partition("@")
         A_inner = None
-        if inner.startswith("split48"):
+        if inner.startswith("split47"):
             eps = float(inner.split("noise=")[1]) if "noise=" in inner else 0.0
             rng_i = np.random.default_rng(3)
 
             def A_inner(z, eps=eps, rng_i=rng_i):
-                y = A(split48(z))
+                y = A(split47(z))
                 if eps:   # the size of the terms taken as |A |z||
                     y = y + eps * np.abs(A(np.abs(z))) * rng_i.choice([-1.0, 1.0], z.size)
                 return y

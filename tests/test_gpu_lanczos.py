@@ -4,7 +4,7 @@ out = A y / beta - (beta/oldb) r1 and y . out / beta, against the FP64 oracle's 
 FP64: within 1e-13 (relative 2-norm and max-norm, tests/closeness.py).  Two-word FP32 (the inner
 iterations of a mixed-precision solve): every value within 2^-44 of the magnitude of its terms,
 |out - ref| <= 2^-44 (|A| |y| / beta + (beta/oldb) |r1|) componentwise (the arithmetic carries
-48 significand bits of each input and rounds each operation to about 2^-48), and the dot within
+47 significand bits of each input, 2^-46 relative, and rounds each operation to about 2^-48), and the dot within
 2^-44 of sum |y| (|A| |y| / beta + ...) / beta.  Shapes span several 32 x 4 patches with ragged
 edges, several time chunks with a ragged last chunk, n = 2, and Neumann grids."""
 import numpy as np
