@@ -53,9 +53,11 @@ extern "C" {
 /* ---- enumerations ---------------------------------------------------------------------- */
 enum pcb_precision { PCB_FP64 = 0, PCB_MIXED = 1 };
 /* PCB_FP64: every step in double precision.
- * PCB_MIXED: the preconditioner (transforms, per-frequency solves, multigrid) runs in FP32;
- * the matvec, residuals, inner products, orthogonalisation and vector updates stay FP64, and an
- * FP64 iterative-refinement loop restores the requested true relative residual. */
+ * PCB_MIXED: the preconditioner (transforms, per-frequency solves, multigrid) runs in FP32; the
+ * operator product of the inner MINRES iterations runs in two-word FP32 arithmetic (theta = 1 and
+ * a constant coefficient; see pcb_lanczos_product); true residuals, the other products, inner
+ * products, orthogonalisation and vector updates stay FP64, and an FP64 iterative-refinement
+ * loop restores the requested true relative residual. */
 
 enum pcb_operator { PCB_OP_A = 0, PCB_OP_AHAT = 1 };
 /* PCB_OP_A    : A     = [[alpha I, T^T], [T, -alpha I]]   (Eq. matrix_A; symmetric)

@@ -51,3 +51,12 @@ def test_create_rejects_invalid_descriptors_without_touching_the_gpu():
     d = _lib.PcbDesc(5, 4, 0.5, 1.0, 1e-2, 3.141592653589793, None, 0, 2, None, 2, 1.0)
     assert lib.pcb_create(ctypes.byref(d), ctypes.byref(h)) == -1
     assert lib.pcb_create(None, None) == -1
+
+
+def test_entry_points_reject_null_problems_without_touching_the_gpu():
+    """Calls on a NULL problem handle return INVALID_ARG before any CUDA call."""
+    lib = _lib.load()
+    dot = ctypes.c_double()
+    assert lib.pcb_lanczos_product(None, 1, None, None, 1.0, 0.0, None, ctypes.byref(dot)) == -1
+    assert lib.pcb_matvec(None, 0, None, None) == -1
+    assert lib.pcb_precond_apply(None, 1, 1, None, None) == -1
